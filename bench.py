@@ -1,0 +1,332 @@
+"""Benchmark: extrapolated blocks/s of batched Fast Selective Extrapolation.
+
+Workload (one step = one pass of the whole hot path over one batch): the
+512x512 synthetic image, 4096 concealment blocks of 32x32 with the centred
+16x16 loss area, DCT u WHT dictionary (K = 2048), I = 100, gamma = 0.5,
+rho_hat = 0.8.  Every step rebuilds the table C (Alg. 2), packs the
+operands, computes the initial projections (eq. 12) and runs the iterations
+(Alg. 3) through the C ABI.  L2 is flushed (256 MiB write) between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec bf16x6]
+
+``--impl reference`` times the FP64 CPU oracle (Alg. 1) on the host cores on
+a bounded sample of the same workload.  Under torchrun (N > 1) each rank
+runs its own full batch (weak scaling, no collective on the data path);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "extrapolated blocks/s (32x32 area, K=2048, 100 iters)"
+UNIT = "blocks/s"
+WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def cpu_baseline(wl, n_blocks: int, threads: int = 0):
+    """Time the FP64 oracle (Alg. 1) on the host cores over the first n_blocks blocks."""
+    import oracle as O
+    phi = O.dict_dct_wht(wl.M, wl.N)
+    dup = O.find_duplicates(phi)
+    w = O.weights(wl.M, wl.N, wl.rho_hat, wl.support)
+    s = np.ascontiguousarray(wl.samples[:n_blocks])
+    cores = threads if threads > 0 else O.max_threads()
+    t0 = time.perf_counter()
+    out, u, c, st = O.se_original_batch(phi, w, s, wl.gamma, wl.iterations, dup, nthreads=cores)
+    dt = time.perf_counter() - t0
+    assert st == 0
+    return n_blocks / dt, cores, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2204_14194_gb300 import workloads as W
+    wl = W.config2()
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_baseline(wl, max(1, sample // 8))
+    vals = []
+    cores = 0
+    for _ in range(args.steps):
+        v, cores, _dt = cpu_baseline(wl, sample)
+        vals.append(v)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blocks": 4096, "sample_blocks_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} of the 4096 blocks per step, original SE (Alg. 1), fp64 C"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = W.config2()
+    n, M, N, K, I = wl.B, wl.M, wl.N, wl.K, wl.iterations
+    ctx = B.Context(local)
+    plan = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec=args.prec)
+    stream = torch.cuda.Stream(device=dev)
+    s_d = torch.from_numpy(wl.samples).to(dev)
+    out_d = torch.empty_like(s_d)
+    u_d = torch.empty((n, I), dtype=torch.int32, device=dev)
+    c_d = torch.empty((n, I), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.reset_tables()
+        plan.extrapolate_strided(s_d, out_d, u_d, c_d, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+    ctx.sync(stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of exactly K steps, L2 flushed between them
+    ctx.set_profiling(True)
+    ctx.stage_times(reset=True)
+    launches0 = ctx.stats()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.sync(stream)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    launches = ctx.stats()["kernel_launches"] - launches0
+    stages = ctx.stage_times(reset=True)
+    ctx.set_profiling(False)
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * n * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    s_h = torch.from_numpy(wl.samples).pin_memory()
+    o_h = torch.empty_like(s_h).pin_memory()
+    for _ in range(2):
+        plan.extrapolate_host(s_h, o_h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.reset_tables()
+        plan.extrapolate_host(s_h, o_h)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * n * args.steps / e2e_s if ws == 1 else None
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = ws * n * args.steps / float(t.item())
+
+    # ---- error against the fp64 form, and the fp64 form's own throughput
+    out_m, u_m, c_m = out_d.cpu().numpy(), u_d.cpu().numpy(), c_d.cpu().numpy()
+    plan64 = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec="fp64")
+    o64 = torch.empty_like(s_d)
+    u64 = torch.empty_like(u_d)
+    c64 = torch.empty_like(c_d)
+    plan64.extrapolate_strided(s_d, o64, u64, c64, stream=stream)
+    ctx.sync(stream)
+    fp64_steps = max(1, min(3, args.steps))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(fp64_steps):
+            plan64.reset_tables()
+            plan64.extrapolate_strided(s_d, o64, u64, c64, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = n * fp64_steps / (e0.elapsed_time(e1) / 1000.0)
+    o64, u64, c64 = o64.cpu().numpy(), u64.cpu().numpy(), c64.cpu().numpy()
+    same = np.all(u_m == u64, axis=1)
+    first_diff = np.where(same, I, np.argmax(u_m != u64, axis=1))
+    rel = []
+    for b in range(n):
+        t = first_diff[b]
+        if t:
+            ref = c64[b, :t]
+            rel.append(np.max(np.abs(c_m[b, :t] - ref) / np.maximum(np.abs(ref), 1e-12 * np.max(np.abs(ref)))))
+    loss = wl.support == 0
+    gt = wl.samples[:, loss]
+
+    def _psnr(o):
+        d = o[:, loss] - gt
+        return 10.0 * np.log10(255.0 ** 2 / float(np.mean(d * d)))
+
+    # ---- roofline of the dominant kernel (the iteration kernel, Alg. 3)
+    hbm_peak, tc_peak, peak_kind = measured_peaks()
+    it_ms, it_n = stages["iterate"]
+    it_avg_s = it_ms / max(it_n, 1) / 1000.0
+    Kp = 2048
+    # algorithmic bytes per launch: one row of C per block-iteration after the
+    # first, R0 read, samples read and output written (fp64)
+    alg_bytes = n * ((I - 1) * Kp * 4 + Kp * 4 + 2 * M * N * 8)
+    achieved = alg_bytes / it_avg_s / 1e9
+    roofline = {"kernel": "iterate_full_kernel<float,1,64,4>", "bound": "hbm", "achieved": achieved,
+                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, dt = cpu_baseline(wl, args.ref_sample)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {args.ref_sample} of the 4096 blocks, original SE (Alg. 1), fp64 C, {dt:.1f} s"}
+
+    sorted_ms = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "M": M, "N": N, "K": K,
+                   "iterations": I, "precision": args.prec + " tensor-core products, fp32 recurrence",
+                   "tables": "rebuilt every step", "l2": "flushed between steps (256 MiB write)"},
+        "latency_ms": {"p50": float(np.percentile(sorted_ms, 50)), "p99": float(np.percentile(sorted_ms, 99)),
+                       "what": "per-batch (4096 blocks) device time"},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * M * N * 8),
+                "d2h_bytes_per_step": int(n * M * N * 8)},
+        "roofline": roofline,
+        "vs_fp64_form": {"fp64_blocks_per_s": fp64_value, "speedup": value / fp64_value,
+                         "index_sequence_identical_frac": float(np.mean(same)),
+                         "max_rel_coef_err_before_first_divergence": float(max(rel)) if rel else 0.0,
+                         "psnr_db": _psnr(out_m), "psnr_fp64_db": _psnr(o64)},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan64.close()
+    plan.close()
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
+    ap.add_argument("--ref-sample", type=int, default=192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

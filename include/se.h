@@ -1,0 +1,232 @@
+/*
+ * se.h -- C ABI of the GB300 Fast Selective Extrapolation library (libse.so).
+ *
+ * Selective Extrapolation (SE) conceals a loss area B of an M x N
+ * extrapolation area L = A u B from the support area A by building the
+ * sparse model g = sum_k c_k phi_k of eq. (1) greedily over a dictionary of
+ * K atoms phi_k.  This library runs the fast formulation (FaSE, Alg. 2 and
+ * Alg. 3 of Seiler & Kaup, "A Fast Algorithm for Selective Signal
+ * Extrapolation with Arbitrary Basis Functions"), which selects the same
+ * atoms with the same coefficients as the original SE of Alg. 1 (Sec. III).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an se_status; nothing aborts, throws or exits
+ *     across this boundary.  On failure se_last_error() describes it.
+ *   - Arrays are row-major: an area is M x N with m the row index; a
+ *     dictionary is atom-major, K x M x N.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's
+ *     device; "host" pointers are ordinary host memory.
+ *   - The caller keeps ownership of every buffer it passes.  Descriptor
+ *     contents (se_plan_desc arrays) are copied before the call returns.
+ *   - Precision and layout of results do not depend on how requests are
+ *     grouped into batches: a block gives the same result alone and mixed
+ *     with others.
+ */
+#ifndef SE_H
+#define SE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SE_OK = 0,
+    SE_PENDING = 1,            /* se_poll: request not finished yet */
+    SE_ERR_INVALID = -1,       /* an argument is out of range (see se_last_error) */
+    SE_ERR_NOMEM = -2,         /* device or host allocation failed, or the HBM budget is too small */
+    SE_ERR_CUDA = -3,          /* a CUDA call failed, or a kernel reported an error status */
+    SE_ERR_TIMEOUT = -4,       /* a bounded wait ran out */
+    SE_ERR_EMPTY_SUPPORT = -5, /* no atom has weighted energy on A (e.g. w == 0 everywhere) */
+    SE_ERR_CANCELLED = -6,     /* the request was cancelled with se_cancel */
+    SE_ERR_UNKNOWN_TICKET = -7 /* se_poll / se_cancel: no such ticket */
+} se_status;
+
+/* Dictionaries.  DCT: 2-D orthonormal DCT-II, atom (p, q) has index p*N + q.
+ * WHT: 2-D Walsh-Hadamard in sequency order (p sign changes along m), index
+ * p*N + q, M and N powers of two.  DCT_WHT: DCT atoms at [0, MN), WHT atoms
+ * at [MN, 2MN) (the union used in Sec. I, Fig. 1).  NUMERIC: caller-given
+ * atoms (the "only numerically defined" case of Sec. III). */
+typedef enum {
+    SE_BASIS_DCT = 1,
+    SE_BASIS_WHT = 2,
+    SE_BASIS_DCT_WHT = 3,
+    SE_BASIS_NUMERIC = 4
+} se_basis;
+
+/* Arithmetic of the scalar-product stage (tables C of eq. 16 and initial
+ * projections R^(0) of eq. 12) and of the running recurrence of eq. (20).
+ *   FP64    every stage in double precision on CUDA cores (the plain form);
+ *   BF16X6  tensor-core products of a 3-way bf16 split (6 partial products,
+ *           ~fp32 accuracy), fp32 accumulation, fp32 recurrence;
+ *   BF16X3  2-way bf16 split (3 partial products), fp32 accumulation;
+ *   BF16    single bf16 products, fp32 accumulation (fastest, ~3 digits). */
+typedef enum {
+    SE_PREC_FP64 = 0,
+    SE_PREC_BF16X6 = 1,
+    SE_PREC_BF16X3 = 3,
+    SE_PREC_BF16 = 4
+} se_prec;
+
+/* How the weighted scalar products between atoms (eq. 16) are provided.
+ * FULL: the K x K table per weighting pattern (Alg. 2), for blocks that use
+ * the plan's pattern.  LAZY: only the columns C(:, u) of atoms actually
+ * selected, computed per block on first selection and cached; required for
+ * blocks with their own support mask.  AUTO: FULL for the plan's pattern,
+ * LAZY for per-block masks. */
+typedef enum {
+    SE_GRAM_AUTO = 0,
+    SE_GRAM_FULL = 1,
+    SE_GRAM_LAZY = 2
+} se_gram;
+
+typedef struct se_ctx_s se_ctx_t;    /* opaque, library-owned */
+typedef struct se_plan_s se_plan_t;  /* opaque, library-owned */
+
+/* Parameters of the method (Sec. II): area size, dictionary, weighting
+ * function (eqs. 4-5), orthogonality-deficiency factor gamma (eq. 8) and the
+ * iteration count I.  All host arrays are copied by se_plan. */
+typedef struct {
+    int M, N;                 /* extrapolation area L is M x N samples, 1 <= M, N <= 256 */
+    se_basis basis;
+    int K;                    /* dictionary size: MN for DCT/WHT, 2MN for DCT_WHT, >= 1 for NUMERIC */
+    const double *dict;       /* NUMERIC: host K x M x N atoms; ignored otherwise */
+    double rho_hat;           /* decay of eq. (5), 0 < rho_hat <= 1 */
+    const double *rho;        /* optional host M x N weights replacing eq. (5); NULL = isotropic */
+    const uint8_t *support;   /* optional host M x N default pattern, 1 = A, 0 = B;
+                                 NULL = centred loss area of (M/2) x (N/2) samples */
+    double gamma;             /* eq. (8), 0 < gamma <= 1 */
+    int iterations;           /* default I >= 1 (eq. 10: exactly I iterations) */
+    se_prec prec;
+    se_gram gram;
+} se_plan_desc;
+
+/* One concealment block for se_extrapolate_batch (all pointers device). */
+typedef struct {
+    const double *samples;    /* M x N samples s; values on B are never read */
+    const uint8_t *support;   /* M x N mask (1 = A, 0 = B), or NULL = the plan's pattern */
+    double *out;              /* M x N result: s on A, the model g on B (Alg. 1/3 last step) */
+    int32_t *sel_idx;         /* optional [iterations] selected atom index u per iteration */
+    double *sel_coef;         /* optional [iterations] coefficient c_u per iteration */
+    int iterations;           /* 0 = the plan's default I */
+} se_block;
+
+/* One request for the serving loop (all pointers host). */
+typedef struct {
+    const double *samples;    /* M x N; copied by se_submit */
+    const uint8_t *support;   /* M x N or NULL = the plan's pattern; copied by se_submit */
+    double *out;              /* M x N, written before se_poll returns SE_OK; owned by the caller */
+    int32_t *sel_idx;         /* optional [iterations], written like out */
+    double *sel_coef;         /* optional [iterations], written like out */
+    int iterations;           /* 0 = the plan's default I */
+} se_request;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory the context allocates for plans, batch workspaces and
+ * serving slots (0 = no bound).  Returns SE_ERR_CUDA if the device cannot
+ * be used. */
+se_status se_ctx_create(int device, size_t hbm_budget_bytes, se_ctx_t **out);
+
+/* Stop the serving thread (pending requests end as SE_ERR_CANCELLED), free
+ * all plans and device memory of the context.  NULL is accepted. */
+se_status se_ctx_destroy(se_ctx_t *ctx);
+
+/* Build a plan: the dictionary (Sec. I / NUMERIC), the default weighting
+ * pattern (eqs. 4-5), the admissible-atom flags (collinear duplicates of a
+ * lower-index atom are never selected, so ties go to the smallest index),
+ * and device copies of the atoms in the plan's precision.  The table C of
+ * eq. (16) for the default pattern is built lazily by the first batch that
+ * needs it (and again after se_plan_reset_tables).  Validation: M, N in
+ * [1, 256]; K must match the basis; WHT needs powers of two; 0 < rho_hat
+ * <= 1; 0 < gamma <= 1; iterations >= 1 -- else SE_ERR_INVALID.  A default
+ * pattern without support returns SE_ERR_EMPTY_SUPPORT. */
+se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out);
+
+/* Free a plan.  The caller must ensure no batch using it is in flight. */
+se_status se_plan_destroy(se_plan_t *plan);
+
+/* Drop the cached table C / D of eq. (16)-(17) so the next batch rebuilds
+ * it (Alg. 2).  Used to time table generation as part of a step. */
+se_status se_plan_reset_tables(se_plan_t *plan);
+
+/* Extrapolate n blocks of one plan, asynchronously on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Runs, on the device:
+ * weighting and operand packing, the table C (Alg. 2) if not cached, the
+ * initial projections R^(0) (eq. 12), the I iterations of Alg. 3
+ * (selection eq. 18, coefficient eq. 19, model eq. 9, update eq. 20) and
+ * the replacement of B.  Device buffers of the blocks must stay valid until
+ * the stream reaches this point; the library's workspace is reused by the
+ * next call on the same context, so calls on one context are serialised on
+ * the host.  Returns SE_ERR_INVALID for bad blocks (NULL samples/out,
+ * iterations < 0), SE_ERR_NOMEM if the workspace exceeds the budget. */
+se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n,
+                               const se_block *blocks, void *cuda_stream);
+
+/* Convenience form of se_extrapolate_batch for n blocks stored contiguously
+ * on the device: samples[n][M][N], out[n][M][N], optional sel_idx /
+ * sel_coef [n][iterations] (iterations = 0: the plan's I), all blocks on
+ * the plan's pattern. */
+se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n,
+                                 const double *samples, double *out,
+                                 int32_t *sel_idx, double *sel_coef,
+                                 int iterations, void *cuda_stream);
+
+/* Same as se_extrapolate_strided but with HOST buffers: copies samples to
+ * the device, runs the batch and copies out (and the optional logs) back
+ * before returning.  Uses pinned staging owned by the context. */
+se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
+                              const double *samples, double *out,
+                              int32_t *sel_idx, double *sel_coef, int iterations);
+
+/* Wait for the work this context queued on `cuda_stream` and report
+ * errors that its kernels recorded in the device status word (SE_ERR_CUDA
+ * with a message, e.g. a bounded wait that ran out).  Clears the word. */
+se_status se_sync(se_ctx_t *ctx, void *cuda_stream);
+
+/* Serving loop.  se_submit copies the request into library memory (the
+ * caller may free samples/support on return), queues it and returns a
+ * ticket.  A scheduler thread admits queued requests into device slots as
+ * slots and HBM budget free up, runs the iteration kernels in slices over
+ * all admitted blocks (continuous batching: requests that arrive while
+ * others run join at the next slice) and copies results into the caller's
+ * out/sel buffers.  Returns SE_ERR_INVALID for a bad request,
+ * SE_ERR_NOMEM if one block can never fit the budget. */
+se_status se_submit(se_ctx_t *ctx, const se_plan_t *plan, const se_request *req,
+                    uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0 = do not wait, < 0 = wait without
+ * limit) for a ticket.  SE_OK: done, out written, the ticket is retired
+ * and latency_s (if non-NULL) receives submit-to-completion seconds.
+ * SE_PENDING: not finished.  Other codes: the request failed (retired). */
+se_status se_poll(se_ctx_t *ctx, uint64_t ticket, int64_t timeout_us, double *latency_s);
+
+/* Cancel a request that has not been admitted yet (SE_OK), or report that
+ * it is already running / done (SE_PENDING / SE_ERR_INVALID). */
+se_status se_cancel(se_ctx_t *ctx, uint64_t ticket);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *se_last_error(void);
+
+/* Statistics of the context since creation: kernels launched by the library,
+ * table builds, serving slices.  Any pointer may be NULL. */
+se_status se_stats(se_ctx_t *ctx, uint64_t *kernel_launches, uint64_t *table_builds,
+                   uint64_t *serving_slices);
+
+/* Per-stage device timing.  When enabled, the library records CUDA events
+ * on the launching stream around each stage of every batch and accumulates
+ * their durations after the batch completes (read with se_stage_times).
+ * Stages: 0 operand packing, 1 table generation (Alg. 2, only when rebuilt),
+ * 2 initial projections (eq. 12), 3 iterations and replacement (Alg. 3).
+ * se_stage_times synchronises the context's outstanding batches, writes up
+ * to n_stages accumulated milliseconds and launch counts (either pointer may
+ * be NULL) and, if reset != 0, clears the accumulators. */
+se_status se_set_profiling(se_ctx_t *ctx, int enable);
+se_status se_stage_times(se_ctx_t *ctx, double *ms, uint64_t *count, int n_stages, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SE_H */

@@ -77,7 +77,7 @@ def _load():
                                 _dp, vp, vp, vp, vp]
         lib.or_fase.restype = ip
         lib.or_se_original_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, ip, vp, _dp, dbl,
-                                             ip, vp, _dp, vp, vp, ip]
+                                             ip, vp, _dp, vp, vp, vp, ip]
         lib.or_se_original_batch.restype = ip
         lib.or_fase_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, _dp, vp, _dp, dbl,
                                       ip, _dp, vp, vp, ip]
@@ -217,22 +217,26 @@ def fase(phi: np.ndarray, w: np.ndarray, Cm: np.ndarray, D: np.ndarray, s: np.nd
 
 def se_original_batch(phi: np.ndarray, w: np.ndarray, s: np.ndarray, gamma: float, I: int,
                       dup: Optional[np.ndarray] = None, iters: Optional[np.ndarray] = None,
-                      nthreads: int = 0):
+                      nthreads: int = 0, margins: bool = False):
     """Alg. 1 over blocks ``s[B, M, N]``; ``w`` is one pattern [M, N] or per block [B, M, N].
 
-    Returns (out [B, M, N], u [B, I], c [B, I], status).  With per-block
-    iteration counts, log entries past a block's count are left as -1 / NaN.
+    Returns (out [B, M, N], u [B, I], c [B, I], status), plus the tie margins
+    [B, I] when ``margins``.  With per-block iteration counts, log entries
+    past a block's count are left as -1 / NaN.
     """
     K = phi.shape[0]
     B, M, N = s.shape
     out = np.empty((B, M, N))
     u = np.full((B, I), -1, dtype=np.int32)
     c = np.full((B, I), np.nan)
+    mg = np.full((B, I), np.nan) if margins else None
     d = None if dup is None else np.ascontiguousarray(dup, dtype=np.uint8)
     it = None if iters is None else np.ascontiguousarray(iters, dtype=np.int32)
     rc = _load().or_se_original_batch(B, M, N, K, _f64(phi), _f64(w), int(w.ndim == 3), _ptr(d),
                                       _f64(s), float(gamma), int(I), _ptr(it), out, _ptr(u),
-                                      _ptr(c), int(nthreads))
+                                      _ptr(c), _ptr(mg), int(nthreads))
+    if margins:
+        return out, u, c, mg, rc
     return out, u, c, rc
 
 

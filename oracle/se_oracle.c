@@ -385,13 +385,13 @@ done:
 
 /* Original SE over B blocks.  Block b uses samples s + b*MN, weights
  * w + (w_stride ? b*MN : 0) and iteration count iters[b] (or I if iters is
- * NULL); logs are [B, I_max] row-major with stride I_max.  nthreads <= 0
+ * NULL); logs (u, c, tie margin) are [B, I] row-major with stride I.  nthreads <= 0
  * lets OpenMP decide.  Returns the first non-zero block status, else 0. */
 int or_se_original_batch(int B, int M, int N, int K, const double *phi,
                          const double *w, int w_stride, const uint8_t *dup,
                          const double *s, double gamma, int I,
                          const int32_t *iters, double *out, int32_t *u_log,
-                         double *c_log, int nthreads)
+                         double *c_log, double *margin_log, int nthreads)
 {
     const int MN = M * N;
     int status = 0;
@@ -404,7 +404,8 @@ int or_se_original_batch(int B, int M, int N, int K, const double *phi,
         int rc = or_se_original(M, N, K, phi, w + (w_stride ? (size_t)b * MN : 0), dup,
                                 s + (size_t)b * MN, gamma, Ib, 0, out + (size_t)b * MN,
                                 NULL, NULL, u_log ? u_log + (size_t)b * I : NULL,
-                                c_log ? c_log + (size_t)b * I : NULL, NULL, NULL);
+                                c_log ? c_log + (size_t)b * I : NULL, NULL,
+                                margin_log ? margin_log + (size_t)b * I : NULL);
         if (rc) {
 #ifdef _OPENMP
 #pragma omp critical

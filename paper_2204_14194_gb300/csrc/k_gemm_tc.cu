@@ -1,0 +1,409 @@
+// k_gemm_tc.cu -- tcgen05 tensor-core GEMM for the scalar-product stages.
+//
+// Computes D[m][n] = sum_pairs sum_k A[m][pa*ka + k] * B[n][pb*ka + k] with
+// bf16 operands (both K-major) and fp32 accumulation in tensor memory.  The
+// "pairs" implement split-precision products: an fp64 operand v is stored as
+// bf16 parts v = h + m + l, and the partial products h*h, h*m, m*h, ... are
+// accumulated into the same TMEM tile, so a 3-part split with 6 products
+// gives ~fp32 accuracy from the bf16 tensor pipe.
+//
+// Used for
+//   * the table of eq. (16), C = G G^T with G = Phi_A diag(sqrt(w)) (Alg. 2;
+//     symmetric mode computes the upper tiles only and mirrors them), and
+//   * the initial projections of eq. (12), R0[b][k] = sum_j G[k][j] X[b][j]
+//     with X = sqrt(w) * s on the support (stored transposed, block-major).
+//
+// Structure (one CTA per 128 x BN output tile, 128 threads):
+//   warp 0 lane 0  TMA producer: cp.async.bulk.tensor 2-D loads of the A and
+//                  B k-slices (64 bf16 = 128 B rows, 128-byte swizzle) into
+//                  a STAGES-deep shared-memory ring, mbarrier complete_tx;
+//   warp 1 lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16, M=128,
+//                  N=BN, K=16 per instruction, accumulator in TMEM;
+//                  tcgen05.commit frees a ring slot when its MMAs retire;
+//   warps 0-3      epilogue: tcgen05.ld 32x32b of their TMEM lane quarter,
+//                  fp32 stores (transposed for R0, mirrored for C).
+// Every mbarrier wait is bounded by %globaltimer; on timeout the CTA records
+// DEV_ERR_WAIT_TIMEOUT, drains what it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "se_internal.h"
+
+namespace se {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                       // bf16 per row of a k-slice (128 bytes)
+constexpr int STAGES = 4;
+constexpr int THREADS = 128;
+constexpr int A_STAGE = BM * BK * 2;         // 16 KiB
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
+constexpr unsigned long long DRAIN_NS = 200000000ull;   // 0.2 s
+
+__device__ __forceinline__ uint32_t saddr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier; false on timeout or abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                          unsigned long long limit_ns)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63u) == 0) {
+            if (abort_flag && *abort_flag) return false;
+            if (gtimer() - t0 > limit_ns) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile whose rows are 128 bytes
+// with the 128-byte swizzle (the layout TMA writes with SWIZZLE_128B):
+// start address >> 4 in bits 0-13, leading byte offset (unused for this
+// layout, 16 B) in bits 16-29, stride byte offset between 8-row groups
+// (1024 B) in bits 32-45, descriptor version 1 in bits 46-47, swizzle mode
+// 2 (128-byte) in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(16u >> 4) << 16;
+    d |= static_cast<uint64_t>(1024u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+
+// Instruction descriptor for kind::f16: fp32 accumulator (bits 4-5 = 1),
+// A and B bf16 (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 =
+// 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+#define TMEM_LD_32x32b_X32(taddr, r)                                                              \
+    asm volatile(                                                                                  \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"              \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),      \
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), \
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),          \
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),          \
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])           \
+        : "r"(taddr))
+
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ TcGemmArgs p, int mt, int nt)
+{
+    constexpr int B_STAGE = BN * BK * 2;
+    constexpr uint32_t TMEM_COLS = BN;            // fp32 accumulator: one column per n
+    constexpr uint32_t IDESC = make_idesc(BM, BN);
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = saddr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gbase = smem_raw + (base - raw);
+    const uint32_t sA = base;
+    const uint32_t sB = base + STAGES * A_STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * (A_STAGE + B_STAGE));
+    const uint32_t full0 = saddr(bars);
+    const uint32_t empty0 = full0 + 8 * STAGES;
+    const uint32_t accum = full0 + 16 * STAGES;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    // tile of this CTA
+    int tm, tn;
+    if (p.symmetric) {
+        int t = blockIdx.x;
+        tm = 0;
+        while (t >= mt - tm) { t -= mt - tm; ++tm; }
+        tn = tm + t;
+    } else {
+        tm = blockIdx.x % mt;
+        tn = blockIdx.x / mt;
+    }
+    (void)nt;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         saddr(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    const int kblocks = p.ka_pad / BK;
+    const int total = p.npairs * kblocks;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- producer
+            int issued = 0;
+            for (int i = 0; i < total; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (i / STAGES) & 1;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, WAIT_NS)) {
+                    *abort_flag = 1;
+                    atomicOr(p.err, 1 << DEV_ERR_WAIT_TIMEOUT);
+                    break;
+                }
+                mbar_expect_tx(full0 + 8 * s, A_STAGE + B_STAGE);
+                const int pair = i / kblocks;
+                const int kb = i - pair * kblocks;
+                tma_load_2d(sA + s * A_STAGE, &tmA, p.pa[pair] * p.ka_pad + kb * BK, tm * BM,
+                            full0 + 8 * s);
+                tma_load_2d(sB + s * B_STAGE, &tmB, p.pb[pair] * p.ka_pad + kb * BK, tn * BN,
+                            full0 + 8 * s);
+                issued = i + 1;
+            }
+            if (*abort_flag) {
+                // let copies already issued land before the CTA exits
+                for (int i = issued - STAGES < 0 ? 0 : issued - STAGES; i < issued; ++i)
+                    mbar_wait(full0 + 8 * (i % STAGES), (i / STAGES) & 1, nullptr, DRAIN_NS);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer
+            for (int i = 0; i < total; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (i / STAGES) & 1;
+                if (!mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_NS)) {
+                    *abort_flag = 1;
+                    atomicOr(p.err, 1 << DEV_ERR_WAIT_TIMEOUT);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = sA + s * A_STAGE;
+                const uint32_t b0 = sB + s * B_STAGE;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    tc_mma(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), IDESC,
+                           (i | kk) != 0 ? 1u : 0u);
+                }
+                tc_commit(empty0 + 8 * s);
+            }
+            tc_commit(accum);   // arrives once every MMA issued above has retired
+        }
+        __syncwarp();
+    }
+
+    // -------------------------------------------------------------- epilogue
+    bool ok = mbar_wait(accum, 0, nullptr, WAIT_NS);
+    if (!ok) atomicOr(p.err, 1 << DEV_ERR_WAIT_TIMEOUT);
+    ok = ok && !*abort_flag;
+    tc_fence_after();
+    __syncwarp();
+
+    const int m = tm * BM + warp * 32 + lane;
+    const bool diag_tile = p.symmetric && tm == tn;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+        TMEM_LD_32x32b_X32(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!ok || m >= p.M) continue;
+        const int n0 = tn * BN + c0;
+        if (!p.symmetric) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + j;
+                if (n < p.N) p.out[static_cast<long long>(n) * p.ldo + m] = __uint_as_float(r[j]);
+            }
+        } else {
+            float *row = p.out + static_cast<long long>(m) * p.ldo;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + j;
+                if (n >= p.N || (diag_tile && n < m)) continue;
+                const float v = __uint_as_float(r[j]);
+                row[n] = v;
+                p.out[static_cast<long long>(n) * p.ldo + m] = v;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn(std::string *why)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    if (!fn && why) *why = "cuTensorMapEncodeTiled is not available from the driver";
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_elems, int box_rows,
+              std::string *why)
+{
+    auto fn = encode_fn(why);
+    if (!fn) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || (pitch_elems * 2) % 16 || cols % BK) {
+        if (why) *why = "tensor map: misaligned base, pitch or width";
+        return false;
+    }
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch_elems) * 2};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (why) *why = "cuTensorMapEncodeTiled failed with code " + std::to_string(static_cast<int>(r));
+        return false;
+    }
+    return true;
+}
+
+template <int BN>
+cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
+{
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why)) return cudaErrorInvalidValue;
+    if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why)) return cudaErrorInvalidValue;
+    const int mt = (a.M + BM - 1) / BM;
+    const int nt = (a.N + BN - 1) / BN;
+    const int grid = a.symmetric ? mt * (mt + 1) / 2 : mt * nt;
+    const size_t smem = static_cast<size_t>(STAGES) * (A_STAGE + BN * BK * 2) + 1024 + 256;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    tc_gemm_kernel<BN><<<grid, THREADS, smem, st>>>(mA, mB, a, mt, nt);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why)
+{
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    if (a.npairs < 1 || a.npairs > 8 || a.ka_pad % BK || a.ka_pad <= 0) {
+        if (why) *why = "tc gemm: bad pair count or inner size";
+        return cudaErrorInvalidValue;
+    }
+    for (int i = 0; i < a.npairs; ++i) {
+        if ((a.pa[i] + 1) * a.ka_pad > a.lda || (a.pb[i] + 1) * a.ka_pad > a.ldb) {
+            if (why) *why = "tc gemm: split part outside the operand row";
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (a.symmetric) {
+        if (a.M != a.N) return cudaErrorInvalidValue;
+        return launch_bn<128>(a, st, why);
+    }
+    return launch_bn<256>(a, st, why);
+}
+
+}  // namespace se

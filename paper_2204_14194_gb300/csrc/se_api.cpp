@@ -1,0 +1,695 @@
+// se_api.cpp -- the C ABI of include/se.h: contexts, plans and the batched
+// extrapolation path (Alg. 2 table generation + Alg. 3 model generation).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "se_host.h"
+
+using namespace se;
+
+namespace {
+
+thread_local std::string g_err;
+
+se_status fail(se_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+}  // namespace
+
+se_status se::set_error(se_status s, const std::string &msg) { return fail(s, msg); }
+
+namespace {
+
+#define SE_CUDA(call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(SE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+#define SE_TRY(expr)                      \
+    do {                                  \
+        se_status s_ = (expr);            \
+        if (s_ != SE_OK) return s_;       \
+    } while (0)
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+se_status se::dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.ptr && b.bytes >= bytes) return SE_OK;
+    b.release();
+    if (ctx->budget && ctx->used.load() + bytes > ctx->budget)
+        return fail(SE_ERR_NOMEM, "HBM budget exceeded: need " + std::to_string(bytes) +
+                                      " more bytes, " + std::to_string(ctx->used.load()) + " of " +
+                                      std::to_string(ctx->budget) + " in use");
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b.ctx = ctx;
+    b.ptr = p;
+    b.bytes = bytes;
+    ctx->used += bytes;
+    return SE_OK;
+}
+
+namespace {
+
+template <typename V>
+se_status upload(se_ctx_s *ctx, DevBuf &b, const std::vector<V> &h)
+{
+    SE_TRY(dev_alloc(ctx, b, h.size() * sizeof(V)));
+    if (!h.empty()) SE_CUDA(cudaMemcpy(b.ptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return SE_OK;
+}
+
+const char *dev_err_text(int bits)
+{
+    if (bits & (1 << DEV_ERR_WAIT_TIMEOUT)) return "a tensor-core pipeline wait timed out";
+    if (bits & (1 << DEV_ERR_BAD_INDEX)) return "no admissible atom could be selected";
+    if (bits & (1 << DEV_ERR_TMEM)) return "tensor memory allocation failed";
+    if (bits & (1 << DEV_ERR_LAZY_CACHE)) return "lazy column cache overflow";
+    return "unknown device error";
+}
+
+}  // namespace
+
+namespace se {
+
+int stage_begin(se_ctx_s *ctx, int stage, cudaStream_t st)
+{
+    if (!ctx->profiling) return -1;
+    std::lock_guard<std::mutex> lk(ctx->pmu);
+    cudaEvent_t ev[2];
+    for (auto &e : ev) {
+        if (!ctx->event_pool.empty()) {
+            e = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            return -1;
+        }
+    }
+    cudaEventRecord(ev[0], st);
+    ctx->pending.push_back({stage, {ev[0], ev[1]}});
+    return static_cast<int>(ctx->pending.size()) - 1;
+}
+
+void stage_end(se_ctx_s *ctx, int token, cudaStream_t st)
+{
+    if (token < 0) return;
+    std::lock_guard<std::mutex> lk(ctx->pmu);
+    if (token < static_cast<int>(ctx->pending.size()))
+        cudaEventRecord(ctx->pending[token].second.second, st);
+}
+
+DevBuf::~DevBuf() { release(); }
+
+Workspace::~Workspace()
+{
+    if (h_desc) cudaFreeHost(h_desc);
+    if (ev_staging) cudaEventDestroy(ev_staging);
+    if (ev_ws) cudaEventDestroy(ev_ws);
+}
+
+cudaError_t Workspace::init()
+{
+    cudaError_t e = cudaEventCreateWithFlags(&ev_staging, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ws, cudaEventDisableTiming);
+    // record once so that the first batch finds both events complete
+    if (e == cudaSuccess) e = cudaEventRecord(ev_staging, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_ws, 0);
+    return e;
+}
+
+void DevBuf::release()
+{
+    if (ptr) {
+        cudaFree(ptr);
+        ctx->used -= bytes;
+    }
+    ptr = nullptr;
+    bytes = 0;
+}
+
+PrecCfg prec_cfg(se_prec p)
+{
+    PrecCfg c;
+    // partial products ordered from the smallest magnitude to the largest
+    switch (p) {
+    case SE_PREC_FP64:
+        c.fp64 = true;
+        break;
+    case SE_PREC_BF16X6: {
+        c.nparts = 3;
+        c.npairs = 6;
+        const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+        for (int i = 0; i < 6; ++i) { c.pa[i] = a[i]; c.pb[i] = b[i]; }
+        break;
+    }
+    case SE_PREC_BF16X3: {
+        c.nparts = 2;
+        c.npairs = 3;
+        const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+        for (int i = 0; i < 3; ++i) { c.pa[i] = a[i]; c.pb[i] = b[i]; }
+        break;
+    }
+    case SE_PREC_BF16:
+    default:
+        c.nparts = 1;
+        c.npairs = 1;
+        break;
+    }
+    return c;
+}
+
+}  // namespace se
+
+namespace {
+
+se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
+{
+    const int Kp = pl->Kp;
+    std::string why;
+    SE_CUDA(launch_tables_diag(pl->d_G64.as<double>(), pl->ka_pad, Kp, pl->nA,
+                               pl->d_diag.as<double>(), st));
+    if (pl->pc.fp64) {
+        SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), pl->K,
+                                               Kp, pl->d_invC.as<double>(), pl->d_Dk.as<double>(),
+                                               pl->d_nadm.as<int>(), st));
+        SE_CUDA(launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad, pl->d_G64.as<double>(),
+                                         pl->ka_pad, Kp, Kp, pl->ka_pad, pl->d_C.as<double>(), Kp, 1,
+                                         st));
+        ctx->launches += 3;
+    } else {
+        SE_CUDA(launch_tables_finalize<float>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), pl->K,
+                                              Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
+                                              pl->d_nadm.as<int>(), st));
+        TcGemmArgs g{};
+        g.A = pl->d_Gbf.ptr;
+        g.B = pl->d_Gbf.ptr;
+        g.M = Kp;
+        g.N = Kp;
+        g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
+        g.ka_pad = pl->ka_pad;
+        g.npairs = pl->pc.npairs;
+        for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+        g.out = pl->d_C.as<float>();
+        g.ldo = Kp;
+        g.symmetric = 1;
+        g.err = ctx->ws_err.as<int>();
+        cudaError_t e = launch_tc_gemm(g, st, &why);
+        if (e != cudaSuccess) return fail(SE_ERR_CUDA, "table GEMM: " + why + " " + cudaGetErrorString(e));
+        ctx->launches += 3;
+    }
+    SE_CUDA(cudaEventRecord(pl->tables_ready, st));
+    pl->tables_valid = true;
+    ctx->table_builds++;
+    return SE_OK;
+}
+
+}  // namespace
+
+// All blocks use the plan's pattern: Alg. 2 tables (cached), eq. (12) GEMM,
+// Alg. 3 iterations.
+se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
+                        int I_max, cudaStream_t st)
+{
+    const int Kp = pl->Kp;
+    const bool fp64 = pl->pc.fp64;
+    const size_t tsz = fp64 ? sizeof(double) : sizeof(float);
+    const size_t xrow = fp64 ? static_cast<size_t>(pl->ka_pad) * sizeof(double)
+                             : static_cast<size_t>(pl->pc.nparts) * pl->ka_pad * 2;
+
+    // the workspace of the previous call must be free before it is reused
+    SE_CUDA(cudaStreamWaitEvent(st, ws.ev_ws, 0));
+    const size_t need_desc = sizeof(BlockDesc) * n, need_x = xrow * n,
+                 need_r0 = tsz * Kp * static_cast<size_t>(n);
+    if (ws.desc.bytes < need_desc || ws.x.bytes < need_x || ws.r0.bytes < need_r0)
+        SE_CUDA(cudaEventSynchronize(ws.ev_ws));
+    SE_TRY(dev_alloc(ctx, ws.desc, need_desc));
+    SE_TRY(dev_alloc(ctx, ws.x, need_x));
+    SE_TRY(dev_alloc(ctx, ws.r0, need_r0));
+
+    // pinned staging of the descriptors: free once the previous copy landed
+    SE_CUDA(cudaEventSynchronize(ws.ev_staging));
+    if (ws.h_desc_cap < static_cast<size_t>(n)) {
+        if (ws.h_desc) cudaFreeHost(ws.h_desc);
+        ws.h_desc = nullptr;
+        ws.h_desc_cap = 0;
+        SE_CUDA(cudaMallocHost(&ws.h_desc, sizeof(BlockDesc) * n));
+        ws.h_desc_cap = n;
+    }
+    std::memcpy(ws.h_desc, hdesc, sizeof(BlockDesc) * n);
+    SE_CUDA(cudaMemcpyAsync(ws.desc.ptr, ws.h_desc, sizeof(BlockDesc) * n,
+                            cudaMemcpyHostToDevice, st));
+    SE_CUDA(cudaEventRecord(ws.ev_staging, st));
+
+    {
+        std::lock_guard<std::mutex> lk(pl->tmu);
+        if (!pl->tables_valid) {
+            const int tok = stage_begin(ctx, 1, st);
+            SE_TRY(build_tables(ctx, pl, st));
+            stage_end(ctx, tok, st);
+        } else {
+            SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
+        }
+    }
+
+    const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
+    std::string why;
+    int tok = stage_begin(ctx, 0, st);
+    if (fp64)
+        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                              pl->ka_pad, 0, nullptr, ws.x.as<double>(), st));
+    else
+        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                              pl->ka_pad, pl->pc.nparts, ws.x.as<uint16_t>(), nullptr, st));
+    stage_end(ctx, tok, st);
+    tok = stage_begin(ctx, 2, st);
+    if (fp64) {
+        SE_CUDA(launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad, ws.x.as<double>(),
+                                         pl->ka_pad, Kp, n, pl->ka_pad, ws.r0.as<double>(), Kp,
+                                         0, st));
+    } else {
+        TcGemmArgs g{};
+        g.A = pl->d_Gbf.ptr;
+        g.B = ws.x.ptr;
+        g.M = Kp;
+        g.N = n;
+        g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
+        g.ka_pad = pl->ka_pad;
+        g.npairs = pl->pc.npairs;
+        for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+        g.out = ws.r0.as<float>();
+        g.ldo = Kp;
+        g.symmetric = 0;
+        g.err = ctx->ws_err.as<int>();
+        cudaError_t e = launch_tc_gemm(g, st, &why);
+        if (e != cudaSuccess) return fail(SE_ERR_CUDA, "projection GEMM: " + why + " " + cudaGetErrorString(e));
+    }
+    stage_end(ctx, tok, st);
+    ctx->launches += 2;
+
+    IterArgs a{};
+    a.blocks = ddesc;
+    a.n = n;
+    a.K = pl->K;
+    a.Kp = Kp;
+    a.R0 = ws.r0.ptr;
+    a.C = pl->d_C.ptr;
+    a.invC = pl->d_invC.ptr;
+    a.Dk = pl->d_Dk.ptr;
+    a.PhiB = pl->d_PhiB.ptr;
+    a.b_idx = pl->d_b_idx.as<int>();
+    a.pat_support = pl->d_pattern.as<uint8_t>();
+    a.nB = pl->nB;
+    a.MN = pl->MN;
+    a.gamma = pl->desc.gamma;
+    a.I_max = I_max;
+    a.err = ctx->ws_err.as<int>();
+    int launched = 0;
+    tok = stage_begin(ctx, 3, st);
+    cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched)
+                         : launch_iterate_full<float>(a, st, &launched);
+    stage_end(ctx, tok, st);
+    if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("iteration kernel: ") + cudaGetErrorString(e));
+    ctx->launches += launched;
+    SE_CUDA(cudaEventRecord(ws.ev_ws, st));
+    return SE_OK;
+}
+
+namespace {
+
+se_status resolve_blocks(se_plan_s *pl, int n, const se_block *blocks, std::vector<BlockDesc> &d,
+                         int *I_max, bool *any_mask)
+{
+    d.resize(n);
+    *I_max = 0;
+    *any_mask = false;
+    for (int i = 0; i < n; ++i) {
+        const se_block &b = blocks[i];
+        if (!b.samples || !b.out) return fail(SE_ERR_INVALID, "block " + std::to_string(i) + ": NULL samples or out");
+        if (b.iterations < 0) return fail(SE_ERR_INVALID, "block " + std::to_string(i) + ": iterations < 0");
+        BlockDesc &x = d[i];
+        x.samples = b.samples;
+        x.support = b.support;
+        x.out = b.out;
+        x.sel_idx = b.sel_idx;
+        x.sel_coef = b.sel_coef;
+        x.iterations = b.iterations ? b.iterations : pl->desc.iterations;
+        x.pad_ = 0;
+        *I_max = std::max(*I_max, x.iterations);
+        *any_mask |= b.support != nullptr;
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *se_last_error(void) { return g_err.c_str(); }
+
+se_status se_ctx_create(int device, size_t hbm_budget_bytes, se_ctx_t **out)
+{
+    if (!out) return fail(SE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    SE_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(SE_ERR_INVALID, "no such CUDA device");
+    SE_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    SE_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return fail(SE_ERR_CUDA, "libse needs a Blackwell (sm_10x) GPU");
+    auto *c = new se_ctx_s();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = c->ws.init();
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(SE_ERR_CUDA, std::string("context set-up: ") + cudaGetErrorString(e));
+    }
+    se_status s = dev_alloc(c, c->ws_err, sizeof(int));
+    if (s != SE_OK) { delete c; return s; }
+    e = cudaMemset(c->ws_err.ptr, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(SE_ERR_CUDA, std::string("context set-up: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return SE_OK;
+}
+
+se_status se_ctx_destroy(se_ctx_t *ctx)
+{
+    if (!ctx) return SE_OK;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    cudaDeviceSynchronize();
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    std::vector<se_plan_s *> plans = ctx->plans;
+    for (auto *p : plans) se_plan_destroy(p);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SE_OK;
+}
+
+se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
+{
+    if (!ctx || !desc || !out) return fail(SE_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const se_plan_desc &d = *desc;
+    if (d.M < 1 || d.N < 1 || d.M > 256 || d.N > 256) return fail(SE_ERR_INVALID, "M and N must be in [1, 256]");
+    if (!(d.rho_hat > 0.0 && d.rho_hat <= 1.0)) return fail(SE_ERR_INVALID, "rho_hat must be in (0, 1]");
+    if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return fail(SE_ERR_INVALID, "gamma must be in (0, 1]");
+    if (d.iterations < 1) return fail(SE_ERR_INVALID, "iterations must be >= 1");
+    if (d.prec != SE_PREC_FP64 && d.prec != SE_PREC_BF16X6 && d.prec != SE_PREC_BF16X3 &&
+        d.prec != SE_PREC_BF16)
+        return fail(SE_ERR_INVALID, "unknown precision");
+    if (d.gram < SE_GRAM_AUTO || d.gram > SE_GRAM_LAZY) return fail(SE_ERR_INVALID, "unknown table mode");
+    SE_CUDA(cudaSetDevice(ctx->device));
+
+    auto pl = std::make_unique<se_plan_s>();
+    pl->ctx = ctx;
+    pl->desc = d;
+    pl->desc.dict = nullptr;
+    pl->desc.rho = nullptr;
+    pl->desc.support = nullptr;
+    pl->M = d.M;
+    pl->N = d.N;
+    pl->MN = d.M * d.N;
+    pl->K = d.K;
+    pl->pc = prec_cfg(d.prec);
+    std::string why;
+    if (!build_dictionary(d.M, d.N, d.basis, d.K, d.dict, pl->phi, &why)) return fail(SE_ERR_INVALID, why);
+    const int MN = pl->MN, K = pl->K;
+    pl->Kp = iterate_kp(K, pl->pc.fp64);
+    if (pl->Kp < 0) return fail(SE_ERR_INVALID, "K is larger than the iteration kernel supports (16384)");
+    find_collinear(K, MN, pl->phi.data(), pl->dup);
+
+    pl->pattern.assign(MN, 1);
+    if (d.support) {
+        for (int i = 0; i < MN; ++i) pl->pattern[i] = d.support[i] ? 1 : 0;
+    } else {
+        for (int m = d.M / 4; m < d.M / 4 + d.M / 2; ++m)
+            for (int n = d.N / 4; n < d.N / 4 + d.N / 2; ++n) pl->pattern[m * d.N + n] = 0;
+    }
+    weighting(d.M, d.N, d.rho_hat, d.rho, pl->pattern.data(), pl->w);
+    for (int i = 0; i < MN; ++i) {
+        if (pl->pattern[i] && !(pl->w[i] >= 0.0 && std::isfinite(pl->w[i])))
+            return fail(SE_ERR_INVALID, "rho must be finite and non-negative");
+        if (pl->pattern[i] && pl->w[i] > 0.0) pl->a_idx.push_back(i);
+        else if (!pl->pattern[i]) pl->b_idx.push_back(i);
+    }
+    // support pixels with zero weight contribute nothing; they keep their samples
+    pl->nA = static_cast<int>(pl->a_idx.size());
+    pl->nB = static_cast<int>(pl->b_idx.size());
+    if (pl->nA == 0) return fail(SE_ERR_EMPTY_SUPPORT, "the default pattern has no weighted support");
+    {   // at least one admissible atom (same rule as the device tables)
+        double mx = 0.0;
+        std::vector<double> dg(K, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+            double s = 0.0;
+            for (int i : pl->a_idx) s += a[i] * a[i] * pl->w[i];
+            dg[k] = s;
+            if (!pl->dup[k]) mx = std::max(mx, s);
+        }
+        int adm = 0;
+        for (int k = 0; k < K; ++k) adm += !pl->dup[k] && mx > 0.0 && dg[k] > 1e-14 * mx;
+        if (adm == 0) return fail(SE_ERR_EMPTY_SUPPORT, "no atom has weighted energy on the support");
+    }
+    pl->ka_pad = static_cast<int>(round_up(pl->nA, 64));
+    const int Kp = pl->Kp, ka = pl->ka_pad;
+
+    std::vector<double> G(static_cast<size_t>(Kp) * ka, 0.0), sqw(pl->nA);
+    for (int j = 0; j < pl->nA; ++j) sqw[j] = std::sqrt(pl->w[pl->a_idx[j]]);
+    for (int k = 0; k < K; ++k) {
+        const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+        for (int j = 0; j < pl->nA; ++j) G[static_cast<size_t>(k) * ka + j] = a[pl->a_idx[j]] * sqw[j];
+    }
+    std::vector<uint8_t> dupp(Kp, 1);
+    for (int k = 0; k < K; ++k) dupp[k] = pl->dup[k];
+    SE_TRY(upload(ctx, pl->d_G64, G));
+    SE_TRY(upload(ctx, pl->d_sqrtw, sqw));
+    SE_TRY(upload(ctx, pl->d_a_idx, pl->a_idx));
+    SE_TRY(upload(ctx, pl->d_b_idx, pl->b_idx));
+    SE_TRY(upload(ctx, pl->d_pattern, pl->pattern));
+    SE_TRY(upload(ctx, pl->d_dup, dupp));
+    const size_t nBa = std::max(pl->nB, 1);
+    if (pl->pc.fp64) {
+        std::vector<double> pb(static_cast<size_t>(Kp) * nBa, 0.0);
+        for (int k = 0; k < K; ++k)
+            for (int j = 0; j < pl->nB; ++j)
+                pb[static_cast<size_t>(k) * nBa + j] = pl->phi[static_cast<size_t>(k) * MN + pl->b_idx[j]];
+        SE_TRY(upload(ctx, pl->d_PhiB, pb));
+    } else {
+        std::vector<float> pb(static_cast<size_t>(Kp) * nBa, 0.0f);
+        for (int k = 0; k < K; ++k)
+            for (int j = 0; j < pl->nB; ++j)
+                pb[static_cast<size_t>(k) * nBa + j] =
+                    static_cast<float>(pl->phi[static_cast<size_t>(k) * MN + pl->b_idx[j]]);
+        SE_TRY(upload(ctx, pl->d_PhiB, pb));
+        SE_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka * 2));
+        SE_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka, ka, ka, pl->pc.nparts,
+                                  pl->d_Gbf.as<uint16_t>(), ctx->stream));
+        ctx->launches++;
+    }
+    const size_t tsz = pl->pc.fp64 ? 8 : 4;
+    SE_TRY(dev_alloc(ctx, pl->d_C, tsz * Kp * static_cast<size_t>(Kp)));
+    SE_TRY(dev_alloc(ctx, pl->d_invC, tsz * Kp));
+    SE_TRY(dev_alloc(ctx, pl->d_Dk, tsz * Kp));
+    SE_TRY(dev_alloc(ctx, pl->d_diag, sizeof(double) * Kp));
+    SE_TRY(dev_alloc(ctx, pl->d_nadm, sizeof(int)));
+    SE_CUDA(cudaEventCreateWithFlags(&pl->tables_ready, cudaEventDisableTiming));
+    SE_CUDA(cudaStreamSynchronize(ctx->stream));
+    se_plan_s *raw = pl.release();
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->plans.push_back(raw);
+    }
+    *out = raw;
+    return SE_OK;
+}
+
+se_status se_plan_destroy(se_plan_t *plan)
+{
+    if (!plan) return SE_OK;
+    se_ctx_s *ctx = plan->ctx;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), plan), ctx->plans.end());
+    }
+    if (plan->tables_ready) cudaEventDestroy(plan->tables_ready);
+    delete plan;
+    return SE_OK;
+}
+
+se_status se_plan_reset_tables(se_plan_t *plan)
+{
+    if (!plan) return fail(SE_ERR_INVALID, "NULL plan");
+    std::lock_guard<std::mutex> lk(plan->tmu);
+    plan->tables_valid = false;
+    return SE_OK;
+}
+
+se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, const se_block *blocks,
+                               void *cuda_stream)
+{
+    if (!ctx || !plan || (n > 0 && !blocks) || n < 0) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    if (n == 0) return SE_OK;
+    if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    se_plan_s *pl = const_cast<se_plan_s *>(plan);
+    std::vector<BlockDesc> d;
+    int I_max = 0;
+    bool any_mask = false;
+    SE_TRY(resolve_blocks(pl, n, blocks, d, &I_max, &any_mask));
+    if (any_mask || pl->desc.gram == SE_GRAM_LAZY)
+        return fail(SE_ERR_INVALID, "per-block support masks need the lazy table path");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return run_batch(ctx, pl, ctx->ws, n, d.data(), I_max, static_cast<cudaStream_t>(cuda_stream));
+}
+
+se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, const double *samples,
+                                 double *out, int32_t *sel_idx, double *sel_coef, int iterations,
+                                 void *cuda_stream)
+{
+    if (!ctx || !plan || n < 0) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    if (n == 0) return SE_OK;
+    if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
+    if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
+    const int I = iterations ? iterations : plan->desc.iterations;
+    std::vector<se_block> b(n);
+    const size_t MN = static_cast<size_t>(plan->MN);
+    for (int i = 0; i < n; ++i) {
+        b[i].samples = samples + MN * i;
+        b[i].support = nullptr;
+        b[i].out = out + MN * i;
+        b[i].sel_idx = sel_idx ? sel_idx + static_cast<size_t>(I) * i : nullptr;
+        b[i].sel_coef = sel_coef ? sel_coef + static_cast<size_t>(I) * i : nullptr;
+        b[i].iterations = I;
+    }
+    return se_extrapolate_batch(ctx, plan, n, b.data(), cuda_stream);
+}
+
+se_status se_sync(se_ctx_t *ctx, void *cuda_stream)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    SE_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream)));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int bits = 0;
+    SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) {
+        SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
+        return fail(SE_ERR_CUDA, std::string("device status: ") + dev_err_text(bits));
+    }
+    return SE_OK;
+}
+
+se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const double *samples,
+                              double *out, int32_t *sel_idx, double *sel_coef, int iterations)
+{
+    if (!ctx || !plan || n < 0) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    if (n == 0) return SE_OK;
+    if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
+    if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    const int I = iterations ? iterations : plan->desc.iterations;
+    const size_t MN = static_cast<size_t>(plan->MN);
+    const size_t io_bytes = 2 * MN * n * sizeof(double) +
+                            (sel_idx ? sizeof(int32_t) * I * static_cast<size_t>(n) : 0) +
+                            (sel_coef ? sizeof(double) * I * static_cast<size_t>(n) : 0) + 64;
+    cudaStream_t st = ctx->stream;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->ws.io.bytes < io_bytes) SE_CUDA(cudaStreamSynchronize(st));
+        SE_TRY(dev_alloc(ctx, ctx->ws.io, io_bytes));
+    }
+    double *d_s = ctx->ws.io.as<double>();
+    double *d_o = d_s + MN * n;
+    char *tail = reinterpret_cast<char *>(d_o + MN * n);
+    int32_t *d_i = sel_idx ? reinterpret_cast<int32_t *>(tail) : nullptr;
+    double *d_c = nullptr;
+    if (sel_coef) {
+        size_t off = sel_idx ? round_up(sizeof(int32_t) * I * static_cast<size_t>(n), 16) : 0;
+        d_c = reinterpret_cast<double *>(tail + off);
+    }
+    SE_CUDA(cudaMemcpyAsync(d_s, samples, MN * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    SE_TRY(se_extrapolate_strided(ctx, plan, n, d_s, d_o, d_i, d_c, I, st));
+    SE_CUDA(cudaMemcpyAsync(out, d_o, MN * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (sel_idx)
+        SE_CUDA(cudaMemcpyAsync(sel_idx, d_i, sizeof(int32_t) * I * static_cast<size_t>(n),
+                                cudaMemcpyDeviceToHost, st));
+    if (sel_coef)
+        SE_CUDA(cudaMemcpyAsync(sel_coef, d_c, sizeof(double) * I * static_cast<size_t>(n),
+                                cudaMemcpyDeviceToHost, st));
+    return se_sync(ctx, st);
+}
+
+se_status se_set_profiling(se_ctx_t *ctx, int enable)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->pmu);
+    ctx->profiling = enable != 0;
+    return SE_OK;
+}
+
+se_status se_stage_times(se_ctx_t *ctx, double *ms, uint64_t *count, int n_stages, int reset)
+{
+    if (!ctx || n_stages < 0) return fail(SE_ERR_INVALID, "NULL context or n_stages < 0");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->pmu);
+    for (auto &p : ctx->pending) {
+        cudaEvent_t a = p.second.first, b = p.second.second;
+        SE_CUDA(cudaEventSynchronize(b));
+        float t = 0.0f;
+        SE_CUDA(cudaEventElapsedTime(&t, a, b));
+        ctx->stage_ms[p.first] += t;
+        ctx->stage_count[p.first] += 1;
+        ctx->event_pool.push_back(a);
+        ctx->event_pool.push_back(b);
+    }
+    ctx->pending.clear();
+    for (int i = 0; i < n_stages && i < se_ctx_s::kStages; ++i) {
+        if (ms) ms[i] = ctx->stage_ms[i];
+        if (count) count[i] = ctx->stage_count[i];
+    }
+    if (reset)
+        for (int i = 0; i < se_ctx_s::kStages; ++i) { ctx->stage_ms[i] = 0.0; ctx->stage_count[i] = 0; }
+    return SE_OK;
+}
+
+se_status se_stats(se_ctx_t *ctx, uint64_t *kernel_launches, uint64_t *table_builds,
+                   uint64_t *serving_slices)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    if (kernel_launches) *kernel_launches = ctx->launches.load();
+    if (table_builds) *table_builds = ctx->table_builds.load();
+    if (serving_slices) *serving_slices = ctx->slices.load();
+    return SE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// se_host.h -- host-side structures of libse.so (contexts, plans, buffers).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/se.h"
+#include "se_internal.h"
+
+struct se_ctx_s;
+
+namespace se {
+
+bool build_dictionary(int M, int N, int basis, int K, const double *numeric,
+                      std::vector<double> &phi, std::string *why);
+void find_collinear(int K, int MN, const double *phi, std::vector<uint8_t> &dup);
+void weighting(int M, int N, double rho_hat, const double *rho, const uint8_t *support,
+               std::vector<double> &w);
+
+// A device allocation charged against the context's HBM budget.
+struct DevBuf {
+    se_ctx_s *ctx = nullptr;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf();
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Device workspace of one in-flight batch (descriptors, packed operands,
+// initial projections, host-call I/O) with its pinned descriptor staging.
+struct Workspace {
+    DevBuf desc, x, r0, io;
+    BlockDesc *h_desc = nullptr;
+    size_t h_desc_cap = 0;
+    cudaEvent_t ev_staging = nullptr;     // the staging copy of the last batch has landed
+    cudaEvent_t ev_ws = nullptr;          // the last batch no longer uses the workspace
+    ~Workspace();
+    cudaError_t init();
+};
+
+// Record a failure for se_last_error() and return the status.
+se_status set_error(se_status s, const std::string &msg);
+
+// Precision set-up derived from se_prec.
+struct PrecCfg {
+    bool fp64 = false;
+    int nparts = 1;
+    int npairs = 1;
+    int pa[8] = {0}, pb[8] = {0};
+};
+PrecCfg prec_cfg(se_prec p);
+
+}  // namespace se
+
+struct se_plan_s;
+
+// Serving request as queued by se_submit.
+struct ServeReq {
+    uint64_t ticket = 0;
+    se_plan_s *plan = nullptr;
+    std::vector<double> samples;
+    std::vector<uint8_t> support;      // empty: plan pattern
+    double *out = nullptr;
+    int32_t *sel_idx = nullptr;
+    double *sel_coef = nullptr;
+    int iterations = 0;
+    double t_submit = 0.0;
+    double t_done = 0.0;
+    int state = 0;                     // 0 queued, 1 running, 2 done, 3 failed, 4 cancelled
+    se_status status = SE_OK;
+};
+
+// One serving lane: a stream with its own batch workspace and I/O buffers.
+struct ServeLane {
+    cudaStream_t st = nullptr;
+    se::Workspace ws;
+    se::DevBuf d_io;
+    char *h_io = nullptr;
+    size_t h_io_cap = 0;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    se_plan_s *plan = nullptr;
+    int I_max = 0;
+    std::vector<std::shared_ptr<ServeReq>> batch;
+    ~ServeLane()
+    {
+        if (h_io) cudaFreeHost(h_io);
+        if (done) cudaEventDestroy(done);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
+struct se_ctx_s {
+    int device = 0;
+    size_t budget = 0;
+    std::atomic<size_t> used{0};
+    cudaStream_t stream = nullptr;        // internal stream (host-buffer calls, serving)
+    std::mutex mu;                        // serialises batch calls (shared workspace)
+
+    // workspace of the batch entry points (grown on demand, reused)
+    se::Workspace ws;
+    se::DevBuf ws_err;                    // device status word shared by all kernels
+
+    // per-stage timing (se_set_profiling)
+    static constexpr int kStages = 4;
+    bool profiling = false;
+    std::mutex pmu;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;   // stage, (start, stop)
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[kStages] = {0, 0, 0, 0};
+    uint64_t stage_count[kStages] = {0, 0, 0, 0};
+
+    std::atomic<uint64_t> launches{0};
+    std::atomic<uint64_t> table_builds{0};
+    std::atomic<uint64_t> slices{0};
+
+    // serving
+    std::mutex smu;
+    std::condition_variable scv;
+    std::deque<std::shared_ptr<ServeReq>> queue;
+    std::map<uint64_t, std::shared_ptr<ServeReq>> tickets;
+    std::thread server;
+    bool stop = false;
+    bool server_started = false;
+    std::vector<std::unique_ptr<ServeLane>> lanes;
+    uint64_t next_ticket = 1;
+    std::vector<se_plan_s *> plans;
+};
+
+struct se_plan_s {
+    se_ctx_s *ctx = nullptr;
+    se_plan_desc desc{};
+    int M = 0, N = 0, MN = 0, K = 0, Kp = 0;
+    se::PrecCfg pc;
+    std::vector<double> phi;              // host K x MN atoms (fp64)
+    std::vector<uint8_t> dup;             // host K flags
+    std::vector<uint8_t> pattern;         // host MN default support
+    std::vector<double> w;                // host MN weights of the default pattern
+    std::vector<int> a_idx, b_idx;
+    int nA = 0, nB = 0, ka_pad = 0;
+
+    // device copies
+    se::DevBuf d_a_idx, d_b_idx, d_sqrtw, d_pattern, d_dup;
+    se::DevBuf d_G64;                     // Kp x ka_pad fp64, G = phi_A sqrt(w)
+    se::DevBuf d_Gbf;                     // Kp x nparts*ka_pad bf16 split of G
+    se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels
+    // tables (eqs. 16-17)
+    se::DevBuf d_C, d_invC, d_Dk, d_diag, d_nadm;
+    bool tables_valid = false;
+    cudaEvent_t tables_ready = nullptr;
+    std::mutex tmu;
+};
+
+namespace se {
+// One batch of blocks of one plan, all on the plan's pattern: tables of
+// Alg. 2 if not cached, eq. (12) GEMM, Alg. 3 iterations, on stream st.
+se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
+                    int I_max, cudaStream_t st);
+se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);
+// Stage timing: stage_begin returns a token (or -1 when profiling is off).
+int stage_begin(se_ctx_s *ctx, int stage, cudaStream_t st);
+void stage_end(se_ctx_s *ctx, int token, cudaStream_t st);
+void serve_shutdown(se_ctx_s *ctx);
+}  // namespace se

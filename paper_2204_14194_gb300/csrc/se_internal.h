@@ -1,0 +1,103 @@
+// se_internal.h -- types shared by the host runtime and the kernel launchers
+// of libse.so.  Not part of the public ABI (include/se.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace se {
+
+// Per-block descriptor as the kernels read it (device copy of se_block,
+// resolved: iterations filled in, support == nullptr means the batch's
+// shared pattern).
+struct BlockDesc {
+    const double *samples;
+    const uint8_t *support;
+    double *out;
+    int32_t *sel_idx;
+    double *sel_coef;
+    int iterations;
+    int pad_;
+};
+
+// Device-side error codes written to the batch status word.
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_ERR_WAIT_TIMEOUT = 1,     // an mbarrier wait ran out of time
+    DEV_ERR_BAD_INDEX = 2,        // a selected index fell outside [0, K)
+    DEV_ERR_TMEM = 3,             // tensor-memory allocation returned an unusable address
+    DEV_ERR_LAZY_CACHE = 4        // lazy column cache overflowed
+};
+
+// ----------------------------------------------------------------- GEMMs
+// D[m][n] = sum_pairs sum_k A[m][pa*ka_pad + k] * B[n][pb*ka_pad + k]
+// with bf16 A (rows M) and B (rows N), fp32 accumulation on tcgen05.
+struct TcGemmArgs {
+    const void *A;       // bf16 [M_rows][lda] (lda in elements)
+    const void *B;       // bf16 [N_rows][ldb]
+    int M, N;            // logical sizes (rows of A, rows of B)
+    int lda, ldb;        // row pitch in elements (multiple of 8)
+    int ka_pad;          // columns of one split part (multiple of 64)
+    int npairs;
+    int pa[8], pb[8];    // split part of A / B for each partial product
+    float *out;          // output
+    long long ldo;       // output row pitch (elements)
+    int symmetric;       // 1: Gram mode (M == N, upper tiles, mirrored store)
+    int *err;            // device status word
+};
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why);
+
+// fp64 (or fp32) CUDA-core GEMM, same contraction with a single part:
+// D[m][n] = sum_k A[m][k] B[n][k]; output mode as above.
+template <typename T>
+cudaError_t launch_simt_gemm(const T *A, int lda, const T *B, int ldb, int M, int N, int Kd,
+                             T *out, long long ldo, int symmetric, cudaStream_t st);
+
+// ------------------------------------------------------------- prep / tables
+// Pack the weighted samples of the shared pattern: for block b and support
+// pixel j, v = sqrtw[j] * samples_b[a_idx[j]] (0 for j >= nA), written as
+// nparts bf16 split parts ([part][ka_pad] per row) and/or as fp64.
+cudaError_t launch_pack_x(const BlockDesc *blocks, int n, const int *a_idx, const double *sqrtw,
+                          int nA, int ka_pad, int nparts, uint16_t *x_bf16, double *x_f64,
+                          cudaStream_t st);
+
+// diag[k] = sum_j G64[k][j]^2 (fp64), then invC / D / admissibility.
+cudaError_t launch_tables_diag(const double *G64, int ldg, int Kp, int nA, double *diag,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup, int K, int Kp, T *invC,
+                                   T *Dk, int *n_admissible, cudaStream_t st);
+
+// ------------------------------------------------------------------ iterate
+struct IterArgs {
+    const BlockDesc *blocks;
+    int n;
+    int K, Kp;              // dictionary size and padded size (row pitch of C, R0)
+    const void *R0;         // [n][Kp] initial projections (eq. 12)
+    const void *C;          // [Kp][Kp] table (eq. 16)
+    const void *invC;       // [Kp] 1 / C_kk (0 for inadmissible)
+    const void *Dk;         // [Kp] 1 / sqrt(C_kk) (NaN for inadmissible)
+    const void *PhiB;       // [Kp][nB] atoms on the pattern's loss pixels
+    const int *b_idx;       // [nB] loss pixel indices of the pattern
+    const uint8_t *pat_support;   // [MN] the pattern (1 = A)
+    int nB;
+    int MN;
+    double gamma;
+    int I_max;              // largest iteration count in the batch
+    int *err;
+    int *work_counter;      // persistent scheduling counter (zeroed by the launcher)
+};
+template <typename T>
+cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches);
+
+// Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
+int iterate_kp(int K, bool fp64);
+
+// Split fp64 rows into bf16 parts: out[r][p * ka_pad + j] for j < cols
+// (zero for cols <= j < ka_pad).
+cudaError_t launch_split_bf16(const double *in, int rows, int cols, int ld_in, int ka_pad,
+                              int nparts, uint16_t *out, cudaStream_t st);
+
+}  // namespace se

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (spec tolerances):
+  * selected index sequence identical up to the first iteration whose
+    oracle tie margin (s1 - s2) / s1 is <= tau (tau = 1e-9 for the fp64
+    form, 1e-4 for the split-bf16 forms);
+  * coefficients within 1e-9 relative (fp64 form) / 1e-3 (mixed forms) on
+    those iterations;
+  * PSNR of the reconstructed loss area within 0.05 dB of the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2204_14194_gb300 import binding as B
+from paper_2204_14194_gb300 import workloads as W
+from helpers import OracleSetup, coef_rel_err, first_near_tie, psnr
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": (1e-9, 1e-9), "bf16x6": (1e-4, 1e-3), "bf16x3": (1e-3, 1e-3)}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.init()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(plan, samples, iterations=None, stream=None):
+    """Run a batch through se_extrapolate_strided; returns numpy out, u, c."""
+    n = samples.shape[0]
+    I = iterations or plan.iterations
+    s = torch.from_numpy(np.ascontiguousarray(samples)).cuda()
+    out = torch.empty_like(s)
+    u = torch.full((n, I), -7, dtype=torch.int32, device="cuda")
+    c = torch.full((n, I), float("nan"), dtype=torch.float64, device="cuda")
+    plan.extrapolate_strided(s, out, u, c, iterations=I, stream=stream)
+    plan.ctx.sync(stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), u.cpu().numpy(), c.cpu().numpy()
+
+
+def check_block(prec, out, u, c, ref_u, ref_c, margin, ref_out, truth, loss):
+    tau, ctol = TOL[prec]
+    t = first_near_tie(margin, tau)
+    assert t >= min(10, len(margin)), f"near tie already at iteration {t}"
+    np.testing.assert_array_equal(u[:t], ref_u[:t])
+    err = coef_rel_err(c[:t], ref_c[:t])
+    assert err.max() <= ctol, (prec, err.max(), int(err.argmax()))
+    if t == len(margin):
+        assert abs(psnr(out, truth, loss) - psnr(ref_out, truth, loss)) <= 0.05
+    return t, float(err.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x3"])
+def test_config1_against_se_oracle(ctx, prec):
+    wl = W.config1()
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec)
+    out, u, c = gpu_run(plan, wl.samples)
+    o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
+    ref = o.se(wl.samples[0], wl.gamma, wl.iterations)
+    loss = wl.support == 0
+    t, e = check_block(prec, out[0], u[0], c[0], ref.u, ref.c, ref.margin, ref.out,
+                       wl.samples[0], loss)
+    # the smallest tie margin of this block is 3.7e-4: above the fp64 and
+    # bf16x6 thresholds (whole sequence compared), below bf16x3's
+    if TOL[prec][0] < ref.margin.min():
+        assert t == wl.iterations
+    np.testing.assert_array_equal(out[0][~loss], wl.samples[0][~loss])
+    if prec == "fp64":
+        np.testing.assert_allclose(out[0][loss], ref.out[loss], rtol=0, atol=1e-9 * 255)
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_config2_scaled_ragged_batch(ctx, prec):
+    """300 blocks of the 512x512 workload: two GEMM column tiles, the second ragged."""
+    wl = W.config2(300)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec)
+    out, u, c = gpu_run(plan, wl.samples)
+    o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, wl.samples, wl.gamma, wl.iterations,
+                                             o.dup, margins=True)
+    assert st == 0
+    loss = wl.support == 0
+    tau, ctol = TOL[prec]
+    full = 0
+    for b in range(wl.B):
+        t = first_near_tie(rm[b], tau)
+        np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+        assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= ctol
+        full += t == wl.iterations
+    assert full >= 0.8 * wl.B
+    lm = np.broadcast_to(loss, out.shape)
+    assert abs(psnr(out, wl.samples, lm) - psnr(ro, wl.samples, lm)) <= 0.05
+    plan.close()
+
+
+def test_config2_full_size_sampled(ctx):
+    """All 4096 blocks in the benchmark's launch configuration; 24 sampled blocks vs the oracle."""
+    wl = W.config2()
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec="bf16x6")
+    out, u, c = gpu_run(plan, wl.samples)
+    assert np.all(u >= 0) and np.all(u < 2048)
+    o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
+    pick = np.random.default_rng(7).choice(wl.B, 24, replace=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, wl.samples[pick], wl.gamma,
+                                             wl.iterations, o.dup, margins=True)
+    loss = wl.support == 0
+    for i, b in enumerate(pick):
+        t = first_near_tie(rm[i], 1e-4)
+        np.testing.assert_array_equal(u[b, :t], ru[i, :t])
+        assert coef_rel_err(c[b, :t], rc[i, :t]).max() <= 1e-3
+    lm = np.broadcast_to(loss, ro.shape)
+    assert abs(psnr(out[pick], wl.samples[pick], lm) - psnr(ro, wl.samples[pick], lm)) <= 0.05
+    # every output keeps the support samples
+    np.testing.assert_array_equal(out[:, ~loss], wl.samples[:, ~loss])
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_per_block_iterations_and_tiny_batches(ctx, prec):
+    wl = W.config2(5)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, 100, prec=prec)
+    o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
+    iters = [1, 7, 100, 33, 2]
+    s = torch.from_numpy(wl.samples).cuda()
+    outs = torch.empty_like(s)
+    us = [torch.full((i,), -1, dtype=torch.int32, device="cuda") for i in iters]
+    cs = [torch.zeros(i, dtype=torch.float64, device="cuda") for i in iters]
+    plan.extrapolate_batch([{"samples": s[b], "out": outs[b], "sel_idx": us[b], "sel_coef": cs[b],
+                             "iterations": iters[b]} for b in range(5)])
+    ctx.sync()
+    torch.cuda.synchronize()
+    tau, ctol = TOL[prec]
+    for b in range(5):
+        ref = o.se(wl.samples[b], wl.gamma, iters[b])
+        t = first_near_tie(ref.margin, tau)
+        np.testing.assert_array_equal(us[b].cpu().numpy()[:t], ref.u[:t])
+        assert coef_rel_err(cs[b].cpu().numpy()[:t], ref.c[:t]).max() <= ctol
+    # a single block alone equals the same block inside a batch (bitwise)
+    one, u1, c1 = gpu_run(plan, wl.samples[2:3], iterations=100)
+    np.testing.assert_array_equal(u1[0], us[2].cpu().numpy())
+    np.testing.assert_array_equal(c1[0], cs[2].cpu().numpy())
+    np.testing.assert_array_equal(one[0], outs[2].cpu().numpy())
+    plan.close()
+
+
+def test_loss_area_values_never_read(ctx):
+    wl = W.config2(40)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, 50, prec="bf16x6")
+    a, ua, ca = gpu_run(plan, wl.samples)
+    s = wl.samples.copy()
+    s[:, wl.support == 0] = np.nan
+    b, ub, cb = gpu_run(plan, s)
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(ca, cb)
+    np.testing.assert_array_equal(a[:, wl.support == 0], b[:, wl.support == 0])
+    plan.close()
+
+
+def test_composition_invariance_and_table_rebuild(ctx):
+    wl = W.config2(600)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, 100, prec="bf16x6")
+    big, ub, cb = gpu_run(plan, wl.samples)
+    plan.reset_tables()
+    small, us, cs = gpu_run(plan, wl.samples[299:302])
+    np.testing.assert_array_equal(small, big[299:302])
+    np.testing.assert_array_equal(us, ub[299:302])
+    np.testing.assert_array_equal(cs, cb[299:302])
+    assert ctx.stats()["table_builds"] >= 2
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
+def test_gaussian_dictionary_K4096_I200(ctx, prec):
+    """The 1920x1080 / Gaussian-dictionary workload, first 40 blocks."""
+    wl = W.config3(40)
+    plan = ctx.plan(32, 32, "numeric", 4096, wl.rho_hat, wl.gamma, wl.iterations, prec=prec,
+                    dictionary=wl.dictionary)
+    out, u, c = gpu_run(plan, wl.samples)
+    o = OracleSetup("numeric", 32, 32, wl.rho_hat, wl.support, numeric=wl.dictionary, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, wl.samples, wl.gamma, wl.iterations,
+                                             o.dup, margins=True)
+    tau, ctol = TOL[prec]
+    for b in range(wl.B):
+        t = first_near_tie(rm[b], tau)
+        np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+        assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= ctol
+    m = wl.psnr_mask
+    assert abs(psnr(out, wl.samples, m) - psnr(ro, wl.samples, m)) <= 0.05
+    plan.close()
+
+
+@pytest.mark.parametrize("L,basis", [(16, "dct_wht"), (64, "dct_wht"), (16, "dct"), (32, "wht")])
+def test_other_sizes_and_bases(ctx, L, basis):
+    K = {"dct_wht": 2 * L * L, "dct": L * L, "wht": L * L}[basis]
+    I = 60
+    s = np.stack([W.patch(L, 500 + i) for i in range(6)])
+    sup = W.centred_support(L, L)
+    o = OracleSetup(basis, L, L, 0.8, sup, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, s, 0.5, I, o.dup, margins=True)
+    for prec in ("fp64", "bf16x6"):
+        plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec)
+        out, u, c = gpu_run(plan, s)
+        tau, ctol = TOL[prec]
+        for b in range(len(s)):
+            t = first_near_tie(rm[b], tau)
+            np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+            assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= ctol
+        plan.close()
+
+
+def test_host_entry_point_matches_device_path(ctx):
+    wl = W.config2(64)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, 100, prec="bf16x6")
+    dev, ud, cd = gpu_run(plan, wl.samples)
+    out = np.empty_like(wl.samples)
+    u = np.empty((64, 100), dtype=np.int32)
+    c = np.empty((64, 100))
+    plan.extrapolate_host(wl.samples, out, u, c)
+    np.testing.assert_array_equal(out, dev)
+    np.testing.assert_array_equal(u, ud)
+    np.testing.assert_array_equal(c, cd)
+    plan.close()
+
+
+def test_invalid_arguments(ctx):
+    with pytest.raises(B.SeError) as e:
+        ctx.plan(32, 32, "dct_wht", 2000, 0.8, 0.5, 100)
+    assert e.value.status == -1
+    with pytest.raises(B.SeError):
+        ctx.plan(32, 32, "dct_wht", 2048, 0.8, 1.5, 100)
+    with pytest.raises(B.SeError):
+        ctx.plan(32, 32, "dct_wht", 2048, 0.0, 0.5, 100)
+    with pytest.raises(B.SeError):
+        ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 0)
+    with pytest.raises(B.SeError):
+        ctx.plan(24, 24, "wht", 576, 0.8, 0.5, 10)
+    with pytest.raises(B.SeError) as e:
+        ctx.plan(8, 8, "dct", 64, 0.8, 0.5, 10, support=np.zeros((8, 8), np.uint8))
+    assert e.value.status == -5
+    plan = ctx.plan(8, 8, "dct", 64, 0.8, 0.5, 10)
+    plan.extrapolate_strided(torch.empty((0, 8, 8), dtype=torch.float64, device="cuda"),
+                             torch.empty((0, 8, 8), dtype=torch.float64, device="cuda"))
+    plan.close()
