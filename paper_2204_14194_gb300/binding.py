@@ -28,7 +28,7 @@ GRAM = {"auto": 0, "full": 1, "lazy": 2}
 EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_plan_reset_tables",
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
-           "se_stage_times"]
+           "se_stage_times", "se_extrapolate_noalloc"]
 STAGES = ["pack", "tables", "projections", "iterate"]
 
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
             "se_extrapolate_batch": ([vp, vp, i32, C.POINTER(Block), vp], i32),
             "se_extrapolate_strided": ([vp, vp, i32, vp, vp, vp, vp, i32, vp], i32),
             "se_extrapolate_host": ([vp, vp, i32, vp, vp, vp, vp, i32], i32),
+            "se_extrapolate_noalloc": ([vp, vp, i32, vp, vp, vp, vp, i32, vp], i32),
             "se_sync": ([vp, vp], i32),
             "se_submit": ([vp, vp, C.POINTER(Request), C.POINTER(u64)], i32),
             "se_poll": ([vp, u64, C.c_int64, C.POINTER(dbl)], i32),
@@ -233,6 +234,15 @@ class Plan:
                                                 _ptr(out), _ptr(sel_idx), _ptr(sel_coef),
                                                 int(iterations), _stream_handle(stream)),
                "se_extrapolate_strided")
+
+    def extrapolate_noalloc(self, samples, out, sel_idx=None, sel_coef=None, iterations: int = 0,
+                            stream=None):
+        """Like extrapolate_strided, with all scratch in the library's static device array."""
+        n = int(samples.shape[0])
+        _check(self._lib.se_extrapolate_noalloc(self.ctx.handle, self.handle, n, _ptr(samples),
+                                                _ptr(out), _ptr(sel_idx), _ptr(sel_coef),
+                                                int(iterations), _stream_handle(stream)),
+               "se_extrapolate_noalloc")
 
     def extrapolate_batch(self, blocks, stream=None):
         """blocks: list of dicts with device tensors samples/out and optional support,

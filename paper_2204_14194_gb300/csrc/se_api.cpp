@@ -333,6 +333,18 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
 
 namespace {
 
+}  // namespace
+
+se_status se::ensure_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(pl->tmu);
+    if (!pl->tables_valid) return build_tables(ctx, pl, st);
+    SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
+    return SE_OK;
+}
+
+namespace {
+
 se_status resolve_blocks(se_plan_s *pl, int n, const se_block *blocks, std::vector<BlockDesc> &d,
                          int *I_max, bool *any_mask)
 {

@@ -171,6 +171,9 @@ namespace se {
 se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                     int I_max, cudaStream_t st);
 se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);
+// Build the plan's tables on stream st if they are not cached (plan memory
+// only, nothing is allocated), else make st wait for the cached build.
+se_status ensure_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
 // Stage timing: stage_begin returns a token (or -1 when profiling is off).
 int stage_begin(se_ctx_s *ctx, int stage, cudaStream_t st);
 void stage_end(se_ctx_s *ctx, int token, cudaStream_t st);

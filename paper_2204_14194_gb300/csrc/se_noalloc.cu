@@ -1,0 +1,179 @@
+// se_noalloc.cu -- se_extrapolate_noalloc: the strided batch entry point for
+// callers that must not allocate memory during the call.
+//
+// Some callers cannot call cudaMalloc (or anything that allocates) once they
+// are running: real-time loops that forbid allocation after start-up, code
+// that runs under an allocator it does not own, or hosts that hand the
+// library only their own input and output buffers.  For them this entry
+// point keeps all per-call scratch -- the block descriptors, the packed
+// weighted samples and the initial projections -- in one file-scope
+// __device__ array of fixed size (kScratchBytes below), which every GPU that
+// loads the library holds until the process exits.  The caller still passes
+// the inputs and outputs; the plan's tables live in memory the plan
+// allocated when it was created.
+//
+// Host code cannot use the array's name as a device address (in host code it
+// names a host-side stand-in).  So the first call on each device, with that
+// device current, looks the address up with cudaGetSymbolAddress and caches
+// it; that first call should therefore come before any stream capture.
+//
+// Every call shares the one array, and it keeps the last call's contents.
+// Nothing in it has to start at zero (every byte a call reads was written by
+// the same call's kernels), so nothing is cleared.  Calls whose work overlaps
+// on the GPU (different streams, or different threads) race on the array and
+// must be serialised by the caller.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "se_host.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = 16u << 20;   // 16 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+
+size_t r256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Block descriptors of a contiguous batch: samples[b], out[b] are M x N,
+// the logs are [b][iterations].
+__global__ void fill_desc_kernel(se::BlockDesc *d, int n, const double *samples, double *out,
+                                 int32_t *sel_idx, double *sel_coef, int iterations, int MN)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    se::BlockDesc x;
+    x.samples = samples + static_cast<size_t>(MN) * b;
+    x.support = nullptr;
+    x.out = out + static_cast<size_t>(MN) * b;
+    x.sel_idx = sel_idx ? sel_idx + static_cast<size_t>(iterations) * b : nullptr;
+    x.sel_coef = sel_coef ? sel_coef + static_cast<size_t>(iterations) * b : nullptr;
+    x.iterations = iterations;
+    x.pad_ = 0;
+    d[b] = x;
+}
+
+se_status scratch_address(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices)
+        return se::set_error(SE_ERR_INVALID, "device index out of range for the static scratch");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p)
+            return se::set_error(SE_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                                  cudaGetErrorString(e));
+        g_scratch_addr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_addr[device]);
+    return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
+                                            const double *samples, double *out, int32_t *sel_idx,
+                                            double *sel_coef, int iterations, void *cuda_stream)
+{
+    using namespace se;
+    if (!ctx || !plan || n < 0) return set_error(SE_ERR_INVALID, "NULL argument or n < 0");
+    if (plan->ctx != ctx) return set_error(SE_ERR_INVALID, "plan belongs to another context");
+    if (n == 0) return SE_OK;
+    if (!samples || !out) return set_error(SE_ERR_INVALID, "NULL samples or out");
+    if (iterations < 0) return set_error(SE_ERR_INVALID, "iterations < 0");
+    se_plan_s *pl = const_cast<se_plan_s *>(plan);
+    const int I = iterations ? iterations : pl->desc.iterations;
+    const bool fp64 = pl->pc.fp64;
+    const int Kp = pl->Kp;
+
+    // scratch layout: descriptors | packed samples | initial projections
+    const size_t desc_b = r256(sizeof(BlockDesc) * static_cast<size_t>(n));
+    const size_t xrow = fp64 ? sizeof(double) * pl->ka_pad : 2u * pl->pc.nparts * pl->ka_pad;
+    const size_t x_b = r256(xrow * n);
+    const size_t r_b = (fp64 ? sizeof(double) : sizeof(float)) * Kp * static_cast<size_t>(n);
+    if (desc_b + x_b + r_b > kScratchBytes) {
+        const size_t per = sizeof(BlockDesc) + xrow + (fp64 ? 8 : 4) * static_cast<size_t>(Kp);
+        return set_error(SE_ERR_INVALID,
+                         "se_extrapolate_noalloc: " + std::to_string(n) +
+                             " blocks need more than the 16 MiB static scratch; at most about " +
+                             std::to_string(kScratchBytes / per) + " blocks of this plan fit");
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(SE_ERR_CUDA, "cudaSetDevice failed");
+    unsigned char *base = nullptr;
+    se_status s = scratch_address(ctx->device, &base);
+    if (s != SE_OK) return s;
+    BlockDesc *d_desc = reinterpret_cast<BlockDesc *>(base);
+    void *d_x = base + desc_b;
+    void *d_r0 = base + desc_b + x_b;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    fill_desc_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_desc, n, samples, out, sel_idx, sel_coef, I,
+                                                      pl->MN);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(SE_ERR_CUDA, std::string("descriptors: ") + cudaGetErrorString(e));
+    s = ensure_tables(ctx, pl, st);
+    if (s != SE_OK) return s;
+
+    std::string why;
+    if (fp64) {
+        e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                          pl->ka_pad, 0, nullptr, static_cast<double *>(d_x), st);
+        if (e == cudaSuccess)
+            e = launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad,
+                                         static_cast<const double *>(d_x), pl->ka_pad, Kp, n,
+                                         pl->ka_pad, static_cast<double *>(d_r0), Kp, 0, st);
+    } else {
+        e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                          pl->ka_pad, pl->pc.nparts, static_cast<uint16_t *>(d_x), nullptr, st);
+        if (e == cudaSuccess) {
+            TcGemmArgs g{};
+            g.A = pl->d_Gbf.ptr;
+            g.B = d_x;
+            g.M = Kp;
+            g.N = n;
+            g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
+            g.ka_pad = pl->ka_pad;
+            g.npairs = pl->pc.npairs;
+            for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+            g.out = static_cast<float *>(d_r0);
+            g.ldo = Kp;
+            g.symmetric = 0;
+            g.err = ctx->ws_err.as<int>();
+            e = launch_tc_gemm(g, st, &why);
+        }
+    }
+    if (e != cudaSuccess)
+        return set_error(SE_ERR_CUDA, "se_extrapolate_noalloc projections: " + why + " " + cudaGetErrorString(e));
+
+    IterArgs a{};
+    a.blocks = d_desc;
+    a.n = n;
+    a.K = pl->K;
+    a.Kp = Kp;
+    a.R0 = d_r0;
+    a.C = pl->d_C.ptr;
+    a.invC = pl->d_invC.ptr;
+    a.Dk = pl->d_Dk.ptr;
+    a.PhiB = pl->d_PhiB.ptr;
+    a.b_idx = pl->d_b_idx.as<int>();
+    a.pat_support = pl->d_pattern.as<uint8_t>();
+    a.nB = pl->nB;
+    a.MN = pl->MN;
+    a.gamma = pl->desc.gamma;
+    a.I_max = I;
+    a.err = ctx->ws_err.as<int>();
+    int launched = 0;
+    e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterate_full<float>(a, st, &launched);
+    if (e != cudaSuccess)
+        return set_error(SE_ERR_CUDA, std::string("se_extrapolate_noalloc iterations: ") + cudaGetErrorString(e));
+    ctx->launches += 3 + launched;
+    return SE_OK;
+}
