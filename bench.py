@@ -34,6 +34,9 @@ if ROOT not in sys.path:
 METRIC = "extrapolated blocks/s (32x32 area, K=2048, 100 iters)"
 UNIT = "blocks/s"
 WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
+# dram__bytes_read.sum + dram__bytes_write.sum of one iterate_f32_kernel launch
+# on this workload (ncu, see profiles/); None once the kernel changes.
+TRAFFIC_ITERATE = 92.73e6
 
 
 def _dist():
@@ -148,6 +151,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import opcount
     from paper_2204_14194_gb300 import workloads as W
 
     ws, rank, local = _dist()
@@ -262,18 +266,31 @@ def run_ours(args):
         d = o[:, loss] - gt
         return 10.0 * np.log10(255.0 ** 2 / float(np.mean(d * d)))
 
-    # ---- roofline of the dominant kernel (the iteration kernel, Alg. 3)
+    # ---- roofline of the dominant kernel (the iteration kernel, Alg. 3).  Its
+    # table C (16 MiB) stays in L2, so it is bound by arithmetic issue, not
+    # HBM: achieved = Table-I FaSE operations of the iterations (I*(5K + 2MN
+    # + 1) per block) / average launch time, peak = fp32 CUDA-core rate
+    # (152 SMs x 128 lanes x 2 flops x max SM clock).
     hbm_peak, tc_peak, peak_kind = measured_peaks()
     it_ms, it_n = stages["iterate"]
     it_avg_s = it_ms / max(it_n, 1) / 1000.0
-    Kp = 2048
-    # algorithmic bytes per launch: one row of C per block-iteration after the
-    # first, R0 read, samples read and output written (fp64)
-    alg_bytes = n * ((I - 1) * Kp * 4 + Kp * 4 + 2 * M * N * 8)
-    achieved = alg_bytes / it_avg_s / 1e9
-    roofline = {"kernel": "iterate_full_kernel<float,1,64,4>", "bound": "hbm", "achieved": achieved,
-                "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_kind": peak_kind}
+    ops = n * I * opcount.fase_iteration_ops(M, N, K)
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = ops / it_avg_s / 1e12
+    roofline = {"kernel": "iterate_f32_kernel<1,64,4>", "bound": "alu", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": TRAFFIC_ITERATE,
+                "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
+                "l2_read_GBps": n * (I - 1) * K * 4 / it_avg_s / 1e9}
+    pr_ms, pr_n = stages["projections"]
+    pr_avg_s = pr_ms / max(pr_n, 1) / 1000.0
+    npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(args.prec, 0)
+    na = int(np.sum(wl.support))
+    tflops = 2.0 * K * n * na * npairs / pr_avg_s / 1e12 if npairs else None
+    roofline_gemm = None if tflops is None else {
+        "kernel": "tc_gemm_kernel<256,1,0> (eq. 12 projections)", "bound": "tensor",
+        "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s", "frac": tflops / tc_peak,
+        "peak_kind": peak_kind + " bf16 dense"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -297,6 +314,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * M * N * 8),
                 "d2h_bytes_per_step": int(n * M * N * 8)},
         "roofline": roofline,
+        "roofline_projections": roofline_gemm,
         "vs_fp64_form": {"fp64_blocks_per_s": fp64_value, "speedup": value / fp64_value,
                          "index_sequence_identical_frac": float(np.mean(same)),
                          "max_rel_coef_err_before_first_divergence": float(max(rel)) if rel else 0.0,

@@ -12,6 +12,8 @@
 //     symmetric mode computes the upper tiles only and mirrors them), and
 //   * the initial projections of eq. (12), R0[b][k] = sum_j G[k][j] X[b][j]
 //     with X = sqrt(w) * s on the support (stored transposed, block-major).
+// An optional per-atom factor (D_k = 1/sqrt(C_kk) of eq. 17) is applied in
+// the epilogue, so the fp32 iteration works on D-scaled projections.
 //
 // Structure (one CTA per 128 x BN output tile, 128 threads):
 //   warp 0 lane 0  TMA producer: cp.async.bulk.tensor 2-D loads of the A and
@@ -37,9 +39,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;                       // bf16 per row of a k-slice (128 bytes)
-constexpr int STAGES = 4;
 constexpr int THREADS = 128;
-constexpr int A_STAGE = BM * BK * 2;         // 16 KiB
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s
 constexpr unsigned long long DRAIN_NS = 200000000ull;   // 0.2 s
 
@@ -161,22 +161,41 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N)
           "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])           \
         : "r"(taddr))
 
-template <int BN>
+// Two stage layouts.  GROUPED: a pipeline stage holds one 64-wide k-slice
+// of every split part of A (NP x 16 KiB) and of B (NP x BN*128 B) and the MMA
+// issuer runs all partial products on it, so each part is fetched once per
+// k-slice.  Otherwise a stage holds the A and B slices of one partial product
+// (pair-major), which needs less shared memory per stage and so allows a
+// deeper ring and wider BN.
+template <int BN, int NP, bool GROUPED>
+struct TcCfg {
+    static constexpr int A_PART = BM * BK * 2;
+    static constexpr int B_PART = BN * BK * 2;
+    static constexpr int STAGE = (GROUPED ? NP : 1) * (A_PART + B_PART);
+    static constexpr int STAGES = (200 * 1024) / STAGE < 2 ? 1 : ((200 * 1024) / STAGE > 6 ? 6 : (200 * 1024) / STAGE);
+    static constexpr size_t SMEM = static_cast<size_t>(STAGES) * STAGE + 1024 + 256;
+};
+
+template <int BN, int NP, bool GROUPED>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ TcGemmArgs p, int mt, int nt)
 {
-    constexpr int B_STAGE = BN * BK * 2;
-    constexpr uint32_t TMEM_COLS = BN;            // fp32 accumulator: one column per n
+    using Cfg = TcCfg<BN, NP, GROUPED>;
+    constexpr int STAGES = Cfg::STAGES;
+    static_assert(STAGES >= 2, "at least double buffering");
+    // Two fp32 accumulators of BN columns: acc0 takes the leading product
+    // (the pair of the two largest parts, main_pair), acc1 every smaller
+    // cross product, so the small terms are summed among themselves and added
+    // to the large ones only once, in the epilogue.
+    constexpr uint32_t TMEM_COLS = 2 * BN;
     constexpr uint32_t IDESC = make_idesc(BM, BN);
 
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = saddr(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
-    const uint32_t sA = base;
-    const uint32_t sB = base + STAGES * A_STAGE;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * (A_STAGE + B_STAGE));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + STAGES * Cfg::STAGE);
     const uint32_t full0 = saddr(bars);
     const uint32_t empty0 = full0 + 8 * STAGES;
     const uint32_t accum = full0 + 16 * STAGES;
@@ -186,7 +205,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
-    // tile of this CTA
     int tm, tn;
     if (p.symmetric) {
         int t = blockIdx.x;
@@ -221,13 +239,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const uint32_t tmem = *tmem_holder;
 
     const int kblocks = p.ka_pad / BK;
-    const int total = p.npairs * kblocks;
+    const int units = GROUPED ? kblocks : p.npairs * kblocks;   // pipeline units
+    int main_pair = 0, first_small = -1;
+    for (int q = 0; q < p.npairs; ++q)
+        if (p.pa[q] + p.pb[q] < p.pa[main_pair] + p.pb[main_pair]) main_pair = q;
+    for (int q = 0; q < p.npairs; ++q)
+        if (q != main_pair) { first_small = q; break; }
+    const bool has_small = first_small >= 0;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------------------------------------------- producer
             int issued = 0;
-            for (int i = 0; i < total; ++i) {
+            for (int i = 0; i < units; ++i) {
                 const int s = i % STAGES;
                 const uint32_t ph = (i / STAGES) & 1;
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, WAIT_NS)) {
@@ -235,17 +259,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     atomicOr(p.err, 1 << DEV_ERR_WAIT_TIMEOUT);
                     break;
                 }
-                mbar_expect_tx(full0 + 8 * s, A_STAGE + B_STAGE);
-                const int pair = i / kblocks;
-                const int kb = i - pair * kblocks;
-                tma_load_2d(sA + s * A_STAGE, &tmA, p.pa[pair] * p.ka_pad + kb * BK, tm * BM,
-                            full0 + 8 * s);
-                tma_load_2d(sB + s * B_STAGE, &tmB, p.pb[pair] * p.ka_pad + kb * BK, tn * BN,
-                            full0 + 8 * s);
+                mbar_expect_tx(full0 + 8 * s, Cfg::STAGE);
+                const uint32_t st0 = base + s * Cfg::STAGE;
+                if (GROUPED) {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        tma_load_2d(st0 + q * Cfg::A_PART, &tmA, q * p.ka_pad + i * BK, tm * BM, full0 + 8 * s);
+                        tma_load_2d(st0 + NP * Cfg::A_PART + q * Cfg::B_PART, &tmB, q * p.ka_pad + i * BK,
+                                    tn * BN, full0 + 8 * s);
+                    }
+                } else {
+                    const int pair = i / kblocks, kb = i - pair * kblocks;
+                    tma_load_2d(st0, &tmA, p.pa[pair] * p.ka_pad + kb * BK, tm * BM, full0 + 8 * s);
+                    tma_load_2d(st0 + Cfg::A_PART, &tmB, p.pb[pair] * p.ka_pad + kb * BK, tn * BN,
+                                full0 + 8 * s);
+                }
                 issued = i + 1;
             }
             if (*abort_flag) {
-                // let copies already issued land before the CTA exits
                 for (int i = issued - STAGES < 0 ? 0 : issued - STAGES; i < issued; ++i)
                     mbar_wait(full0 + 8 * (i % STAGES), (i / STAGES) & 1, nullptr, DRAIN_NS);
             }
@@ -254,7 +285,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer
-            for (int i = 0; i < total; ++i) {
+            for (int i = 0; i < units; ++i) {
                 const int s = i % STAGES;
                 const uint32_t ph = (i / STAGES) & 1;
                 if (!mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_NS)) {
@@ -263,12 +294,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = sA + s * A_STAGE;
-                const uint32_t b0 = sB + s * B_STAGE;
+                const uint32_t st0 = base + s * Cfg::STAGE;
+                if (GROUPED) {
+                    for (int q = 0; q < p.npairs; ++q) {
+                        const uint32_t a0 = st0 + p.pa[q] * Cfg::A_PART;
+                        const uint32_t b0 = st0 + NP * Cfg::A_PART + p.pb[q] * Cfg::B_PART;
+                        const bool big = q == main_pair;
+                        const uint32_t d = big ? tmem : tmem + BN;
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    tc_mma(tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), IDESC,
-                           (i | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const bool first = i == 0 && kk == 0 && (big || q == first_small);
+                            tc_mma(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), IDESC,
+                                   first ? 0u : 1u);
+                        }
+                    }
+                } else {
+                    const int pair = i / kblocks, kb = i - pair * kblocks;
+                    const bool big = pair == main_pair;
+                    const uint32_t d = big ? tmem : tmem + BN;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const bool first = kb == 0 && kk == 0 && (big || pair == first_small);
+                        tc_mma(d, smem_desc(st0 + kk * 32), smem_desc(st0 + Cfg::A_PART + kk * 32), IDESC,
+                               first ? 0u : 1u);
+                    }
                 }
                 tc_commit(empty0 + 8 * s);
             }
@@ -292,13 +341,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
         TMEM_LD_32x32b_X32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (has_small) {
+            uint32_t q[32];
+            TMEM_LD_32x32b_X32(taddr + BN, q);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(q[j]) + __uint_as_float(r[j]));
+        }
         if (!ok || m >= p.M) continue;
         const int n0 = tn * BN + c0;
+        const float sm = p.scale ? p.scale[m] : 1.0f;
         if (!p.symmetric) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int n = n0 + j;
-                if (n < p.N) p.out[static_cast<long long>(n) * p.ldo + m] = __uint_as_float(r[j]);
+                if (n < p.N) p.out[static_cast<long long>(n) * p.ldo + m] = __uint_as_float(r[j]) * sm;
             }
         } else {
             float *row = p.out + static_cast<long long>(m) * p.ldo;
@@ -307,8 +364,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const int n = n0 + j;
                 if (n >= p.N || (diag_tile && n < m)) continue;
                 const float v = __uint_as_float(r[j]);
-                row[n] = v;
-                p.out[static_cast<long long>(n) * p.ldo + m] = v;
+                row[n] = p.scale ? v * p.scale[n] : v;
+                p.out[static_cast<long long>(n) * p.ldo + m] = v * sm;
             }
         }
     }
@@ -362,25 +419,25 @@ bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_
     return true;
 }
 
-template <int BN>
+template <int BN, int NP, bool GROUPED>
 cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 {
+    using Cfg = TcCfg<BN, NP, GROUPED>;
     CUtensorMap mA, mB;
     if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why)) return cudaErrorInvalidValue;
     if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why)) return cudaErrorInvalidValue;
     const int mt = (a.M + BM - 1) / BM;
     const int nt = (a.N + BN - 1) / BN;
     const int grid = a.symmetric ? mt * (mt + 1) / 2 : mt * nt;
-    const size_t smem = static_cast<size_t>(STAGES) * (A_STAGE + BN * BK * 2) + 1024 + 256;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN>,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP, GROUPED>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+                                             static_cast<int>(Cfg::SMEM));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_gemm_kernel<BN><<<grid, THREADS, smem, st>>>(mA, mB, a, mt, nt);
+    tc_gemm_kernel<BN, NP, GROUPED><<<grid, THREADS, Cfg::SMEM, st>>>(mA, mB, a, mt, nt);
     return cudaGetLastError();
 }
 
@@ -393,17 +450,31 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
         if (why) *why = "tc gemm: bad pair count or inner size";
         return cudaErrorInvalidValue;
     }
+    int np = 0;
     for (int i = 0; i < a.npairs; ++i) {
-        if ((a.pa[i] + 1) * a.ka_pad > a.lda || (a.pb[i] + 1) * a.ka_pad > a.ldb) {
-            if (why) *why = "tc gemm: split part outside the operand row";
-            return cudaErrorInvalidValue;
-        }
+        np = a.pa[i] + 1 > np ? a.pa[i] + 1 : np;
+        np = a.pb[i] + 1 > np ? a.pb[i] + 1 : np;
     }
+    if (np * a.ka_pad > a.lda || np * a.ka_pad > a.ldb) {
+        if (why) *why = "tc gemm: split part outside the operand row";
+        return cudaErrorInvalidValue;
+    }
+    if (a.symmetric && a.M != a.N) return cudaErrorInvalidValue;
+    // The table (square, symmetric) uses 128 x 128 tiles with all parts of a
+    // k-slice per stage; the projections use 128 x 256 tiles streamed one
+    // partial product per stage (measured faster for the wide, short-K case).
     if (a.symmetric) {
-        if (a.M != a.N) return cudaErrorInvalidValue;
-        return launch_bn<128>(a, st, why);
+        switch (np) {
+        case 1: return launch_bn<128, 1, true>(a, st, why);
+        case 2: return launch_bn<128, 2, true>(a, st, why);
+        case 3: return launch_bn<128, 3, true>(a, st, why);
+        default: break;
+        }
+    } else if (np <= 3) {
+        return launch_bn<256, 1, false>(a, st, why);
     }
-    return launch_bn<256>(a, st, why);
+    if (why) *why = "tc gemm: more than 3 split parts";
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace se

@@ -26,20 +26,18 @@
 
 #include "se_internal.h"
 
+#ifndef SE_ITER_ASYNC
+#define SE_ITER_ASYNC 2      // 0: row of T in registers, 1: cp.async to shared, 2: TMA bulk copy
+#endif
+
 namespace se {
 namespace {
 
 template <typename T> struct Vec;
-template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
 
 template <typename T>
 __device__ __forceinline__ void vget(const typename Vec<T>::type &v, T *o);
-template <>
-__device__ __forceinline__ void vget<float>(const float4 &v, float *o)
-{
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
 template <>
 __device__ __forceinline__ void vget<double>(const double2 &v, double *o)
 {
@@ -190,6 +188,297 @@ iterate_full_kernel(const IterArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// fp32 form, on D-scaled quantities.  With R'_k = R_k D_k and the table row
+// T[u][k] = C(k, u) D_k (both scaled in the GEMM epilogues), eq. (18) is
+// u = argmax |R'_k|, eq. (19) is c = gamma R'_u D_u (since 1/C_uu = D_u^2)
+// and eq. (20) is R'_k -= c T[u][k]: one FFMA and one FMNMX per atom and
+// iteration, no per-atom loads besides the row of T.  Inadmissible atoms have
+// D = NaN, so their R' is NaN and fmaxf never selects them.
+//
+// Scores |R'| are >= 0, so their IEEE bit patterns order like unsigned
+// integers and the warp maximum is one redux.sync.  The fused update keeps
+// four independent running maxima (one per position of the float4) instead
+// of a compare-and-select chain; only the lane(s) holding the maximum then
+// look for its smallest index, scanning the chain(s) whose maximum matched.
+// Ties therefore still go to the smallest k, as in the generic path.
+template <int W, int VPT>
+__device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const float (&m)[4], int tid,
+                                           int lane, int warp, Cand<float> *slot, int &u, float &ru)
+{
+    constexpr int NT = 32 * W;
+    constexpr int NCH = VPT / 4;
+    const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+    const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+    int kc = INT_MAX;
+    float rc = 0.0f;
+    if (mx == M) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (m[j] == M) {
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int k = ch * NT * 4 + tid * 4 + j;
+                    const float2 q = R2[ch * 2 + (j >> 1)];
+                    const float r = (j & 1) ? q.y : q.x;
+                    if (k < kc && fabsf(r) == M) {
+                        kc = k;
+                        rc = r;
+                    }
+                }
+            }
+        }
+    }
+    const int kw = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
+    const int owner = kw == INT_MAX ? 0 : (kw >> 2) % NT % 32;
+    const float rw = __shfl_sync(0xffffffffu, rc, owner);
+    if constexpr (W == 1) {
+        u = kw;
+        ru = rw;
+    } else {
+        if (lane == 0) slot[warp] = Cand<float>{M, kw, rw};
+        __syncthreads();
+        float sb = slot[0].s;
+        int kb = slot[0].k;
+        float rb = slot[0].r;
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            const Cand<float> c = slot[w];
+            if (better(c.s, c.k, sb, kb)) { sb = c.s; kb = c.k; rb = c.r; }
+        }
+        u = kb;
+        ru = rb;
+    }
+}
+
+#ifndef SE_ITER_MAX3
+#define SE_ITER_MAX3 1       // 1: three-input max instruction, 0: two fmaxf
+#endif
+
+// max(m, |a|, |b|); NaN inputs are ignored (maxNum semantics).
+__device__ __forceinline__ float max3_abs(float m, float a, float b)
+{
+#if SE_ITER_MAX3
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(fabsf(a)), "f"(fabsf(b)));
+    return r;
+#else
+    return fmaxf(m, fmaxf(fabsf(a), fabsf(b)));
+#endif
+}
+
+// The row of T is copied global -> shared with cp.async (16 bytes per
+// thread and chunk, L1-allocating), so the in-flight row holds no registers;
+// each thread later reads back exactly the chunks it copied itself, so only
+// its own cp.async group has to complete.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// One bulk (TMA) copy of a whole row of T into shared memory, completing on
+// an mbarrier; waits are bounded by %globaltimer.
+__device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
+    uint32_t ok = 0;
+    unsigned long long t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(m), "r"(parity) : "memory");
+        if (ok) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (i == 0) t0 = t;
+        else if (t - t0 > 2000000000ull) return false;
+    }
+}
+
+// Register budget: VPT projections (the row of T is staged in shared memory
+// when SE_ITER_ASYNC, in registers otherwise); the launch bound keeps at
+// least SE_ITER_MIN_WARPS warps per SM resident.
+#ifndef SE_ITER_MIN_WARPS
+#define SE_ITER_MIN_WARPS 16
+#endif
+template <int W, int VPT, int BPC>
+__global__ void __launch_bounds__(32 * W * BPC, (SE_ITER_MIN_WARPS + W * BPC - 1) / (W * BPC))
+iterate_f32_kernel(const IterArgs a)
+{
+    static_assert(W == 1 || BPC == 1, "multi-warp blocks use one block per CTA");
+    static_assert(VPT % 4 == 0, "whole float4 chunks");
+    constexpr int NT = 32 * W;
+    constexpr int NCH = VPT / 4;
+    const int Kp = a.Kp;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sBar = reinterpret_cast<uint64_t *>(smem);                     // [BPC] (bulk copies)
+    float *sT = reinterpret_cast<float *>(smem + 16 * BPC);                  // [BPC][Kp] if async
+    Cand<float> *sRed = reinterpret_cast<Cand<float> *>(sT + (SE_ITER_ASYNC ? BPC * Kp : 0));
+    float *sC = reinterpret_cast<float *>(sRed + 2 * W);                      // [BPC][I_max]
+    int *sU = reinterpret_cast<int *>(sC + BPC * a.I_max);                    // [BPC][I_max]
+
+    const int g = threadIdx.x / NT;
+    const int tid = threadIdx.x % NT;
+    const int lane = threadIdx.x & 31;
+    const int warp = tid >> 5;
+    float *logC = sC + g * a.I_max;
+    int *logU = sU + g * a.I_max;
+    float *myT = sT + g * Kp;
+    uint64_t *myBar = sBar + 2 * g;
+    if (SE_ITER_ASYNC == 2 && tid == 0) {
+        const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(myBar));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if constexpr (W > 1) __syncthreads(); else __syncwarp();
+    uint32_t phase = 0;
+    bool failed = false;
+    const float *Ttab = static_cast<const float *>(a.C);
+    const float *Dk = static_cast<const float *>(a.Dk);
+    const float gamma = static_cast<float>(a.gamma);
+
+    for (int b = blockIdx.x * BPC + g; b < a.n; b += gridDim.x * BPC) {
+        const BlockDesc bd = a.blocks[b];
+        const int I = bd.iterations;
+        const float *R0 = static_cast<const float *>(a.R0) + static_cast<size_t>(b) * Kp;
+
+        // R2[2 ch + h] holds projections k = ch*NT*4 + tid*4 + 2h + {0, 1}
+        float2 R2[VPT / 2];
+        float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+            const float4 v = *reinterpret_cast<const float4 *>(R0 + ch * NT * 4 + tid * 4);
+            R2[ch * 2 + 0] = make_float2(v.x, v.y);
+            R2[ch * 2 + 1] = make_float2(v.z, v.w);
+            m[0] = fmaxf(m[0], fabsf(v.x));
+            m[1] = fmaxf(m[1], fabsf(v.y));
+            m[2] = fmaxf(m[2], fabsf(v.z));
+            m[3] = fmaxf(m[3], fabsf(v.w));
+        }
+
+        for (int nu = 0; nu < I; ++nu) {
+            int u;
+            float ru;
+            select_f32<W, VPT>(R2, m, tid, lane, warp, sRed + (nu & 1) * W, u, ru);
+            if (u < 0 || u >= a.K) {
+                if (tid == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+                u = 0;
+                ru = 0.0f;
+            }
+            const float *trow = Ttab + static_cast<size_t>(u) * Kp;
+            const bool more = nu + 1 < I;
+            if (SE_ITER_ASYNC == 1 && more) {
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch)
+                    cp_async16(myT + ch * NT * 4 + tid * 4, trow + ch * NT * 4 + tid * 4);
+            }
+            if (SE_ITER_ASYNC == 2 && more && tid == 0)
+                bulk_row(myT, trow, static_cast<uint32_t>(Kp * sizeof(float)), myBar);
+            const float c = gamma * ru * __ldg(Dk + u);
+            if (tid == 0) { logU[nu] = u; logC[nu] = c; }
+            if (!more) break;
+
+            m[0] = m[1] = m[2] = m[3] = 0.0f;
+            if (SE_ITER_ASYNC == 1) cp_async_wait_all();
+            if (SE_ITER_ASYNC == 2) {
+                if (!bar_wait(myBar, phase)) {
+                    if (tid == 0) atomicOr(a.err, 1 << DEV_ERR_WAIT_TIMEOUT);
+                    failed = true;
+                    bar_wait(myBar, phase);   // let the copy in flight land before leaving
+                }
+                phase ^= 1u;
+                if (failed) break;
+            }
+            const float2 nc = make_float2(-c, -c);
+            static_assert(NCH % 2 == 0, "chunks are processed in pairs");
+#pragma unroll
+            for (int ch = 0; ch < NCH; ch += 2) {
+                const int off0 = ch * NT * 4 + tid * 4, off1 = off0 + NT * 4;
+                const float4 v0 = SE_ITER_ASYNC ? *reinterpret_cast<const float4 *>(myT + off0)
+                                                : __ldg(reinterpret_cast<const float4 *>(trow + off0));
+                const float4 v1 = SE_ITER_ASYNC ? *reinterpret_cast<const float4 *>(myT + off1)
+                                                : __ldg(reinterpret_cast<const float4 *>(trow + off1));
+                float2 &a0 = R2[ch * 2 + 0], &a1 = R2[ch * 2 + 1];
+                float2 &b0 = R2[ch * 2 + 2], &b1 = R2[ch * 2 + 3];
+                a0 = __ffma2_rn(nc, make_float2(v0.x, v0.y), a0);
+                a1 = __ffma2_rn(nc, make_float2(v0.z, v0.w), a1);
+                b0 = __ffma2_rn(nc, make_float2(v1.x, v1.y), b0);
+                b1 = __ffma2_rn(nc, make_float2(v1.z, v1.w), b1);
+                m[0] = max3_abs(m[0], a0.x, b0.x);
+                m[1] = max3_abs(m[1], a0.y, b0.y);
+                m[2] = max3_abs(m[2], a1.x, b1.x);
+                m[3] = max3_abs(m[3], a1.y, b1.y);
+            }
+        }
+        if constexpr (W > 1) __syncthreads(); else __syncwarp();
+        if (failed) break;
+
+        const double *smp = bd.samples;
+        double *out = bd.out;
+        const float *PhiB = static_cast<const float *>(a.PhiB);
+        for (int j = tid; j < a.nB; j += NT) {
+            // four independent partial sums keep four row gathers in flight
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int nu = 0;
+            for (; nu + 4 <= I; nu += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc[q] = fmaf(logC[nu + q], __ldg(PhiB + static_cast<size_t>(logU[nu + q]) * a.nB + j), acc[q]);
+            }
+            for (; nu < I; ++nu)
+                acc[0] = fmaf(logC[nu], __ldg(PhiB + static_cast<size_t>(logU[nu]) * a.nB + j), acc[0]);
+            out[a.b_idx[j]] = static_cast<double>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        }
+        for (int p = tid; p < a.MN; p += NT)
+            if (a.pat_support[p]) out[p] = smp[p];
+        if (bd.sel_idx)
+            for (int nu = tid; nu < I; nu += NT) bd.sel_idx[nu] = logU[nu];
+        if (bd.sel_coef)
+            for (int nu = tid; nu < I; nu += NT) bd.sel_coef[nu] = static_cast<double>(logC[nu]);
+        if constexpr (W > 1) __syncthreads(); else __syncwarp();
+    }
+}
+
+template <int W, int VPT, int BPC>
+cudaError_t launch_f32(const IterArgs &a, cudaStream_t st, int *launches)
+{
+    constexpr int threads = 32 * W * BPC;
+    if (a.Kp != 32 * W * VPT) return cudaErrorInvalidValue;
+    const size_t smem = 16 * BPC + (SE_ITER_ASYNC ? sizeof(float) * BPC * a.Kp : 0) +
+                        sizeof(Cand<float>) * 2 * W + (sizeof(float) + sizeof(int)) * BPC * a.I_max + 16;
+    auto kern = iterate_f32_kernel<W, VPT, BPC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int need = (a.n + BPC - 1) / BPC;
+    const int grid = need < sms * per_sm ? need : sms * per_sm;
+    kern<<<grid, threads, smem, st>>>(a);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
 template <typename T, int W, int VPT, int BPC>
 cudaError_t launch_cfg(const IterArgs &a, cudaStream_t st, int *launches)
 {
@@ -232,12 +521,12 @@ template <>
 cudaError_t launch_iterate_full<float>(const IterArgs &a, cudaStream_t st, int *launches)
 {
     switch (a.Kp) {
-    case 512: return launch_cfg<float, 1, 16, 4>(a, st, launches);
-    case 1024: return launch_cfg<float, 1, 32, 4>(a, st, launches);
-    case 2048: return launch_cfg<float, 1, 64, 4>(a, st, launches);
-    case 4096: return launch_cfg<float, 2, 64, 1>(a, st, launches);
-    case 8192: return launch_cfg<float, 4, 64, 1>(a, st, launches);
-    case 16384: return launch_cfg<float, 8, 64, 1>(a, st, launches);
+    case 512: return launch_f32<1, 16, 4>(a, st, launches);
+    case 1024: return launch_f32<1, 32, 4>(a, st, launches);
+    case 2048: return launch_f32<1, 64, 4>(a, st, launches);
+    case 4096: return launch_f32<2, 64, 1>(a, st, launches);
+    case 8192: return launch_f32<4, 64, 1>(a, st, launches);
+    case 16384: return launch_f32<8, 64, 1>(a, st, launches);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -10,23 +10,95 @@
 namespace se {
 namespace {
 
-__device__ __forceinline__ uint16_t bf16_bits(double v)
+// Exact split of a double into bf16 parts without fp64 arithmetic (GB300's
+// fp64 pipe is narrow).  From the IEEE-754 binary64 fields, hi is x truncated
+// to 24 significant bits (a float, exact) and lo the remaining 29 mantissa
+// bits scaled by 2^(e - 1075) (one int->float rounding, < 2^-47 |x|).  Then
+// h = bf16(hi), m = bf16(hi - h), l = bf16((hi - h - m) + lo): the first two
+// differences are exact in fp32, so x - (h + m + l) is below ~2^-26 |x|.
+// Zeros, subnormals, infinities, NaN and values outside the fp32 range go
+// through the ordinary conversion (lo = 0).
+__device__ __forceinline__ void f64_split_pair(double x, float &hi, float &lo)
 {
-    __nv_bfloat16 h = __float2bfloat16_rn(static_cast<float>(v));
-    return *reinterpret_cast<uint16_t *>(&h);
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+    const int e = static_cast<int>((b >> 52) & 0x7FF);
+    const int ef = e - 1023 + 127;
+    if (e == 0 || e == 0x7FF || ef <= 0 || ef >= 255) {
+        hi = __double2float_rn(x);
+        lo = 0.0f;
+        return;
+    }
+    const unsigned long long mant = b & ((1ull << 52) - 1);
+    hi = __uint_as_float(sign | (static_cast<uint32_t>(ef) << 23) | static_cast<uint32_t>(mant >> 29));
+    const uint32_t rest = static_cast<uint32_t>(mant & ((1u << 29) - 1));
+    const int es = e - 1075 + 127;                         // exponent of 2^(e - 1075)
+    const float scale = es >= 1 ? __uint_as_float(static_cast<uint32_t>(es) << 23) : 0.0f;
+    lo = __uint_as_float(sign | __float_as_uint(static_cast<float>(rest) * scale));
 }
 
-__device__ __forceinline__ double bf16_value(uint16_t bits)
+__device__ __forceinline__ uint16_t bf16_of(float v)
 {
-    __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&bits);
-    return static_cast<double>(__bfloat162float(h));
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t *>(&h);
 }
 
-// Weighted samples of the shared pattern, x_b[j] = sqrt(w[j]) s_b[a_idx[j]]
-// on the support pixels (so that sum_j G[k][j] x_b[j] = sum s phi_k w, eq. 12),
-// zero in the padding.  Split parts: v = h + m + l with each part the bf16
-// rounding of what the previous parts left; part p of block b lives at
-// x_bf16[b][p * ka_pad + j].
+__device__ __forceinline__ float bf16_to_f(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
+
+// Parts of x: part 0 = h, 1 = m, 2 = l (nparts <= 3; fewer parts simply
+// drop the smaller ones).
+__device__ __forceinline__ void split_parts(double x, uint16_t (&p)[3])
+{
+    float hi, lo;
+    f64_split_pair(x, hi, lo);
+    p[0] = bf16_of(hi);
+    const float r = hi - bf16_to_f(p[0]);
+    p[1] = bf16_of(r);
+    p[2] = bf16_of((r - bf16_to_f(p[1])) + lo);
+}
+
+__device__ __forceinline__ void split_store2(double v0, double v1, int nparts, uint16_t *dst,
+                                             int ka_pad)
+{
+    uint16_t a[3], b[3];
+    split_parts(v0, a);
+    split_parts(v1, b);
+    for (int p = 0; p < nparts; ++p)
+        *reinterpret_cast<uint32_t *>(dst + static_cast<size_t>(p) * ka_pad) =
+            static_cast<uint32_t>(a[p]) | (static_cast<uint32_t>(b[p]) << 16);
+}
+
+// One warp per block: the block's samples are staged in shared memory with
+// coalesced loads, then gathered at the support pixels two at a time, so the
+// bf16 parts are written as 4-byte pairs (128 bytes per warp store).  The
+// split path packs the raw samples s (the weights sit in the dictionary
+// operand Phi_A w); the fp64 path (x_f64) packs sqrt(w) s in double.
+__global__ void __launch_bounds__(256)
+pack_x_staged_kernel(const BlockDesc *__restrict__ blocks, int n, const int *__restrict__ a_idx,
+                     const double *__restrict__ sqrtw, int nA, int ka_pad, int nparts, int MN,
+                     uint16_t *__restrict__ xb, double *__restrict__ xd)
+{
+    extern __shared__ double stage[];
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * warps + warp;
+    if (b >= n) return;
+    double *sm = stage + static_cast<size_t>(warp) * MN;
+    const double *s = blocks[b].samples;
+    for (int i = lane; i < MN; i += 32) sm[i] = s[i];
+    __syncwarp();
+    const size_t rowb = static_cast<size_t>(b) * nparts * ka_pad;
+    for (int j = 2 * lane; j < ka_pad; j += 64) {
+        const double s0 = j < nA ? sm[a_idx[j]] : 0.0;
+        const double s1 = j + 1 < nA ? sm[a_idx[j + 1]] : 0.0;
+        if (xd)
+            *reinterpret_cast<double2 *>(xd + static_cast<size_t>(b) * ka_pad + j) =
+                make_double2(j < nA ? sqrtw[j] * s0 : 0.0, j + 1 < nA ? sqrtw[j + 1] * s1 : 0.0);
+        if (xb) split_store2(s0, s1, nparts, xb + rowb + j, ka_pad);
+    }
+}
+
+// Direct-gather form for areas too large to stage.
 __global__ void pack_x_kernel(const BlockDesc *__restrict__ blocks, const int *__restrict__ a_idx,
                               const double *__restrict__ sqrtw, int nA, int ka_pad, int nparts,
                               uint16_t *__restrict__ xb, double *__restrict__ xd)
@@ -34,40 +106,36 @@ __global__ void pack_x_kernel(const BlockDesc *__restrict__ blocks, const int *_
     const int b = blockIdx.x;
     const double *s = blocks[b].samples;
     const size_t rowb = static_cast<size_t>(b) * nparts * ka_pad;
-    for (int j = threadIdx.x; j < ka_pad; j += blockDim.x) {
-        const double v = j < nA ? sqrtw[j] * s[a_idx[j]] : 0.0;
-        if (xd) xd[static_cast<size_t>(b) * ka_pad + j] = v;
-        if (xb) {
-            double rest = v;
-            for (int p = 0; p < nparts; ++p) {
-                const uint16_t h = bf16_bits(rest);
-                xb[rowb + static_cast<size_t>(p) * ka_pad + j] = h;
-                rest -= bf16_value(h);
-            }
-        }
+    for (int j = 2 * threadIdx.x; j < ka_pad; j += 2 * blockDim.x) {
+        const double s0 = j < nA ? s[a_idx[j]] : 0.0;
+        const double s1 = j + 1 < nA ? s[a_idx[j + 1]] : 0.0;
+        if (xd)
+            *reinterpret_cast<double2 *>(xd + static_cast<size_t>(b) * ka_pad + j) =
+                make_double2(j < nA ? sqrtw[j] * s0 : 0.0, j + 1 < nA ? sqrtw[j + 1] * s1 : 0.0);
+        if (xb) split_store2(s0, s1, nparts, xb + rowb + j, ka_pad);
     }
 }
 
-// Split fp64 rows into bf16 parts (same rule as pack_x_kernel).
+// Split fp64 rows into bf16 parts (same rule as the sample packing).
 __global__ void split_bf16_kernel(const double *__restrict__ in, int cols, int ld_in, int ka_pad,
                                   int nparts, uint16_t *__restrict__ out)
 {
     const int r = blockIdx.x;
     const size_t rowo = static_cast<size_t>(r) * nparts * ka_pad;
     for (int j = threadIdx.x; j < ka_pad; j += blockDim.x) {
-        double rest = j < cols ? in[static_cast<size_t>(r) * ld_in + j] : 0.0;
-        for (int p = 0; p < nparts; ++p) {
-            const uint16_t h = bf16_bits(rest);
-            out[rowo + static_cast<size_t>(p) * ka_pad + j] = h;
-            rest -= bf16_value(h);
-        }
+        uint16_t q[3];
+        split_parts(j < cols ? in[static_cast<size_t>(r) * ld_in + j] : 0.0, q);
+        for (int p = 0; p < nparts; ++p) out[rowo + static_cast<size_t>(p) * ka_pad + j] = q[p];
     }
 }
 
 // diag[k] = sum_j G[k][j]^2 = sum phi_k^2 w = C_kk (eq. 16 on the diagonal),
-// one warp per atom, fp64.
-__global__ void diag_kernel(const double *__restrict__ G, int ldg, int Kp, int nA,
-                            double *__restrict__ diag)
+// one warp per atom, fp64.  The largest diagonal entry of the non-duplicate
+// atoms is accumulated in *dmax as an unsigned 64-bit maximum (non-negative
+// doubles order like their bit patterns); *dmax must start at 0.
+__global__ void diag_kernel(const double *__restrict__ G, int ldg, int K, int Kp, int nA,
+                            const uint8_t *__restrict__ dup, double *__restrict__ diag,
+                            unsigned long long *__restrict__ dmax)
 {
     const int k = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
@@ -79,7 +147,10 @@ __global__ void diag_kernel(const double *__restrict__ G, int ldg, int Kp, int n
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) diag[k] = acc;
+    if (lane == 0) {
+        diag[k] = acc;
+        if (k < K && !dup[k]) atomicMax(dmax, static_cast<unsigned long long>(__double_as_longlong(acc)));
+    }
 }
 
 // Admissibility and the per-atom constants of eqs. (17)-(19): atom k may be
@@ -88,44 +159,20 @@ __global__ void diag_kernel(const double *__restrict__ G, int ldg, int Kp, int n
 // (NaN if inadmissible, so |R_k| D_k never wins a comparison).
 template <typename T>
 __global__ void finalize_kernel(const double *__restrict__ diag, const uint8_t *__restrict__ dup,
-                                int K, int Kp, T *__restrict__ invC, T *__restrict__ Dk,
-                                int *__restrict__ n_adm)
+                                const unsigned long long *__restrict__ dmax, int K, int Kp,
+                                T *__restrict__ invC, T *__restrict__ Dk, int *__restrict__ n_adm)
 {
-    __shared__ double smax[32];
-    __shared__ int scnt[32];
-    double mx = 0.0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-        if (!dup[k]) mx = fmax(mx, diag[k]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) smax[threadIdx.x / 32] = mx;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < blockDim.x / 32 ? smax[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (threadIdx.x == 0) smax[0] = v;
-    }
-    __syncthreads();
-    mx = smax[0];
-    int cnt = 0;
-    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+    const double mx = __longlong_as_double(static_cast<long long>(*dmax));
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    bool adm = false;
+    if (k < Kp) {
         const double d = k < K ? diag[k] : 0.0;
-        const bool adm = k < K && !dup[k] && mx > 0.0 && d > 1e-14 * mx;
+        adm = k < K && !dup[k] && mx > 0.0 && d > 1e-14 * mx;
         invC[k] = adm ? static_cast<T>(1.0 / d) : static_cast<T>(0);
         Dk[k] = adm ? static_cast<T>(1.0 / sqrt(d)) : static_cast<T>(NAN);
-        cnt += adm;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) scnt[threadIdx.x / 32] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) t += scnt[w];
-        *n_adm = t;
-    }
+    const unsigned cnt = __popc(__ballot_sync(0xffffffffu, adm));
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(n_adm, static_cast<int>(cnt));
 }
 
 // Plain tiled GEMM on CUDA cores: D[m][n] = sum_k A[m][k] B[n][k], 64 x 64
@@ -201,11 +248,26 @@ simt_gemm_kernel(const T *__restrict__ A, int lda, const T *__restrict__ B, int 
 }  // namespace
 
 cudaError_t launch_pack_x(const BlockDesc *blocks, int n, const int *a_idx, const double *sqrtw,
-                          int nA, int ka_pad, int nparts, uint16_t *x_bf16, double *x_f64,
+                          int nA, int ka_pad, int nparts, int MN, uint16_t *x_bf16, double *x_f64,
                           cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    pack_x_kernel<<<n, 256, 0, st>>>(blocks, a_idx, sqrtw, nA, ka_pad, nparts, x_bf16, x_f64);
+    const size_t per_warp = sizeof(double) * static_cast<size_t>(MN);
+    if (per_warp <= 48 * 1024) {
+        int warps = static_cast<int>(96 * 1024 / per_warp);
+        warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
+        const size_t smem = per_warp * warps;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(pack_x_staged_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem));
+            if (e != cudaSuccess) return e;
+        }
+        pack_x_staged_kernel<<<(n + warps - 1) / warps, 32 * warps, smem, st>>>(
+            blocks, n, a_idx, sqrtw, nA, ka_pad, nparts, MN, x_bf16, x_f64);
+    } else {
+        pack_x_kernel<<<n, 256, 0, st>>>(blocks, a_idx, sqrtw, nA, ka_pad, nparts, x_bf16, x_f64);
+    }
     return cudaGetLastError();
 }
 
@@ -217,18 +279,22 @@ cudaError_t launch_split_bf16(const double *in, int rows, int cols, int ld_in, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_tables_diag(const double *G64, int ldg, int Kp, int nA, double *diag,
-                               cudaStream_t st)
+cudaError_t launch_tables_diag(const double *G64, int ldg, int K, int Kp, int nA, const uint8_t *dup,
+                               double *diag, unsigned long long *dmax, int *n_adm, cudaStream_t st)
 {
-    diag_kernel<<<(Kp + 7) / 8, 256, 0, st>>>(G64, ldg, Kp, nA, diag);
+    cudaError_t e = cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_adm, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    diag_kernel<<<(Kp + 7) / 8, 256, 0, st>>>(G64, ldg, K, Kp, nA, dup, diag, dmax);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup, int K, int Kp, T *invC,
-                                   T *Dk, int *n_admissible, cudaStream_t st)
+cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup,
+                                   const unsigned long long *dmax, int K, int Kp, T *invC, T *Dk,
+                                   int *n_admissible, cudaStream_t st)
 {
-    finalize_kernel<T><<<1, 1024, 0, st>>>(diag, dup, K, Kp, invC, Dk, n_admissible);
+    finalize_kernel<T><<<(Kp + 255) / 256, 256, 0, st>>>(diag, dup, dmax, K, Kp, invC, Dk, n_admissible);
     return cudaGetLastError();
 }
 
@@ -243,10 +309,12 @@ cudaError_t launch_simt_gemm(const T *A, int lda, const T *B, int ldb, int M, in
     return cudaGetLastError();
 }
 
-template cudaError_t launch_tables_finalize<float>(const double *, const uint8_t *, int, int, float *,
+template cudaError_t launch_tables_finalize<float>(const double *, const uint8_t *,
+                                                   const unsigned long long *, int, int, float *,
                                                    float *, int *, cudaStream_t);
-template cudaError_t launch_tables_finalize<double>(const double *, const uint8_t *, int, int,
-                                                    double *, double *, int *, cudaStream_t);
+template cudaError_t launch_tables_finalize<double>(const double *, const uint8_t *,
+                                                    const unsigned long long *, int, int, double *,
+                                                    double *, int *, cudaStream_t);
 template cudaError_t launch_simt_gemm<double>(const double *, int, const double *, int, int, int, int,
                                               double *, long long, int, cudaStream_t);
 template cudaError_t launch_simt_gemm<float>(const float *, int, const float *, int, int, int, int,

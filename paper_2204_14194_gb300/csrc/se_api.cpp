@@ -183,19 +183,21 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 {
     const int Kp = pl->Kp;
     std::string why;
-    SE_CUDA(launch_tables_diag(pl->d_G64.as<double>(), pl->ka_pad, Kp, pl->nA,
-                               pl->d_diag.as<double>(), st));
+    unsigned long long *dmax = reinterpret_cast<unsigned long long *>(pl->d_nadm.as<char>() + 8);
+    SE_CUDA(launch_tables_diag(pl->d_G64.as<double>(), pl->ka_pad, pl->K, Kp, pl->nA,
+                               pl->d_dup.as<uint8_t>(), pl->d_diag.as<double>(), dmax,
+                               pl->d_nadm.as<int>(), st));
     if (pl->pc.fp64) {
-        SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), pl->K,
-                                               Kp, pl->d_invC.as<double>(), pl->d_Dk.as<double>(),
-                                               pl->d_nadm.as<int>(), st));
+        SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
+                                               pl->K, Kp, pl->d_invC.as<double>(),
+                                               pl->d_Dk.as<double>(), pl->d_nadm.as<int>(), st));
         SE_CUDA(launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad, pl->d_G64.as<double>(),
                                          pl->ka_pad, Kp, Kp, pl->ka_pad, pl->d_C.as<double>(), Kp, 1,
                                          st));
         ctx->launches += 3;
     } else {
-        SE_CUDA(launch_tables_finalize<float>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), pl->K,
-                                              Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
+        SE_CUDA(launch_tables_finalize<float>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
+                                              pl->K, Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
                                               pl->d_nadm.as<int>(), st));
         TcGemmArgs g{};
         g.A = pl->d_Gbf.ptr;
@@ -210,6 +212,7 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         g.ldo = Kp;
         g.symmetric = 1;
         g.err = ctx->ws_err.as<int>();
+        g.scale = pl->d_Dk.as<float>();
         cudaError_t e = launch_tc_gemm(g, st, &why);
         if (e != cudaSuccess) return fail(SE_ERR_CUDA, "table GEMM: " + why + " " + cudaGetErrorString(e));
         ctx->launches += 3;
@@ -273,10 +276,10 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     int tok = stage_begin(ctx, 0, st);
     if (fp64)
         SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                              pl->ka_pad, 0, nullptr, ws.x.as<double>(), st));
+                              pl->ka_pad, 0, pl->MN, nullptr, ws.x.as<double>(), st));
     else
         SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                              pl->ka_pad, pl->pc.nparts, ws.x.as<uint16_t>(), nullptr, st));
+                              pl->ka_pad, pl->pc.nparts, pl->MN, ws.x.as<uint16_t>(), nullptr, st));
     stage_end(ctx, tok, st);
     tok = stage_begin(ctx, 2, st);
     if (fp64) {
@@ -285,7 +288,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
                                          0, st));
     } else {
         TcGemmArgs g{};
-        g.A = pl->d_Gbf.ptr;
+        g.A = pl->d_Gwbf.ptr;
         g.B = ws.x.ptr;
         g.M = Kp;
         g.N = n;
@@ -297,6 +300,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         g.ldo = Kp;
         g.symmetric = 0;
         g.err = ctx->ws_err.as<int>();
+        g.scale = pl->d_Dk.as<float>();
         cudaError_t e = launch_tc_gemm(g, st, &why);
         if (e != cudaSuccess) return fail(SE_ERR_CUDA, "projection GEMM: " + why + " " + cudaGetErrorString(e));
     }
@@ -503,6 +507,7 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     for (int k = 0; k < K; ++k) dupp[k] = pl->dup[k];
     SE_TRY(upload(ctx, pl->d_G64, G));
     SE_TRY(upload(ctx, pl->d_sqrtw, sqw));
+
     SE_TRY(upload(ctx, pl->d_a_idx, pl->a_idx));
     SE_TRY(upload(ctx, pl->d_b_idx, pl->b_idx));
     SE_TRY(upload(ctx, pl->d_pattern, pl->pattern));
@@ -524,14 +529,27 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         SE_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka * 2));
         SE_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka, ka, ka, pl->pc.nparts,
                                   pl->d_Gbf.as<uint16_t>(), ctx->stream));
-        ctx->launches++;
+        // Phi_A w for the projections of eq. (12): the samples enter unweighted
+        std::vector<double> Gw(static_cast<size_t>(Kp) * ka, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+            for (int j = 0; j < pl->nA; ++j)
+                Gw[static_cast<size_t>(k) * ka + j] = a[pl->a_idx[j]] * pl->w[pl->a_idx[j]];
+        }
+        DevBuf tmp;
+        SE_TRY(upload(ctx, tmp, Gw));
+        SE_TRY(dev_alloc(ctx, pl->d_Gwbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka * 2));
+        SE_CUDA(launch_split_bf16(tmp.as<double>(), Kp, ka, ka, ka, pl->pc.nparts,
+                                  pl->d_Gwbf.as<uint16_t>(), ctx->stream));
+        SE_CUDA(cudaStreamSynchronize(ctx->stream));
+        ctx->launches += 2;
     }
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
     SE_TRY(dev_alloc(ctx, pl->d_C, tsz * Kp * static_cast<size_t>(Kp)));
     SE_TRY(dev_alloc(ctx, pl->d_invC, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_Dk, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_diag, sizeof(double) * Kp));
-    SE_TRY(dev_alloc(ctx, pl->d_nadm, sizeof(int)));
+    SE_TRY(dev_alloc(ctx, pl->d_nadm, 16));   // admissible count (int) + largest C_kk (8 bytes at +8)
     SE_CUDA(cudaEventCreateWithFlags(&pl->tables_ready, cudaEventDisableTiming));
     SE_CUDA(cudaStreamSynchronize(ctx->stream));
     se_plan_s *raw = pl.release();

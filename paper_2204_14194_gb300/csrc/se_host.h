@@ -156,7 +156,8 @@ struct se_plan_s {
     // device copies
     se::DevBuf d_a_idx, d_b_idx, d_sqrtw, d_pattern, d_dup;
     se::DevBuf d_G64;                     // Kp x ka_pad fp64, G = phi_A sqrt(w)
-    se::DevBuf d_Gbf;                     // Kp x nparts*ka_pad bf16 split of G
+    se::DevBuf d_Gbf;                     // Kp x nparts*ka_pad bf16 split of G (tables)
+    se::DevBuf d_Gwbf;                    // Kp x nparts*ka_pad bf16 split of Phi_A w (projections)
     se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels
     // tables (eqs. 16-17)
     se::DevBuf d_C, d_invC, d_Dk, d_diag, d_nadm;

@@ -45,6 +45,8 @@ struct TcGemmArgs {
     float *out;          // output
     long long ldo;       // output row pitch (elements)
     int symmetric;       // 1: Gram mode (M == N, upper tiles, mirrored store)
+    const float *scale;  // optional per-atom factors: out[n][m] = D[m][n] * scale[m]; in Gram
+                         // mode also out[m][n] = D[m][n] * scale[n] (NULL: no scaling)
     int *err;            // device status word
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why);
@@ -56,27 +58,31 @@ cudaError_t launch_simt_gemm(const T *A, int lda, const T *B, int ldb, int M, in
                              T *out, long long ldo, int symmetric, cudaStream_t st);
 
 // ------------------------------------------------------------- prep / tables
-// Pack the weighted samples of the shared pattern: for block b and support
-// pixel j, v = sqrtw[j] * samples_b[a_idx[j]] (0 for j >= nA), written as
-// nparts bf16 split parts ([part][ka_pad] per row) and/or as fp64.
+// Pack the samples of the shared pattern's support pixels: for block b and
+// support pixel j, the raw sample s_b[a_idx[j]] as nparts exact bf16 split
+// parts ([part][ka_pad] per row; the weights are in the dictionary operand)
+// and/or sqrtw[j] * s_b[a_idx[j]] in fp64; zero for j >= nA.
 cudaError_t launch_pack_x(const BlockDesc *blocks, int n, const int *a_idx, const double *sqrtw,
-                          int nA, int ka_pad, int nparts, uint16_t *x_bf16, double *x_f64,
+                          int nA, int ka_pad, int nparts, int MN, uint16_t *x_bf16, double *x_f64,
                           cudaStream_t st);
 
-// diag[k] = sum_j G64[k][j]^2 (fp64), then invC / D / admissibility.
-cudaError_t launch_tables_diag(const double *G64, int ldg, int Kp, int nA, double *diag,
+// diag[k] = sum_j G64[k][j]^2 (fp64) and the largest admissible diagonal
+// entry (dmax, 8 bytes); then invC / D / admissibility (n_admissible).
+cudaError_t launch_tables_diag(const double *G64, int ldg, int K, int Kp, int nA, const uint8_t *dup,
+                               double *diag, unsigned long long *dmax, int *n_admissible,
                                cudaStream_t st);
 template <typename T>
-cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup, int K, int Kp, T *invC,
-                                   T *Dk, int *n_admissible, cudaStream_t st);
+cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup,
+                                   const unsigned long long *dmax, int K, int Kp, T *invC, T *Dk,
+                                   int *n_admissible, cudaStream_t st);
 
 // ------------------------------------------------------------------ iterate
 struct IterArgs {
     const BlockDesc *blocks;
     int n;
     int K, Kp;              // dictionary size and padded size (row pitch of C, R0)
-    const void *R0;         // [n][Kp] initial projections (eq. 12)
-    const void *C;          // [Kp][Kp] table (eq. 16)
+    const void *R0;         // [n][Kp] initial projections (eq. 12); fp32 form: scaled by D_k
+    const void *C;          // [Kp][Kp] table (eq. 16); fp32 form: rows scaled, T[u][k] = C(k,u) D_k
     const void *invC;       // [Kp] 1 / C_kk (0 for inadmissible)
     const void *Dk;         // [Kp] 1 / sqrt(C_kk) (NaN for inadmissible)
     const void *PhiB;       // [Kp][nB] atoms on the pattern's loss pixels

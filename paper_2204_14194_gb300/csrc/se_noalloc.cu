@@ -125,17 +125,17 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     std::string why;
     if (fp64) {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                          pl->ka_pad, 0, nullptr, static_cast<double *>(d_x), st);
+                          pl->ka_pad, 0, pl->MN, nullptr, static_cast<double *>(d_x), st);
         if (e == cudaSuccess)
             e = launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad,
                                          static_cast<const double *>(d_x), pl->ka_pad, Kp, n,
                                          pl->ka_pad, static_cast<double *>(d_r0), Kp, 0, st);
     } else {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                          pl->ka_pad, pl->pc.nparts, static_cast<uint16_t *>(d_x), nullptr, st);
+                          pl->ka_pad, pl->pc.nparts, pl->MN, static_cast<uint16_t *>(d_x), nullptr, st);
         if (e == cudaSuccess) {
             TcGemmArgs g{};
-            g.A = pl->d_Gbf.ptr;
+            g.A = pl->d_Gwbf.ptr;
             g.B = d_x;
             g.M = Kp;
             g.N = n;
@@ -147,6 +147,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
             g.ldo = Kp;
             g.symmetric = 0;
             g.err = ctx->ws_err.as<int>();
+            g.scale = pl->d_Dk.as<float>();
             e = launch_tc_gemm(g, st, &why);
         }
     }
