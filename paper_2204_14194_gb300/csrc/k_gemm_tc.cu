@@ -216,6 +216,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         tn = blockIdx.x / mt;
     }
     (void)nt;
+    int n_eff = p.N;
+    if (p.n_dev) {
+        const int nd = *p.n_dev;
+        n_eff = nd < p.N ? nd : p.N;
+        if (tn * BN >= n_eff) return;   // whole tile beyond the live rows: nothing to do
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -355,7 +361,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int n = n0 + j;
-                if (n < p.N) p.out[static_cast<long long>(n) * p.ldo + m] = __uint_as_float(r[j]) * sm;
+                if (n < n_eff) {
+                    const long long row = p.out_rows ? p.out_rows[n] : static_cast<long long>(n) * p.ldo;
+                    p.out[row + m] = __uint_as_float(r[j]) * sm;
+                }
             }
         } else {
             float *row = p.out + static_cast<long long>(m) * p.ldo;
@@ -450,20 +459,22 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
         if (why) *why = "tc gemm: bad pair count or inner size";
         return cudaErrorInvalidValue;
     }
-    int np = 0;
+    int npa = 0, npb = 0;
     for (int i = 0; i < a.npairs; ++i) {
-        np = a.pa[i] + 1 > np ? a.pa[i] + 1 : np;
-        np = a.pb[i] + 1 > np ? a.pb[i] + 1 : np;
+        npa = a.pa[i] + 1 > npa ? a.pa[i] + 1 : npa;
+        npb = a.pb[i] + 1 > npb ? a.pb[i] + 1 : npb;
     }
-    if (np * a.ka_pad > a.lda || np * a.ka_pad > a.ldb) {
+    if (npa * a.ka_pad > a.lda || npb * a.ka_pad > a.ldb) {
         if (why) *why = "tc gemm: split part outside the operand row";
         return cudaErrorInvalidValue;
     }
+    const int np = npa > npb ? npa : npb;
     if (a.symmetric && a.M != a.N) return cudaErrorInvalidValue;
     // The table (square, symmetric) uses 128 x 128 tiles with all parts of a
     // k-slice per stage; the projections use 128 x 256 tiles streamed one
     // partial product per stage (measured faster for the wide, short-K case).
     if (a.symmetric) {
+        if (npa != npb) return cudaErrorInvalidValue;
         switch (np) {
         case 1: return launch_bn<128, 1, true>(a, st, why);
         case 2: return launch_bn<128, 2, true>(a, st, why);

@@ -44,7 +44,6 @@ __device__ __forceinline__ void vget<double>(const double2 &v, double *o)
     o[0] = v.x; o[1] = v.y;
 }
 
-template <typename T> struct Cand { T s; int k; T r; };
 
 // (a) beats (b): larger score, then smaller index.
 template <typename T>

@@ -1,0 +1,300 @@
+// k_lazy.cu -- Fast Selective Extrapolation with per-block weighting patterns.
+//
+// When every block has its own support mask, the table C of eq. (16) is
+// different for every block and building it whole (Alg. 2) would cost
+// 2 K^2 |A| per block.  This path builds only what the iterations use:
+//   * R^(0)_b = Phi (rho m_b s_b)          (eq. 12, one GEMM over the batch)
+//   * C_b(k, k) = (Phi^2 rho) m_b          (eq. 16 diagonal, one GEMM)
+//   * C_b(:, u) = (Phi rho)(m_b phi_u)     (eq. 16 column, on the first
+//                                           selection of atom u by block b,
+//                                           batched over the blocks that
+//                                           need one in the same round)
+// Columns are cached per block, so an atom selected again costs nothing.
+// The iterations advance in lock-step rounds over the batch: a round kernel
+// applies the previous update (eq. 20), selects (eq. 18) and records the
+// coefficient (eq. 19), and queues a column request when the selected atom
+// has no cached column; a packing kernel and a GEMM whose tiles past the
+// device-side request count exit at once serve the requests before the next
+// round.  Projections are kept D-scaled (R'_k = R_k D_b,k) as in the full
+// path.  The model on the block's loss pixels is evaluated at the end.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+
+#include "se_internal.h"
+
+namespace se {
+namespace {
+
+template <typename T> __device__ __forceinline__ T nan_of();
+template <> __device__ __forceinline__ float nan_of<float>() { return __int_as_float(0x7fc00000); }
+template <> __device__ __forceinline__ double nan_of<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+__device__ __forceinline__ uint16_t bf16b(float v)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+__device__ __forceinline__ float bf16f(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
+
+// Exact-enough split of a double into three bf16 parts (same rule as the
+// shared-pattern packing; see k_simt.cu).
+__device__ __forceinline__ void split3(double x, uint16_t (&p)[3])
+{
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t sign = static_cast<uint32_t>(b >> 32) & 0x80000000u;
+    const int e = static_cast<int>((b >> 52) & 0x7FF);
+    const int ef = e - 1023 + 127;
+    float hi, lo;
+    if (e == 0 || e == 0x7FF || ef <= 0 || ef >= 255) {
+        hi = __double2float_rn(x);
+        lo = 0.0f;
+    } else {
+        const unsigned long long mant = b & ((1ull << 52) - 1);
+        hi = __uint_as_float(sign | (static_cast<uint32_t>(ef) << 23) | static_cast<uint32_t>(mant >> 29));
+        const uint32_t rest = static_cast<uint32_t>(mant & ((1u << 29) - 1));
+        const int es = e - 1075 + 127;
+        const float scale = es >= 1 ? __uint_as_float(static_cast<uint32_t>(es) << 23) : 0.0f;
+        lo = __uint_as_float(sign | __float_as_uint(static_cast<float>(rest) * scale));
+    }
+    p[0] = bf16b(hi);
+    const float r = hi - bf16f(p[0]);
+    p[1] = bf16b(r);
+    p[2] = bf16b((r - bf16f(p[1])) + lo);
+}
+
+// Masked samples x_b[p] = m_b[p] s_b[p] (as 3 bf16 parts or fp64) and the
+// mask itself as one exact bf16 part (1 or 0).  Rows are [part][MN_pad].
+__global__ void lazy_pack_kernel(const BlockDesc *__restrict__ blocks, int MN, int MN_pad,
+                                 uint16_t *__restrict__ xb, double *__restrict__ xd,
+                                 uint16_t *__restrict__ mb, double *__restrict__ md)
+{
+    const int b = blockIdx.x;
+    const double *s = blocks[b].samples;
+    const uint8_t *m = blocks[b].support;
+    for (int p = threadIdx.x; p < MN_pad; p += blockDim.x) {
+        const bool in = p < MN && m[p];
+        const double v = in ? s[p] : 0.0;
+        if (xb) {
+            uint16_t q[3];
+            split3(v, q);
+            for (int t = 0; t < 3; ++t) xb[(static_cast<size_t>(b) * 3 + t) * MN_pad + p] = q[t];
+        }
+        if (xd) xd[static_cast<size_t>(b) * MN_pad + p] = v;
+        if (mb) mb[static_cast<size_t>(b) * MN_pad + p] = in ? 0x3F80 : 0;   // bf16 1.0 / 0.0
+        if (md) md[static_cast<size_t>(b) * MN_pad + p] = in ? 1.0 : 0.0;
+    }
+}
+
+// Column requests: v_j[p] = m_b[p] phi_u[p] for request j (block b, atom u).
+__global__ void lazy_pack_cols_kernel(const BlockDesc *__restrict__ blocks, const int *__restrict__ miss_n,
+                                      const int *__restrict__ miss_blk, const int *__restrict__ cur_u,
+                                      const double *__restrict__ Phi64, int MN, int MN_pad,
+                                      uint16_t *__restrict__ vb, double *__restrict__ vd)
+{
+    const int j = blockIdx.x;
+    if (j >= *miss_n) return;
+    const int b = miss_blk[j];
+    const int u = cur_u[b];
+    const uint8_t *m = blocks[b].support;
+    const double *phi = Phi64 + static_cast<size_t>(u) * MN;
+    for (int p = threadIdx.x; p < MN_pad; p += blockDim.x) {
+        const double v = (p < MN && m[p]) ? phi[p] : 0.0;
+        if (vb) {
+            uint16_t q[3];
+            split3(v, q);
+            for (int t = 0; t < 3; ++t) vb[(static_cast<size_t>(j) * 3 + t) * MN_pad + p] = q[t];
+        }
+        if (vd) vd[static_cast<size_t>(j) * MN_pad + p] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_argmax(T &s, int &k, T &r, Cand<T> *red)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const T so = __shfl_xor_sync(0xffffffffu, s, o);
+        const int ko = __shfl_xor_sync(0xffffffffu, k, o);
+        const T ro = __shfl_xor_sync(0xffffffffu, r, o);
+        if (so > s || (so == s && ko < k)) { s = so; k = ko; r = ro; }
+    }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = Cand<T>{s, k, r};
+    __syncthreads();
+    s = red[0].s; k = red[0].k; r = red[0].r;
+    for (int w = 1; w < nw; ++w) {
+        const Cand<T> c = red[w];
+        if (c.s > s || (c.s == s && c.k < k)) { s = c.s; k = c.k; r = c.r; }
+    }
+    __syncthreads();
+}
+
+// Per block: admissibility (not a duplicate, C_kk > 1e-14 max C_jj), D = 1 /
+// sqrt(C_kk) (NaN if inadmissible) and R' = R0 D, in place.
+template <typename T>
+__global__ void lazy_init_kernel(LazyArgs a)
+{
+    __shared__ T red[32];
+    const int b = blockIdx.x;
+    const T *diag = static_cast<const T *>(a.diag) + static_cast<size_t>(b) * a.Kp;
+    T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
+    T *D = static_cast<T *>(a.Dk) + static_cast<size_t>(b) * a.Kp;
+    T mx = T(0);
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x)
+        if (!a.dup[k]) mx = fmax(mx, diag[k]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    int cnt = 0;
+    for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
+        const T d = diag[k];
+        const bool adm = k < a.K && !a.dup[k] && mx > T(0) && d > T(1e-14) * mx;
+        const T Dv = adm ? T(1) / sqrt(d) : nan_of<T>();
+        D[k] = Dv;
+        R[k] = R[k] * Dv;
+        a.slot_of[static_cast<size_t>(b) * a.Kp + k] = -1;
+        cnt += adm;
+    }
+    cnt = __syncthreads_count(cnt > 0);
+    if (threadIdx.x == 0) {
+        a.n_slots[b] = cnt > 0 ? 0 : -1;       // -1: no admissible atom, block is skipped
+        if (cnt == 0) atomicOr(a.err, 1 << DEV_ERR_EMPTY_SUPPORT);
+    }
+}
+
+// One round nu for every block: R' -= c_prev D col(u_prev); select u; record
+// c; request the column of u if it is not cached and another round follows.
+template <typename T>
+__global__ void lazy_round_kernel(LazyArgs a, int nu)
+{
+    __shared__ Cand<T> red[32];
+    const int b = blockIdx.x;
+    const int Ib = a.blocks[b].iterations;
+    if (nu >= Ib || a.n_slots[b] < 0) return;
+    T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
+    const T *D = static_cast<const T *>(a.Dk) + static_cast<size_t>(b) * a.Kp;
+    int *slot_of = a.slot_of + static_cast<size_t>(b) * a.Kp;
+    const T *col = nullptr;
+    T cprev = T(0);
+    if (nu > 0) {
+        const int up = a.cur_u[b];
+        cprev = static_cast<const T *>(a.cur_c)[b];
+        col = static_cast<const T *>(a.cache) +
+              (static_cast<size_t>(b) * a.slots + slot_of[up]) * a.Kp;
+    }
+    T s = T(-1), rb = T(0);
+    int kb = INT_MAX;
+    for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
+        T r = R[k];
+        if (col) {
+            r = fma(-cprev, col[k] * D[k], r);
+            R[k] = r;
+        }
+        const T sc = fabs(r);
+        if (sc > s) { s = sc; kb = k; rb = r; }
+    }
+    block_argmax<T>(s, kb, rb, red);
+    int u = kb;
+    if (u < 0 || u >= a.K) {
+        if (threadIdx.x == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+        u = 0;
+        rb = T(0);
+    }
+    if (threadIdx.x == 0) {
+        const T c = static_cast<T>(a.gamma) * rb * D[u];
+        a.cur_u[b] = u;
+        static_cast<T *>(a.cur_c)[b] = c;
+        a.u_log[static_cast<size_t>(b) * a.I_max + nu] = u;
+        static_cast<T *>(a.c_log)[static_cast<size_t>(b) * a.I_max + nu] = c;
+        if (nu + 1 < Ib && slot_of[u] < 0) {
+            const int sl = a.n_slots[b]++;
+            if (sl >= a.slots) {
+                atomicOr(a.err, 1 << DEV_ERR_LAZY_CACHE);
+                a.n_slots[b] = -1;
+            } else {
+                slot_of[u] = sl;
+                const int j = atomicAdd(a.miss_n, 1);
+                a.miss_blk[j] = b;
+                a.miss_rows[j] = (static_cast<long long>(b) * a.slots + sl) * a.Kp;
+            }
+        }
+    }
+}
+
+// Model on the block's loss pixels (eq. 9) and replacement; logs out.
+template <typename T>
+__global__ void lazy_model_kernel(LazyArgs a)
+{
+    const int b = blockIdx.x;
+    const BlockDesc bd = a.blocks[b];
+    const int I = a.n_slots[b] < 0 ? 0 : bd.iterations;
+    const int *ul = a.u_log + static_cast<size_t>(b) * a.I_max;
+    const T *cl = static_cast<const T *>(a.c_log) + static_cast<size_t>(b) * a.I_max;
+    const T *Phi = static_cast<const T *>(a.Phi);
+    for (int p = threadIdx.x; p < a.MN; p += blockDim.x) {
+        if (bd.support[p]) {
+            bd.out[p] = bd.samples[p];
+        } else {
+            T acc = T(0);
+            for (int nu = 0; nu < I; ++nu) acc = fma(cl[nu], Phi[static_cast<size_t>(ul[nu]) * a.MN + p], acc);
+            bd.out[p] = static_cast<double>(acc);
+        }
+    }
+    if (bd.sel_idx)
+        for (int nu = threadIdx.x; nu < I; nu += blockDim.x) bd.sel_idx[nu] = ul[nu];
+    if (bd.sel_coef)
+        for (int nu = threadIdx.x; nu < I; nu += blockDim.x) bd.sel_coef[nu] = static_cast<double>(cl[nu]);
+}
+
+}  // namespace
+
+cudaError_t launch_lazy_pack(const BlockDesc *blocks, int n, int MN, int MN_pad, uint16_t *xb,
+                             double *xd, uint16_t *mb, double *md, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    lazy_pack_kernel<<<n, 256, 0, st>>>(blocks, MN, MN_pad, xb, xd, mb, md);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lazy_pack_cols(const BlockDesc *blocks, int n, const int *miss_n, const int *miss_blk,
+                                  const int *cur_u, const double *Phi64, int MN, int MN_pad,
+                                  uint16_t *vb, double *vd, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    lazy_pack_cols_kernel<<<n, 256, 0, st>>>(blocks, miss_n, miss_blk, cur_u, Phi64, MN, MN_pad, vb, vd);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st)
+{
+    lazy_init_kernel<T><<<a.n, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st)
+{
+    lazy_round_kernel<T><<<a.n, 256, 0, st>>>(a, nu);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st)
+{
+    lazy_model_kernel<T><<<a.n, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_lazy_init<float>(const LazyArgs &, cudaStream_t);
+template cudaError_t launch_lazy_init<double>(const LazyArgs &, cudaStream_t);
+template cudaError_t launch_lazy_round<float>(const LazyArgs &, int, cudaStream_t);
+template cudaError_t launch_lazy_round<double>(const LazyArgs &, int, cudaStream_t);
+template cudaError_t launch_lazy_model<float>(const LazyArgs &, cudaStream_t);
+template cudaError_t launch_lazy_model<double>(const LazyArgs &, cudaStream_t);
+
+}  // namespace se

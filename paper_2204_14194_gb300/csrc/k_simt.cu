@@ -182,7 +182,8 @@ __global__ void finalize_kernel(const double *__restrict__ diag, const uint8_t *
 template <typename T>
 __global__ void __launch_bounds__(256)
 simt_gemm_kernel(const T *__restrict__ A, int lda, const T *__restrict__ B, int ldb, int M, int N,
-                 int Kd, T *__restrict__ out, long long ldo, int symmetric, int mt)
+                 int Kd, T *__restrict__ out, long long ldo, int symmetric, int mt,
+                 const long long *__restrict__ out_rows, const int *__restrict__ n_dev)
 {
     __shared__ T As[16][65];
     __shared__ T Bs[16][65];
@@ -195,6 +196,11 @@ simt_gemm_kernel(const T *__restrict__ A, int lda, const T *__restrict__ B, int 
     } else {
         tm = blockIdx.x % mt;
         tn = blockIdx.x / mt;
+    }
+    if (n_dev) {
+        const int nd = *n_dev;
+        N = nd < N ? nd : N;
+        if (tn * 64 >= N) return;
     }
     const int tx = threadIdx.x & 15;
     const int ty = threadIdx.x >> 4;
@@ -236,7 +242,7 @@ simt_gemm_kernel(const T *__restrict__ A, int lda, const T *__restrict__ B, int 
             const int n = tn * 64 + tx + 16 * j;
             if (n >= N) continue;
             if (!symmetric) {
-                out[static_cast<long long>(n) * ldo + m] = acc[i][j];
+                out[(out_rows ? out_rows[n] : static_cast<long long>(n) * ldo) + m] = acc[i][j];
             } else if (!diag_tile || n >= m) {
                 out[static_cast<long long>(m) * ldo + n] = acc[i][j];
                 out[static_cast<long long>(n) * ldo + m] = acc[i][j];
@@ -299,13 +305,26 @@ cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup,
 }
 
 template <typename T>
+cudaError_t launch_simt_gemm_ex(const T *A, int lda, const T *B, int ldb, int M, int N, int Kd,
+                                T *out, long long ldo, const long long *out_rows, const int *n_dev,
+                                cudaStream_t st)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int mt = (M + 63) / 64, nt = (N + 63) / 64;
+    simt_gemm_kernel<T><<<mt * nt, 256, 0, st>>>(A, lda, B, ldb, M, N, Kd, out, ldo, 0, mt, out_rows,
+                                                  n_dev);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_simt_gemm(const T *A, int lda, const T *B, int ldb, int M, int N, int Kd, T *out,
                              long long ldo, int symmetric, cudaStream_t st)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     const int mt = (M + 63) / 64, nt = (N + 63) / 64;
     const int grid = symmetric ? mt * (mt + 1) / 2 : mt * nt;
-    simt_gemm_kernel<T><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, Kd, out, ldo, symmetric, mt);
+    simt_gemm_kernel<T><<<grid, 256, 0, st>>>(A, lda, B, ldb, M, N, Kd, out, ldo, symmetric, mt,
+                                              nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -319,5 +338,8 @@ template cudaError_t launch_simt_gemm<double>(const double *, int, const double 
                                               double *, long long, int, cudaStream_t);
 template cudaError_t launch_simt_gemm<float>(const float *, int, const float *, int, int, int, int,
                                              float *, long long, int, cudaStream_t);
+template cudaError_t launch_simt_gemm_ex<double>(const double *, int, const double *, int, int, int,
+                                                 int, double *, long long, const long long *,
+                                                 const int *, cudaStream_t);
 
 }  // namespace se

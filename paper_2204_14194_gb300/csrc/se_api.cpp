@@ -82,6 +82,7 @@ const char *dev_err_text(int bits)
     if (bits & (1 << DEV_ERR_BAD_INDEX)) return "no admissible atom could be selected";
     if (bits & (1 << DEV_ERR_TMEM)) return "tensor memory allocation failed";
     if (bits & (1 << DEV_ERR_LAZY_CACHE)) return "lazy column cache overflow";
+    if (bits & (1 << DEV_ERR_EMPTY_SUPPORT)) return "a block's own mask leaves no admissible atom";
     return "unknown device error";
 }
 
@@ -469,6 +470,7 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         for (int m = d.M / 4; m < d.M / 4 + d.M / 2; ++m)
             for (int n = d.N / 4; n < d.N / 4 + d.N / 2; ++n) pl->pattern[m * d.N + n] = 0;
     }
+    if (d.rho) pl->rho_map.assign(d.rho, d.rho + MN);
     weighting(d.M, d.N, d.rho_hat, d.rho, pl->pattern.data(), pl->w);
     for (int i = 0; i < MN; ++i) {
         if (pl->pattern[i] && !(pl->w[i] >= 0.0 && std::isfinite(pl->w[i])))
@@ -596,10 +598,27 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, cons
     int I_max = 0;
     bool any_mask = false;
     SE_TRY(resolve_blocks(pl, n, blocks, d, &I_max, &any_mask));
-    if (any_mask || pl->desc.gram == SE_GRAM_LAZY)
-        return fail(SE_ERR_INVALID, "per-block support masks need the lazy table path");
+    if (any_mask && pl->desc.gram == SE_GRAM_FULL)
+        return fail(SE_ERR_INVALID, "per-block support masks need the lazy table path (plan gram is FULL)");
+    // blocks on the plan's pattern use the full table (unless LAZY is forced);
+    // blocks with their own mask use lazily computed columns
+    std::vector<BlockDesc> full, lazy;
+    int I_full = 0, I_lazy = 0;
+    for (auto &x : d) {
+        if (!x.support && pl->desc.gram != SE_GRAM_LAZY) {
+            full.push_back(x);
+            I_full = std::max(I_full, x.iterations);
+        } else {
+            if (!x.support) x.support = pl->d_pattern.as<uint8_t>();
+            lazy.push_back(x);
+            I_lazy = std::max(I_lazy, x.iterations);
+        }
+    }
     std::lock_guard<std::mutex> lk(ctx->mu);
-    return run_batch(ctx, pl, ctx->ws, n, d.data(), I_max, static_cast<cudaStream_t>(cuda_stream));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (!full.empty()) SE_TRY(run_batch(ctx, pl, ctx->ws, static_cast<int>(full.size()), full.data(), I_full, st));
+    if (!lazy.empty()) SE_TRY(run_lazy(ctx, pl, ctx->ws, static_cast<int>(lazy.size()), lazy.data(), I_lazy, st));
+    return SE_OK;
 }
 
 se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, const double *samples,
@@ -634,7 +653,8 @@ se_status se_sync(se_ctx_t *ctx, void *cuda_stream)
     SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
     if (bits) {
         SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
-        return fail(SE_ERR_CUDA, std::string("device status: ") + dev_err_text(bits));
+        const se_status code = bits == (1 << DEV_ERR_EMPTY_SUPPORT) ? SE_ERR_EMPTY_SUPPORT : SE_ERR_CUDA;
+        return fail(code, std::string("device status: ") + dev_err_text(bits));
     }
     return SE_OK;
 }

@@ -44,6 +44,9 @@ struct DevBuf {
 // initial projections, host-call I/O) with its pinned descriptor staging.
 struct Workspace {
     DevBuf desc, x, r0, io;
+    // per-block-mask (lazy) path
+    DevBuf lz_R, lz_D, lz_diag, lz_slot, lz_nslots, lz_cache, lz_ulog, lz_clog, lz_cur, lz_miss,
+        lz_x, lz_mk, lz_v;
     BlockDesc *h_desc = nullptr;
     size_t h_desc_cap = 0;
     cudaEvent_t ev_staging = nullptr;     // the staging copy of the last batch has landed
@@ -150,6 +153,7 @@ struct se_plan_s {
     std::vector<uint8_t> dup;             // host K flags
     std::vector<uint8_t> pattern;         // host MN default support
     std::vector<double> w;                // host MN weights of the default pattern
+    std::vector<double> rho_map;          // host MN user weights replacing eq. (5), or empty
     std::vector<int> a_idx, b_idx;
     int nA = 0, nB = 0, ka_pad = 0;
 
@@ -162,6 +166,11 @@ struct se_plan_s {
     // tables (eqs. 16-17)
     se::DevBuf d_C, d_invC, d_Dk, d_diag, d_nadm;
     bool tables_valid = false;
+    // per-block-mask (lazy) operands, built on first use: Phi (fp64 and the
+    // plan precision), Phi rho and Phi^2 rho over all MN pixels (bf16 parts or fp64)
+    bool lazy_ready = false;
+    int MN_pad = 0;
+    se::DevBuf d_Phi64, d_PhiT, d_ArBf, d_AdBf, d_Ar64, d_Ad64;
     cudaEvent_t tables_ready = nullptr;
     std::mutex tmu;
 };
@@ -171,6 +180,9 @@ namespace se {
 // Alg. 2 if not cached, eq. (12) GEMM, Alg. 3 iterations, on stream st.
 se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                     int I_max, cudaStream_t st);
+// Blocks with their own masks (desc.support set for every block): lazy columns.
+se_status run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
+                   int I_max, cudaStream_t st);
 se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);
 // Build the plan's tables on stream st if they are not cached (plan memory
 // only, nothing is allocated), else make st wait for the cached build.

@@ -28,8 +28,12 @@ enum DevErr : int {
     DEV_ERR_WAIT_TIMEOUT = 1,     // an mbarrier wait ran out of time
     DEV_ERR_BAD_INDEX = 2,        // a selected index fell outside [0, K)
     DEV_ERR_TMEM = 3,             // tensor-memory allocation returned an unusable address
-    DEV_ERR_LAZY_CACHE = 4        // lazy column cache overflowed
+    DEV_ERR_LAZY_CACHE = 4,       // lazy column cache overflowed
+    DEV_ERR_EMPTY_SUPPORT = 5     // a block's own mask leaves no admissible atom
 };
+
+// Argmax candidate exchanged between warps: score, index, value.
+template <typename T> struct Cand { T s; int k; T r; };
 
 // ----------------------------------------------------------------- GEMMs
 // D[m][n] = sum_pairs sum_k A[m][pa*ka_pad + k] * B[n][pb*ka_pad + k]
@@ -47,6 +51,8 @@ struct TcGemmArgs {
     int symmetric;       // 1: Gram mode (M == N, upper tiles, mirrored store)
     const float *scale;  // optional per-atom factors: out[n][m] = D[m][n] * scale[m]; in Gram
                          // mode also out[m][n] = D[m][n] * scale[n] (NULL: no scaling)
+    const long long *out_rows;  // optional (non-symmetric): element (n, m) goes to out[out_rows[n] + m]
+    const int *n_dev;    // optional device count: only rows n < min(N, *n_dev) of B are used
     int *err;            // device status word
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why);
@@ -56,6 +62,11 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
 template <typename T>
 cudaError_t launch_simt_gemm(const T *A, int lda, const T *B, int ldb, int M, int N, int Kd,
                              T *out, long long ldo, int symmetric, cudaStream_t st);
+// With optional output row offsets and device-side row count (as TcGemmArgs).
+template <typename T>
+cudaError_t launch_simt_gemm_ex(const T *A, int lda, const T *B, int ldb, int M, int N, int Kd,
+                                T *out, long long ldo, const long long *out_rows, const int *n_dev,
+                                cudaStream_t st);
 
 // ------------------------------------------------------------- prep / tables
 // Pack the samples of the shared pattern's support pixels: for block b and
@@ -97,6 +108,38 @@ struct IterArgs {
 };
 template <typename T>
 cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches);
+
+// ------------------------------------------------------------ lazy columns
+struct LazyArgs {
+    const BlockDesc *blocks;   // device; support = the block's own mask
+    int n, K, Kp, MN, I_max;
+    const uint8_t *dup;        // [Kp] inadmissible-by-duplication flags (padding = 1)
+    const void *Phi;           // [Kp][MN] atoms (T) for the model
+    void *R;                   // [n][Kp] projections; unscaled R0 before init, then D-scaled
+    void *Dk;                  // [n][Kp] D_b,k
+    const void *diag;          // [n][Kp] C_b(k, k)
+    int *slot_of;              // [n][Kp] cache slot of atom k or -1
+    int *n_slots;              // [n] slots used (-1: block skipped)
+    void *cache;               // [n][slots][Kp] columns C_b(:, u) (unscaled)
+    int slots;
+    int *u_log;                // [n][I_max]
+    void *c_log;               // [n][I_max] (T)
+    int *cur_u;                // [n]
+    void *cur_c;               // [n] (T)
+    int *miss_n;               // column requests of the current round
+    int *miss_blk;             // [n]
+    long long *miss_rows;      // [n] element offset of the requested cache row
+    double gamma;
+    int *err;
+};
+cudaError_t launch_lazy_pack(const BlockDesc *blocks, int n, int MN, int MN_pad, uint16_t *xb,
+                             double *xd, uint16_t *mb, double *md, cudaStream_t st);
+cudaError_t launch_lazy_pack_cols(const BlockDesc *blocks, int n, const int *miss_n, const int *miss_blk,
+                                  const int *cur_u, const double *Phi64, int MN, int MN_pad,
+                                  uint16_t *vb, double *vd, cudaStream_t st);
+template <typename T> cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st);
+template <typename T> cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st);
+template <typename T> cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st);
 
 // Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
 int iterate_kp(int K, bool fp64);

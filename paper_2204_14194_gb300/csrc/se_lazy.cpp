@@ -1,0 +1,257 @@
+// se_lazy.cpp -- host side of the per-block-mask path (lazily computed
+// columns of the table of eq. (16)); kernels in k_lazy.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "se_host.h"
+
+using namespace se;
+
+namespace {
+
+#define LZ_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return set_error(SE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LZ_TRY(expr)                \
+    do {                            \
+        se_status s_ = (expr);      \
+        if (s_ != SE_OK) return s_; \
+    } while (0)
+
+size_t r64(size_t v) { return (v + 63) / 64 * 64; }
+
+template <typename V>
+se_status upload_vec(se_ctx_s *ctx, DevBuf &b, const std::vector<V> &h)
+{
+    LZ_TRY(dev_alloc(ctx, b, h.size() * sizeof(V)));
+    LZ_CUDA(cudaMemcpy(b.ptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return SE_OK;
+}
+
+// Plan-level operands over all MN pixels: rho (the unmasked weights of
+// eq. 5, or the user's map), Phi rho and Phi^2 rho, and the atoms themselves.
+se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(pl->tmu);
+    if (pl->lazy_ready) return SE_OK;
+    const int K = pl->K, Kp = pl->Kp, MN = pl->MN;
+    const int MNp = static_cast<int>(r64(MN));
+    std::vector<uint8_t> all(MN, 1);
+    std::vector<double> rho;
+    weighting(pl->M, pl->N, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
+              all.data(), rho);
+    std::vector<double> phi(static_cast<size_t>(Kp) * MN, 0.0), ar(static_cast<size_t>(Kp) * MNp, 0.0),
+        ad(static_cast<size_t>(Kp) * MNp, 0.0);
+    for (int k = 0; k < K; ++k) {
+        const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+        std::memcpy(phi.data() + static_cast<size_t>(k) * MN, a, sizeof(double) * MN);
+        for (int p = 0; p < MN; ++p) {
+            ar[static_cast<size_t>(k) * MNp + p] = a[p] * rho[p];
+            ad[static_cast<size_t>(k) * MNp + p] = a[p] * a[p] * rho[p];
+        }
+    }
+    LZ_TRY(upload_vec(ctx, pl->d_Phi64, phi));
+    if (pl->pc.fp64) {
+        LZ_TRY(upload_vec(ctx, pl->d_Ar64, ar));
+        LZ_TRY(upload_vec(ctx, pl->d_Ad64, ad));
+    } else {
+        std::vector<float> pf(phi.begin(), phi.end());
+        LZ_TRY(upload_vec(ctx, pl->d_PhiT, pf));
+        DevBuf tmp;
+        LZ_TRY(upload_vec(ctx, tmp, ar));
+        LZ_TRY(dev_alloc(ctx, pl->d_ArBf, static_cast<size_t>(Kp) * 3 * MNp * 2));
+        LZ_CUDA(launch_split_bf16(tmp.as<double>(), Kp, MNp, MNp, MNp, 3, pl->d_ArBf.as<uint16_t>(), st));
+        LZ_CUDA(cudaStreamSynchronize(st));
+        LZ_CUDA(cudaMemcpy(tmp.ptr, ad.data(), sizeof(double) * ad.size(), cudaMemcpyHostToDevice));
+        LZ_TRY(dev_alloc(ctx, pl->d_AdBf, static_cast<size_t>(Kp) * 3 * MNp * 2));
+        LZ_CUDA(launch_split_bf16(tmp.as<double>(), Kp, MNp, MNp, MNp, 3, pl->d_AdBf.as<uint16_t>(), st));
+        LZ_CUDA(cudaStreamSynchronize(st));
+        ctx->launches += 2;
+    }
+    pl->MN_pad = MNp;
+    pl->lazy_ready = true;
+    return SE_OK;
+}
+
+TcGemmArgs gemm_args(const void *A, const void *B, int M, int N, int lda, int ldb, int ka, int np,
+                     const int *pa, const int *pb, float *out, long long ldo, int *err)
+{
+    TcGemmArgs g{};
+    g.A = A;
+    g.B = B;
+    g.M = M;
+    g.N = N;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ka_pad = ka;
+    g.npairs = np;
+    for (int i = 0; i < np; ++i) { g.pa[i] = pa[i]; g.pb[i] = pb[i]; }
+    g.out = out;
+    g.ldo = ldo;
+    g.err = err;
+    return g;
+}
+
+}  // namespace
+
+se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
+                       int I_max, cudaStream_t st)
+{
+    LZ_TRY(ensure_lazy_plan(ctx, pl, st));
+    const bool fp64 = pl->pc.fp64;
+    const size_t tsz = fp64 ? 8 : 4;
+    const int Kp = pl->Kp, MN = pl->MN, MNp = pl->MN_pad;
+    const int slots = std::max(1, I_max - 1);
+    const size_t opnd = fp64 ? 8 * static_cast<size_t>(MNp) * 3 : 2 * static_cast<size_t>(MNp) * 7;
+    const size_t per_block = tsz * Kp * 3 + 4 * static_cast<size_t>(Kp) +
+                             static_cast<size_t>(slots) * Kp * tsz + static_cast<size_t>(I_max) * (4 + tsz) +
+                             opnd + sizeof(BlockDesc) + 64;
+    size_t avail;
+    if (ctx->budget) {
+        avail = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+    } else {
+        size_t fr = 0, tot = 0;
+        LZ_CUDA(cudaMemGetInfo(&fr, &tot));
+        avail = std::min(fr / 2, static_cast<size_t>(16) << 30);
+    }
+    int wave = static_cast<int>(std::min<size_t>(n, avail / per_block));
+    if (wave < 1) return set_error(SE_ERR_NOMEM, "one block of this plan does not fit the HBM budget");
+
+    // buffers for a whole wave, reused by every wave
+    LZ_CUDA(cudaStreamWaitEvent(st, ws.ev_ws, 0));
+    LZ_CUDA(cudaEventSynchronize(ws.ev_ws));
+    LZ_TRY(dev_alloc(ctx, ws.desc, sizeof(BlockDesc) * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_R, tsz * Kp * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_D, tsz * Kp * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_diag, tsz * Kp * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_slot, 4 * static_cast<size_t>(Kp) * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_nslots, 4 * static_cast<size_t>(wave)));
+    LZ_TRY(dev_alloc(ctx, ws.lz_cache, tsz * Kp * static_cast<size_t>(slots) * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_ulog, 4 * static_cast<size_t>(I_max) * wave));
+    LZ_TRY(dev_alloc(ctx, ws.lz_clog, tsz * I_max * static_cast<size_t>(wave)));
+    LZ_TRY(dev_alloc(ctx, ws.lz_cur, (4 + 8) * static_cast<size_t>(wave) + 16));
+    LZ_TRY(dev_alloc(ctx, ws.lz_miss, 16 + (4 + 8) * static_cast<size_t>(wave) + 16));
+    if (fp64) {
+        LZ_TRY(dev_alloc(ctx, ws.lz_x, 8 * static_cast<size_t>(MNp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_mk, 8 * static_cast<size_t>(MNp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_v, 8 * static_cast<size_t>(MNp) * wave));
+    } else {
+        LZ_TRY(dev_alloc(ctx, ws.lz_x, 2 * 3 * static_cast<size_t>(MNp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_mk, 2 * static_cast<size_t>(MNp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_v, 2 * 3 * static_cast<size_t>(MNp) * wave));
+    }
+    char *cur = ws.lz_cur.as<char>();
+    char *mis = ws.lz_miss.as<char>();
+    int *miss_n = reinterpret_cast<int *>(mis);
+    long long *miss_rows = reinterpret_cast<long long *>(mis + 16);
+    int *miss_blk = reinterpret_cast<int *>(mis + 16 + 8 * static_cast<size_t>(wave));
+    double *cur_c = reinterpret_cast<double *>(cur);
+    int *cur_u = reinterpret_cast<int *>(cur + 8 * static_cast<size_t>(wave));
+
+    const int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
+    const int paD[3] = {2, 1, 0}, pbD[3] = {0, 0, 0};
+    std::string why;
+
+    for (int w0 = 0; w0 < n; w0 += wave) {
+        const int nw = std::min(wave, n - w0);
+        // descriptors of this wave (pinned staging, like the shared-pattern path)
+        LZ_CUDA(cudaEventSynchronize(ws.ev_staging));
+        if (ws.h_desc_cap < static_cast<size_t>(nw)) {
+            if (ws.h_desc) cudaFreeHost(ws.h_desc);
+            ws.h_desc = nullptr;
+            ws.h_desc_cap = 0;
+            LZ_CUDA(cudaMallocHost(&ws.h_desc, sizeof(BlockDesc) * nw));
+            ws.h_desc_cap = nw;
+        }
+        std::memcpy(ws.h_desc, hdesc + w0, sizeof(BlockDesc) * nw);
+        LZ_CUDA(cudaMemcpyAsync(ws.desc.ptr, ws.h_desc, sizeof(BlockDesc) * nw, cudaMemcpyHostToDevice, st));
+        LZ_CUDA(cudaEventRecord(ws.ev_staging, st));
+        const BlockDesc *dd = ws.desc.as<BlockDesc>();
+
+        int tok = stage_begin(ctx, 0, st);
+        LZ_CUDA(launch_lazy_pack(dd, nw, MN, MNp, fp64 ? nullptr : ws.lz_x.as<uint16_t>(),
+                                 fp64 ? ws.lz_x.as<double>() : nullptr,
+                                 fp64 ? nullptr : ws.lz_mk.as<uint16_t>(),
+                                 fp64 ? ws.lz_mk.as<double>() : nullptr, st));
+        stage_end(ctx, tok, st);
+        tok = stage_begin(ctx, 2, st);
+        if (fp64) {
+            LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_x.as<double>(), MNp, Kp, nw,
+                                                MNp, ws.lz_R.as<double>(), Kp, nullptr, nullptr, st));
+            LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ad64.as<double>(), MNp, ws.lz_mk.as<double>(), MNp, Kp,
+                                                nw, MNp, ws.lz_diag.as<double>(), Kp, nullptr, nullptr, st));
+        } else {
+            TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_x.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6, pb6,
+                                     ws.lz_R.as<float>(), Kp, ctx->ws_err.as<int>());
+            cudaError_t e = launch_tc_gemm(g, st, &why);
+            if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy projections: " + why);
+            g = gemm_args(pl->d_AdBf.ptr, ws.lz_mk.ptr, Kp, nw, 3 * MNp, MNp, MNp, 3, paD, pbD,
+                          ws.lz_diag.as<float>(), Kp, ctx->ws_err.as<int>());
+            e = launch_tc_gemm(g, st, &why);
+            if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy diagonal: " + why);
+        }
+        stage_end(ctx, tok, st);
+
+        LazyArgs a{};
+        a.blocks = dd;
+        a.n = nw;
+        a.K = pl->K;
+        a.Kp = Kp;
+        a.MN = MN;
+        a.I_max = I_max;
+        a.dup = pl->d_dup.as<uint8_t>();
+        a.Phi = fp64 ? pl->d_Phi64.ptr : pl->d_PhiT.ptr;
+        a.R = ws.lz_R.ptr;
+        a.Dk = ws.lz_D.ptr;
+        a.diag = ws.lz_diag.ptr;
+        a.slot_of = ws.lz_slot.as<int>();
+        a.n_slots = ws.lz_nslots.as<int>();
+        a.cache = ws.lz_cache.ptr;
+        a.slots = slots;
+        a.u_log = ws.lz_ulog.as<int>();
+        a.c_log = ws.lz_clog.ptr;
+        a.cur_u = cur_u;
+        a.cur_c = cur_c;
+        a.miss_n = miss_n;
+        a.miss_blk = miss_blk;
+        a.miss_rows = miss_rows;
+        a.gamma = pl->desc.gamma;
+        a.err = ctx->ws_err.as<int>();
+
+        tok = stage_begin(ctx, 3, st);
+        LZ_CUDA(fp64 ? launch_lazy_init<double>(a, st) : launch_lazy_init<float>(a, st));
+        for (int nu = 0; nu < I_max; ++nu) {
+            LZ_CUDA(cudaMemsetAsync(miss_n, 0, sizeof(int), st));
+            LZ_CUDA(fp64 ? launch_lazy_round<double>(a, nu, st) : launch_lazy_round<float>(a, nu, st));
+            if (nu + 1 == I_max) break;
+            LZ_CUDA(launch_lazy_pack_cols(dd, nw, miss_n, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
+                                          fp64 ? nullptr : ws.lz_v.as<uint16_t>(),
+                                          fp64 ? ws.lz_v.as<double>() : nullptr, st));
+            if (fp64) {
+                LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_v.as<double>(), MNp, Kp,
+                                                    nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, miss_n,
+                                                    st));
+            } else {
+                TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_v.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6,
+                                         pb6, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
+                g.out_rows = miss_rows;
+                g.n_dev = miss_n;
+                cudaError_t e = launch_tc_gemm(g, st, &why);
+                if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy columns: " + why);
+            }
+            ctx->launches += 4;
+        }
+        LZ_CUDA(fp64 ? launch_lazy_model<double>(a, st) : launch_lazy_model<float>(a, st));
+        stage_end(ctx, tok, st);
+        ctx->launches += 6;
+    }
+    LZ_CUDA(cudaEventRecord(ws.ev_ws, st));
+    return SE_OK;
+}
