@@ -331,6 +331,80 @@ def run_ours(args):
     return 0
 
 
+def run_workload(args):
+    """Secondary measurements (not the headline): the 1920x1080 Gaussian-dictionary
+    workload (shared pattern, K = 4096, I = 200) and the mixed-size workload with
+    per-block masks (16/32/64 areas, I in [50, 500])."""
+    import torch
+    from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import workloads as W
+
+    # one context (and stream) per plan, so the three area sizes overlap on the device
+    ctxs, streams, groups = [], [], []
+    if args.workload == "gauss1080":
+        wl = W.config3(args.blocks or None)
+        ctxs.append(B.Context(0))
+        streams.append(torch.cuda.Stream())
+        plan = ctxs[0].plan(32, 32, "numeric", 4096, wl.rho_hat, wl.gamma, wl.iterations, prec=args.prec,
+                            dictionary=wl.dictionary)
+        s = torch.from_numpy(wl.samples).cuda()
+        groups.append((plan, s, torch.empty_like(s), None, wl.iterations))
+        name = wl.name
+    else:
+        for wl in W.config4(args.blocks or 20000):
+            c = B.Context(0)
+            ctxs.append(c)
+            streams.append(torch.cuda.Stream())
+            plan = c.plan(wl.M, wl.N, "dct_wht", wl.K, wl.rho_hat, wl.gamma, int(wl.iters_per_block.max()),
+                          prec=args.prec)
+            s = torch.from_numpy(wl.samples).cuda()
+            m = torch.from_numpy(wl.support).cuda()
+            groups.append((plan, s, torch.empty_like(s), m, wl.iters_per_block))
+        name = "mixed_%dblk_16-32-64_masks_I50-500" % sum(g[1].shape[0] for g in groups)
+    descs = [None if g[3] is None else
+             [{"samples": g[1][b], "support": g[3][b], "out": g[2][b], "iterations": int(g[4][b])}
+              for b in range(g[1].shape[0])] for g in groups]
+
+    def step():
+        for (plan, s, o, m, it), d, stream in zip(groups, descs, streams):
+            plan.reset_tables()
+            if d is None:
+                plan.extrapolate_strided(s, o, stream=stream)
+            else:
+                plan.extrapolate_batch(d, stream=stream)
+
+    def sync():
+        for c, st in zip(ctxs, streams):
+            c.sync(st)
+
+    for _ in range(args.warmup):
+        step()
+    sync()
+    for c in ctxs:
+        c.set_profiling(True)
+        c.stage_times(reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sync()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    nb = sum(g[1].shape[0] for g in groups)
+    stages = {}
+    for c in ctxs:
+        for k, v in c.stage_times(reset=True).items():
+            stages[k] = stages.get(k, 0.0) + v[0] / args.steps
+    line = {"metric": "extrapolated blocks/s", "workload": name, "value": nb / (ms / 1000.0),
+            "unit": "blocks/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "precision": args.prec, "timing": "host wall clock around the steps (several streams)",
+            "stages_ms_per_step_summed_over_streams": stages}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,7 +414,12 @@ def main():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
     ap.add_argument("--ref-sample", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed"],
+                    help="img512 is the headline; the others are secondary measurements")
+    ap.add_argument("--blocks", type=int, default=0, help="block count for --workload gauss1080/mixed")
     args = ap.parse_args()
+    if args.workload != "img512":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

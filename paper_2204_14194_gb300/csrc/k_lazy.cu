@@ -173,6 +173,7 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
 {
     __shared__ Cand<T> red[32];
     const int b = blockIdx.x;
+    if (b == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
     const int Ib = a.blocks[b].iterations;
     if (nu >= Ib || a.n_slots[b] < 0) return;
     T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
@@ -217,7 +218,7 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
                 a.n_slots[b] = -1;
             } else {
                 slot_of[u] = sl;
-                const int j = atomicAdd(a.miss_n, 1);
+                const int j = atomicAdd(a.miss_n + (nu & 1), 1);
                 a.miss_blk[j] = b;
                 a.miss_rows[j] = (static_cast<long long>(b) * a.slots + sl) * a.Kp;
             }

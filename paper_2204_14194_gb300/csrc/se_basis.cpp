@@ -14,7 +14,7 @@ namespace se {
 
 // 2-D orthonormal DCT-II, atom (p, q) at index p*N + q (separable product of
 // the 1-D DCT-II rows with the sqrt(1/L) / sqrt(2/L) normalisation).
-static void dct_rows(int L, std::vector<double> &T)
+void dct_rows(int L, std::vector<double> &T)
 {
     const double pi = 3.14159265358979323846;
     T.assign(static_cast<size_t>(L) * L, 0.0);
@@ -27,7 +27,7 @@ static void dct_rows(int L, std::vector<double> &T)
 // Walsh functions in sequency order: wal_p(m) = (-1)^(sum_i r_i(p) m_i) with
 // r_i(p) the bits of the Gray code of p taken in reverse order, so that
 // wal_p has exactly p sign changes.
-static void walsh_seq_rows(int L, std::vector<double> &T)
+void walsh_seq_rows(int L, std::vector<double> &T)
 {
     int bits = 0;
     while ((1 << bits) < L) ++bits;

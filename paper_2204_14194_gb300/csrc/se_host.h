@@ -24,6 +24,9 @@ namespace se {
 bool build_dictionary(int M, int N, int basis, int K, const double *numeric,
                       std::vector<double> &phi, std::string *why);
 void find_collinear(int K, int MN, const double *phi, std::vector<uint8_t> &dup);
+// 1-D bases: orthonormal DCT-II rows and +-1 Walsh rows in sequency order (L x L).
+void dct_rows(int L, std::vector<double> &T);
+void walsh_seq_rows(int L, std::vector<double> &T);
 void weighting(int M, int N, double rho_hat, const double *rho, const uint8_t *support,
                std::vector<double> &w);
 
@@ -171,6 +174,10 @@ struct se_plan_s {
     bool lazy_ready = false;
     int MN_pad = 0;
     se::DevBuf d_Phi64, d_PhiT, d_ArBf, d_AdBf, d_Ar64, d_Ad64;
+    // transform-domain form for DCT / WHT dictionaries: 1-D bases and rho
+    bool sep = false;
+    int sep_ntr = 0, sep_koff[2] = {0, 0};
+    se::DevBuf d_sepM[2], d_sepN[2], d_rho;
     cudaEvent_t tables_ready = nullptr;
     std::mutex tmu;
 };

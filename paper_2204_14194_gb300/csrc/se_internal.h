@@ -126,7 +126,8 @@ struct LazyArgs {
     void *c_log;               // [n][I_max] (T)
     int *cur_u;                // [n]
     void *cur_c;               // [n] (T)
-    int *miss_n;               // column requests of the current round
+    int *miss_n;               // [2] column requests; round nu counts in miss_n[nu & 1]
+                               // and clears miss_n[(nu + 1) & 1] for the next round
     int *miss_blk;             // [n]
     long long *miss_rows;      // [n] element offset of the requested cache row
     double gamma;
@@ -140,6 +141,26 @@ cudaError_t launch_lazy_pack_cols(const BlockDesc *blocks, int n, const int *mis
 template <typename T> cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st);
 template <typename T> cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st);
 template <typename T> cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st);
+
+// Separable transform-domain scalar products (DCT / WHT dictionaries).
+struct SepArgs {
+    int M, N;
+    int ntr;                    // 1 or 2 transforms (DCT u WHT)
+    const void *TM[2];          // [M][M] 1-D basis rows of transform t (T)
+    const void *TN[2];          // [N][N]
+    int koff[2];                // first atom index of transform t
+    int mode;                   // 0: R0, 1: diagonal, 2: column of the current atom
+    const BlockDesc *blocks;    // support = the block's mask
+    const double *rho;          // [MN] weights of eq. (5) without the mask
+    const int *n_dev;           // optional live item count
+    const int *item_blk;        // optional block of item i (mode 2), else i
+    const int *cur_u;           // mode 2: atom of block b
+    void *out;                  // T output
+    long long ldo;              // row pitch for row b when out_rows is NULL
+    const long long *out_rows;  // optional element offset of item i's row
+    int n;
+};
+template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st);
 
 // Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
 int iterate_kp(int K, bool fp64);

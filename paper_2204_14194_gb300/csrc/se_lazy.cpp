@@ -75,9 +75,65 @@ se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         LZ_CUDA(cudaStreamSynchronize(st));
         ctx->launches += 2;
     }
+    // transform-domain operands when the atoms are products of 1-D bases
+    const int basis = pl->desc.basis;
+    const size_t tsz = pl->pc.fp64 ? 8 : 4;
+    const size_t smem = tsz * (2 * static_cast<size_t>(MN) + pl->M * pl->M + pl->N * pl->N);
+    if ((basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT) &&
+        smem <= 227 * 1024) {
+        LZ_TRY(upload_vec(ctx, pl->d_rho, rho));
+        int t = 0;
+        auto add = [&](bool wht, int koff) -> se_status {
+            std::vector<double> tm, tn;
+            if (wht) {
+                walsh_seq_rows(pl->M, tm);
+                walsh_seq_rows(pl->N, tn);
+                for (auto &v : tm) v /= std::sqrt(static_cast<double>(pl->M));
+                for (auto &v : tn) v /= std::sqrt(static_cast<double>(pl->N));
+            } else {
+                dct_rows(pl->M, tm);
+                dct_rows(pl->N, tn);
+            }
+            if (pl->pc.fp64) {
+                LZ_TRY(upload_vec(ctx, pl->d_sepM[t], tm));
+                LZ_TRY(upload_vec(ctx, pl->d_sepN[t], tn));
+            } else {
+                LZ_TRY(upload_vec(ctx, pl->d_sepM[t], std::vector<float>(tm.begin(), tm.end())));
+                LZ_TRY(upload_vec(ctx, pl->d_sepN[t], std::vector<float>(tn.begin(), tn.end())));
+            }
+            pl->sep_koff[t] = koff;
+            ++t;
+            return SE_OK;
+        };
+        if (basis == SE_BASIS_DCT || basis == SE_BASIS_DCT_WHT) LZ_TRY(add(false, 0));
+        if (basis == SE_BASIS_WHT) LZ_TRY(add(true, 0));
+        if (basis == SE_BASIS_DCT_WHT) LZ_TRY(add(true, MN));
+        pl->sep_ntr = t;
+        pl->sep = true;
+    }
     pl->MN_pad = MNp;
     pl->lazy_ready = true;
     return SE_OK;
+}
+
+SepArgs sep_args(se_plan_s *pl, const BlockDesc *dd, int nw, int mode, void *out, long long ldo)
+{
+    SepArgs s{};
+    s.M = pl->M;
+    s.N = pl->N;
+    s.ntr = pl->sep_ntr;
+    for (int t = 0; t < pl->sep_ntr; ++t) {
+        s.TM[t] = pl->d_sepM[t].ptr;
+        s.TN[t] = pl->d_sepN[t].ptr;
+        s.koff[t] = pl->sep_koff[t];
+    }
+    s.mode = mode;
+    s.blocks = dd;
+    s.rho = pl->d_rho.as<double>();
+    s.out = out;
+    s.ldo = ldo;
+    s.n = nw;
+    return s;
 }
 
 TcGemmArgs gemm_args(const void *A, const void *B, int M, int N, int lda, int ldb, int ka, int np,
@@ -99,6 +155,41 @@ TcGemmArgs gemm_args(const void *A, const void *B, int M, int N, int lda, int ld
     return g;
 }
 
+se_status dense_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const BlockDesc *dd, int nw,
+                            cudaStream_t st)
+{
+    // eq. 12 and the diagonal of eq. 16 as tensor-core GEMMs over all MN pixels
+    const bool fp64 = pl->pc.fp64;
+    const int Kp = pl->Kp, MN = pl->MN, MNp = pl->MN_pad;
+    const int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
+    const int paD[3] = {2, 1, 0}, pbD[3] = {0, 0, 0};
+    std::string why;
+    int tok = stage_begin(ctx, 0, st);
+    LZ_CUDA(launch_lazy_pack(dd, nw, MN, MNp, fp64 ? nullptr : ws.lz_x.as<uint16_t>(),
+                             fp64 ? ws.lz_x.as<double>() : nullptr,
+                             fp64 ? nullptr : ws.lz_mk.as<uint16_t>(),
+                             fp64 ? ws.lz_mk.as<double>() : nullptr, st));
+    stage_end(ctx, tok, st);
+    tok = stage_begin(ctx, 2, st);
+    if (fp64) {
+        LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_x.as<double>(), MNp, Kp, nw,
+                                            MNp, ws.lz_R.as<double>(), Kp, nullptr, nullptr, st));
+        LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ad64.as<double>(), MNp, ws.lz_mk.as<double>(), MNp, Kp,
+                                            nw, MNp, ws.lz_diag.as<double>(), Kp, nullptr, nullptr, st));
+    } else {
+        TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_x.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6, pb6,
+                                 ws.lz_R.as<float>(), Kp, ctx->ws_err.as<int>());
+        cudaError_t e = launch_tc_gemm(g, st, &why);
+        if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy projections: " + why);
+        g = gemm_args(pl->d_AdBf.ptr, ws.lz_mk.ptr, Kp, nw, 3 * MNp, MNp, MNp, 3, paD, pbD,
+                      ws.lz_diag.as<float>(), Kp, ctx->ws_err.as<int>());
+        e = launch_tc_gemm(g, st, &why);
+        if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy diagonal: " + why);
+    }
+    stage_end(ctx, tok, st);
+    return SE_OK;
+}
+
 }  // namespace
 
 se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
@@ -117,9 +208,11 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
     if (ctx->budget) {
         avail = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
     } else {
+        // no budget: a wave may use up to 45% of the free HBM (at most 96 GiB),
+        // so even 64 x 64 blocks with K = 8192 and I = 500 run thousands per wave
         size_t fr = 0, tot = 0;
         LZ_CUDA(cudaMemGetInfo(&fr, &tot));
-        avail = std::min(fr / 2, static_cast<size_t>(16) << 30);
+        avail = std::min(fr / 100 * 45, static_cast<size_t>(96) << 30);
     }
     int wave = static_cast<int>(std::min<size_t>(n, avail / per_block));
     if (wave < 1) return set_error(SE_ERR_NOMEM, "one block of this plan does not fit the HBM budget");
@@ -156,7 +249,6 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
     int *cur_u = reinterpret_cast<int *>(cur + 8 * static_cast<size_t>(wave));
 
     const int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
-    const int paD[3] = {2, 1, 0}, pbD[3] = {0, 0, 0};
     std::string why;
 
     for (int w0 = 0; w0 < n; w0 += wave) {
@@ -175,29 +267,18 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         LZ_CUDA(cudaEventRecord(ws.ev_staging, st));
         const BlockDesc *dd = ws.desc.as<BlockDesc>();
 
-        int tok = stage_begin(ctx, 0, st);
-        LZ_CUDA(launch_lazy_pack(dd, nw, MN, MNp, fp64 ? nullptr : ws.lz_x.as<uint16_t>(),
-                                 fp64 ? ws.lz_x.as<double>() : nullptr,
-                                 fp64 ? nullptr : ws.lz_mk.as<uint16_t>(),
-                                 fp64 ? ws.lz_mk.as<double>() : nullptr, st));
-        stage_end(ctx, tok, st);
-        tok = stage_begin(ctx, 2, st);
-        if (fp64) {
-            LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_x.as<double>(), MNp, Kp, nw,
-                                                MNp, ws.lz_R.as<double>(), Kp, nullptr, nullptr, st));
-            LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ad64.as<double>(), MNp, ws.lz_mk.as<double>(), MNp, Kp,
-                                                nw, MNp, ws.lz_diag.as<double>(), Kp, nullptr, nullptr, st));
+        int tok;
+        if (pl->sep) {
+            // eq. 12 and the diagonal of eq. 16 as separable transforms
+            tok = stage_begin(ctx, 2, st);
+            SepArgs sa = sep_args(pl, dd, nw, 0, ws.lz_R.ptr, Kp);
+            LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+            sa = sep_args(pl, dd, nw, 1, ws.lz_diag.ptr, Kp);
+            LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+            stage_end(ctx, tok, st);
         } else {
-            TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_x.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6, pb6,
-                                     ws.lz_R.as<float>(), Kp, ctx->ws_err.as<int>());
-            cudaError_t e = launch_tc_gemm(g, st, &why);
-            if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy projections: " + why);
-            g = gemm_args(pl->d_AdBf.ptr, ws.lz_mk.ptr, Kp, nw, 3 * MNp, MNp, MNp, 3, paD, pbD,
-                          ws.lz_diag.as<float>(), Kp, ctx->ws_err.as<int>());
-            e = launch_tc_gemm(g, st, &why);
-            if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy diagonal: " + why);
+            LZ_TRY(dense_projections(ctx, pl, ws, dd, nw, st));
         }
-        stage_end(ctx, tok, st);
 
         LazyArgs a{};
         a.blocks = dd;
@@ -226,27 +307,38 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         a.err = ctx->ws_err.as<int>();
 
         tok = stage_begin(ctx, 3, st);
+        LZ_CUDA(cudaMemsetAsync(miss_n, 0, 2 * sizeof(int), st));
         LZ_CUDA(fp64 ? launch_lazy_init<double>(a, st) : launch_lazy_init<float>(a, st));
         for (int nu = 0; nu < I_max; ++nu) {
-            LZ_CUDA(cudaMemsetAsync(miss_n, 0, sizeof(int), st));
             LZ_CUDA(fp64 ? launch_lazy_round<double>(a, nu, st) : launch_lazy_round<float>(a, nu, st));
             if (nu + 1 == I_max) break;
-            LZ_CUDA(launch_lazy_pack_cols(dd, nw, miss_n, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
+            int *req = miss_n + (nu & 1);
+            if (pl->sep) {
+                SepArgs sa = sep_args(pl, dd, nw, 2, ws.lz_cache.ptr, Kp);
+                sa.n_dev = req;
+                sa.item_blk = miss_blk;
+                sa.cur_u = cur_u;
+                sa.out_rows = miss_rows;
+                LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+                ctx->launches += 2;
+                continue;
+            }
+            LZ_CUDA(launch_lazy_pack_cols(dd, nw, req, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
                                           fp64 ? nullptr : ws.lz_v.as<uint16_t>(),
                                           fp64 ? ws.lz_v.as<double>() : nullptr, st));
             if (fp64) {
                 LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_v.as<double>(), MNp, Kp,
-                                                    nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, miss_n,
+                                                    nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, req,
                                                     st));
             } else {
                 TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_v.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6,
                                          pb6, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
                 g.out_rows = miss_rows;
-                g.n_dev = miss_n;
+                g.n_dev = req;
                 cudaError_t e = launch_tc_gemm(g, st, &why);
                 if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy columns: " + why);
             }
-            ctx->launches += 4;
+            ctx->launches += 3;
         }
         LZ_CUDA(fp64 ? launch_lazy_model<double>(a, st) : launch_lazy_model<float>(a, st));
         stage_end(ctx, tok, st);
