@@ -405,6 +405,83 @@ def run_workload(args):
     return 0
 
 
+def run_serve(args):
+    """Serving measurement: open-loop Poisson arrivals of single-block requests of
+    mixed area size (16/32/64), DCT u WHT or Gaussian dictionaries with K = 2MN,
+    random per-request masks, I in [100, 300], under an HBM budget; latency is
+    completion minus the scheduled arrival time."""
+    import threading as th
+    from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import workloads as W
+
+    rng = np.random.default_rng(5)
+    ctx = B.Context(0, hbm_budget_bytes=int(args.budget_gb * (1 << 30)))
+    plans = {}
+    for L in (16, 32, 64):
+        plans[("dct_wht", L)] = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, 300, prec=args.prec)
+        if args.gauss_share > 0:
+            plans[("gauss", L)] = ctx.plan(L, L, "numeric", 2 * L * L, 0.8, 0.5, 300, prec=args.prec,
+                                           dictionary=W.gaussian_dictionary(2 * L * L, L, L, 900 + L))
+    pool = 256
+    samp = {L: [W.patch(L, 50000 + 1000 * L + i) for i in range(pool)] for L in (16, 32, 64)}
+    mrng = np.random.default_rng(6)
+    masks = {L: [W.rect_support(L, L, mrng) if i % 2 else W.holes_support(L, L, mrng) for i in range(pool)]
+             for L in (16, 32, 64)}
+    total_t = args.warm_s + args.duration
+    n = int(args.rate * total_t)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
+    sizes = rng.choice([16, 32, 64], size=n)
+    gauss = rng.random(n) < args.gauss_share
+    iters = rng.integers(100, 301, size=n)
+    pick = rng.integers(0, pool, size=n)
+    outs = {L: np.empty((pool, L, L)) for L in (16, 32, 64)}   # results are not checked here
+    tickets = [None] * n
+    t_sub = np.zeros(n)
+    lat = np.full(n, np.nan)
+    start = time.perf_counter() + 0.2
+
+    def submitter():
+        for i in range(n):
+            target = start + arrivals[i]
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 2e-4:
+                    time.sleep(target - now - 1e-4)
+            L = int(sizes[i])
+            p = plans[("gauss" if gauss[i] else "dct_wht", L)]
+            t_sub[i] = time.perf_counter()
+            tickets[i] = ctx.submit(p, samp[L][pick[i]], outs[L][pick[i]], iterations=int(iters[i]),
+                                    support=masks[L][pick[i]])
+
+    th_sub = th.Thread(target=submitter)
+    th_sub.start()
+    done = 0
+    for i in range(n):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        st, l = ctx.poll(tickets[i], timeout_us=-1)
+        lat[i] = (t_sub[i] - (start + arrivals[i])) + l
+        done += 1
+    th_sub.join()
+    t_end = time.perf_counter()
+    keep = arrivals >= args.warm_s
+    L_ms = lat[keep] * 1000.0
+    line = {"metric": "serving latency and throughput", "workload":
+            "poisson %.0f req/s, %.0f s (+%.0f s warm-up), areas 16/32/64, K = 2MN, %d%% Gaussian, "
+            "per-request masks, I in [100,300], budget %.0f GB" % (args.rate, args.duration, args.warm_s,
+                                                                  100 * args.gauss_share, args.budget_gb),
+            "offered_rate": args.rate, "requests": int(keep.sum()),
+            "throughput_blocks_per_s": done / (t_end - start),
+            "latency_ms": {"p50": float(np.percentile(L_ms, 50)), "p99": float(np.percentile(L_ms, 99)),
+                           "max": float(L_ms.max())},
+            "serving_slices": ctx.stats()["serving_slices"], "precision": args.prec}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,10 +491,17 @@ def main():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
     ap.add_argument("--ref-sample", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed"],
+    ap.add_argument("--rate", type=float, default=50000.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: measured seconds")
+    ap.add_argument("--warm-s", type=float, default=1.0, help="serving: warm-up seconds")
+    ap.add_argument("--gauss-share", type=float, default=0.5, help="serving: share of Gaussian dictionaries")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM budget")
+    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed", "serve"],
                     help="img512 is the headline; the others are secondary measurements")
     ap.add_argument("--blocks", type=int, default=0, help="block count for --workload gauss1080/mixed")
     args = ap.parse_args()
+    if args.workload == "serve":
+        return run_serve(args)
     if args.workload != "img512":
         return run_workload(args)
     if args.impl == "reference":

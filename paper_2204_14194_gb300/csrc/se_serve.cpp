@@ -8,9 +8,11 @@
 // the device.  A batch holds requests of one plan (any mix of per-request
 // iteration counts).  Completion is detected with events; results are
 // copied into the caller's buffers by the scheduler, and se_poll waits on a
-// condition variable.  Every result is computed by the same kernels with the
-// same per-block arithmetic as se_extrapolate_batch, so it does not depend on
-// which other requests shared its batch.
+// condition variable.  Requests with their own support mask go through the
+// per-block-mask (lazy column) path inside the same lane.  Every result is
+// computed by the same kernels with the same per-block arithmetic as
+// se_extrapolate_batch, so it does not depend on which other requests shared
+// its batch.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -39,15 +41,18 @@ namespace {
 
 // Byte offsets of one lane batch inside its I/O buffer.
 struct IoLayout {
-    size_t samples, out, idx, coef, total;
+    size_t samples, masks, out, idx, coef, total;
 };
 
+// samples | masks (requests with their own support) | out | logs; the H2D copy
+// covers [samples, out), the D2H copy [out, total).
 IoLayout io_layout(int n, int MN, int I)
 {
     auto r16 = [](size_t v) { return (v + 15) / 16 * 16; };
     IoLayout L;
     L.samples = 0;
-    L.out = r16(sizeof(double) * MN * static_cast<size_t>(n));
+    L.masks = r16(sizeof(double) * MN * static_cast<size_t>(n));
+    L.out = L.masks + r16(static_cast<size_t>(MN) * n);
     L.idx = L.out + r16(sizeof(double) * MN * static_cast<size_t>(n));
     L.coef = L.idx + r16(sizeof(int32_t) * I * static_cast<size_t>(n));
     L.total = L.coef + r16(sizeof(double) * I * static_cast<size_t>(n));
@@ -127,23 +132,43 @@ bool launch(se_ctx_s *ctx, ServeLane &lane, std::vector<std::shared_ptr<ServeReq
         return true;
     }
     char *d = static_cast<char *>(lane.d_io.ptr);
-    std::vector<BlockDesc> desc(n);
+    // requests on the plan's pattern use the full table, requests with their
+    // own mask (or every request when the plan forces LAZY) lazy columns
+    std::vector<BlockDesc> full, lazy;
+    int I_full = 0, I_lazy = 0;
     for (int i = 0; i < n; ++i) {
         ServeReq &r = *lane.batch[i];
         std::memcpy(lane.h_io + L.samples + sizeof(double) * MN * i, r.samples.data(),
                     sizeof(double) * MN);
-        desc[i].samples = reinterpret_cast<const double *>(d + L.samples) + static_cast<size_t>(MN) * i;
-        desc[i].support = nullptr;
-        desc[i].out = reinterpret_cast<double *>(d + L.out) + static_cast<size_t>(MN) * i;
-        desc[i].sel_idx = reinterpret_cast<int32_t *>(d + L.idx) + static_cast<size_t>(I_max) * i;
-        desc[i].sel_coef = reinterpret_cast<double *>(d + L.coef) + static_cast<size_t>(I_max) * i;
-        desc[i].iterations = r.iterations;
-        desc[i].pad_ = 0;
+        BlockDesc x;
+        x.samples = reinterpret_cast<const double *>(d + L.samples) + static_cast<size_t>(MN) * i;
+        x.support = nullptr;
+        if (!r.support.empty()) {
+            std::memcpy(lane.h_io + L.masks + static_cast<size_t>(MN) * i, r.support.data(), MN);
+            x.support = reinterpret_cast<const uint8_t *>(d + L.masks) + static_cast<size_t>(MN) * i;
+        } else if (pl->desc.gram == SE_GRAM_LAZY) {
+            x.support = pl->d_pattern.as<uint8_t>();
+        }
+        x.out = reinterpret_cast<double *>(d + L.out) + static_cast<size_t>(MN) * i;
+        x.sel_idx = reinterpret_cast<int32_t *>(d + L.idx) + static_cast<size_t>(I_max) * i;
+        x.sel_coef = reinterpret_cast<double *>(d + L.coef) + static_cast<size_t>(I_max) * i;
+        x.iterations = r.iterations;
+        x.pad_ = 0;
+        if (x.support) {
+            lazy.push_back(x);
+            I_lazy = std::max(I_lazy, x.iterations);
+        } else {
+            full.push_back(x);
+            I_full = std::max(I_full, x.iterations);
+        }
     }
-    cudaError_t e = cudaMemcpyAsync(d + L.samples, lane.h_io + L.samples, sizeof(double) * MN * n,
+    cudaError_t e = cudaMemcpyAsync(d + L.samples, lane.h_io + L.samples, L.out - L.samples,
                                     cudaMemcpyHostToDevice, lane.st);
     if (e == cudaSuccess) {
-        s = run_batch(ctx, pl, lane.ws, n, desc.data(), I_max, lane.st);
+        if (!full.empty())
+            s = run_batch(ctx, pl, lane.ws, static_cast<int>(full.size()), full.data(), I_full, lane.st);
+        if (s == SE_OK && !lazy.empty())
+            s = run_lazy(ctx, pl, lane.ws, static_cast<int>(lazy.size()), lazy.data(), I_lazy, lane.st);
         if (s == SE_OK) {
             e = cudaMemcpyAsync(lane.h_io + L.out, d + L.out, L.total - L.out, cudaMemcpyDeviceToHost,
                                 lane.st);
@@ -244,13 +269,15 @@ se_status se_submit(se_ctx_t *ctx, const se_plan_t *plan, const se_request *req,
     if (plan->ctx != ctx) return set_error(SE_ERR_INVALID, "plan belongs to another context");
     if (!req->samples || !req->out) return set_error(SE_ERR_INVALID, "NULL samples or out");
     if (req->iterations < 0) return set_error(SE_ERR_INVALID, "iterations < 0");
-    if (req->support) return set_error(SE_ERR_INVALID, "per-request support masks need the lazy table path");
+    if (req->support && plan->desc.gram == SE_GRAM_FULL)
+        return set_error(SE_ERR_INVALID, "per-request support masks need the lazy table path (plan gram is FULL)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(SE_ERR_CUDA, "cudaSetDevice failed");
     se_status s = ensure_server(ctx);
     if (s != SE_OK) return s;
     auto r = std::make_shared<ServeReq>();
     r->plan = const_cast<se_plan_s *>(plan);
     r->samples.assign(req->samples, req->samples + plan->MN);
+    if (req->support) r->support.assign(req->support, req->support + plan->MN);
     r->out = req->out;
     r->sel_idx = req->sel_idx;
     r->sel_coef = req->sel_coef;

@@ -113,3 +113,45 @@ def test_budget_too_small_rejects(ctx):
         assert e.value.status == -2
     finally:
         small.close()
+
+
+def test_masked_requests_alone_equal_mixed(ctx):
+    """Requests with their own support masks (lazy columns inside the serving
+    lanes) give bitwise the same result alone and mixed with pattern requests."""
+    p16 = ctx.plan(16, 16, "dct_wht", 512, 0.8, 0.5, 120, prec="bf16x6")
+    rng = np.random.default_rng(11)
+    samples = [W.patch(16, 1200 + i) for i in range(40)]
+    masks = [W.rect_support(16, 16, rng) if i % 2 else W.holes_support(16, 16, rng) for i in range(40)]
+    iters = [int(v) for v in rng.integers(30, 121, size=40)]
+
+    def run(indices, with_mask):
+        tick = []
+        for i in indices:
+            out = np.empty((16, 16))
+            u = np.empty(iters[i], dtype=np.int32)
+            t = ctx.submit(p16, samples[i], out, u, None, iterations=iters[i],
+                           support=masks[i] if with_mask[i] else None)
+            tick.append((i, t, out, u))
+        res = {}
+        for i, t, out, u in tick:
+            st, lat = ctx.poll(t, timeout_us=60_000_000)
+            assert st == B.SE_OK
+            res[i] = (out, u)
+        return res
+
+    with_mask = [i % 3 != 0 for i in range(40)]
+    alone = run([5], with_mask)
+    mixed = run(list(range(40)), with_mask)
+    np.testing.assert_array_equal(alone[5][0], mixed[5][0])
+    np.testing.assert_array_equal(alone[5][1], mixed[5][1])
+    # and the same as the batched entry point with the same mask
+    s = torch.from_numpy(samples[5][None].copy()).cuda()
+    m = torch.from_numpy(masks[5]).cuda()
+    o = torch.empty_like(s)
+    ud = torch.empty(iters[5], dtype=torch.int32, device="cuda")
+    p16.extrapolate_batch([{"samples": s[0], "support": m, "out": o[0], "sel_idx": ud,
+                            "iterations": iters[5]}])
+    ctx.sync()
+    np.testing.assert_array_equal(o.cpu().numpy()[0], mixed[5][0])
+    np.testing.assert_array_equal(ud.cpu().numpy(), mixed[5][1])
+    p16.close()
