@@ -46,6 +46,22 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Weak scaling: every rank processes its own units; value = all units / job time."""
+    return world * units_per_rank * steps / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -208,12 +224,8 @@ def run_ours(args):
     launches = ctx.stats()["kernel_launches"] - launches0
     stages = ctx.stage_times(reset=True)
     ctx.set_profiling(False)
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * n * args.steps / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms))
+    value = job_throughput(n, ws, args.steps, total_ms / 1000.0)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     s_h = torch.from_numpy(wl.samples).pin_memory()
@@ -225,12 +237,8 @@ def run_ours(args):
     for _ in range(args.steps):
         plan.reset_tables()
         plan.extrapolate_host(s_h, o_h)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = ws * n * args.steps / e2e_s if ws == 1 else None
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_value = ws * n * args.steps / float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_value = job_throughput(n, ws, args.steps, e2e_s)
 
     # ---- error against the fp64 form, and the fp64 form's own throughput
     out_m, u_m, c_m = out_d.cpu().numpy(), u_d.cpu().numpy(), c_d.cpu().numpy()
