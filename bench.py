@@ -36,7 +36,7 @@ UNIT = "blocks/s"
 WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # dram__bytes_read.sum + dram__bytes_write.sum of one iterate_f32_kernel launch
 # on this workload (ncu, see profiles/); None once the kernel changes.
-TRAFFIC_ITERATE = 92.73e6
+TRAFFIC_ITERATE = None
 
 
 def _dist():

@@ -238,7 +238,9 @@ se_status se_stats(se_ctx_t *ctx, uint64_t *kernel_launches, uint64_t *table_bui
  * on the launching stream around each stage of every batch and accumulates
  * their durations after the batch completes (read with se_stage_times).
  * Stages: 0 operand packing, 1 table generation (Alg. 2, only when rebuilt),
- * 2 initial projections (eq. 12), 3 iterations and replacement (Alg. 3).
+ * 2 initial projections (eq. 12), 3 iterations (Alg. 3; for the fp64 form
+ * and for per-block masks this includes the model and replacement), 4 model
+ * evaluation and replacement (eq. 9, the fp32 shared-pattern form).
  * se_stage_times synchronises the context's outstanding batches, writes up
  * to n_stages accumulated milliseconds and launch counts (either pointer may
  * be NULL) and, if reset != 0, clears the accumulators. */

@@ -29,7 +29,7 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc"]
-STAGES = ["pack", "tables", "projections", "iterate"]
+STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
 class SeError(RuntimeError):
@@ -163,10 +163,10 @@ class Context:
 
     def stage_times(self, reset: bool = True):
         """{stage: (milliseconds, launches)} accumulated since the last reset."""
-        ms = (C.c_double * 4)()
-        cnt = (C.c_uint64 * 4)()
-        _check(self._lib.se_stage_times(self.handle, ms, cnt, 4, int(bool(reset))), "se_stage_times")
-        return {STAGES[i]: (ms[i], cnt[i]) for i in range(4)}
+        ms = (C.c_double * len(STAGES))()
+        cnt = (C.c_uint64 * len(STAGES))()
+        _check(self._lib.se_stage_times(self.handle, ms, cnt, len(STAGES), int(bool(reset))), "se_stage_times")
+        return {STAGES[i]: (ms[i], cnt[i]) for i in range(len(STAGES))}
 
     def plan(self, M: int, N: int, basis: str, K: int, rho_hat: float, gamma: float,
              iterations: int, prec: str = "bf16x6", gram: str = "auto",

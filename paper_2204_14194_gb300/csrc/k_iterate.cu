@@ -390,7 +390,15 @@ iterate_f32_kernel(const IterArgs a)
             if (SE_ITER_ASYNC == 2 && more && tid == 0)
                 bulk_row(myT, trow, static_cast<uint32_t>(Kp * sizeof(float)), myBar);
             const float c = gamma * ru * __ldg(Dk + u);
-            if (tid == 0) { logU[nu] = u; logC[nu] = c; }
+            if (tid == 0) {
+                if (a.log_u) {
+                    a.log_u[static_cast<size_t>(b) * a.I_max + nu] = u;
+                    a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
+                } else {
+                    logU[nu] = u;
+                    logC[nu] = c;
+                }
+            }
             if (!more) break;
 
             m[0] = m[1] = m[2] = m[3] = 0.0f;
@@ -427,22 +435,26 @@ iterate_f32_kernel(const IterArgs a)
         }
         if constexpr (W > 1) __syncthreads(); else __syncwarp();
         if (failed) break;
+        if (a.log_u) continue;                  // the model kernel evaluates the model
 
         const double *smp = bd.samples;
         double *out = bd.out;
         const float *PhiB = static_cast<const float *>(a.PhiB);
-        for (int j = tid; j < a.nB; j += NT) {
-            // four independent partial sums keep four row gathers in flight
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            int nu = 0;
-            for (; nu + 4 <= I; nu += 4) {
+        // model on the loss pixels: each thread owns 8 pixels per pass and walks
+        // the selection log once, so every logged atom's row is read with 8
+        // independent coalesced loads in flight
+        for (int j0 = tid; j0 < a.nB; j0 += 8 * NT) {
+            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            for (int nu = 0; nu < I; ++nu) {
+                const float cn = logC[nu];
+                const float *row = PhiB + static_cast<size_t>(logU[nu]) * a.nB + j0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    acc[q] = fmaf(logC[nu + q], __ldg(PhiB + static_cast<size_t>(logU[nu + q]) * a.nB + j), acc[q]);
+                for (int q = 0; q < 8; ++q)
+                    if (j0 + q * NT < a.nB) acc[q] = fmaf(cn, __ldg(row + q * NT), acc[q]);
             }
-            for (; nu < I; ++nu)
-                acc[0] = fmaf(logC[nu], __ldg(PhiB + static_cast<size_t>(logU[nu]) * a.nB + j), acc[0]);
-            out[a.b_idx[j]] = static_cast<double>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q * NT < a.nB) out[a.b_idx[j0 + q * NT]] = static_cast<double>(acc[q]);
         }
         for (int p = tid; p < a.MN; p += NT)
             if (a.pat_support[p]) out[p] = smp[p];
@@ -452,6 +464,56 @@ iterate_f32_kernel(const IterArgs a)
             for (int nu = tid; nu < I; nu += NT) bd.sel_coef[nu] = static_cast<double>(logC[nu]);
         if constexpr (W > 1) __syncthreads(); else __syncwarp();
     }
+}
+
+
+// Model on the loss pixels (eq. 9) and replacement for the fp32 form, from
+// the selection log: one warp per block, each lane owning 8 loss pixels per
+// pass, the log walked once with the 8 row gathers of four logged atoms in
+// flight; support pixels are copied from the samples; user logs filled.
+__global__ void __launch_bounds__(256) model_f32_kernel(const IterArgs a)
+{
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= a.n) return;
+    const BlockDesc bd = a.blocks[b];
+    const int I = bd.iterations;
+    const int *lu = a.log_u + static_cast<size_t>(b) * a.I_max;
+    const float *lc = a.log_c + static_cast<size_t>(b) * a.I_max;
+    const float *PhiB = static_cast<const float *>(a.PhiB);
+    for (int j0 = lane; j0 < a.nB; j0 += 256) {
+        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        int nu = 0;
+        for (; nu + 4 <= I; nu += 4) {
+            const float *r[4];
+            float cn[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                r[t] = PhiB + static_cast<size_t>(lu[nu + t]) * a.nB + j0;
+                cn[t] = lc[nu + t];
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (j0 + q * 32 < a.nB) acc[q] = fmaf(cn[t], __ldg(r[t] + q * 32), acc[q]);
+        }
+        for (; nu < I; ++nu) {
+            const float *r0 = PhiB + static_cast<size_t>(lu[nu]) * a.nB + j0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (j0 + q * 32 < a.nB) acc[q] = fmaf(lc[nu], __ldg(r0 + q * 32), acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (j0 + q * 32 < a.nB) bd.out[a.b_idx[j0 + q * 32]] = static_cast<double>(acc[q]);
+    }
+    for (int p = lane; p < a.MN; p += 32)
+        if (a.pat_support[p]) bd.out[p] = bd.samples[p];
+    if (bd.sel_idx)
+        for (int nu = lane; nu < I; nu += 32) bd.sel_idx[nu] = lu[nu];
+    if (bd.sel_coef)
+        for (int nu = lane; nu < I; nu += 32) bd.sel_coef[nu] = static_cast<double>(lc[nu]);
 }
 
 template <int W, int VPT, int BPC>
@@ -514,6 +576,13 @@ int iterate_kp(int K, bool fp64)
     for (int i = 0; i < 6; ++i)
         if (K <= caps[i]) return caps[i];
     return -1;
+}
+
+cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    model_f32_kernel<<<(a.n + 7) / 8, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <>

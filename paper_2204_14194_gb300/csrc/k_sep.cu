@@ -10,6 +10,8 @@
 //                          sum w phi_k^2 = sum w t_p^2 t'_q^2)
 //   mode 2  C_b(:, u)     x = rho m_b phi_u               (eq. 16 column; phi_u
 //                          rebuilt from its two 1-D rows)
+//   mode 3  C(:, i)       x = rho m phi_i on the shared pattern (table rows of
+//                          Alg. 2 one atom per item)
 // A dictionary may hold two transforms (the DCT u WHT union); transform t
 // writes atoms koff[t] + p N + q.  One CTA per item, the item's x and the
 // intermediate Z = x T_N^T staged in shared memory with the 1-D bases.
@@ -34,10 +36,18 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
     T *Tn = Tm + M * M;                           // [N][N]
 
     const int b = a.item_blk ? a.item_blk[i] : i;
-    const BlockDesc bd = a.blocks[b];
+    const uint8_t *mask;
+    const double *smp = nullptr;
     const T *rowM = nullptr, *rowN = nullptr;
-    if (a.mode == 2) {
-        const int u = a.cur_u[b];
+    if (a.mode == 3) {
+        mask = a.pattern;
+    } else {
+        const BlockDesc bd = a.blocks[b];
+        mask = bd.support ? bd.support : a.pattern;
+        smp = bd.samples;
+    }
+    if (a.mode >= 2) {
+        const int u = a.mode == 3 ? i : a.cur_u[b];
         const int t = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
         const int ku = u - a.koff[t];
         rowM = static_cast<const T *>(a.TM[t]) + static_cast<size_t>(ku / N) * M;
@@ -45,9 +55,9 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
     }
     for (int p = threadIdx.x; p < MN; p += blockDim.x) {
         const int m = p / N, n = p - m * N;
-        T v = bd.support[p] ? static_cast<T>(a.rho[p]) : T(0);
-        if (a.mode == 0) v = bd.support[p] ? v * static_cast<T>(bd.samples[p]) : T(0);
-        else if (a.mode == 2) v *= rowM[m] * rowN[n];
+        T v = mask[p] ? static_cast<T>(a.rho[p]) : T(0);
+        if (a.mode == 0) v = mask[p] ? v * static_cast<T>(smp[p]) : T(0);
+        else if (a.mode >= 2) v *= rowM[m] * rowN[n];
         X[p] = v;
     }
     T *out = static_cast<T *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
@@ -82,7 +92,7 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
             const T *tr = Tm + p * M;
             T acc = T(0);
             for (int m = 0; m < M; ++m) acc = fma(tr[m], Z[m * N + q], acc);
-            out[a.koff[t] + e] = acc;
+            out[a.koff[t] + e] = acc * (sizeof(T) == 4 && a.scale ? static_cast<T>(a.scale[a.koff[t] + e]) : T(1));
         }
     }
 }
@@ -105,10 +115,18 @@ __global__ void __launch_bounds__(256) sep_tiled_kernel(const SepArgs a)
     float *TnT = TmT + M * M;                       // [N][N]
 
     const int b = a.item_blk ? a.item_blk[i] : i;
-    const BlockDesc bd = a.blocks[b];
+    const uint8_t *mask;
+    const double *smp = nullptr;
     const float *rowM = nullptr, *rowN = nullptr;
-    if (a.mode == 2) {
-        const int u = a.cur_u[b];
+    if (a.mode == 3) {
+        mask = a.pattern;
+    } else {
+        const BlockDesc bd = a.blocks[b];
+        mask = bd.support ? bd.support : a.pattern;
+        smp = bd.samples;
+    }
+    if (a.mode >= 2) {
+        const int u = a.mode == 3 ? i : a.cur_u[b];
         const int t = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
         const int ku = u - a.koff[t];
         rowM = static_cast<const float *>(a.TM[t]) + static_cast<size_t>(ku / N) * M;
@@ -116,12 +134,13 @@ __global__ void __launch_bounds__(256) sep_tiled_kernel(const SepArgs a)
     }
     for (int p = threadIdx.x; p < MN; p += blockDim.x) {
         const int m = p / N, n = p - m * N;
-        float v = bd.support[p] ? static_cast<float>(a.rho[p]) : 0.0f;
-        if (a.mode == 0) v = bd.support[p] ? v * static_cast<float>(bd.samples[p]) : 0.0f;
-        else if (a.mode == 2) v *= rowM[m] * rowN[n];
+        float v = mask[p] ? static_cast<float>(a.rho[p]) : 0.0f;
+        if (a.mode == 0) v = mask[p] ? v * static_cast<float>(smp[p]) : 0.0f;
+        else if (a.mode >= 2) v *= rowM[m] * rowN[n];
         XT[n * M + m] = v;
     }
     float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
+    const float *scale = a.scale;
     const int tilesM = M / 4, tilesN = N / 4;
 
     for (int t = 0; t < a.ntr; ++t) {
@@ -170,9 +189,14 @@ __global__ void __launch_bounds__(256) sep_tiled_kernel(const SepArgs a)
                     for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(ts[r], zs[c], acc[r][c]);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) out[a.koff[t] + (p0 + r) * N + q0 + c] = acc[r][c];
+            for (int r = 0; r < 4; ++r) {
+                const int k0 = a.koff[t] + (p0 + r) * N + q0;
+                if (scale) {
+                    const float4 sv = *reinterpret_cast<const float4 *>(scale + k0);
+                    acc[r][0] *= sv.x; acc[r][1] *= sv.y; acc[r][2] *= sv.z; acc[r][3] *= sv.w;
+                }
+                *reinterpret_cast<float4 *>(out + k0) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            }
         }
     }
 }

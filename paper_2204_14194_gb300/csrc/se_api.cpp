@@ -243,9 +243,12 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
                  need_r0 = tsz * Kp * static_cast<size_t>(n);
     if (ws.desc.bytes < need_desc || ws.x.bytes < need_x || ws.r0.bytes < need_r0)
         SE_CUDA(cudaEventSynchronize(ws.ev_ws));
+    const size_t need_logs = fp64 ? 16 : 8 * static_cast<size_t>(n) * I_max;
+    if (ws.logs.bytes < need_logs) SE_CUDA(cudaEventSynchronize(ws.ev_ws));
     SE_TRY(dev_alloc(ctx, ws.desc, need_desc));
     SE_TRY(dev_alloc(ctx, ws.x, need_x));
     SE_TRY(dev_alloc(ctx, ws.r0, need_r0));
+    SE_TRY(dev_alloc(ctx, ws.logs, need_logs));
 
     // pinned staging of the descriptors: free once the previous copy landed
     SE_CUDA(cudaEventSynchronize(ws.ev_staging));
@@ -325,11 +328,21 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     a.gamma = pl->desc.gamma;
     a.I_max = I_max;
     a.err = ctx->ws_err.as<int>();
+    if (!fp64) {
+        a.log_u = ws.logs.as<int>();
+        a.log_c = reinterpret_cast<float *>(ws.logs.as<int>() + static_cast<size_t>(n) * I_max);
+    }
     int launched = 0;
     tok = stage_begin(ctx, 3, st);
     cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched)
                          : launch_iterate_full<float>(a, st, &launched);
     stage_end(ctx, tok, st);
+    if (e == cudaSuccess && !fp64) {
+        tok = stage_begin(ctx, 4, st);
+        e = launch_model_f32(a, st);
+        stage_end(ctx, tok, st);
+        ++launched;
+    }
     if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("iteration kernel: ") + cudaGetErrorString(e));
     ctx->launches += launched;
     SE_CUDA(cudaEventRecord(ws.ev_ws, st));

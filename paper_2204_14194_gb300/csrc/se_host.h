@@ -46,7 +46,7 @@ struct DevBuf {
 // Device workspace of one in-flight batch (descriptors, packed operands,
 // initial projections, host-call I/O) with its pinned descriptor staging.
 struct Workspace {
-    DevBuf desc, x, r0, io;
+    DevBuf desc, x, r0, io, logs;
     // per-block-mask (lazy) path
     DevBuf lz_R, lz_D, lz_diag, lz_slot, lz_nslots, lz_cache, lz_ulog, lz_clog, lz_cur, lz_miss,
         lz_x, lz_mk, lz_v;
@@ -122,13 +122,13 @@ struct se_ctx_s {
     se::DevBuf ws_err;                    // device status word shared by all kernels
 
     // per-stage timing (se_set_profiling)
-    static constexpr int kStages = 4;
+    static constexpr int kStages = 5;
     bool profiling = false;
     std::mutex pmu;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;   // stage, (start, stop)
     std::vector<cudaEvent_t> event_pool;
-    double stage_ms[kStages] = {0, 0, 0, 0};
-    uint64_t stage_count[kStages] = {0, 0, 0, 0};
+    double stage_ms[kStages] = {0, 0, 0, 0, 0};
+    uint64_t stage_count[kStages] = {0, 0, 0, 0, 0};
 
     std::atomic<uint64_t> launches{0};
     std::atomic<uint64_t> table_builds{0};

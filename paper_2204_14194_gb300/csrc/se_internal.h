@@ -104,7 +104,8 @@ struct IterArgs {
     double gamma;
     int I_max;              // largest iteration count in the batch
     int *err;
-    int *work_counter;      // persistent scheduling counter (zeroed by the launcher)
+    int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
+    float *log_c;           //   model kernel; NULL: the iteration kernel evaluates the model
 };
 template <typename T>
 cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches);
@@ -149,8 +150,11 @@ struct SepArgs {
     const void *TM[2];          // [M][M] 1-D basis rows of transform t (T)
     const void *TN[2];          // [N][N]
     int koff[2];                // first atom index of transform t
-    int mode;                   // 0: R0, 1: diagonal, 2: column of the current atom
-    const BlockDesc *blocks;    // support = the block's mask
+    int mode;                   // 0: R0, 1: diagonal, 2: column of the current atom,
+                                // 3: column of atom i (item i) on the pattern
+    const BlockDesc *blocks;    // support = the block's mask (NULL: pattern)
+    const uint8_t *pattern;     // mask used when a block's support is NULL, and by mode 3
+    const float *scale;         // optional per-atom factor applied to every output (fp32 form)
     const double *rho;          // [MN] weights of eq. (5) without the mask
     const int *n_dev;           // optional live item count
     const int *item_blk;        // optional block of item i (mode 2), else i
@@ -161,6 +165,10 @@ struct SepArgs {
     int n;
 };
 template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st);
+
+// Model on the loss pixels and replacement from the selection log written by
+// the fp32 iteration kernel (eq. 9 and the last step of Alg. 3).
+cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st);
 
 // Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
 int iterate_kp(int K, bool fp64);
