@@ -82,6 +82,23 @@ typedef enum {
     SE_GRAM_LAZY = 2
 } se_gram;
 
+/* How the scalar products of the shared-pattern path (table C of eq. 16 and
+ * projections R^(0) of eq. 12) are computed.
+ * DENSE: as matrix products over the support pixels (tensor cores in the
+ * bf16 forms, CUDA cores in FP64).  TRANSFORM: for DCT, WHT and DCT_WHT
+ * dictionaries, whose atoms are products of 1-D basis rows, every weighted
+ * scalar product with a signal is an entry of a separable 2-D transform of
+ * that weighted signal (Sec. VI, eqs. 21-23): fp32 (fp64 in the FP64 form)
+ * transforms on CUDA cores, 2MN(M+N) operations per signal instead of
+ * 2KMN; the bf16 split of `prec` is then not used.  Requires a separable
+ * basis whose transform operands fit in shared memory (else SE_ERR_INVALID).
+ * AUTO: TRANSFORM where it applies, DENSE otherwise. */
+typedef enum {
+    SE_PRODUCTS_AUTO = 0,
+    SE_PRODUCTS_DENSE = 1,
+    SE_PRODUCTS_TRANSFORM = 2
+} se_products;
+
 typedef struct se_ctx_s se_ctx_t;    /* opaque, library-owned */
 typedef struct se_plan_s se_plan_t;  /* opaque, library-owned */
 
@@ -101,6 +118,7 @@ typedef struct {
     int iterations;           /* default I >= 1 (eq. 10: exactly I iterations) */
     se_prec prec;
     se_gram gram;
+    se_products products;     /* scalar products of the shared-pattern path */
 } se_plan_desc;
 
 /* One concealment block for se_extrapolate_batch (all pointers device). */

@@ -23,6 +23,7 @@ SE_ERR = {-1: "SE_ERR_INVALID", -2: "SE_ERR_NOMEM", -3: "SE_ERR_CUDA", -4: "SE_E
 BASIS = {"dct": 1, "wht": 2, "dct_wht": 3, "numeric": 4}
 PREC = {"fp64": 0, "bf16x6": 1, "bf16x3": 3, "bf16": 4}
 GRAM = {"auto": 0, "full": 1, "lazy": 2}
+PRODUCTS = {"auto": 0, "dense": 1, "transform": 2}
 
 # every entry point declared in include/se.h
 EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_plan_reset_tables",
@@ -42,7 +43,7 @@ class PlanDesc(C.Structure):
     _fields_ = [("M", C.c_int), ("N", C.c_int), ("basis", C.c_int), ("K", C.c_int),
                 ("dict", C.c_void_p), ("rho_hat", C.c_double), ("rho", C.c_void_p),
                 ("support", C.c_void_p), ("gamma", C.c_double), ("iterations", C.c_int),
-                ("prec", C.c_int), ("gram", C.c_int)]
+                ("prec", C.c_int), ("gram", C.c_int), ("products", C.c_int)]
 
 
 class Block(C.Structure):
@@ -171,9 +172,9 @@ class Context:
     def plan(self, M: int, N: int, basis: str, K: int, rho_hat: float, gamma: float,
              iterations: int, prec: str = "bf16x6", gram: str = "auto",
              dictionary: Optional[np.ndarray] = None, support: Optional[np.ndarray] = None,
-             rho: Optional[np.ndarray] = None) -> "Plan":
+             rho: Optional[np.ndarray] = None, products: str = "auto") -> "Plan":
         return Plan(self, M, N, basis, K, rho_hat, gamma, iterations, prec, gram, dictionary,
-                    support, rho)
+                    support, rho, products)
 
     # serving -------------------------------------------------------------
     def submit(self, plan: "Plan", samples: np.ndarray, out: np.ndarray,
@@ -204,16 +205,18 @@ class Plan:
     """An se_plan_t.  Host arrays are copied by the library."""
 
     def __init__(self, ctx: Context, M, N, basis, K, rho_hat, gamma, iterations, prec, gram,
-                 dictionary, support, rho):
+                 dictionary, support, rho, products="auto"):
         self.ctx = ctx
         self._lib = ctx._lib
         self.M, self.N, self.K, self.iterations = int(M), int(N), int(K), int(iterations)
         self.prec = prec
+        self.products = products
         d = None if dictionary is None else np.ascontiguousarray(dictionary, dtype=np.float64)
         sup = None if support is None else np.ascontiguousarray(support, dtype=np.uint8)
         rh = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
         desc = PlanDesc(int(M), int(N), BASIS[basis], int(K), _ptr(d), float(rho_hat), _ptr(rh),
-                        _ptr(sup), float(gamma), int(iterations), PREC[prec], GRAM[gram])
+                        _ptr(sup), float(gamma), int(iterations), PREC[prec], GRAM[gram],
+                        PRODUCTS[products])
         h = C.c_void_p()
         _check(self._lib.se_plan(ctx.handle, C.byref(desc), C.byref(h)), "se_plan")
         self.handle = h

@@ -481,35 +481,55 @@ __global__ void __launch_bounds__(256) model_f32_kernel(const IterArgs a)
     const int *lu = a.log_u + static_cast<size_t>(b) * a.I_max;
     const float *lc = a.log_c + static_cast<size_t>(b) * a.I_max;
     const float *PhiB = static_cast<const float *>(a.PhiB);
-    for (int j0 = lane; j0 < a.nB; j0 += 256) {
-        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        int nu = 0;
-        for (; nu + 4 <= I; nu += 4) {
-            const float *r[4];
-            float cn[4];
+
+    // support pixels keep their samples; the loads of a round of 8 pixels per
+    // lane are all issued before the first store
+    for (int p0 = 0; p0 < a.MN; p0 += 256) {
+        bool on[8];
+        double v[8];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                r[t] = PhiB + static_cast<size_t>(lu[nu + t]) * a.nB + j0;
-                cn[t] = lc[nu + t];
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (j0 + q * 32 < a.nB) acc[q] = fmaf(cn[t], __ldg(r[t] + q * 32), acc[q]);
+        for (int q = 0; q < 8; ++q) {
+            const int p = p0 + q * 32 + lane;
+            on[q] = p < a.MN && a.pat_support[p];
         }
-        for (; nu < I; ++nu) {
-            const float *r0 = PhiB + static_cast<size_t>(lu[nu]) * a.nB + j0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (j0 + q * 32 < a.nB) acc[q] = fmaf(lc[nu], __ldg(r0 + q * 32), acc[q]);
+        for (int q = 0; q < 8; ++q) v[q] = on[q] ? bd.samples[p0 + q * 32 + lane] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (on[q]) bd.out[p0 + q * 32 + lane] = v[q];
+    }
+
+    // g on B (eq. 9): lane j0 + 32 q of a chunk of 256 loss pixels sums c_nu
+    // phi_u_nu over the log; 32 log entries per coalesced load, broadcast by
+    // shuffles, 8 atoms' rows in flight
+    for (int c0 = 0; c0 < a.nB; c0 += 256) {   // every lane runs every chunk (shuffles)
+        const int j0 = c0 + lane;
+        float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        for (int nu0 = 0; nu0 < I; nu0 += 32) {
+            const bool live = nu0 + lane < I;
+            const int my_u = live ? lu[nu0 + lane] : 0;
+            const float my_c = live ? lc[nu0 + lane] : 0.0f;   // padded entries add 0 * phi_0
+            const int cnt = min(32, I - nu0);
+            for (int t0 = 0; t0 < cnt; t0 += 8) {
+                float cn[8], ph[8][8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int u = __shfl_sync(0xffffffffu, my_u, t0 + t);
+                    cn[t] = __shfl_sync(0xffffffffu, my_c, t0 + t);
+                    const float *r = PhiB + static_cast<size_t>(u) * a.nB + j0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) ph[t][q] = j0 + q * 32 < a.nB ? __ldg(r + q * 32) : 0.0f;
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[q] = fmaf(cn[t], ph[t][q], acc[q]);
+            }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q)
             if (j0 + q * 32 < a.nB) bd.out[a.b_idx[j0 + q * 32]] = static_cast<double>(acc[q]);
     }
-    for (int p = lane; p < a.MN; p += 32)
-        if (a.pat_support[p]) bd.out[p] = bd.samples[p];
     if (bd.sel_idx)
         for (int nu = lane; nu < I; nu += 32) bd.sel_idx[nu] = lu[nu];
     if (bd.sel_coef)

@@ -13,8 +13,11 @@
 //   mode 3  C(:, i)       x = rho m phi_i on the shared pattern (table rows of
 //                          Alg. 2 one atom per item)
 // A dictionary may hold two transforms (the DCT u WHT union); transform t
-// writes atoms koff[t] + p N + q.  One CTA per item, the item's x and the
-// intermediate Z = x T_N^T staged in shared memory with the 1-D bases.
+// writes atoms koff[t] + p N + q.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
 #include <cuda_runtime.h>
 
 #include "se_internal.h"
@@ -95,132 +98,485 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
             out[a.koff[t] + e] = acc * (sizeof(T) == 4 && a.scale ? static_cast<T>(a.scale[a.koff[t] + e]) : T(1));
         }
     }
+    for (int k = a.koff[a.ntr - 1] + MN + threadIdx.x; k < a.kfill; k += blockDim.x)
+        out[k] = a.scale ? static_cast<T>(NAN) : T(0);
 }
 
-// fp32 form with 4 x 4 register tiles (M, N multiples of 4).  Operands are
-// staged transposed so that every shared-memory read is a float4 shared by
-// the threads of a tile row or column:
-//   XT[n][m] = x[m][n],  TnT[n][q] = t'_q[n],  TmT[m][p] = t_p[m],
-//   Z[m][q] = sum_n XT[n][m] TnT[n][q],   Y[p][q] = sum_m TmT[m][p] Z[m][q].
-__global__ void __launch_bounds__(256) sep_tiled_kernel(const SepArgs a)
+// fp32 form: transform rows resident in shared memory for the CTA's
+// lifetime, one item per group of 64 threads (named barriers per group),
+// TS x TS register tiles with paired FMAs.  Per item and transform t:
+//   U[p][n] = sum_m t_p[m] x[m][n]      (k = m: TmT[m][p..], X[m][n..]),
+//             kept transposed, UT[n][p];
+//   Y[p][q] = sum_n U[p][n] t'_q[n]     (k = n: UT[n][p..], TnT[n][q..]),
+// written to global memory straight from the registers.  x is staged row-major
+// (conflict-free, coalesced); the constant rows are staged transposed once.
+constexpr int kSepGroup = 64;
+
+template <int TS> struct VecT;
+template <> struct VecT<4> {
+    using type = float4;
+    __device__ static void get(const float *p, float (&v)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static void put(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct VecT<2> {
+    using type = float2;
+    __device__ static void get(const float *p, float (&v)[2])
+    {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ static void put(float *p, const float (&v)[2])
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+};
+
+// barrier of one group (ids 1-4; 0 is __syncthreads), immediate ids so that
+// the kernel holds five hardware barriers rather than all sixteen
+__device__ __forceinline__ void group_sync(int id)
 {
-    const int i = blockIdx.x;
-    if (a.n_dev && i >= *a.n_dev) return;
-    if (i >= a.n) return;
-    const int M = a.M, N = a.N, MN = M * N;
+    switch (id) {
+    case 1: asm volatile("bar.sync 1, %0;" ::"n"(kSepGroup) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"n"(kSepGroup) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"n"(kSepGroup) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"n"(kSepGroup) : "memory"); break;
+    }
+}
+
+// acc[r][c] += a[r] * b[c] for a TS x TS tile, two columns per paired FMA
+template <int TS>
+__device__ __forceinline__ void outer_fma(float (&acc)[TS][TS], const float (&av)[TS], const float (&bv)[TS])
+{
+#pragma unroll
+    for (int r = 0; r < TS; ++r)
+#pragma unroll
+        for (int c = 0; c < TS; c += 2) {
+            const float2 o = __ffma2_rn(make_float2(av[r], av[r]), make_float2(bv[c], bv[c + 1]),
+                                        make_float2(acc[r][c], acc[r][c + 1]));
+            acc[r][c] = o.x;
+            acc[r][c + 1] = o.y;
+        }
+}
+
+// Copy the constants' shared-memory image (TmT, TnT per transform, then
+// rho) with coalesced 16-byte loads, eight in flight per thread; mode 1 uses
+// the squared transform rows.
+__device__ __forceinline__ void stage_image(const SepArgs &a, float *dst, int cst_floats, int total_floats)
+{
+    const float4 *src = reinterpret_cast<const float4 *>(a.img);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    const int n4 = (total_floats + 3) / 4;
+    for (int e0 = threadIdx.x; e0 < n4; e0 += 8 * blockDim.x) {
+        float4 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + j * blockDim.x;
+            if (e < n4) v[j] = __ldg(src + e);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + j * blockDim.x;
+            if (e >= n4) continue;
+            float4 w = v[j];
+            if (a.mode == 1 && 4 * e < cst_floats) {
+                w.x *= w.x; w.y *= w.y; w.z *= w.z; w.w *= w.w;
+            }
+            d4[e] = w;
+        }
+    }
+}
+
+template <int TS, int MC, int NC>
+__global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int groups)
+{
+    // MC, NC: compile-time area size (0 = taken from the arguments)
+    const int M = MC ? MC : a.M, N = NC ? NC : a.N, MN = M * N;
     extern __shared__ __align__(16) unsigned char smem[];
-    float *XT = reinterpret_cast<float *>(smem);    // [N][M]
-    float *Z = XT + MN;                             // [M][N]
-    float *TmT = Z + MN;                            // [M][M]
-    float *TnT = TmT + M * M;                       // [N][N]
+    float *cst = reinterpret_cast<float *>(smem);       // per transform: TmT [M][M], TnT [N][N]
+    const int cstride = M * M + N * N;
+    float *Wr = cst + a.ntr * cstride;                  // [MN] rho (unmasked weights)
+    const int g = threadIdx.x / kSepGroup, tg = threadIdx.x % kSepGroup;
+    float *X = Wr + MN + static_cast<size_t>(g) * 2 * MN;   // [M][N]
+    float *UT = X + MN;                                     // [N][M]
 
-    const int b = a.item_blk ? a.item_blk[i] : i;
-    const uint8_t *mask;
-    const double *smp = nullptr;
-    const float *rowM = nullptr, *rowN = nullptr;
-    if (a.mode == 3) {
-        mask = a.pattern;
-    } else {
-        const BlockDesc bd = a.blocks[b];
-        mask = bd.support ? bd.support : a.pattern;
-        smp = bd.samples;
-    }
-    if (a.mode >= 2) {
-        const int u = a.mode == 3 ? i : a.cur_u[b];
-        const int t = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
-        const int ku = u - a.koff[t];
-        rowM = static_cast<const float *>(a.TM[t]) + static_cast<size_t>(ku / N) * M;
-        rowN = static_cast<const float *>(a.TN[t]) + static_cast<size_t>(ku % N) * N;
-    }
-    for (int p = threadIdx.x; p < MN; p += blockDim.x) {
-        const int m = p / N, n = p - m * N;
-        float v = mask[p] ? static_cast<float>(a.rho[p]) : 0.0f;
-        if (a.mode == 0) v = mask[p] ? v * static_cast<float>(smp[p]) : 0.0f;
-        else if (a.mode >= 2) v *= rowM[m] * rowN[n];
-        XT[n * M + m] = v;
-    }
-    float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
-    const float *scale = a.scale;
-    const int tilesM = M / 4, tilesN = N / 4;
+    stage_image(a, cst, a.ntr * cstride, a.ntr * cstride + MN);
+    __syncthreads();
 
-    for (int t = 0; t < a.ntr; ++t) {
-        const float *gm = static_cast<const float *>(a.TM[t]);
-        const float *gn = static_cast<const float *>(a.TN[t]);
-        __syncthreads();
-        for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-            const float v = gm[e];
-            const int p = e / M, m = e - p * M;
-            TmT[m * M + p] = a.mode == 1 ? v * v : v;
+    const int n_items = a.n_dev ? min(a.n, *a.n_dev) : a.n;
+    constexpr int tilesMC = MC / TS, tilesNC = NC / TS;
+    const int tilesM = MC ? tilesMC : M / TS, tilesN = NC ? tilesNC : N / TS;
+    for (int i = blockIdx.x * groups + g; i < n_items; i += gridDim.x * groups) {
+        const int b = a.item_blk ? a.item_blk[i] : i;
+        const uint8_t *mask;
+        const double *smp = nullptr;
+        const float *rowM = nullptr, *rowN = nullptr;   // the 1-D rows of atom u (global)
+        if (a.mode == 3) {
+            mask = a.pattern;
+        } else {
+            const BlockDesc bd = a.blocks[b];
+            mask = bd.support ? bd.support : a.pattern;
+            smp = bd.samples;
         }
-        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-            const float v = gn[e];
-            const int q = e / N, n = e - q * N;
-            TnT[n * N + q] = a.mode == 1 ? v * v : v;
+        if (a.mode >= 2) {
+            const int u = a.mode == 3 ? i : a.cur_u[b];
+            const int t = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
+            const int ku = u - a.koff[t];
+            rowM = static_cast<const float *>(a.TM[t]) + static_cast<size_t>(ku / N) * M;
+            rowN = static_cast<const float *>(a.TN[t]) + static_cast<size_t>(ku % N) * N;
         }
-        __syncthreads();
-        for (int tile = threadIdx.x; tile < tilesM * tilesN; tile += blockDim.x) {
-            const int m0 = 4 * (tile / tilesN), q0 = 4 * (tile % tilesN);
-            float acc[4][4] = {};
-            for (int n = 0; n < N; ++n) {
-                const float4 xv = *reinterpret_cast<const float4 *>(XT + n * M + m0);
-                const float4 tv = *reinterpret_cast<const float4 *>(TnT + n * N + q0);
-                const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ts[4] = {tv.x, tv.y, tv.z, tv.w};
+        // x on the item's support; 8 pixels per thread per round, every load
+        // of a round issued before the first use (samples on B are not read)
+        for (int p0 = 0; p0 < MN; p0 += 8 * kSepGroup) {
+            bool on[8];
+            float ex[8];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(xs[r], ts[c], acc[r][c]);
+            for (int j = 0; j < 8; ++j) {
+                const int p = p0 + j * kSepGroup + tg;
+                on[j] = p < MN && mask[p] != 0;
+                ex[j] = (a.mode >= 2 && p < MN) ? rowM[p / N] * rowN[p % N] : 1.0f;
             }
+            double sv[8];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                *reinterpret_cast<float4 *>(Z + (m0 + r) * N + q0) =
-                    make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-        }
-        __syncthreads();
-        for (int tile = threadIdx.x; tile < tilesM * tilesN; tile += blockDim.x) {
-            const int p0 = 4 * (tile / tilesN), q0 = 4 * (tile % tilesN);
-            float acc[4][4] = {};
-            for (int m = 0; m < M; ++m) {
-                const float4 tv = *reinterpret_cast<const float4 *>(TmT + m * M + p0);
-                const float4 zv = *reinterpret_cast<const float4 *>(Z + m * N + q0);
-                const float ts[4] = {tv.x, tv.y, tv.z, tv.w}, zs[4] = {zv.x, zv.y, zv.z, zv.w};
+            for (int j = 0; j < 8; ++j) sv[j] = (a.mode == 0 && on[j]) ? smp[p0 + j * kSepGroup + tg] : 0.0;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(ts[r], zs[c], acc[r][c]);
+            for (int j = 0; j < 8; ++j) {
+                const int p = p0 + j * kSepGroup + tg;
+                if (p >= MN) continue;
+                float v = on[j] ? Wr[p] : 0.0f;
+                if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
+                else if (a.mode >= 2) v *= ex[j];
+                X[p] = v;
             }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int k0 = a.koff[t] + (p0 + r) * N + q0;
-                if (scale) {
-                    const float4 sv = *reinterpret_cast<const float4 *>(scale + k0);
-                    acc[r][0] *= sv.x; acc[r][1] *= sv.y; acc[r][2] *= sv.z; acc[r][3] *= sv.w;
+        }
+        float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
+        group_sync(1 + g);
+
+        for (int t = 0; t < a.ntr; ++t) {
+            const float *TmT = cst + t * cstride, *TnT = TmT + M * M;
+            if (t) group_sync(1 + g);   // the previous transform is done reading UT
+            for (int tile = tg; tile < tilesM * tilesN; tile += kSepGroup) {
+                const int p0 = TS * (tile / tilesN), n0 = TS * (tile % tilesN);
+                float acc[TS][TS] = {};
+#pragma unroll 8
+                for (int m = 0; m < M; ++m) {
+                    float av[TS], bv[TS];
+                    VecT<TS>::get(TmT + m * M + p0, av);
+                    VecT<TS>::get(X + m * N + n0, bv);
+                    outer_fma<TS>(acc, av, bv);
                 }
-                *reinterpret_cast<float4 *>(out + k0) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+#pragma unroll
+                for (int c = 0; c < TS; ++c) {
+                    float col[TS];
+#pragma unroll
+                    for (int r = 0; r < TS; ++r) col[r] = acc[r][c];
+                    VecT<TS>::put(UT + (n0 + c) * M + p0, col);
+                }
+            }
+            group_sync(1 + g);
+            for (int tile = tg; tile < tilesM * tilesN; tile += kSepGroup) {
+                const int p0 = TS * (tile / tilesN), q0 = TS * (tile % tilesN);
+                float acc[TS][TS] = {};
+#pragma unroll 8
+                for (int n = 0; n < N; ++n) {
+                    float av[TS], bv[TS];
+                    VecT<TS>::get(UT + n * M + p0, av);
+                    VecT<TS>::get(TnT + n * N + q0, bv);
+                    outer_fma<TS>(acc, av, bv);
+                }
+#pragma unroll
+                for (int r = 0; r < TS; ++r) {
+                    const int k0 = a.koff[t] + (p0 + r) * N + q0;
+                    if (a.scale) {
+                        float sv[TS];
+                        VecT<TS>::get(a.scale + k0, sv);
+#pragma unroll
+                        for (int c = 0; c < TS; ++c) acc[r][c] *= sv[c];
+                    }
+                    VecT<TS>::put(out + k0, acc[r]);
+                }
             }
         }
+        for (int k = a.koff[a.ntr - 1] + MN + tg; k < a.kfill; k += kSepGroup)
+            out[k] = a.scale ? NAN : 0.0f;
+        // the next item's X is written only after every thread of the group has
+        // passed the barrier that follows it, i.e. finished this item
+    }
+}
+
+// fp32 form, one warp per item: lane tiles of TP x TQ outputs (the 32 lanes
+// cover (M / TP) x (N / TQ) tiles exactly), so the phases need only warp
+// synchronisation and the 16 warps of an SM work on independent items.
+// Same arithmetic order as sep_group_kernel: U = T_M x over m, then
+// Y = U T_N^T over n.
+template <int Nv>
+__device__ __forceinline__ void lds_vec(const float *p, float (&v)[Nv])
+{
+    if constexpr (Nv % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p + j);
+            v[j] = t.x; v[j + 1] = t.y; v[j + 2] = t.z; v[j + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p + j);
+            v[j] = t.x; v[j + 1] = t.y;
+        }
+    }
+}
+
+template <int Nv>
+__device__ __forceinline__ void sts_vec(float *p, const float (&v)[Nv])
+{
+    if constexpr (Nv % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 4)
+            *reinterpret_cast<float4 *>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 2) *reinterpret_cast<float2 *>(p + j) = make_float2(v[j], v[j + 1]);
+    }
+}
+
+template <int TP, int TQ>
+__device__ __forceinline__ void outer_fma_pq(float (&acc)[TP][TQ], const float (&av)[TP], const float (&bv)[TQ])
+{
+#pragma unroll
+    for (int r = 0; r < TP; ++r)
+#pragma unroll
+        for (int c = 0; c < TQ; c += 2) {
+            const float2 o = __ffma2_rn(make_float2(av[r], av[r]), make_float2(bv[c], bv[c + 1]),
+                                        make_float2(acc[r][c], acc[r][c + 1]));
+            acc[r][c] = o.x;
+            acc[r][c + 1] = o.y;
+        }
+}
+
+template <int M, int N, int TP, int TQ>
+__global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
+{
+    constexpr int MN = M * N, tilesN = N / TQ;
+    static_assert((M / TP) * (N / TQ) == 32, "one tile per lane");
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *cst = reinterpret_cast<float *>(smem);        // per transform: TmT [M][M], TnT [N][N]
+    constexpr int cstride = M * M + N * N;
+    float *Wr = cst + a.ntr * cstride;                   // [MN] rho (unmasked weights)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    float *X = Wr + MN + w * 2 * MN;                     // [M][N]
+    float *UT = X + MN;                                  // [N][M]
+
+    stage_image(a, cst, a.ntr * cstride, a.ntr * cstride + MN);
+    __syncthreads();
+
+    const int n_items = a.n_dev ? min(a.n, *a.n_dev) : a.n;
+    const int p0 = TP * (lane / tilesN), c0 = TQ * (lane % tilesN);
+    for (int i = blockIdx.x * wpc + w; i < n_items; i += gridDim.x * wpc) {
+        const int b = a.item_blk ? a.item_blk[i] : i;
+        const uint8_t *mask;
+        const double *smp = nullptr;
+        const float *rowM = nullptr, *rowN = nullptr;
+        if (a.mode == 3) {
+            mask = a.pattern;
+        } else {
+            const BlockDesc bd = a.blocks[b];
+            mask = bd.support ? bd.support : a.pattern;
+            smp = bd.samples;
+        }
+        if (a.mode >= 2) {
+            const int u = a.mode == 3 ? i : a.cur_u[b];
+            const int t = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
+            const int ku = u - a.koff[t];
+            rowM = static_cast<const float *>(a.TM[t]) + static_cast<size_t>(ku / N) * M;
+            rowN = static_cast<const float *>(a.TN[t]) + static_cast<size_t>(ku % N) * N;
+        }
+        __syncwarp();   // the previous item's last reads of X and UT are done
+        constexpr int R = MN / 32 < 16 ? MN / 32 : 16;
+#pragma unroll 1
+        for (int q0 = 0; q0 < MN; q0 += 32 * R) {
+            bool on[R];
+            float ex[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int p = q0 + j * 32 + lane;
+                on[j] = mask[p] != 0;
+                ex[j] = a.mode >= 2 ? rowM[p / N] * rowN[p % N] : 1.0f;
+            }
+            double sv[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) sv[j] = (a.mode == 0 && on[j]) ? smp[q0 + j * 32 + lane] : 0.0;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int p = q0 + j * 32 + lane;
+                float v = on[j] ? Wr[p] : 0.0f;
+                if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
+                else if (a.mode >= 2) v *= ex[j];
+                X[p] = v;
+            }
+        }
+        float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
+        __syncwarp();
+
+        for (int t = 0; t < a.ntr; ++t) {
+            const float *TmT = cst + t * cstride, *TnT = TmT + M * M;
+            if (t) __syncwarp();   // the previous transform is done reading UT
+            {
+                float acc[TP][TQ] = {};
+#pragma unroll 8
+                for (int m = 0; m < M; ++m) {
+                    float av[TP], bv[TQ];
+                    lds_vec<TP>(TmT + m * M + p0, av);
+                    lds_vec<TQ>(X + m * N + c0, bv);
+                    outer_fma_pq<TP, TQ>(acc, av, bv);
+                }
+#pragma unroll
+                for (int c = 0; c < TQ; ++c) {
+                    float col[TP];
+#pragma unroll
+                    for (int r = 0; r < TP; ++r) col[r] = acc[r][c];
+                    sts_vec<TP>(UT + (c0 + c) * M + p0, col);
+                }
+            }
+            __syncwarp();
+            {
+                float acc[TP][TQ] = {};
+#pragma unroll 8
+                for (int n = 0; n < N; ++n) {
+                    float av[TP], bv[TQ];
+                    lds_vec<TP>(UT + n * M + p0, av);
+                    lds_vec<TQ>(TnT + n * N + c0, bv);
+                    outer_fma_pq<TP, TQ>(acc, av, bv);
+                }
+#pragma unroll
+                for (int r = 0; r < TP; ++r) {
+                    const int k0 = a.koff[t] + (p0 + r) * N + c0;
+                    if (a.scale) {
+                        float sv[TQ];
+                        lds_vec<TQ>(a.scale + k0, sv);
+#pragma unroll
+                        for (int c = 0; c < TQ; ++c) acc[r][c] *= sv[c];
+                    }
+                    sts_vec<TQ>(out + k0, acc[r]);
+                }
+            }
+        }
+        for (int k = a.koff[a.ntr - 1] + MN + lane; k < a.kfill; k += 32)
+            out[k] = a.scale ? NAN : 0.0f;
     }
 }
 
 }  // namespace
 
+// SE_SEP_KERNEL=group selects the 64-thread-group kernel for every size
+// (comparison of the two schedules)
+bool sep_force_group()
+{
+    static const int v = [] {
+        const char *e = std::getenv("SE_SEP_KERNEL");
+        return e && std::strcmp(e, "group") == 0 ? 1 : 0;
+    }();
+    return v != 0;
+}
+
+template <int TS, int MC, int NC>
+cudaError_t launch_sep_group(const SepArgs &a, cudaStream_t st, bool *done)
+{
+    *done = false;
+    const size_t MN = static_cast<size_t>(a.M) * a.N;
+    const size_t cst = 4 * a.ntr * (static_cast<size_t>(a.M) * a.M + static_cast<size_t>(a.N) * a.N) + 4 * MN;
+    int groups = 4;
+    while (groups > 0 && cst + 8 * MN * groups > 227 * 1024) groups /= 2;
+    if (groups == 0) return cudaSuccess;
+    const size_t smem = cst + 8 * MN * groups;
+    static bool attr = false;
+    static int sms = 0;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sep_group_kernel<TS, MC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_group_kernel<TS, MC, NC>,
+                                                                  kSepGroup * groups, smem);
+    if (e != cudaSuccess) return e;
+    const int want = (a.n + groups - 1) / groups;
+    const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
+    sep_group_kernel<TS, MC, NC><<<grid, kSepGroup * groups, smem, st>>>(a, groups);
+    *done = true;
+    return cudaGetLastError();
+}
+
+template <int M, int N, int TP, int TQ>
+cudaError_t launch_sep_warp(const SepArgs &a, cudaStream_t st)
+{
+    constexpr int wpc = 4;
+    const size_t smem = 4 * (a.ntr * static_cast<size_t>(M * M + N * N) + M * N + 2 * M * N * wpc);
+    static bool attr = false;
+    static int sms = 0;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sep_warp_kernel<M, N, TP, TQ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_warp_kernel<M, N, TP, TQ>,
+                                                                  32 * wpc, smem);
+    if (e != cudaSuccess) return e;
+    const int want = (a.n + wpc - 1) / wpc;
+    const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
+    sep_warp_kernel<M, N, TP, TQ><<<grid, 32 * wpc, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_sep(const SepArgs &a, cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (sizeof(T) == 4) {
+        bool done = false;
+        cudaError_t e = cudaSuccess;
+        if (a.M == 32 && a.N == 32 && !sep_force_group())
+            return launch_sep_warp<32, 32, 8, 4>(a, st);
+        if (a.M == 16 && a.N == 16 && !sep_force_group())
+            return launch_sep_warp<16, 16, 4, 2>(a, st);
+        if (a.M == 32 && a.N == 32)
+            e = launch_sep_group<4, 32, 32>(a, st, &done);
+        else if (a.M == 64 && a.N == 64)
+            e = launch_sep_group<4, 64, 64>(a, st, &done);
+        else if (a.M == 16 && a.N == 16)
+            e = launch_sep_group<2, 16, 16>(a, st, &done);
+        else if (a.M % 4 == 0 && a.N % 4 == 0 && a.M * a.N >= 1024)
+            e = launch_sep_group<4, 0, 0>(a, st, &done);
+        else if (a.M % 2 == 0 && a.N % 2 == 0)
+            e = launch_sep_group<2, 0, 0>(a, st, &done);
+        if (e != cudaSuccess || done) return e;
+    }
     const size_t smem = sizeof(T) * (2 * static_cast<size_t>(a.M) * a.N + a.M * a.M + a.N * a.N);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    const bool tiled = sizeof(T) == 4 && a.M % 4 == 0 && a.N % 4 == 0;
-    static bool attr[2] = {false, false};
-    if (!attr[tiled]) {
-        cudaError_t e = tiled ? cudaFuncSetAttribute(sep_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     227 * 1024)
-                              : cudaFuncSetAttribute(sep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     227 * 1024);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
         if (e != cudaSuccess) return e;
-        attr[tiled] = true;
+        attr = true;
     }
-    if (tiled) sep_tiled_kernel<<<a.n, 256, smem, st>>>(a);
-    else sep_kernel<T><<<a.n, 256, smem, st>>>(a);
+    sep_kernel<T><<<a.n, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -178,6 +178,34 @@ PrecCfg prec_cfg(se_prec p)
 
 }  // namespace se
 
+// Separable-transform products on the plan's pattern: mode 0 gives R^(0)
+// (eq. 12) of every block, mode 3 the rows of C (eq. 16).  In the fp32 form
+// both carry the factor D_k of the recurrence; padded atoms [K, Kp) read NaN
+// there (never selected) and 0 in the fp64 form (zero criterion).
+SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out)
+{
+    SepArgs s{};
+    s.M = pl->M;
+    s.N = pl->N;
+    s.ntr = pl->sep_ntr;
+    for (int t = 0; t < pl->sep_ntr; ++t) {
+        s.TM[t] = pl->d_sepM[t].ptr;
+        s.TN[t] = pl->d_sepN[t].ptr;
+        s.koff[t] = pl->sep_koff[t];
+    }
+    s.mode = mode;
+    s.blocks = dd;
+    s.pattern = pl->d_pattern.as<uint8_t>();
+    s.scale = pl->pc.fp64 ? nullptr : pl->d_Dk.as<float>();
+    s.rho = pl->d_rho.as<double>();
+    s.img = pl->d_sep_img.as<float>();
+    s.out = out;
+    s.ldo = pl->Kp;
+    s.n = n;
+    s.kfill = pl->Kp;
+    return s;
+}
+
 namespace {
 
 se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
@@ -188,7 +216,21 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
     SE_CUDA(launch_tables_diag(pl->d_G64.as<double>(), pl->ka_pad, pl->K, Kp, pl->nA,
                                pl->d_dup.as<uint8_t>(), pl->d_diag.as<double>(), dmax,
                                pl->d_nadm.as<int>(), st));
-    if (pl->pc.fp64) {
+    if (pl->sep_full) {
+        // C(:, i) for every atom i as a separable transform of w phi_i (Sec. VI);
+        // fp32 rows carry the factor D_k of the recurrence
+        if (pl->pc.fp64)
+            SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
+                                                   pl->K, Kp, pl->d_invC.as<double>(),
+                                                   pl->d_Dk.as<double>(), pl->d_nadm.as<int>(), st));
+        else
+            SE_CUDA(launch_tables_finalize<float>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
+                                                  pl->K, Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
+                                                  pl->d_nadm.as<int>(), st));
+        SepArgs sa = pattern_sep_args(pl, 3, nullptr, pl->K, pl->d_C.ptr);
+        SE_CUDA(pl->pc.fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+        ctx->launches += 3;
+    } else if (pl->pc.fp64) {
         SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
                                                pl->K, Kp, pl->d_invC.as<double>(),
                                                pl->d_Dk.as<double>(), pl->d_nadm.as<int>(), st));
@@ -224,6 +266,50 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
     return SE_OK;
 }
 
+// eq. (12) as packing of the weighted support samples and a matrix product
+// with the weighted atoms (tensor cores in the bf16 forms).
+se_status dense_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const BlockDesc *ddesc,
+                                    int n, cudaStream_t st)
+{
+    const int Kp = pl->Kp;
+    const bool fp64 = pl->pc.fp64;
+    std::string why;
+    int tok = stage_begin(ctx, 0, st);
+    if (fp64)
+        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                              pl->ka_pad, 0, pl->MN, nullptr, ws.x.as<double>(), st));
+    else
+        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
+                              pl->ka_pad, pl->pc.nparts, pl->MN, ws.x.as<uint16_t>(), nullptr, st));
+    stage_end(ctx, tok, st);
+    tok = stage_begin(ctx, 2, st);
+    if (fp64) {
+        SE_CUDA(launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad, ws.x.as<double>(),
+                                         pl->ka_pad, Kp, n, pl->ka_pad, ws.r0.as<double>(), Kp,
+                                         0, st));
+    } else {
+        TcGemmArgs g{};
+        g.A = pl->d_Gwbf.ptr;
+        g.B = ws.x.ptr;
+        g.M = Kp;
+        g.N = n;
+        g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
+        g.ka_pad = pl->ka_pad;
+        g.npairs = pl->pc.npairs;
+        for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+        g.out = ws.r0.as<float>();
+        g.ldo = Kp;
+        g.symmetric = 0;
+        g.err = ctx->ws_err.as<int>();
+        g.scale = pl->d_Dk.as<float>();
+        cudaError_t e = launch_tc_gemm(g, st, &why);
+        if (e != cudaSuccess) return fail(SE_ERR_CUDA, "projection GEMM: " + why + " " + cudaGetErrorString(e));
+    }
+    stage_end(ctx, tok, st);
+    ctx->launches += 2;
+    return SE_OK;
+}
+
 }  // namespace
 
 // All blocks use the plan's pattern: Alg. 2 tables (cached), eq. (12) GEMM,
@@ -239,7 +325,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
 
     // the workspace of the previous call must be free before it is reused
     SE_CUDA(cudaStreamWaitEvent(st, ws.ev_ws, 0));
-    const size_t need_desc = sizeof(BlockDesc) * n, need_x = xrow * n,
+    const size_t need_desc = sizeof(BlockDesc) * n, need_x = pl->sep_full ? 16 : xrow * n,
                  need_r0 = tsz * Kp * static_cast<size_t>(n);
     if (ws.desc.bytes < need_desc || ws.x.bytes < need_x || ws.r0.bytes < need_r0)
         SE_CUDA(cudaEventSynchronize(ws.ev_ws));
@@ -276,40 +362,17 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     }
 
     const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
-    std::string why;
-    int tok = stage_begin(ctx, 0, st);
-    if (fp64)
-        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                              pl->ka_pad, 0, pl->MN, nullptr, ws.x.as<double>(), st));
-    else
-        SE_CUDA(launch_pack_x(ddesc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
-                              pl->ka_pad, pl->pc.nparts, pl->MN, ws.x.as<uint16_t>(), nullptr, st));
-    stage_end(ctx, tok, st);
-    tok = stage_begin(ctx, 2, st);
-    if (fp64) {
-        SE_CUDA(launch_simt_gemm<double>(pl->d_G64.as<double>(), pl->ka_pad, ws.x.as<double>(),
-                                         pl->ka_pad, Kp, n, pl->ka_pad, ws.r0.as<double>(), Kp,
-                                         0, st));
+    int tok;
+    if (pl->sep_full) {
+        // eq. (12) as a separable transform of w s per block: no packing stage
+        tok = stage_begin(ctx, 2, st);
+        SepArgs sa = pattern_sep_args(pl, 0, ddesc, n, ws.r0.ptr);
+        SE_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+        stage_end(ctx, tok, st);
+        ctx->launches += 1;
     } else {
-        TcGemmArgs g{};
-        g.A = pl->d_Gwbf.ptr;
-        g.B = ws.x.ptr;
-        g.M = Kp;
-        g.N = n;
-        g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
-        g.ka_pad = pl->ka_pad;
-        g.npairs = pl->pc.npairs;
-        for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
-        g.out = ws.r0.as<float>();
-        g.ldo = Kp;
-        g.symmetric = 0;
-        g.err = ctx->ws_err.as<int>();
-        g.scale = pl->d_Dk.as<float>();
-        cudaError_t e = launch_tc_gemm(g, st, &why);
-        if (e != cudaSuccess) return fail(SE_ERR_CUDA, "projection GEMM: " + why + " " + cudaGetErrorString(e));
+        SE_TRY(dense_pattern_projections(ctx, pl, ws, ddesc, n, st));
     }
-    stage_end(ctx, tok, st);
-    ctx->launches += 2;
 
     IterArgs a{};
     a.blocks = ddesc;
@@ -456,6 +519,8 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         d.prec != SE_PREC_BF16)
         return fail(SE_ERR_INVALID, "unknown precision");
     if (d.gram < SE_GRAM_AUTO || d.gram > SE_GRAM_LAZY) return fail(SE_ERR_INVALID, "unknown table mode");
+    if (d.products < SE_PRODUCTS_AUTO || d.products > SE_PRODUCTS_TRANSFORM)
+        return fail(SE_ERR_INVALID, "unknown product mode");
     SE_CUDA(cudaSetDevice(ctx->device));
 
     auto pl = std::make_unique<se_plan_s>();
@@ -558,6 +623,13 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
                                   pl->d_Gwbf.as<uint16_t>(), ctx->stream));
         SE_CUDA(cudaStreamSynchronize(ctx->stream));
         ctx->launches += 2;
+    }
+    if (d.products != SE_PRODUCTS_DENSE) {
+        SE_TRY(ensure_sep_ops(ctx, pl.get()));
+        if (!pl->sep && d.products == SE_PRODUCTS_TRANSFORM)
+            return fail(SE_ERR_INVALID, "transform products need a DCT / WHT dictionary whose "
+                                        "transforms fit in shared memory");
+        pl->sep_full = pl->sep;
     }
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
     SE_TRY(dev_alloc(ctx, pl->d_C, tsz * Kp * static_cast<size_t>(Kp)));

@@ -175,9 +175,11 @@ struct se_plan_s {
     int MN_pad = 0;
     se::DevBuf d_Phi64, d_PhiT, d_ArBf, d_AdBf, d_Ar64, d_Ad64;
     // transform-domain form for DCT / WHT dictionaries: 1-D bases and rho
-    bool sep = false;
+    bool sep = false, sep_checked = false;
+    bool sep_full = false;       // shared-pattern tables and projections by transforms
     int sep_ntr = 0, sep_koff[2] = {0, 0};
     se::DevBuf d_sepM[2], d_sepN[2], d_rho;
+    se::DevBuf d_sep_img;        // fp32 constants in the transform kernels' shared-memory layout
     cudaEvent_t tables_ready = nullptr;
     std::mutex tmu;
 };
@@ -188,6 +190,14 @@ namespace se {
 se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                     int I_max, cudaStream_t st);
 // Blocks with their own masks (desc.support set for every block): lazy columns.
+// Upload the transform-domain operands (weights without mask, 1-D basis
+// rows) when the plan's dictionary is separable; sets pl->sep.  Idempotent;
+// the caller holds pl->tmu or owns the plan exclusively.
+se_status ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl);
+// Transform-domain products on the plan's pattern (needs pl->sep): mode 0
+// R^(0) of n blocks, mode 3 the first n rows of C, written to out with row
+// pitch Kp.
+SepArgs pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out);
 se_status run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                    int I_max, cudaStream_t st);
 se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);

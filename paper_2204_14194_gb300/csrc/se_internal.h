@@ -163,6 +163,10 @@ struct SepArgs {
     long long ldo;              // row pitch for row b when out_rows is NULL
     const long long *out_rows;  // optional element offset of item i's row
     int n;
+    int kfill;                  // entries [K, kfill) of each row are set to the padding
+                                // value (NaN with scale, else 0); 0 = none
+    const float *img;           // fp32 shared-memory image of the constants: per transform
+                                // TmT [M][M] (t_p[m] at m M + p), TnT [N][N]; then rho [MN]
 };
 template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st);
 

@@ -75,12 +75,29 @@ se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         LZ_CUDA(cudaStreamSynchronize(st));
         ctx->launches += 2;
     }
-    // transform-domain operands when the atoms are products of 1-D bases
+    LZ_TRY(se::ensure_sep_ops(ctx, pl));
+    pl->MN_pad = MNp;
+    pl->lazy_ready = true;
+    return SE_OK;
+}
+
+}  // namespace
+
+// Transform-domain operands when the atoms are products of 1-D bases: the
+// unmasked weights rho and the 1-D basis rows of each transform.
+se_status se::ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl)
+{
+    if (pl->sep_checked) return SE_OK;
+    const int MN = pl->MN;
     const int basis = pl->desc.basis;
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
     const size_t smem = tsz * (2 * static_cast<size_t>(MN) + pl->M * pl->M + pl->N * pl->N);
     if ((basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT) &&
         smem <= 227 * 1024) {
+        std::vector<uint8_t> all(MN, 1);
+        std::vector<double> rho;
+        weighting(pl->M, pl->N, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
+                  all.data(), rho);
         LZ_TRY(upload_vec(ctx, pl->d_rho, rho));
         int t = 0;
         auto add = [&](bool wht, int koff) -> se_status {
@@ -110,11 +127,30 @@ se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         if (basis == SE_BASIS_DCT_WHT) LZ_TRY(add(true, MN));
         pl->sep_ntr = t;
         pl->sep = true;
+        if (!pl->pc.fp64) {
+            // the constants as the fp32 kernels hold them in shared memory
+            const int M = pl->M, N = pl->N;
+            std::vector<float> img;
+            img.reserve(static_cast<size_t>(t) * (M * M + N * N) + MN);
+            for (int k = 0; k < t; ++k) {
+                std::vector<float> tm(static_cast<size_t>(M) * M), tn(static_cast<size_t>(N) * N);
+                LZ_CUDA(cudaMemcpy(tm.data(), pl->d_sepM[k].ptr, tm.size() * 4, cudaMemcpyDeviceToHost));
+                LZ_CUDA(cudaMemcpy(tn.data(), pl->d_sepN[k].ptr, tn.size() * 4, cudaMemcpyDeviceToHost));
+                for (int m = 0; m < M; ++m)
+                    for (int p = 0; p < M; ++p) img.push_back(tm[static_cast<size_t>(p) * M + m]);
+                for (int n = 0; n < N; ++n)
+                    for (int q = 0; q < N; ++q) img.push_back(tn[static_cast<size_t>(q) * N + n]);
+            }
+            for (int p = 0; p < MN; ++p) img.push_back(static_cast<float>(rho[p]));
+            while (img.size() % 4) img.push_back(0.0f);
+            LZ_TRY(upload_vec(ctx, pl->d_sep_img, img));
+        }
     }
-    pl->MN_pad = MNp;
-    pl->lazy_ready = true;
+    pl->sep_checked = true;
     return SE_OK;
 }
+
+namespace {
 
 SepArgs sep_args(se_plan_s *pl, const BlockDesc *dd, int nw, int mode, void *out, long long ldo)
 {
@@ -130,6 +166,7 @@ SepArgs sep_args(se_plan_s *pl, const BlockDesc *dd, int nw, int mode, void *out
     s.mode = mode;
     s.blocks = dd;
     s.rho = pl->d_rho.as<double>();
+    s.img = pl->d_sep_img.as<float>();
     s.out = out;
     s.ldo = ldo;
     s.n = nw;

@@ -97,10 +97,10 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     // scratch layout: descriptors | packed samples | initial projections
     const size_t desc_b = r256(sizeof(BlockDesc) * static_cast<size_t>(n));
     const size_t xrow = fp64 ? sizeof(double) * pl->ka_pad : 2u * pl->pc.nparts * pl->ka_pad;
-    const size_t x_b = r256(xrow * n);
+    const size_t x_b = pl->sep_full ? 0 : r256(xrow * n);
     const size_t r_b = (fp64 ? sizeof(double) : sizeof(float)) * Kp * static_cast<size_t>(n);
     if (desc_b + x_b + r_b > kScratchBytes) {
-        const size_t per = sizeof(BlockDesc) + xrow + (fp64 ? 8 : 4) * static_cast<size_t>(Kp);
+        const size_t per = sizeof(BlockDesc) + (pl->sep_full ? 0 : xrow) + (fp64 ? 8 : 4) * static_cast<size_t>(Kp);
         return set_error(SE_ERR_INVALID,
                          "se_extrapolate_noalloc: " + std::to_string(n) +
                              " blocks need more than the 16 MiB static scratch; at most about " +
@@ -123,7 +123,10 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     if (s != SE_OK) return s;
 
     std::string why;
-    if (fp64) {
+    if (pl->sep_full) {
+        const SepArgs sa = pattern_sep_args(pl, 0, d_desc, n, d_r0);
+        e = fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st);
+    } else if (fp64) {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
                           pl->ka_pad, 0, pl->MN, nullptr, static_cast<double *>(d_x), st);
         if (e == cudaSuccess)

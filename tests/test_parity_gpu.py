@@ -59,10 +59,12 @@ def check_block(prec, out, u, c, ref_u, ref_c, margin, ref_out, truth, loss):
     return t, float(err.max())
 
 
+@pytest.mark.parametrize("products", ["dense", "transform"])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x3"])
-def test_config1_against_se_oracle(ctx, prec):
+def test_config1_against_se_oracle(ctx, prec, products):
     wl = W.config1()
-    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec,
+                    products=products)
     out, u, c = gpu_run(plan, wl.samples)
     o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
     ref = o.se(wl.samples[0], wl.gamma, wl.iterations)
@@ -79,11 +81,13 @@ def test_config1_against_se_oracle(ctx, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("products", ["dense", "transform"])
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
-def test_config2_scaled_ragged_batch(ctx, prec):
+def test_config2_scaled_ragged_batch(ctx, prec, products):
     """300 blocks of the 512x512 workload: two GEMM column tiles, the second ragged."""
     wl = W.config2(300)
-    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations, prec=prec,
+                    products=products)
     out, u, c = gpu_run(plan, wl.samples)
     o = OracleSetup("dct_wht", 32, 32, wl.rho_hat, wl.support, tables=False)
     ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, wl.samples, wl.gamma, wl.iterations,
@@ -199,8 +203,12 @@ def test_gaussian_dictionary_K4096_I200(ctx, prec):
     plan.close()
 
 
-@pytest.mark.parametrize("L,basis", [(16, "dct_wht"), (64, "dct_wht"), (16, "dct"), (32, "wht")])
-def test_other_sizes_and_bases(ctx, L, basis):
+@pytest.mark.parametrize("products", ["dense", "transform"])
+@pytest.mark.parametrize("L,basis", [(16, "dct_wht"), (64, "dct_wht"), (16, "dct"), (32, "wht"),
+                                     (12, "dct"), (10, "dct")])
+def test_other_sizes_and_bases(ctx, L, basis, products):
+    """Includes K < Kp (12x12, 10x10: padded atoms) and sizes that are not a
+    multiple of 4 (10x10: the untiled transform kernel)."""
     K = {"dct_wht": 2 * L * L, "dct": L * L, "wht": L * L}[basis]
     I = 60
     s = np.stack([W.patch(L, 500 + i) for i in range(6)])
@@ -208,7 +216,7 @@ def test_other_sizes_and_bases(ctx, L, basis):
     o = OracleSetup(basis, L, L, 0.8, sup, tables=False)
     ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, s, 0.5, I, o.dup, margins=True)
     for prec in ("fp64", "bf16x6"):
-        plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec)
+        plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec, products=products)
         out, u, c = gpu_run(plan, s)
         tau, ctol = TOL[prec]
         for b in range(len(s)):
@@ -230,6 +238,35 @@ def test_host_entry_point_matches_device_path(ctx):
     np.testing.assert_array_equal(u, ud)
     np.testing.assert_array_equal(c, cd)
     plan.close()
+
+
+def test_dense_and_transform_products_agree(ctx):
+    """The two ways of forming the scalar products (tensor-core GEMMs on the
+    support pixels vs separable transforms, Sec. VI) select the same atoms on
+    the full-size workload wherever no near tie decides."""
+    wl = W.config2(1024)
+    res = {}
+    for products in ("dense", "transform"):
+        plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, wl.iterations,
+                        prec="bf16x6", products=products)
+        res[products] = gpu_run(plan, wl.samples)
+        plan.close()
+    (od, ud, cd), (ot, ut, ct) = res["dense"], res["transform"]
+    same = np.all(ud == ut, axis=1)
+    assert same.mean() >= 0.97
+    for b in np.where(same)[0][:64]:
+        assert coef_rel_err(ct[b], cd[b]).max() <= 1e-3
+    loss = np.broadcast_to(wl.support == 0, od.shape)
+    assert abs(psnr(od, wl.samples, loss) - psnr(ot, wl.samples, loss)) <= 0.05
+
+
+def test_transform_products_need_a_separable_basis(ctx):
+    dic = W.gaussian_dictionary(256, 16, 16, 3)
+    with pytest.raises(B.SeError) as e:
+        ctx.plan(16, 16, "numeric", 256, 0.8, 0.5, 10, dictionary=dic, products="transform")
+    assert e.value.status == -1
+    # AUTO falls back to the dense products for a numeric dictionary
+    ctx.plan(16, 16, "numeric", 256, 0.8, 0.5, 10, dictionary=dic).close()
 
 
 def test_invalid_arguments(ctx):
