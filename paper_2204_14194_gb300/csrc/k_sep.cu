@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
     const int b = a.item_blk ? a.item_blk[i] : i;
     const uint8_t *mask;
     const double *smp = nullptr;
+    double *dst = nullptr;
     const T *rowM = nullptr, *rowN = nullptr;
     if (a.mode == 3) {
         mask = a.pattern;
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
         const BlockDesc bd = a.blocks[b];
         mask = bd.support ? bd.support : a.pattern;
         smp = bd.samples;
+        if (a.mode == 0 && a.copy_support) dst = bd.out;
     }
     if (a.mode >= 2) {
         const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -59,8 +61,13 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
     for (int p = threadIdx.x; p < MN; p += blockDim.x) {
         const int m = p / N, n = p - m * N;
         T v = mask[p] ? static_cast<T>(a.rho[p]) : T(0);
-        if (a.mode == 0) v = mask[p] ? v * static_cast<T>(smp[p]) : T(0);
-        else if (a.mode >= 2) v *= rowM[m] * rowN[n];
+        if (a.mode == 0) {
+            const double sp = mask[p] ? smp[p] : 0.0;
+            v = mask[p] ? v * static_cast<T>(sp) : T(0);
+            if (dst && mask[p]) dst[p] = sp;
+        } else if (a.mode >= 2) {
+            v *= rowM[m] * rowN[n];
+        }
         X[p] = v;
     }
     T *out = static_cast<T *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
@@ -216,6 +223,7 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
         const int b = a.item_blk ? a.item_blk[i] : i;
         const uint8_t *mask;
         const double *smp = nullptr;
+        double *dst = nullptr;
         const float *rowM = nullptr, *rowN = nullptr;   // the 1-D rows of atom u (global)
         if (a.mode == 3) {
             mask = a.pattern;
@@ -223,6 +231,7 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
             const BlockDesc bd = a.blocks[b];
             mask = bd.support ? bd.support : a.pattern;
             smp = bd.samples;
+            if (a.mode == 0 && a.copy_support) dst = bd.out;
         }
         if (a.mode >= 2) {
             const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -253,6 +262,7 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
                 if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
                 else if (a.mode >= 2) v *= ex[j];
                 X[p] = v;
+                if (dst && on[j]) dst[p] = sv[j];
             }
         }
         float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
@@ -383,6 +393,7 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
         const int b = a.item_blk ? a.item_blk[i] : i;
         const uint8_t *mask;
         const double *smp = nullptr;
+        double *dst = nullptr;
         const float *rowM = nullptr, *rowN = nullptr;
         if (a.mode == 3) {
             mask = a.pattern;
@@ -390,6 +401,7 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
             const BlockDesc bd = a.blocks[b];
             mask = bd.support ? bd.support : a.pattern;
             smp = bd.samples;
+            if (a.mode == 0 && a.copy_support) dst = bd.out;
         }
         if (a.mode >= 2) {
             const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -420,6 +432,7 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
                 if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
                 else if (a.mode >= 2) v *= ex[j];
                 X[p] = v;
+                if (dst && on[j]) dst[p] = sv[j];
             }
         }
         float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
@@ -470,6 +483,95 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
         }
         for (int k = a.koff[a.ntr - 1] + MN + lane; k < a.kfill; k += 32)
             out[k] = a.scale ? NAN : 0.0f;
+    }
+}
+
+// Model (eq. 9) for separable dictionaries, one warp per block.  Shared
+// memory holds the 1-D rows of every transform, T_t[p][m] then T'_t[q][n];
+// a log entry u = koff[t] + p N + q contributes c t_p[m] t'_q[n].  The
+// entries of the log pass through a per-warp table (row offsets and c, one
+// 16-byte broadcast read per entry).  Outputs of the loss bounding box
+// (Mb x Nb) are taken RP per lane: with COL (Nb divides 32, whole chunks of
+// 32 RP outputs, row runs aligned to RP floats) every lane keeps one column n
+// and RP consecutive rows, reading t_p[m..m+RP) as vectors; otherwise each
+// output reads both factors.
+template <bool COL, int RP>
+__global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const SepArgs s, int m0, int Mb,
+                                                        int n0, int Nb)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *Ts = reinterpret_cast<float *>(smem);
+    const int M = s.M, N = s.N, MN = M * N, cstride = M * M + N * N;
+    int4 *Etab = reinterpret_cast<int4 *>(Ts + ((s.ntr * cstride + 3) & ~3)) + (threadIdx.x >> 5) * 32;
+    for (int t = 0; t < s.ntr; ++t) {
+        const float *gm = static_cast<const float *>(s.TM[t]);
+        const float *gn = static_cast<const float *>(s.TN[t]);
+        for (int e = threadIdx.x; e < M * M; e += blockDim.x) Ts[t * cstride + e] = gm[e];
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) Ts[t * cstride + M * M + e] = gn[e];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+    const int nbox = Mb * Nb;
+    constexpr int CH = 32 * RP;   // outputs per chunk
+    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc) {
+        const BlockDesc bd = a.blocks[b];
+        const int I = bd.iterations;
+        const int *lu = a.log_u + static_cast<size_t>(b) * a.I_max;
+        const float *lc = a.log_c + static_cast<size_t>(b) * a.I_max;
+
+        for (int o0 = 0; o0 < nbox; o0 += CH) {
+            // COL: column n0 + lane % Nb, rows mb .. mb + RP - 1
+            const int mb = m0 + o0 / Nb + RP * (lane / Nb);
+            int mo[RP], no[RP];
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                const int o = o0 + lane + 32 * r;
+                const int oc = o < nbox ? o : 0;
+                mo[r] = COL ? mb + r : m0 + oc / Nb;
+                no[r] = COL ? n0 + lane % Nb : n0 + oc % Nb;
+            }
+            float acc[RP];
+#pragma unroll
+            for (int r = 0; r < RP; ++r) acc[r] = 0.0f;
+            for (int nu0 = 0; nu0 < I; nu0 += 32) {
+                int u = nu0 + lane < I ? lu[nu0 + lane] : -1;
+                float cf = 0.0f;                                   // padded entries add 0
+                if (u >= 0 && u < s.koff[s.ntr - 1] + MN) cf = lc[nu0 + lane];
+                else u = 0;
+                const int t = (s.ntr > 1 && u >= s.koff[1]) ? 1 : 0;
+                const int ku = u - s.koff[t];
+                __syncwarp();   // the previous round's reads of the table are done
+                Etab[lane] = make_int4(t * cstride + (ku / N) * M, t * cstride + M * M + (ku % N) * N,
+                                       __float_as_int(cf), 0);
+                __syncwarp();
+                const int cnt = min(32, I - nu0);
+                for (int k = 0; k < cnt; ++k) {
+                    const int4 e = Etab[k];
+                    const float c = __int_as_float(e.z);
+                    if (COL) {
+                        const float cb = c * Ts[e.y + no[0]];
+                        float tv[RP];
+                        lds_vec<RP>(Ts + e.x + mb, tv);
+#pragma unroll
+                        for (int r = 0; r < RP; ++r) acc[r] = fmaf(cb, tv[r], acc[r]);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < RP; ++r) acc[r] = fmaf(c * Ts[e.y + no[r]], Ts[e.x + mo[r]], acc[r]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+                const int o = o0 + lane + 32 * r;
+                if (o >= nbox) continue;
+                const int p = mo[r] * N + no[r];
+                if (!a.pat_support[p]) bd.out[p] = static_cast<double>(acc[r]);
+            }
+        }
+        if (bd.sel_idx)
+            for (int nu = lane; nu < I; nu += 32) bd.sel_idx[nu] = lu[nu];
+        if (bd.sel_coef)
+            for (int nu = lane; nu < I; nu += 32) bd.sel_coef[nu] = static_cast<double>(lc[nu]);
     }
 }
 
@@ -578,6 +680,52 @@ cudaError_t launch_sep(const SepArgs &a, cudaStream_t st)
     }
     sep_kernel<T><<<a.n, 256, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <bool COL, int RP>
+cudaError_t launch_sep_model_t(const IterArgs &a, const SepArgs &s, int m0, int Mb, int n0, int Nb, size_t smem,
+                               cudaStream_t st)
+{
+    static bool attr = false;
+    static int sms = 0;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sep_model_kernel<COL, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_model_kernel<COL, RP>, 256, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min((a.n + 7) / 8, sms * std::max(per_sm, 1)));
+    sep_model_kernel<COL, RP><<<grid, 256, smem, st>>>(a, s, m0, Mb, n0, Nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,
+                             cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    const int Mb = m1 - m0, Nb = n1 - n0;
+    if (Mb <= 0 || Nb <= 0 || m0 < 0 || n0 < 0 || m1 > s.M || n1 > s.N) return cudaErrorInvalidValue;
+    const size_t smem = 4 * ((s.ntr * (static_cast<size_t>(s.M) * s.M + static_cast<size_t>(s.N) * s.N) + 3) & ~size_t(3)) +
+                        8 * 32 * sizeof(int4);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    // small boxes take 2 outputs per lane, else 8; one column and RP
+    // consecutive rows per lane when Nb divides 32, the box holds whole
+    // chunks and the row runs are aligned for vector reads
+    const int nbox = Mb * Nb;
+    const int rp = nbox <= 64 ? 2 : 8;
+    const bool col = 32 % Nb == 0 && nbox % (32 * rp) == 0 && m0 % (rp == 8 ? 4 : 2) == 0 &&
+                     s.M % (rp == 8 ? 4 : 2) == 0 && s.N % 2 == 0;
+    if (rp == 2)
+        return col ? launch_sep_model_t<true, 2>(a, s, m0, Mb, n0, Nb, smem, st)
+                   : launch_sep_model_t<false, 2>(a, s, m0, Mb, n0, Nb, smem, st);
+    return col ? launch_sep_model_t<true, 8>(a, s, m0, Mb, n0, Nb, smem, st)
+               : launch_sep_model_t<false, 8>(a, s, m0, Mb, n0, Nb, smem, st);
 }
 
 template cudaError_t launch_sep<float>(const SepArgs &, cudaStream_t);

@@ -203,7 +203,19 @@ SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n
     s.ldo = pl->Kp;
     s.n = n;
     s.kfill = pl->Kp;
+    // the separable model kernel leaves the support pixels to this pass
+    s.copy_support = mode == 0 && !pl->pc.fp64 && pl->nB > 0;
     return s;
+}
+
+// Model and replacement after the fp32 iteration kernel wrote its log:
+// separable outer products for transform plans, gathered atom values else.
+cudaError_t se::launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st)
+{
+    if (pl->sep_full && pl->nB > 0)
+        return launch_sep_model(a, pattern_sep_args(pl, 0, nullptr, 0, nullptr), pl->box[0], pl->box[1],
+                                pl->box[2], pl->box[3], st);
+    return launch_model_f32(a, st);
 }
 
 namespace {
@@ -402,7 +414,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     stage_end(ctx, tok, st);
     if (e == cudaSuccess && !fp64) {
         tok = stage_begin(ctx, 4, st);
-        e = launch_model_f32(a, st);
+        e = launch_model(pl, a, st);
         stage_end(ctx, tok, st);
         ++launched;
     }
@@ -556,6 +568,13 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         if (pl->pattern[i] && pl->w[i] > 0.0) pl->a_idx.push_back(i);
         else if (!pl->pattern[i]) pl->b_idx.push_back(i);
     }
+    pl->box[0] = d.M; pl->box[1] = 0; pl->box[2] = d.N; pl->box[3] = 0;
+    for (int m = 0; m < d.M; ++m)
+        for (int n = 0; n < d.N; ++n)
+            if (!pl->pattern[m * d.N + n]) {
+                pl->box[0] = std::min(pl->box[0], m); pl->box[1] = std::max(pl->box[1], m + 1);
+                pl->box[2] = std::min(pl->box[2], n); pl->box[3] = std::max(pl->box[3], n + 1);
+            }
     // support pixels with zero weight contribute nothing; they keep their samples
     pl->nA = static_cast<int>(pl->a_idx.size());
     pl->nB = static_cast<int>(pl->b_idx.size());

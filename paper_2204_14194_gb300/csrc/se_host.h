@@ -177,6 +177,7 @@ struct se_plan_s {
     // transform-domain form for DCT / WHT dictionaries: 1-D bases and rho
     bool sep = false, sep_checked = false;
     bool sep_full = false;       // shared-pattern tables and projections by transforms
+    int box[4] = {0, 0, 0, 0};   // bounding box [m0, m1) x [n0, n1) of the pattern's B
     int sep_ntr = 0, sep_koff[2] = {0, 0};
     se::DevBuf d_sepM[2], d_sepN[2], d_rho;
     se::DevBuf d_sep_img;        // fp32 constants in the transform kernels' shared-memory layout
@@ -198,6 +199,9 @@ se_status ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl);
 // R^(0) of n blocks, mode 3 the first n rows of C, written to out with row
 // pitch Kp.
 SepArgs pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out);
+// Model (eq. 9) and replacement from the log of the fp32 iteration kernel
+// (a.log_u / a.log_c set), for blocks on the plan's pattern.
+cudaError_t launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st);
 se_status run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                    int I_max, cudaStream_t st);
 se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);

@@ -165,6 +165,8 @@ struct SepArgs {
     int n;
     int kfill;                  // entries [K, kfill) of each row are set to the padding
                                 // value (NaN with scale, else 0); 0 = none
+    int copy_support;           // mode 0: also write the samples on the item's support to its
+                                // out (the replacement of Alg. 3 on A, fused with the read)
     const float *img;           // fp32 shared-memory image of the constants: per transform
                                 // TmT [M][M] (t_p[m] at m M + p), TnT [N][N]; then rho [MN]
 };
@@ -173,6 +175,15 @@ template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st);
 // Model on the loss pixels and replacement from the selection log written by
 // the fp32 iteration kernel (eq. 9 and the last step of Alg. 3).
 cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st);
+
+// The same for separable dictionaries: g[m][n] = sum_nu c_nu t_p[m] t'_q[n]
+// over the log, from the 1-D rows held in shared memory (no gather of atom
+// values); evaluated on the bounding box [m0, m1) x [n0, n1) of B and
+// written on its loss pixels.  The support pixels are not written here: the
+// projection pass (mode 0 with copy_support) has copied them.  Uses s.M,
+// s.N, s.ntr, s.TM, s.TN, s.koff.
+cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,
+                             cudaStream_t st);
 
 // Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
 int iterate_kp(int K, bool fp64);

@@ -98,9 +98,11 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     const size_t desc_b = r256(sizeof(BlockDesc) * static_cast<size_t>(n));
     const size_t xrow = fp64 ? sizeof(double) * pl->ka_pad : 2u * pl->pc.nparts * pl->ka_pad;
     const size_t x_b = pl->sep_full ? 0 : r256(xrow * n);
-    const size_t r_b = (fp64 ? sizeof(double) : sizeof(float)) * Kp * static_cast<size_t>(n);
-    if (desc_b + x_b + r_b > kScratchBytes) {
-        const size_t per = sizeof(BlockDesc) + (pl->sep_full ? 0 : xrow) + (fp64 ? 8 : 4) * static_cast<size_t>(Kp);
+    const size_t r_b = r256((fp64 ? sizeof(double) : sizeof(float)) * Kp * static_cast<size_t>(n));
+    const size_t log_b = fp64 ? 0 : 8 * static_cast<size_t>(n) * I;   // selection log of the fp32 form
+    if (desc_b + x_b + r_b + log_b > kScratchBytes) {
+        const size_t per = sizeof(BlockDesc) + (pl->sep_full ? 0 : xrow) + (fp64 ? 8 : 4) * static_cast<size_t>(Kp) +
+                           (fp64 ? 0 : 8 * static_cast<size_t>(I));
         return set_error(SE_ERR_INVALID,
                          "se_extrapolate_noalloc: " + std::to_string(n) +
                              " blocks need more than the 16 MiB static scratch; at most about " +
@@ -113,6 +115,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     BlockDesc *d_desc = reinterpret_cast<BlockDesc *>(base);
     void *d_x = base + desc_b;
     void *d_r0 = base + desc_b + x_b;
+    int *d_log = reinterpret_cast<int *>(base + desc_b + x_b + r_b);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
     fill_desc_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_desc, n, samples, out, sel_idx, sel_coef, I,
@@ -174,8 +177,16 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     a.gamma = pl->desc.gamma;
     a.I_max = I;
     a.err = ctx->ws_err.as<int>();
+    if (!fp64) {   // the same model kernel as the batched entry points
+        a.log_u = d_log;
+        a.log_c = reinterpret_cast<float *>(d_log + static_cast<size_t>(n) * I);
+    }
     int launched = 0;
     e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterate_full<float>(a, st, &launched);
+    if (e == cudaSuccess && !fp64) {
+        e = launch_model(pl, a, st);
+        ++launched;
+    }
     if (e != cudaSuccess)
         return set_error(SE_ERR_CUDA, std::string("se_extrapolate_noalloc iterations: ") + cudaGetErrorString(e));
     ctx->launches += 3 + launched;
