@@ -179,7 +179,9 @@ def run_ours(args):
     wl = W.config2()
     n, M, N, K, I = wl.B, wl.M, wl.N, wl.K, wl.iterations
     ctx = B.Context(local)
-    plan = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec=args.prec)
+    plan = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec=args.prec, products=args.products)
+    # AUTO takes the transform-domain products for this separable dictionary
+    products = "dense" if args.products == "dense" else "transform"
     stream = torch.cuda.Stream(device=dev)
     s_d = torch.from_numpy(wl.samples).to(dev)
     out_d = torch.empty_like(s_d)
@@ -242,7 +244,7 @@ def run_ours(args):
 
     # ---- error against the fp64 form, and the fp64 form's own throughput
     out_m, u_m, c_m = out_d.cpu().numpy(), u_d.cpu().numpy(), c_d.cpu().numpy()
-    plan64 = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec="fp64")
+    plan64 = ctx.plan(M, N, wl.basis, K, wl.rho_hat, wl.gamma, I, prec="fp64", products=args.products)
     o64 = torch.empty_like(s_d)
     u64 = torch.empty_like(u_d)
     c64 = torch.empty_like(c_d)
@@ -292,13 +294,29 @@ def run_ours(args):
                 "l2_read_GBps": n * (I - 1) * K * 4 / it_avg_s / 1e9}
     pr_ms, pr_n = stages["projections"]
     pr_avg_s = pr_ms / max(pr_n, 1) / 1000.0
-    npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(args.prec, 0)
     na = int(np.sum(wl.support))
-    tflops = 2.0 * K * n * na * npairs / pr_avg_s / 1e12 if npairs else None
-    roofline_gemm = None if tflops is None else {
-        "kernel": "tc_gemm_kernel<256,1,0> (eq. 12 projections)", "bound": "tensor",
-        "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s", "frac": tflops / tc_peak,
-        "peak_kind": peak_kind + " bf16 dense"}
+    if products == "transform":
+        # eq. 12 as two separable 2-D transforms per block (DCT and WHT halves):
+        # 2 MN (M + N) flops each; algorithmic bytes: samples on A read and
+        # written to the output (8 B each), R^(0) written (4 B per atom)
+        ntr = 2 if wl.basis == "dct_wht" else 1
+        if args.prec == "fp64":
+            roofline_gemm = None
+        else:
+            tflops = n * ntr * 2.0 * M * N * (M + N) / pr_avg_s / 1e12
+            gbs = n * (16.0 * na + 4.0 * K) / pr_avg_s / 1e9
+            roofline_gemm = {
+                "kernel": "sep_warp_kernel<32,32,8,4> (eq. 12 as separable transforms, Sec. VI)",
+                "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": tflops / alu_peak, "hbm_GBps": gbs, "hbm_frac": gbs / hbm_peak,
+                "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz"}
+    else:
+        npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(args.prec, 0)
+        tflops = 2.0 * K * n * na * npairs / pr_avg_s / 1e12 if npairs else None
+        roofline_gemm = None if tflops is None else {
+            "kernel": "tc_gemm_kernel<256,1,0> (eq. 12 projections)", "bound": "tensor",
+            "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s", "frac": tflops / tc_peak,
+            "peak_kind": peak_kind + " bf16 dense"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -312,7 +330,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "blocks_per_gpu": n, "M": M, "N": N, "K": K,
-                   "iterations": I, "precision": args.prec + " tensor-core products, fp32 recurrence",
+                   "iterations": I, "products": products,
+                   "precision": ("fp32 separable transforms for tables and projections" if products == "transform"
+                                 else args.prec + " tensor-core products") + ", fp32 recurrence"
+                                if args.prec != "fp64" else "fp64 throughout",
                    "tables": "rebuilt every step", "l2": "flushed between steps (256 MiB write)"},
         "latency_ms": {"p50": float(np.percentile(sorted_ms, 50)), "p99": float(np.percentile(sorted_ms, 99)),
                        "what": "per-batch (4096 blocks) device time"},
@@ -497,6 +518,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
+    ap.add_argument("--products", default="auto", choices=["auto", "dense", "transform"],
+                    help="scalar products of tables and projections (Sec. VI transforms or matrix products)")
     ap.add_argument("--ref-sample", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rate", type=float, default=50000.0, help="serving: arrivals per second")

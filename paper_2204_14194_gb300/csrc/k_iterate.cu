@@ -201,6 +201,9 @@ iterate_full_kernel(const IterArgs a)
 // of a compare-and-select chain; only the lane(s) holding the maximum then
 // look for its smallest index, scanning the chain(s) whose maximum matched.
 // Ties therefore still go to the smallest k, as in the generic path.
+#ifndef SE_ITER_SCAN_BREAK
+#define SE_ITER_SCAN_BREAK 1  // 1: the winning lane stops its scan at the first match
+#endif
 template <int W, int VPT>
 __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const float (&m)[4], int tid,
                                            int lane, int warp, Cand<float> *slot, int &u, float &ru)
@@ -223,6 +226,9 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
                     if (k < kc && fabsf(r) == M) {
                         kc = k;
                         rc = r;
+#if SE_ITER_SCAN_BREAK
+                        break;   // k grows with ch: the first match is this chain's smallest index
+#endif
                     }
                 }
             }

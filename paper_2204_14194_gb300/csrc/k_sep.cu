@@ -370,11 +370,22 @@ __device__ __forceinline__ void outer_fma_pq(float (&acc)[TP][TQ], const float (
         }
 }
 
-template <int M, int N, int TP, int TQ>
-__global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
+// UT[n][p] position: with SW the 4-float slots of a row are XOR-permuted by
+// (n / 4) mod 8, so that the 8 lanes storing one row each (different n, same
+// p) hit different banks; reads of a row stay aligned 16-byte slots.
+template <int M, bool SW>
+__device__ __forceinline__ int ut_index(int n, int p)
+{
+    if constexpr (SW) return n * M + ((((p >> 2) ^ (n >> 2)) & 7) << 2) + (p & ~31) + (p & 3);
+    else return n * M + p;
+}
+
+template <int M, int N, int TP, int TQ, int WPC>
+__global__ void __launch_bounds__(32 * WPC) sep_warp_kernel(const SepArgs a)
 {
     constexpr int MN = M * N, tilesN = N / TQ;
     static_assert((M / TP) * (N / TQ) == 32, "one tile per lane");
+    constexpr bool SW = M == 32 && TP % 4 == 0;
     extern __shared__ __align__(16) unsigned char smem[];
     float *cst = reinterpret_cast<float *>(smem);        // per transform: TmT [M][M], TnT [N][N]
     constexpr int cstride = M * M + N * N;
@@ -452,10 +463,13 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
                 }
 #pragma unroll
                 for (int c = 0; c < TQ; ++c) {
-                    float col[TP];
 #pragma unroll
-                    for (int r = 0; r < TP; ++r) col[r] = acc[r][c];
-                    sts_vec<TP>(UT + (c0 + c) * M + p0, col);
+                    for (int r0 = 0; r0 < TP; r0 += 4) {
+                        float col[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) col[r] = acc[r0 + r][c];
+                        sts_vec<4>(UT + ut_index<M, SW>(c0 + c, p0 + r0), col);
+                    }
                 }
             }
             __syncwarp();
@@ -464,7 +478,13 @@ __global__ void __launch_bounds__(256) sep_warp_kernel(const SepArgs a)
 #pragma unroll 8
                 for (int n = 0; n < N; ++n) {
                     float av[TP], bv[TQ];
-                    lds_vec<TP>(UT + n * M + p0, av);
+#pragma unroll
+                    for (int r0 = 0; r0 < TP; r0 += 4) {
+                        float v4[4];
+                        lds_vec<4>(UT + ut_index<M, SW>(n, p0 + r0), v4);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) av[r0 + r] = v4[r];
+                    }
                     lds_vec<TQ>(TnT + n * N + c0, bv);
                     outer_fma_pq<TP, TQ>(acc, av, bv);
                 }
@@ -623,12 +643,12 @@ cudaError_t launch_sep_group(const SepArgs &a, cudaStream_t st, bool *done)
 template <int M, int N, int TP, int TQ>
 cudaError_t launch_sep_warp(const SepArgs &a, cudaStream_t st)
 {
-    constexpr int wpc = 4;
+    constexpr int wpc = 10;   // 2 CTAs of 10 warps per SM at 32 x 32 (shared memory bound)
     const size_t smem = 4 * (a.ntr * static_cast<size_t>(M * M + N * N) + M * N + 2 * M * N * wpc);
     static bool attr = false;
     static int sms = 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sep_warp_kernel<M, N, TP, TQ>,
+        cudaError_t e = cudaFuncSetAttribute(sep_warp_kernel<M, N, TP, TQ, wpc>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         int dev = 0;
@@ -637,12 +657,12 @@ cudaError_t launch_sep_warp(const SepArgs &a, cudaStream_t st)
         attr = true;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_warp_kernel<M, N, TP, TQ>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_warp_kernel<M, N, TP, TQ, wpc>,
                                                                   32 * wpc, smem);
     if (e != cudaSuccess) return e;
     const int want = (a.n + wpc - 1) / wpc;
     const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
-    sep_warp_kernel<M, N, TP, TQ><<<grid, 32 * wpc, smem, st>>>(a);
+    sep_warp_kernel<M, N, TP, TQ, wpc><<<grid, 32 * wpc, smem, st>>>(a);
     return cudaGetLastError();
 }
 
