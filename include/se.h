@@ -265,6 +265,36 @@ se_status se_stats(se_ctx_t *ctx, uint64_t *kernel_launches, uint64_t *table_bui
 se_status se_set_profiling(se_ctx_t *ctx, int enable);
 se_status se_stage_times(se_ctx_t *ctx, double *ms, uint64_t *count, int n_stages, int reset);
 
+/* Measured choice between the full table (Alg. 2) and lazily computed
+ * columns for blocks on a plan's pattern under SE_GRAM_AUTO.  While the table
+ * is not built, a batch of pattern blocks is served lazily as long as the
+ * extra cost of the blocks served lazily since the table was last needed,
+ * plus this batch, stays below one table build; otherwise the table is built
+ * (and then kept).  The three costs -- one table build, one block with the
+ * table, one block with lazy columns -- are measured with CUDA events on
+ * every batch and by se_plan_autotune, which runs n_probe (1..65536) seeded
+ * synthetic blocks of the plan's pattern through both paths, synchronously
+ * on cuda_stream, after a warm-up that also lets the autotuner time the
+ * kernel variants of these shapes.  The plan's table is left built.  Uses the
+ * context's batch workspace and two temporary device buffers of n_probe M N
+ * doubles (SE_ERR_NOMEM beyond the budget). */
+se_status se_plan_autotune(se_ctx_t *ctx, se_plan_t *plan, int n_probe, void *cuda_stream);
+/* The plan's measured costs in milliseconds (0 = not measured yet); any
+ * pointer may be NULL. */
+se_status se_plan_costs(const se_plan_t *plan, double *table_ms, double *full_ms_per_block,
+                        double *lazy_ms_per_block);
+
+/* CUDA graphs: the lock-step rounds of the lazy path are captured once per
+ * (plan, wave size, iteration count, workspace) and replayed (default on;
+ * at most 32 graphs per context, the least recently used dropped first). */
+se_status se_set_graphs(se_ctx_t *ctx, int enable);
+/* Autotuner and graph counters: shapes tuned (each timed its candidates
+ * once), graphs captured, graph replays.  Any pointer may be NULL.  The
+ * autotuner times interchangeable kernel variants (identical results) on
+ * the first launch of a shape; SE_TUNE_FILE (environment) names a file that
+ * stores the choices across processes. */
+se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_builds, uint64_t *graph_replays);
+
 #ifdef __cplusplus
 }
 #endif

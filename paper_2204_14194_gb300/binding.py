@@ -29,7 +29,8 @@ PRODUCTS = {"auto": 0, "dense": 1, "transform": 2}
 EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_plan_reset_tables",
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
-           "se_stage_times", "se_extrapolate_noalloc"]
+           "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
+           "se_set_graphs", "se_tuning_stats"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -95,6 +96,10 @@ def load(build_if_missing: bool = True):
             "se_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_set_profiling": ([vp, i32], i32),
             "se_stage_times": ([vp, C.POINTER(dbl), C.POINTER(u64), i32, i32], i32),
+            "se_plan_autotune": ([vp, vp, i32, vp], i32),
+            "se_plan_costs": ([vp, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl)], i32),
+            "se_set_graphs": ([vp, i32], i32),
+            "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -158,6 +163,14 @@ class Context:
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
         _check(self._lib.se_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)), "se_stats")
         return {"kernel_launches": a.value, "table_builds": b.value, "serving_slices": c.value}
+
+    def tuning_stats(self):
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(self._lib.se_tuning_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)), "se_tuning_stats")
+        return {"tunings": a.value, "graph_builds": b.value, "graph_replays": c.value}
+
+    def set_graphs(self, enable: bool = True):
+        _check(self._lib.se_set_graphs(self.handle, int(bool(enable))), "se_set_graphs")
 
     def set_profiling(self, enable: bool = True):
         _check(self._lib.se_set_profiling(self.handle, int(bool(enable))), "se_set_profiling")
@@ -228,6 +241,18 @@ class Plan:
 
     def reset_tables(self):
         _check(self._lib.se_plan_reset_tables(self.handle), "se_plan_reset_tables")
+
+    def autotune(self, n_probe: int = 256, stream=None):
+        """Measure table / full / lazy costs on n_probe synthetic blocks (synchronous)."""
+        _check(self._lib.se_plan_autotune(self.ctx.handle, self.handle, int(n_probe), _stream_handle(stream)),
+               "se_plan_autotune")
+        return self.costs()
+
+    def costs(self):
+        """{'table_ms', 'full_ms_per_block', 'lazy_ms_per_block'} (0 = not measured yet)."""
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        _check(self._lib.se_plan_costs(self.handle, C.byref(a), C.byref(b), C.byref(c)), "se_plan_costs")
+        return {"table_ms": a.value, "full_ms_per_block": b.value, "lazy_ms_per_block": c.value}
 
     def extrapolate_strided(self, samples, out, sel_idx=None, sel_coef=None, iterations: int = 0,
                             stream=None):

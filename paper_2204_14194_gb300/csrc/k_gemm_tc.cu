@@ -452,7 +452,12 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 
 }  // namespace
 
-cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why)
+int tc_gemm_variants(const TcGemmArgs &a)
+{
+    return a.symmetric ? 1 : 2;
+}
+
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant)
 {
     if (a.M <= 0 || a.N <= 0) return cudaSuccess;
     if (a.npairs < 1 || a.npairs > 8 || a.ka_pad % BK || a.ka_pad <= 0) {
@@ -482,7 +487,7 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
         default: break;
         }
     } else if (np <= 3) {
-        return launch_bn<256, 1, false>(a, st, why);
+        return variant == 1 ? launch_bn<128, 1, false>(a, st, why) : launch_bn<256, 1, false>(a, st, why);
     }
     if (why) *why = "tc gemm: more than 3 split parts";
     return cudaErrorInvalidValue;

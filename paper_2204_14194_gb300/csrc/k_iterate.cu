@@ -612,21 +612,28 @@ cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st)
 }
 
 template <>
-cudaError_t launch_iterate_full<float>(const IterArgs &a, cudaStream_t st, int *launches)
+cudaError_t launch_iterate_full<float>(const IterArgs &a, cudaStream_t st, int *launches, int variant)
 {
+    // variant 1: twice the warps per block with half the projections per
+    // lane (same selections and updates, another occupancy / latency balance)
     switch (a.Kp) {
     case 512: return launch_f32<1, 16, 4>(a, st, launches);
     case 1024: return launch_f32<1, 32, 4>(a, st, launches);
-    case 2048: return launch_f32<1, 64, 4>(a, st, launches);
-    case 4096: return launch_f32<2, 64, 1>(a, st, launches);
-    case 8192: return launch_f32<4, 64, 1>(a, st, launches);
+    case 2048: return variant == 1 ? launch_f32<2, 32, 1>(a, st, launches) : launch_f32<1, 64, 4>(a, st, launches);
+    case 4096: return variant == 1 ? launch_f32<4, 32, 1>(a, st, launches) : launch_f32<2, 64, 1>(a, st, launches);
+    case 8192: return variant == 1 ? launch_f32<8, 32, 1>(a, st, launches) : launch_f32<4, 64, 1>(a, st, launches);
     case 16384: return launch_f32<8, 64, 1>(a, st, launches);
     default: return cudaErrorInvalidValue;
     }
 }
 
+int iterate_variants(int Kp, bool fp64)
+{
+    return !fp64 && (Kp == 2048 || Kp == 4096 || Kp == 8192) ? 2 : 1;
+}
+
 template <>
-cudaError_t launch_iterate_full<double>(const IterArgs &a, cudaStream_t st, int *launches)
+cudaError_t launch_iterate_full<double>(const IterArgs &a, cudaStream_t st, int *launches, int)
 {
     switch (a.Kp) {
     case 512: return launch_cfg<double, 1, 16, 4>(a, st, launches);

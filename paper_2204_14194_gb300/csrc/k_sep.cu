@@ -15,8 +15,6 @@
 // A dictionary may hold two transforms (the DCT u WHT union); transform t
 // writes atoms koff[t] + p N + q.
 #include <algorithm>
-#include <cstdlib>
-#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -597,17 +595,6 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
 
 }  // namespace
 
-// SE_SEP_KERNEL=group selects the 64-thread-group kernel for every size
-// (comparison of the two schedules)
-bool sep_force_group()
-{
-    static const int v = [] {
-        const char *e = std::getenv("SE_SEP_KERNEL");
-        return e && std::strcmp(e, "group") == 0 ? 1 : 0;
-    }();
-    return v != 0;
-}
-
 template <int TS, int MC, int NC>
 cudaError_t launch_sep_group(const SepArgs &a, cudaStream_t st, bool *done)
 {
@@ -666,16 +653,21 @@ cudaError_t launch_sep_warp(const SepArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+int sep_variants(const SepArgs &a, bool fp64)
+{
+    return !fp64 && ((a.M == 32 && a.N == 32) || (a.M == 16 && a.N == 16)) ? 2 : 1;
+}
+
 template <typename T>
-cudaError_t launch_sep(const SepArgs &a, cudaStream_t st)
+cudaError_t launch_sep(const SepArgs &a, cudaStream_t st, int variant)
 {
     if (a.n <= 0) return cudaSuccess;
     if (sizeof(T) == 4) {
         bool done = false;
         cudaError_t e = cudaSuccess;
-        if (a.M == 32 && a.N == 32 && !sep_force_group())
+        if (a.M == 32 && a.N == 32 && variant == 0)
             return launch_sep_warp<32, 32, 8, 4>(a, st);
-        if (a.M == 16 && a.N == 16 && !sep_force_group())
+        if (a.M == 16 && a.N == 16 && variant == 0)
             return launch_sep_warp<16, 16, 4, 2>(a, st);
         if (a.M == 32 && a.N == 32)
             e = launch_sep_group<4, 32, 32>(a, st, &done);
@@ -748,7 +740,7 @@ cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1
                : launch_sep_model_t<false, 8>(a, s, m0, Mb, n0, Nb, smem, st);
 }
 
-template cudaError_t launch_sep<float>(const SepArgs &, cudaStream_t);
-template cudaError_t launch_sep<double>(const SepArgs &, cudaStream_t);
+template cudaError_t launch_sep<float>(const SepArgs &, cudaStream_t, int);
+template cudaError_t launch_sep<double>(const SepArgs &, cudaStream_t, int);
 
 }  // namespace se

@@ -251,6 +251,21 @@ simt_gemm_kernel(const T *__restrict__ A, int lda, const T *__restrict__ B, int 
     }
 }
 
+// Seeded synthetic samples in [0, 255) for probe batches (a 32-bit integer
+// hash of the element index and the seed; no dependence on the method).
+__global__ void probe_samples_kernel(double *s, long long total, uint32_t seed)
+{
+    const long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (i >= total) return;
+    uint32_t h = static_cast<uint32_t>(i) * 0x9E3779B1u ^ (static_cast<uint32_t>(i >> 32) + seed) * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    s[i] = 255.0 * static_cast<double>(h >> 8) / 16777216.0;
+}
+
 }  // namespace
 
 cudaError_t launch_pack_x(const BlockDesc *blocks, int n, const int *a_idx, const double *sqrtw,
@@ -341,5 +356,12 @@ template cudaError_t launch_simt_gemm<float>(const float *, int, const float *, 
 template cudaError_t launch_simt_gemm_ex<double>(const double *, int, const double *, int, int, int,
                                                  int, double *, long long, const long long *,
                                                  const int *, cudaStream_t);
+
+cudaError_t launch_probe_samples(double *s, long long total, uint32_t seed, cudaStream_t st)
+{
+    if (total <= 0) return cudaSuccess;
+    probe_samples_kernel<<<static_cast<unsigned>((total + 255) / 256), 256, 0, st>>>(s, total, seed);
+    return cudaGetLastError();
+}
 
 }  // namespace se

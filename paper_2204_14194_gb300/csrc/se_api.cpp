@@ -208,6 +208,21 @@ SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n
     return s;
 }
 
+// SE_GRAM_AUTO: pattern blocks go to the lazy path while that is measured to
+// be cheaper than building the table (see choose_lazy_for_pattern).
+void se::route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::vector<BlockDesc> &lazy,
+                              int *I_full, int *I_lazy)
+{
+    if (full.empty() || !choose_lazy_for_pattern(pl, static_cast<int>(full.size()))) return;
+    for (auto &x : full) {
+        x.support = pl->d_pattern.as<uint8_t>();
+        lazy.push_back(x);
+        *I_lazy = std::max(*I_lazy, x.iterations);
+    }
+    full.clear();
+    *I_full = 0;
+}
+
 // Model and replacement after the fp32 iteration kernel wrote its log:
 // separable outer products for transform plans, gathered atom values else.
 cudaError_t se::launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st)
@@ -218,7 +233,27 @@ cudaError_t se::launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st)
     return launch_model_f32(a, st);
 }
 
+// A transform-domain launch through the autotuner (schedules with identical
+// results; one key per area size and transform count).
+cudaError_t se::run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st)
+{
+    const bool fp64 = pl->pc.fp64;
+    const int nv = sep_variants(sa, fp64);
+    const std::string key = "sep:" + std::to_string(sa.M) + "x" + std::to_string(sa.N) + ":t" +
+                            std::to_string(sa.ntr) + (fp64 ? ":f64" : ":f32");
+    return tune_run(ctx, key, nv, st, [&](int v) {
+        return fp64 ? launch_sep<double>(sa, st, v) : launch_sep<float>(sa, st, v);
+    });
+}
+
 namespace {
+
+std::string nclass(int n)
+{
+    int c = 0;
+    while ((1 << c) < n) ++c;
+    return std::to_string(c);
+}
 
 se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 {
@@ -240,7 +275,7 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
                                                   pl->K, Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
                                                   pl->d_nadm.as<int>(), st));
         SepArgs sa = pattern_sep_args(pl, 3, nullptr, pl->K, pl->d_C.ptr);
-        SE_CUDA(pl->pc.fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+        SE_CUDA(run_sep(ctx, pl, sa, st));
         ctx->launches += 3;
     } else if (pl->pc.fp64) {
         SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
@@ -314,7 +349,10 @@ se_status dense_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws,
         g.symmetric = 0;
         g.err = ctx->ws_err.as<int>();
         g.scale = pl->d_Dk.as<float>();
-        cudaError_t e = launch_tc_gemm(g, st, &why);
+        const std::string key = "gemm_proj:" + std::to_string(Kp) + ":" + std::to_string(pl->ka_pad) + ":p" +
+                                std::to_string(pl->pc.npairs) + ":n" + nclass(n);
+        cudaError_t e = tune_run(ctx, key, tc_gemm_variants(g), st,
+                                 [&](int v) { return launch_tc_gemm(g, st, &why, v); });
         if (e != cudaSuccess) return fail(SE_ERR_CUDA, "projection GEMM: " + why + " " + cudaGetErrorString(e));
     }
     stage_end(ctx, tok, st);
@@ -366,7 +404,9 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         std::lock_guard<std::mutex> lk(pl->tmu);
         if (!pl->tables_valid) {
             const int tok = stage_begin(ctx, 1, st);
+            cudaEvent_t pa = probe_begin(ctx, st);
             SE_TRY(build_tables(ctx, pl, st));
+            probe_end(ctx, pl, 0, 0, pa, st);
             stage_end(ctx, tok, st);
         } else {
             SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
@@ -374,12 +414,13 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     }
 
     const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
+    cudaEvent_t probe = probe_begin(ctx, st);
     int tok;
     if (pl->sep_full) {
         // eq. (12) as a separable transform of w s per block: no packing stage
         tok = stage_begin(ctx, 2, st);
         SepArgs sa = pattern_sep_args(pl, 0, ddesc, n, ws.r0.ptr);
-        SE_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+        SE_CUDA(run_sep(ctx, pl, sa, st));
         stage_end(ctx, tok, st);
         ctx->launches += 1;
     } else {
@@ -409,8 +450,12 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     }
     int launched = 0;
     tok = stage_begin(ctx, 3, st);
-    cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched)
-                         : launch_iterate_full<float>(a, st, &launched);
+    const std::string ikey = std::string("iterate:") + (fp64 ? "f64:" : "f32:") + std::to_string(Kp);
+    cudaError_t e = tune_run(ctx, ikey, iterate_variants(Kp, fp64), st, [&](int v) {
+        launched = 0;
+        return fp64 ? launch_iterate_full<double>(a, st, &launched, v)
+                    : launch_iterate_full<float>(a, st, &launched, v);
+    });
     stage_end(ctx, tok, st);
     if (e == cudaSuccess && !fp64) {
         tok = stage_begin(ctx, 4, st);
@@ -420,6 +465,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     }
     if (e != cudaSuccess) return fail(SE_ERR_CUDA, std::string("iteration kernel: ") + cudaGetErrorString(e));
     ctx->launches += launched;
+    probe_end(ctx, pl, 1, n, probe, st);
     SE_CUDA(cudaEventRecord(ws.ev_ws, st));
     return SE_OK;
 }
@@ -482,6 +528,7 @@ se_status se_ctx_create(int device, size_t hbm_budget_bytes, se_ctx_t **out)
     auto *c = new se_ctx_s();
     c->device = device;
     c->budget = hbm_budget_bytes;
+    c->tuner.load_env();
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = c->ws.init();
     if (e != cudaSuccess) {
@@ -511,6 +558,11 @@ se_status se_ctx_destroy(se_ctx_t *ctx)
         cudaEventDestroy(p.second.second);
     }
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    ctx->tuner.save();
+    graphs_clear(ctx);
+    probes_poll(ctx, true);
+    for (auto e : ctx->probe_pool) cudaEventDestroy(e);
+    ctx->probe_pool.clear();
     std::vector<se_plan_s *> plans = ctx->plans;
     for (auto *p : plans) se_plan_destroy(p);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -673,6 +725,8 @@ se_status se_plan_destroy(se_plan_t *plan)
     se_ctx_s *ctx = plan->ctx;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    probes_poll(ctx, true, plan);
+    graphs_drop_plan(ctx, plan);
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
         ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), plan), ctx->plans.end());
@@ -719,6 +773,8 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, cons
         }
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
+    probes_poll(ctx, false);
+    route_pattern_blocks(pl, full, lazy, &I_full, &I_lazy);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     if (!full.empty()) SE_TRY(run_batch(ctx, pl, ctx->ws, static_cast<int>(full.size()), full.data(), I_full, st));
     if (!lazy.empty()) SE_TRY(run_lazy(ctx, pl, ctx->ws, static_cast<int>(lazy.size()), lazy.data(), I_lazy, st));
@@ -843,6 +899,84 @@ se_status se_stats(se_ctx_t *ctx, uint64_t *kernel_launches, uint64_t *table_bui
     if (kernel_launches) *kernel_launches = ctx->launches.load();
     if (table_builds) *table_builds = ctx->table_builds.load();
     if (serving_slices) *serving_slices = ctx->slices.load();
+    return SE_OK;
+}
+
+se_status se_plan_autotune(se_ctx_t *ctx, se_plan_t *plan, int n_probe, void *cuda_stream)
+{
+    if (!ctx || !plan) return fail(SE_ERR_INVALID, "NULL context or plan");
+    if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
+    if (n_probe < 1 || n_probe > 65536) return fail(SE_ERR_INVALID, "n_probe must be in [1, 65536]");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    se_plan_s *pl = plan;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    const size_t MN = static_cast<size_t>(pl->MN);
+    DevBuf smp, out;
+    SE_TRY(dev_alloc(ctx, smp, sizeof(double) * MN * n_probe));
+    SE_TRY(dev_alloc(ctx, out, sizeof(double) * MN * n_probe));
+    SE_CUDA(launch_probe_samples(smp.as<double>(), static_cast<long long>(MN) * n_probe, 0x5e1eu, st));
+    const int I = pl->desc.iterations;
+    std::vector<BlockDesc> full(n_probe), lazy;
+    for (int i = 0; i < n_probe; ++i) {
+        full[i] = BlockDesc{};
+        full[i].samples = smp.as<double>() + MN * i;
+        full[i].out = out.as<double>() + MN * i;
+        full[i].iterations = I;
+    }
+    lazy = full;
+    for (auto &x : lazy) x.support = pl->d_pattern.as<uint8_t>();
+    // warm-up (operands, tuner choices, graph capture), then the measured pass
+    for (int pass = 0; pass < 2; ++pass) {
+        {
+            std::lock_guard<std::mutex> tl(pl->tmu);
+            pl->tables_valid = false;
+        }
+        SE_TRY(run_batch(ctx, pl, ctx->ws, n_probe, full.data(), I, st));
+        SE_TRY(run_lazy(ctx, pl, ctx->ws, n_probe, lazy.data(), I, st));
+        SE_CUDA(cudaStreamSynchronize(st));
+        probes_poll(ctx, true, pl);
+        if (pass == 0) {
+            std::lock_guard<std::mutex> cl(pl->cmu);
+            pl->t_table_ms = pl->t_full_blk_ms = pl->t_lazy_blk_ms = pl->lazy_regret_ms = 0.0;
+        }
+    }
+    int bits = 0;
+    SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) {
+        SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
+        return fail(SE_ERR_CUDA, std::string("autotune: ") + dev_err_text(bits));
+    }
+    return SE_OK;
+}
+
+se_status se_plan_costs(const se_plan_t *plan, double *table_ms, double *full_ms_per_block,
+                        double *lazy_ms_per_block)
+{
+    if (!plan) return fail(SE_ERR_INVALID, "NULL plan");
+    se_plan_s *pl = const_cast<se_plan_s *>(plan);
+    probes_poll(pl->ctx, false, pl);
+    std::lock_guard<std::mutex> lk(pl->cmu);
+    if (table_ms) *table_ms = pl->t_table_ms;
+    if (full_ms_per_block) *full_ms_per_block = pl->t_full_blk_ms;
+    if (lazy_ms_per_block) *lazy_ms_per_block = pl->t_lazy_blk_ms;
+    return SE_OK;
+}
+
+se_status se_set_graphs(se_ctx_t *ctx, int enable)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->graphs_enabled = enable != 0;
+    return SE_OK;
+}
+
+se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_builds, uint64_t *graph_replays)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    if (tunings) *tunings = ctx->tunings.load();
+    if (graph_builds) *graph_builds = ctx->graph_builds.load();
+    if (graph_replays) *graph_replays = ctx->graph_replays.load();
     return SE_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -70,9 +71,50 @@ struct PrecCfg {
 };
 PrecCfg prec_cfg(se_prec p);
 
+// Autotuner state of a context (se_tune.cpp): the chosen variant per shape
+// key, the candidates' measured times, the persistence file and forced choices.
+struct Tuner {
+    std::mutex mu;
+    std::map<std::string, int> best;
+    std::map<std::string, std::vector<float>> ms;
+    std::string file;
+    std::vector<std::pair<std::string, int>> force;
+    void load_env();
+    void save() const;
+};
+
 }  // namespace se
 
 struct se_plan_s;
+
+namespace se {
+// Identity of a captured lazy round loop: plan, wave size, iteration count
+// and the workspace addresses baked into its kernel arguments.
+struct GraphKey {
+    const se_plan_s *plan = nullptr;
+    int nw = 0, I_max = 0;
+    const void *ptr[8] = {};
+    bool operator==(const GraphKey &o) const
+    {
+        if (plan != o.plan || nw != o.nw || I_max != o.I_max) return false;
+        for (int i = 0; i < 8; ++i)
+            if (ptr[i] != o.ptr[i]) return false;
+        return true;
+    }
+};
+struct CachedGraph {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last = 0;
+};
+// Cost probe: events around a table build (which 0), a shared-pattern batch
+// without the table (1) or a lazy batch (2) of n blocks, read once complete.
+struct CostProbe {
+    se_plan_s *plan = nullptr;
+    int which = 0, n = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+}  // namespace se
 
 // Serving request as queued by se_submit.
 struct ServeReq {
@@ -134,6 +176,19 @@ struct se_ctx_s {
     std::atomic<uint64_t> table_builds{0};
     std::atomic<uint64_t> slices{0};
 
+    // autotuner, measured costs and graph cache (se_tune.cpp)
+    se::Tuner tuner;
+    std::atomic<uint64_t> tunings{0};
+    std::mutex cpmu;
+    std::vector<se::CostProbe> probes;
+    std::vector<cudaEvent_t> probe_pool;
+    bool graphs_enabled = true;
+    static constexpr size_t kGraphCache = 32;
+    std::mutex gmu;
+    std::vector<se::CachedGraph> graphs;
+    uint64_t graph_clock = 0;
+    std::atomic<uint64_t> graph_builds{0}, graph_replays{0};
+
     // serving
     std::mutex smu;
     std::condition_variable scv;
@@ -183,6 +238,11 @@ struct se_plan_s {
     se::DevBuf d_sep_img;        // fp32 constants in the transform kernels' shared-memory layout
     cudaEvent_t tables_ready = nullptr;
     std::mutex tmu;
+    // measured costs (ms) for the full-versus-lazy choice: one table build, one
+    // block with the table built, one block with lazy columns; and the extra
+    // cost of the pattern blocks served lazily since the table was last needed
+    std::mutex cmu;
+    double t_table_ms = 0.0, t_full_blk_ms = 0.0, t_lazy_blk_ms = 0.0, lazy_regret_ms = 0.0;
 };
 
 namespace se {
@@ -212,4 +272,34 @@ se_status ensure_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
 int stage_begin(se_ctx_s *ctx, int stage, cudaStream_t st);
 void stage_end(se_ctx_s *ctx, int token, cudaStream_t st);
 void serve_shutdown(se_ctx_s *ctx);
+
+// While an object of this type lives, the calling thread's tune_run calls do
+// not time candidates (they take the cached choice or the first candidate);
+// used by the allocation-free entry point.
+struct NoTuneScope {
+    NoTuneScope();
+    ~NoTuneScope();
+};
+// A transform-domain launch with the schedule chosen by the autotuner.
+cudaError_t run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st);
+// Move pattern blocks to the lazy list when the measured costs favour it.
+void route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::vector<BlockDesc> &lazy,
+                          int *I_full, int *I_lazy);
+// Autotuner: run the fastest of n_cand interchangeable launches (identical
+// results) for this shape key, timing all of them on first use.
+cudaError_t tune_run(se_ctx_s *ctx, const std::string &key, int n_cand, cudaStream_t st,
+                     const std::function<cudaError_t(int)> &run);
+// SE_GRAM_AUTO, table not built: serve n pattern blocks lazily (true) or
+// build the table (false), from the plan's measured costs.
+bool choose_lazy_for_pattern(se_plan_s *pl, int n);
+void record_cost(se_plan_s *pl, int which, double ms, int n);
+// Cost probes around a stage (events from a pool; read when complete).
+cudaEvent_t probe_begin(se_ctx_s *ctx, cudaStream_t st);
+void probe_end(se_ctx_s *ctx, se_plan_s *pl, int which, int n, cudaEvent_t a, cudaStream_t st);
+void probes_poll(se_ctx_s *ctx, bool wait, const se_plan_s *only = nullptr);
+// Replay (or capture, then replay) the launches that record() issues.
+cudaError_t graph_run(se_ctx_s *ctx, const GraphKey &key, cudaStream_t st,
+                      const std::function<cudaError_t(cudaStream_t)> &record);
+void graphs_clear(se_ctx_s *ctx);
+void graphs_drop_plan(se_ctx_s *ctx, const se_plan_s *pl);
 }  // namespace se

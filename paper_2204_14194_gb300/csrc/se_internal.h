@@ -55,7 +55,11 @@ struct TcGemmArgs {
     const int *n_dev;    // optional device count: only rows n < min(N, *n_dev) of B are used
     int *err;            // device status word
 };
-cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why);
+// variant (non-symmetric products only): 0 = 128 x 256 tiles, 1 = 128 x 128
+// tiles; both stream one partial product per stage, so they accumulate in the
+// same order and give identical results.
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant = 0);
+int tc_gemm_variants(const TcGemmArgs &a);
 
 // fp64 (or fp32) CUDA-core GEMM, same contraction with a single part:
 // D[m][n] = sum_k A[m][k] B[n][k]; output mode as above.
@@ -107,8 +111,11 @@ struct IterArgs {
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
     float *log_c;           //   model kernel; NULL: the iteration kernel evaluates the model
 };
+// variant < iterate_variants(Kp, fp64): launch shapes with identical results
+// (see launch_iterate_full<float>).
 template <typename T>
-cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches);
+cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches, int variant = 0);
+int iterate_variants(int Kp, bool fp64);
 
 // ------------------------------------------------------------ lazy columns
 struct LazyArgs {
@@ -170,7 +177,10 @@ struct SepArgs {
     const float *img;           // fp32 shared-memory image of the constants: per transform
                                 // TmT [M][M] (t_p[m] at m M + p), TnT [N][N]; then rho [MN]
 };
-template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st);
+// variant < sep_variants(a, fp64): schedules with identical results (fp32:
+// 0 = one warp per item, 1 = one 64-thread group per item, where both exist).
+template <typename T> cudaError_t launch_sep(const SepArgs &a, cudaStream_t st, int variant = 0);
+int sep_variants(const SepArgs &a, bool fp64);
 
 // Model on the loss pixels and replacement from the selection log written by
 // the fp32 iteration kernel (eq. 9 and the last step of Alg. 3).
@@ -184,6 +194,9 @@ cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st);
 // s.N, s.ntr, s.TM, s.TN, s.koff.
 cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,
                              cudaStream_t st);
+
+// Seeded synthetic samples in [0, 255) for the probe batches of the tuner.
+cudaError_t launch_probe_samples(double *s, long long total, uint32_t seed, cudaStream_t st);
 
 // Padded dictionary size the iteration kernel uses for K atoms (-1: too large).
 int iterate_kp(int K, bool fp64);

@@ -309,9 +309,9 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
             // eq. 12 and the diagonal of eq. 16 as separable transforms
             tok = stage_begin(ctx, 2, st);
             SepArgs sa = sep_args(pl, dd, nw, 0, ws.lz_R.ptr, Kp);
-            LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+            LZ_CUDA(run_sep(ctx, pl, sa, st));
             sa = sep_args(pl, dd, nw, 1, ws.lz_diag.ptr, Kp);
-            LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
+            LZ_CUDA(run_sep(ctx, pl, sa, st));
             stage_end(ctx, tok, st);
         } else {
             LZ_TRY(dense_projections(ctx, pl, ws, dd, nw, st));
@@ -344,42 +344,63 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         a.err = ctx->ws_err.as<int>();
 
         tok = stage_begin(ctx, 3, st);
+        cudaEvent_t probe = probe_begin(ctx, st);
         LZ_CUDA(cudaMemsetAsync(miss_n, 0, 2 * sizeof(int), st));
         LZ_CUDA(fp64 ? launch_lazy_init<double>(a, st) : launch_lazy_init<float>(a, st));
-        for (int nu = 0; nu < I_max; ++nu) {
-            LZ_CUDA(fp64 ? launch_lazy_round<double>(a, nu, st) : launch_lazy_round<float>(a, nu, st));
-            if (nu + 1 == I_max) break;
-            int *req = miss_n + (nu & 1);
-            if (pl->sep) {
-                SepArgs sa = sep_args(pl, dd, nw, 2, ws.lz_cache.ptr, Kp);
-                sa.n_dev = req;
-                sa.item_blk = miss_blk;
-                sa.cur_u = cur_u;
-                sa.out_rows = miss_rows;
-                LZ_CUDA(fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st));
-                ctx->launches += 2;
-                continue;
-            }
-            LZ_CUDA(launch_lazy_pack_cols(dd, nw, req, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
+        // the I_max lock-step rounds: round kernel (update, select, request the
+        // new atom's column) and the column computation for the blocks that
+        // missed; every argument is fixed by the plan, the wave and the
+        // workspace, so the loop is captured once as a CUDA graph and replayed
+        auto rounds = [&](cudaStream_t s) -> cudaError_t {
+            for (int nu = 0; nu < I_max; ++nu) {
+                cudaError_t e = fp64 ? launch_lazy_round<double>(a, nu, s) : launch_lazy_round<float>(a, nu, s);
+                if (e != cudaSuccess || nu + 1 == I_max) return e;
+                int *req = miss_n + (nu & 1);
+                if (pl->sep) {
+                    SepArgs sa = sep_args(pl, dd, nw, 2, ws.lz_cache.ptr, Kp);
+                    sa.n_dev = req;
+                    sa.item_blk = miss_blk;
+                    sa.cur_u = cur_u;
+                    sa.out_rows = miss_rows;
+                    e = run_sep(ctx, pl, sa, s);
+                    if (e != cudaSuccess) return e;
+                    continue;
+                }
+                e = launch_lazy_pack_cols(dd, nw, req, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
                                           fp64 ? nullptr : ws.lz_v.as<uint16_t>(),
-                                          fp64 ? ws.lz_v.as<double>() : nullptr, st));
-            if (fp64) {
-                LZ_CUDA(launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_v.as<double>(), MNp, Kp,
-                                                    nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, req,
-                                                    st));
-            } else {
-                TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_v.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6,
-                                         pb6, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
-                g.out_rows = miss_rows;
-                g.n_dev = req;
-                cudaError_t e = launch_tc_gemm(g, st, &why);
-                if (e != cudaSuccess) return set_error(SE_ERR_CUDA, "lazy columns: " + why);
+                                          fp64 ? ws.lz_v.as<double>() : nullptr, s);
+                if (e != cudaSuccess) return e;
+                if (fp64) {
+                    e = launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_v.as<double>(), MNp, Kp,
+                                                    nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, req, s);
+                } else {
+                    TcGemmArgs g = gemm_args(pl->d_ArBf.ptr, ws.lz_v.ptr, Kp, nw, 3 * MNp, 3 * MNp, MNp, 6, pa6,
+                                             pb6, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
+                    g.out_rows = miss_rows;
+                    g.n_dev = req;
+                    e = launch_tc_gemm(g, s, &why);
+                }
+                if (e != cudaSuccess) return e;
             }
-            ctx->launches += 3;
+            return cudaSuccess;
+        };
+        GraphKey gk;
+        gk.plan = pl;
+        gk.nw = nw;
+        gk.I_max = I_max;
+        const void *ptrs[8] = {ws.desc.ptr, ws.lz_R.ptr, ws.lz_cache.ptr, ws.lz_v.ptr,
+                               ws.lz_miss.ptr, ws.lz_cur.ptr, ws.lz_ulog.ptr, ws.lz_clog.ptr};
+        for (int i = 0; i < 8; ++i) gk.ptr[i] = ptrs[i];
+        {
+            cudaError_t e = graph_run(ctx, gk, st, rounds);
+            if (e != cudaSuccess)
+                return set_error(SE_ERR_CUDA, std::string("lazy rounds: ") + why + " " + cudaGetErrorString(e));
         }
+        ctx->launches += static_cast<uint64_t>(I_max) + static_cast<uint64_t>(I_max - 1) * (pl->sep ? 1 : 2);
         LZ_CUDA(fp64 ? launch_lazy_model<double>(a, st) : launch_lazy_model<float>(a, st));
+        probe_end(ctx, pl, 2, nw, probe, st);
         stage_end(ctx, tok, st);
-        ctx->launches += 6;
+        ctx->launches += 4 + (pl->sep ? 2 : 0);
     }
     LZ_CUDA(cudaEventRecord(ws.ev_ws, st));
     return SE_OK;

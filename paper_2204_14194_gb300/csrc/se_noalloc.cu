@@ -109,6 +109,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
                              std::to_string(kScratchBytes / per) + " blocks of this plan fit");
     }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(SE_ERR_CUDA, "cudaSetDevice failed");
+    NoTuneScope no_tune;   // no timing runs (and no events) inside this call
     unsigned char *base = nullptr;
     se_status s = scratch_address(ctx->device, &base);
     if (s != SE_OK) return s;
@@ -128,7 +129,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     std::string why;
     if (pl->sep_full) {
         const SepArgs sa = pattern_sep_args(pl, 0, d_desc, n, d_r0);
-        e = fp64 ? launch_sep<double>(sa, st) : launch_sep<float>(sa, st);
+        e = run_sep(ctx, pl, sa, st);
     } else if (fp64) {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
                           pl->ka_pad, 0, pl->MN, nullptr, static_cast<double *>(d_x), st);

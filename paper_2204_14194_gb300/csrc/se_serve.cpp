@@ -162,6 +162,8 @@ bool launch(se_ctx_s *ctx, ServeLane &lane, std::vector<std::shared_ptr<ServeReq
             I_full = std::max(I_full, x.iterations);
         }
     }
+    probes_poll(ctx, false);
+    route_pattern_blocks(pl, full, lazy, &I_full, &I_lazy);
     cudaError_t e = cudaMemcpyAsync(d + L.samples, lane.h_io + L.samples, L.out - L.samples,
                                     cudaMemcpyHostToDevice, lane.st);
     if (e == cudaSuccess) {

@@ -1,0 +1,184 @@
+"""Autotuner, measured full-versus-lazy choice and CUDA graphs, on the GPU.
+
+The autotuner may only choose between launches with identical results, so
+every forced variant must reproduce the default bit for bit; the routing of
+pattern blocks under SE_GRAM_AUTO must follow the ski-rental rule on the
+measured costs; replayed graphs of the lazy rounds must give the same
+results as direct launches.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2204_14194_gb300 import binding as B
+from paper_2204_14194_gb300 import workloads as W
+from helpers import coef_rel_err, first_near_tie
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(force=None, tune_file=None):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    old = {k: os.environ.get(k) for k in ("SE_TUNE_FORCE", "SE_TUNE_FILE")}
+    for k, v in (("SE_TUNE_FORCE", force), ("SE_TUNE_FILE", tune_file)):
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    try:
+        return B.Context(0)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _run(ctx, plan, samples, masks=None, iters=None):
+    n, M, N = samples.shape
+    I = plan.iterations
+    s = torch.from_numpy(samples).cuda()
+    out = torch.empty_like(s)
+    u = torch.full((n, I), -1, dtype=torch.int32, device="cuda")
+    c = torch.full((n, I), float("nan"), dtype=torch.float64, device="cuda")
+    if masks is None:
+        plan.extrapolate_strided(s, out, u, c)
+    else:
+        m = torch.from_numpy(masks).cuda()
+        plan.extrapolate_batch([{"samples": s[b], "support": m[b], "out": out[b], "sel_idx": u[b],
+                                 "sel_coef": c[b], "iterations": int(iters[b]) if iters is not None else I}
+                                for b in range(n)])
+    ctx.sync()
+    return out.cpu().numpy(), u.cpu().numpy(), c.cpu().numpy()
+
+
+CASES = [
+    # (name, M, basis, K, I, n, prec)
+    ("dctwht32", 32, "dct_wht", 2048, 60, 200, "bf16x6"),   # transform schedule, iterate Kp 2048
+    ("dctwht16", 16, "dct_wht", 512, 60, 300, "bf16x6"),    # transform schedule 16 x 16
+    ("gauss32", 32, "numeric", 4096, 40, 300, "bf16x6"),    # GEMM tile, iterate Kp 4096
+    ("dctwht64", 64, "dct_wht", 8192, 20, 40, "bf16x6"),    # iterate Kp 8192
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_forced_variants_are_bitwise_identical(case):
+    name, L, basis, K, I, n, prec = case
+    samples = np.stack([W.patch(L, 4000 + i) for i in range(n)])
+    dic = W.gaussian_dictionary(K, L, L, 91) if basis == "numeric" else None
+    res = []
+    for v in (0, 1):
+        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},iterate:={v}")
+        try:
+            plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec, dictionary=dic)
+            res.append(_run(ctx, plan, samples))
+            plan.close()
+        finally:
+            ctx.close()
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_autotuner_times_each_shape_once_and_persists(tmp_path):
+    f = str(tmp_path / "tune.txt")
+    ctx = _ctx(tune_file=f)
+    try:
+        plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 40, prec="bf16x6")
+        samples = np.stack([W.patch(32, 50 + i) for i in range(64)])
+        r1 = _run(ctx, plan, samples)
+        t1 = ctx.tuning_stats()["tunings"]
+        assert t1 >= 2          # the transform schedule and the iteration kernel shape
+        r2 = _run(ctx, plan, samples)
+        assert ctx.tuning_stats()["tunings"] == t1
+        for a, b in zip(r1, r2):
+            np.testing.assert_array_equal(a, b)
+        plan.close()
+    finally:
+        ctx.close()
+    lines = open(f).read().split("\n")
+    keys = [l.split()[0] for l in lines if l.strip()]
+    assert any(k.startswith("sep:32x32") for k in keys)
+    assert any(k.startswith("iterate:f32:2048") for k in keys)
+    # a new context reads the choices back: nothing left to time
+    ctx = _ctx(tune_file=f)
+    try:
+        plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 40, prec="bf16x6")
+        _run(ctx, plan, samples)
+        assert ctx.tuning_stats()["tunings"] == 0
+        plan.close()
+    finally:
+        ctx.close()
+
+
+def test_measured_costs_route_pattern_blocks():
+    """After se_plan_autotune, a pattern batch without a built table goes to
+    the lazy path exactly when the ski-rental rule says so, and both routes
+    match the oracle."""
+    ctx = _ctx()
+    try:
+        L, I = 16, 80
+        plan = ctx.plan(L, L, "dct_wht", 512, 0.8, 0.5, I, prec="bf16x6")
+        costs = plan.autotune(128)
+        assert costs["table_ms"] > 0 and costs["full_ms_per_block"] > 0 and costs["lazy_ms_per_block"] > 0
+        extra = costs["lazy_ms_per_block"] - costs["full_ms_per_block"]
+        regret = 0.0   # extra cost of the pattern blocks served lazily since the last table build
+        sup = W.centred_support(L, L)
+        o = O
+        phi = o.dict_dct_wht(L, L)
+        dup = o.find_duplicates(phi)
+        w = o.weights(L, L, 0.8, sup)
+        for n in (1, 4096):
+            plan.reset_tables()
+            samples = np.stack([W.patch(L, 700 + i) for i in range(n)])
+            builds0 = ctx.stats()["table_builds"]
+            out, u, c = _run(ctx, plan, samples)
+            built = ctx.stats()["table_builds"] > builds0
+            expect_lazy = extra <= 0 or regret + n * extra < costs["table_ms"]
+            assert built == (not expect_lazy), (n, costs, regret)
+            regret = regret + n * extra if expect_lazy and extra > 0 else 0.0
+            pick = np.arange(min(n, 6))
+            ro, ru, rc, rm, st = o.se_original_batch(phi, w, samples[pick], 0.5, I, dup, margins=True)
+            for i, b in enumerate(pick):
+                t = first_near_tie(rm[i], 1e-4)
+                np.testing.assert_array_equal(u[b, :t], ru[i, :t])
+                assert coef_rel_err(c[b, :t], rc[i, :t]).max() <= 1e-3
+            # costs were re-measured by the batch, so the next decision reads them again
+            costs = plan.costs()
+            extra = costs["lazy_ms_per_block"] - costs["full_ms_per_block"]
+        plan.close()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("basis,K", [("dct_wht", 512), ("numeric", 512)])
+def test_graph_replay_matches_direct_launches(basis, K):
+    L, n = 16, 48
+    rng = np.random.default_rng(3)
+    samples = np.stack([W.patch(L, 900 + i) for i in range(n)])
+    masks = np.stack([W.rect_support(L, L, rng) if i % 2 else W.holes_support(L, L, rng) for i in range(n)])
+    iters = rng.integers(20, 90, size=n)
+    dic = W.gaussian_dictionary(K, L, L, 5) if basis == "numeric" else None
+    ctx = _ctx()
+    try:
+        plan = ctx.plan(L, L, basis, K, 0.8, 0.5, 90, prec="bf16x6", dictionary=dic)
+        ctx.set_graphs(False)
+        direct = _run(ctx, plan, samples, masks, iters)
+        ctx.set_graphs(True)
+        g0 = ctx.tuning_stats()
+        first = _run(ctx, plan, samples, masks, iters)
+        again = _run(ctx, plan, samples, masks, iters)
+        g1 = ctx.tuning_stats()
+        assert g1["graph_builds"] >= g0["graph_builds"] + 1
+        assert g1["graph_replays"] >= g0["graph_replays"] + 1
+        for ref in (first, again):
+            for a, b in zip(direct, ref):
+                np.testing.assert_array_equal(a, b)
+        plan.close()
+    finally:
+        ctx.close()
