@@ -34,9 +34,12 @@ if ROOT not in sys.path:
 METRIC = "extrapolated blocks/s (32x32 area, K=2048, 100 iters)"
 UNIT = "blocks/s"
 WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
-# dram__bytes_read.sum + dram__bytes_write.sum of one iterate_f32_kernel launch
-# on this workload (ncu, see profiles/); None once the kernel changes.
-TRAFFIC_ITERATE = None
+# Launch shapes of the iteration kernel by autotuner variant, and the
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the shape the
+# traffic was captured for (ncu on this workload, see profiles/); None for a
+# shape without a capture or once the kernel changes.
+ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
+TRAFFIC_ITERATE = {0: 46.35e6}
 
 
 def _dist():
@@ -134,13 +137,20 @@ def cpu_baseline(wl, n_blocks: int, threads: int = 0):
     return n_blocks / dt, cores, dt
 
 
+def calibrated_sample(wl, seconds: float) -> int:
+    """Blocks of the oracle that take about `seconds` on the host cores (from a 16-block run)."""
+    rate, _, _ = cpu_baseline(wl, 16)
+    return int(max(16, min(wl.B, rate * seconds)))
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     from paper_2204_14194_gb300 import workloads as W
     wl = W.config2()
-    sample = args.ref_sample
+    # each step a bounded sample: the whole run (warm-up steps at 1/8 size) takes about 2 minutes
+    sample = args.ref_sample or calibrated_sample(wl, 120.0 / (args.steps + args.warmup / 8.0))
     for _ in range(args.warmup):
         cpu_baseline(wl, max(1, sample // 8))
     vals = []
@@ -201,8 +211,6 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- timed region: device time of exactly K steps, L2 flushed between them
-    ctx.set_profiling(True)
-    ctx.stage_times(reset=True)
     launches0 = ctx.stats()["kernel_launches"]
     clocks = ClockSampler(local)
     clocks.start()
@@ -224,10 +232,21 @@ def run_ours(args):
     ctx.sync(stream)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     launches = ctx.stats()["kernel_launches"] - launches0
-    stages = ctx.stage_times(reset=True)
-    ctx.set_profiling(False)
     total_ms = max_over_ranks(sum(step_ms))
     value = job_throughput(n, ws, args.steps, total_ms / 1000.0)
+
+    # ---- per-stage device times (CUDA events around each stage on the launching
+    # stream), in a separate pass so that the events do not touch the timed steps
+    prof_steps = min(args.steps, 100)
+    ctx.set_profiling(True)
+    ctx.stage_times(reset=True)
+    with torch.cuda.stream(stream):
+        for i in range(prof_steps):
+            flush.fill_(float(i))
+            step()
+    ctx.sync(stream)
+    stages = ctx.stage_times(reset=True)
+    ctx.set_profiling(False)
 
     # ---- end to end through the host-buffer entry point (pinned host memory)
     s_h = torch.from_numpy(wl.samples).pin_memory()
@@ -287,9 +306,10 @@ def run_ours(args):
     ops = n * I * opcount.fase_iteration_ops(M, N, K)
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = ops / it_avg_s / 1e12
-    roofline = {"kernel": "iterate_f32_kernel<1,64,4>", "bound": "alu", "achieved": achieved,
+    variant = max(ctx.tuned_variant("iterate:f32:%d" % K), 0)
+    roofline = {"kernel": ITERATE_SHAPES.get(variant, "iterate_f32_kernel"), "bound": "alu", "achieved": achieved,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": TRAFFIC_ITERATE,
+                "traffic": TRAFFIC_ITERATE.get(variant),
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
                 "l2_read_GBps": n * (I - 1) * K * 4 / it_avg_s / 1e9}
     pr_ms, pr_n = stages["projections"]
@@ -320,9 +340,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, dt = cpu_baseline(wl, args.ref_sample)
+        sample = args.ref_sample or calibrated_sample(wl, 15.0)
+        v, cores, dt = cpu_baseline(wl, sample)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {args.ref_sample} of the 4096 blocks, original SE (Alg. 1), fp64 C, {dt:.1f} s"}
+               "sample": f"first {sample} of the 4096 blocks, original SE (Alg. 1), fp64 C, {dt:.1f} s"}
 
     sorted_ms = sorted(step_ms)
     line = {
@@ -337,7 +358,8 @@ def run_ours(args):
                    "tables": "rebuilt every step", "l2": "flushed between steps (256 MiB write)"},
         "latency_ms": {"p50": float(np.percentile(sorted_ms, 50)), "p99": float(np.percentile(sorted_ms, 99)),
                        "what": "per-batch (4096 blocks) device time"},
-        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "stages_ms_per_step": {k: v[0] / prof_steps for k, v in stages.items()},
+        "stages_note": f"CUDA events around each stage, separate pass of {prof_steps} steps",
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(n * M * N * 8),
@@ -394,6 +416,9 @@ def run_workload(args):
              [{"samples": g[1][b], "support": g[3][b], "out": g[2][b], "iterations": int(g[4][b])}
               for b in range(g[1].shape[0])] for g in groups]
 
+    for c in ctxs:
+        c.set_graphs(not args.no_graphs)
+
     def step():
         for (plan, s, o, m, it), d, stream in zip(groups, descs, streams):
             plan.reset_tables()
@@ -427,6 +452,8 @@ def run_workload(args):
     line = {"metric": "extrapolated blocks/s", "workload": name, "value": nb / (ms / 1000.0),
             "unit": "blocks/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
             "precision": args.prec, "timing": "host wall clock around the steps (several streams)",
+            "graphs": not args.no_graphs,
+            "tuning": [c.tuning_stats() for c in ctxs],
             "stages_ms_per_step_summed_over_streams": stages}
     print(json.dumps(line), flush=True)
     for c in ctxs:
@@ -520,7 +547,9 @@ def main():
     ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
     ap.add_argument("--products", default="auto", choices=["auto", "dense", "transform"],
                     help="scalar products of tables and projections (Sec. VI transforms or matrix products)")
-    ap.add_argument("--ref-sample", type=int, default=192)
+    ap.add_argument("--no-graphs", action="store_true", help="launch the lazy rounds without CUDA graphs")
+    ap.add_argument("--ref-sample", type=int, default=0,
+                    help="oracle blocks per CPU measurement (0: sized from a calibration run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rate", type=float, default=50000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: measured seconds")

@@ -294,6 +294,9 @@ se_status se_set_graphs(se_ctx_t *ctx, int enable);
  * the first launch of a shape; SE_TUNE_FILE (environment) names a file that
  * stores the choices across processes. */
 se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_builds, uint64_t *graph_replays);
+/* The variant the autotuner keeps for a shape key (e.g. "iterate:f32:2048",
+ * "sep:32x32:t2:f32"), or -1 in *variant when that key has not been tuned. */
+se_status se_tuned_variant(se_ctx_t *ctx, const char *key, int *variant);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
-           "se_set_graphs", "se_tuning_stats"]
+           "se_set_graphs", "se_tuning_stats", "se_tuned_variant"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
             "se_plan_costs": ([vp, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl)], i32),
             "se_set_graphs": ([vp, i32], i32),
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
+            "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -168,6 +169,12 @@ class Context:
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
         _check(self._lib.se_tuning_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)), "se_tuning_stats")
         return {"tunings": a.value, "graph_builds": b.value, "graph_replays": c.value}
+
+    def tuned_variant(self, key: str) -> int:
+        """The autotuner's kept variant for a shape key, -1 if not tuned."""
+        v = C.c_int()
+        _check(self._lib.se_tuned_variant(self.handle, key.encode(), C.byref(v)), "se_tuned_variant")
+        return v.value
 
     def set_graphs(self, enable: bool = True):
         _check(self._lib.se_set_graphs(self.handle, int(bool(enable))), "se_set_graphs")

@@ -980,4 +980,13 @@ se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_buil
     return SE_OK;
 }
 
+se_status se_tuned_variant(se_ctx_t *ctx, const char *key, int *variant)
+{
+    if (!ctx || !key || !variant) return fail(SE_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->tuner.mu);
+    auto it = ctx->tuner.best.find(key);
+    *variant = it == ctx->tuner.best.end() ? -1 : it->second;
+    return SE_OK;
+}
+
 }  // extern "C"
