@@ -461,6 +461,48 @@ def run_workload(args):
     return 0
 
 
+def run_single(args):
+    """Latency of one 32 x 32 block (the single-block workload: one patch, K = 2048
+    DCT u WHT, I = 100): device time per call with CUDA events, table cached and
+    rebuilt before every call, in the default (fp32) and the fp64 form."""
+    import torch
+    from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import workloads as W
+
+    wl = W.config1()
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream()
+    s = torch.from_numpy(wl.samples).cuda()
+    out = torch.empty_like(s)
+    res = {}
+    for prec in ("bf16x6", "fp64"):
+        plan = ctx.plan(32, 32, wl.basis, wl.K, wl.rho_hat, wl.gamma, wl.iterations, prec=prec,
+                        products=args.products)
+        for rebuild in (False, True):
+            for _ in range(max(args.warmup, 3)):
+                plan.extrapolate_strided(s, out, stream=stream)
+            ctx.sync(stream)
+            ms = []
+            for _ in range(args.steps):
+                if rebuild:
+                    plan.reset_tables()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    plan.extrapolate_strided(s, out, stream=stream)
+                    b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            res[f"{prec}_{'tables_rebuilt' if rebuild else 'tables_cached'}"] = {
+                "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99))}
+        plan.close()
+    print(json.dumps({"metric": "single-block latency (32x32 area, K=2048, 100 iters)", "unit": "ms",
+                      "steps": args.steps, "latency": res,
+                      "timing": "CUDA events around each call on its stream, synchronised per call"}), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_serve(args):
     """Serving measurement: open-loop Poisson arrivals of single-block requests of
     mixed area size (16/32/64), DCT u WHT or Gaussian dictionaries with K = 2MN,
@@ -556,12 +598,14 @@ def main():
     ap.add_argument("--warm-s", type=float, default=1.0, help="serving: warm-up seconds")
     ap.add_argument("--gauss-share", type=float, default=0.5, help="serving: share of Gaussian dictionaries")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM budget")
-    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed", "serve"],
+    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed", "serve", "single"],
                     help="img512 is the headline; the others are secondary measurements")
     ap.add_argument("--blocks", type=int, default=0, help="block count for --workload gauss1080/mixed")
     args = ap.parse_args()
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "single":
+        return run_single(args)
     if args.workload != "img512":
         return run_workload(args)
     if args.impl == "reference":

@@ -199,14 +199,17 @@ se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n,
  * a deployment variant of the same computation and gives the same results as
  * se_extrapolate_strided.  Arguments as there (device buffers, contiguous
  * blocks on the plan's pattern).  Per-call scratch (descriptors, packed
- * samples, initial projections) lives in one static 16 MiB device array
- * that every GPU loading the library holds until exit; n is limited by it
- * (about 1300 blocks of 32 x 32 with K = 2048 in the split-bf16 forms, about
- * 750 in the fp64 form) and larger n returns SE_ERR_INVALID with the limit
- * in se_last_error().  The first call on a device looks up the array's
- * device address and should come before any stream capture.  All calls
- * share the array: calls whose work overlaps on the GPU race, so serialise
- * them.  The plan's table is built into plan memory on first use. */
+ * samples of the dense products, initial projections, the selection log)
+ * lives in one static 16 MiB device array that every GPU loading the library
+ * holds until exit; n is limited by it (for 32 x 32 blocks with K = 2048 and
+ * I = 100: about 1800 with transform products, 1200 with dense split-bf16
+ * products, 1000 in the fp64 form) and larger n returns SE_ERR_INVALID with
+ * the limit in se_last_error().  The first call on a device looks up the
+ * array's device address and should come before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU race, so
+ * serialise them.  The plan's table is built into plan memory on first use;
+ * the autotuner times no candidates inside this call (it takes its kept
+ * choice, else the first variant). */
 se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
                                  const double *samples, double *out, int32_t *sel_idx,
                                  double *sel_coef, int iterations, void *cuda_stream);
