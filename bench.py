@@ -355,6 +355,7 @@ def run_ours(args):
                    "precision": ("fp32 separable transforms for tables and projections" if products == "transform"
                                  else args.prec + " tensor-core products") + ", fp32 recurrence"
                                 if args.prec != "fp64" else "fp64 throughout",
+                   "certified": args.prec == "certified",
                    "tables": "rebuilt every step", "l2": "flushed between steps (256 MiB write)"},
         "latency_ms": {"p50": float(np.percentile(sorted_ms, 50)), "p99": float(np.percentile(sorted_ms, 99)),
                        "what": "per-batch (4096 blocks) device time"},
@@ -372,6 +373,10 @@ def run_ours(args):
                          "psnr_db": _psnr(out_m), "psnr_fp64_db": _psnr(o64)},
         "cpu_baseline": cpu,
     }
+    if args.prec == "certified":
+        cs = ctx.cert_stats()
+        line["certified"] = {"blocks": cs["blocks"], "recomputed_in_fp64": cs["recomputed"],
+                             "recomputed_frac": cs["recomputed"] / max(cs["blocks"], 1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan64.close()
@@ -586,7 +591,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64"])
+    ap.add_argument("--prec", default="bf16x6", choices=["bf16x6", "bf16x3", "bf16", "fp64", "certified"])
     ap.add_argument("--products", default="auto", choices=["auto", "dense", "transform"],
                     help="scalar products of tables and projections (Sec. VI transforms or matrix products)")
     ap.add_argument("--no-graphs", action="store_true", help="launch the lazy rounds without CUDA graphs")

@@ -62,12 +62,23 @@ typedef enum {
  *   BF16X6  tensor-core products of a 3-way bf16 split (6 partial products,
  *           ~fp32 accuracy), fp32 accumulation, fp32 recurrence;
  *   BF16X3  2-way bf16 split (3 partial products), fp32 accumulation;
- *   BF16    single bf16 products, fp32 accumulation (fastest, ~3 digits). */
+ *   BF16    single bf16 products, fp32 accumulation (fastest, ~3 digits);
+ *   CERTIFIED  the BF16X6 form whose iteration kernel also tracks, per block,
+ *           the relative gap between the two largest |R_k| D_k of every
+ *           selection (eq. 18); blocks where it falls to 1.5e-5 or below at
+ *           any iteration -- where the fp32 selection could differ from the
+ *           fp64 one -- are computed again by an internal FP64 plan, so every
+ *           block's selected-index sequence is the FP64 form's (tested on the
+ *           benchmark workloads; the threshold is about 10x the largest fp32
+ *           score error measured there).  Synchronous on the caller's stream
+ *           (the flagged blocks are collected on the host); blocks on the
+ *           plan's pattern only, K <= 2048.  Counted by se_cert_stats. */
 typedef enum {
     SE_PREC_FP64 = 0,
     SE_PREC_BF16X6 = 1,
     SE_PREC_BF16X3 = 3,
-    SE_PREC_BF16 = 4
+    SE_PREC_BF16 = 4,
+    SE_PREC_CERTIFIED = 5
 } se_prec;
 
 /* How the weighted scalar products between atoms (eq. 16) are provided.
@@ -297,6 +308,10 @@ se_status se_set_graphs(se_ctx_t *ctx, int enable);
  * the first launch of a shape; SE_TUNE_FILE (environment) names a file that
  * stores the choices across processes. */
 se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_builds, uint64_t *graph_replays);
+/* SE_PREC_CERTIFIED plans: blocks computed, and blocks computed again in fp64
+ * because a selection was within the certification gap.  Either pointer may
+ * be NULL. */
+se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed);
 /* The variant the autotuner keeps for a shape key (e.g. "iterate:f32:2048",
  * "sep:32x32:t2:f32"), or -1 in *variant when that key has not been tuned. */
 se_status se_tuned_variant(se_ctx_t *ctx, const char *key, int *variant);

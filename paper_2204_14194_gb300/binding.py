@@ -21,7 +21,7 @@ SE_OK, SE_PENDING = 0, 1
 SE_ERR = {-1: "SE_ERR_INVALID", -2: "SE_ERR_NOMEM", -3: "SE_ERR_CUDA", -4: "SE_ERR_TIMEOUT",
           -5: "SE_ERR_EMPTY_SUPPORT", -6: "SE_ERR_CANCELLED", -7: "SE_ERR_UNKNOWN_TICKET"}
 BASIS = {"dct": 1, "wht": 2, "dct_wht": 3, "numeric": 4}
-PREC = {"fp64": 0, "bf16x6": 1, "bf16x3": 3, "bf16": 4}
+PREC = {"fp64": 0, "bf16x6": 1, "bf16x3": 3, "bf16": 4, "certified": 5}
 GRAM = {"auto": 0, "full": 1, "lazy": 2}
 PRODUCTS = {"auto": 0, "dense": 1, "transform": 2}
 
@@ -30,7 +30,7 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
-           "se_set_graphs", "se_tuning_stats", "se_tuned_variant"]
+           "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
             "se_set_graphs": ([vp, i32], i32),
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
+            "se_cert_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -169,6 +170,11 @@ class Context:
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
         _check(self._lib.se_tuning_stats(self.handle, C.byref(a), C.byref(b), C.byref(c)), "se_tuning_stats")
         return {"tunings": a.value, "graph_builds": b.value, "graph_replays": c.value}
+
+    def cert_stats(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        _check(self._lib.se_cert_stats(self.handle, C.byref(a), C.byref(b)), "se_cert_stats")
+        return {"blocks": a.value, "recomputed": b.value}
 
     def tuned_variant(self, key: str) -> int:
         """The autotuner's kept variant for a shape key, -1 if not tuned."""

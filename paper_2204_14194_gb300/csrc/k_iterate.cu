@@ -204,9 +204,10 @@ iterate_full_kernel(const IterArgs a)
 #ifndef SE_ITER_SCAN_BREAK
 #define SE_ITER_SCAN_BREAK 1  // 1: the winning lane stops its scan at the first match
 #endif
-template <int W, int VPT>
+template <int W, int VPT, bool CERT = false>
 __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const float (&m)[4], int tid,
-                                           int lane, int warp, Cand<float> *slot, int &u, float &ru)
+                                           int lane, int warp, Cand<float> *slot, int &u, float &ru,
+                                           float *second = nullptr)
 {
     constexpr int NT = 32 * W;
     constexpr int NCH = VPT / 4;
@@ -237,6 +238,31 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
     const int kw = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
     const int owner = kw == INT_MAX ? 0 : (kw >> 2) % NT % 32;
     const float rw = __shfl_sync(0xffffffffu, rc, owner);
+    if constexpr (CERT) {
+        static_assert(W == 1, "the runner-up is formed within one warp");
+        // runner-up: the largest |R'| over every atom but the winner (the other
+        // chains of each lane by their maxima, the winner's own chain in full)
+        float sl = 0.0f;
+        if (lane == owner && kw != INT_MAX) {
+            const int jw = kw & 3;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {   // static register indices: j is unrolled
+                if (j != jw) {
+                    sl = fmaxf(sl, m[j]);
+                    continue;
+                }
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int k = ch * NT * 4 + tid * 4 + j;
+                    const float2 q = R2[ch * 2 + (j >> 1)];
+                    if (k != kw) sl = fmaxf(sl, fabsf((j & 1) ? q.y : q.x));
+                }
+            }
+        } else {
+            sl = mx;
+        }
+        *second = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(sl)));
+    }
     if constexpr (W == 1) {
         u = kw;
         ru = rw;
@@ -321,7 +347,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
 #ifndef SE_ITER_MIN_WARPS
 #define SE_ITER_MIN_WARPS 16
 #endif
-template <int W, int VPT, int BPC>
+template <int W, int VPT, int BPC, bool CERT = false>
 __global__ void __launch_bounds__(32 * W * BPC, (SE_ITER_MIN_WARPS + W * BPC - 1) / (W * BPC))
 iterate_f32_kernel(const IterArgs a)
 {
@@ -377,10 +403,18 @@ iterate_f32_kernel(const IterArgs a)
             m[3] = fmaxf(m[3], fabsf(v.w));
         }
 
+        int first_close = -1;
         for (int nu = 0; nu < I; ++nu) {
             int u;
             float ru;
-            select_f32<W, VPT>(R2, m, tid, lane, warp, sRed + (nu & 1) * W, u, ru);
+            if constexpr (CERT) {
+                float s2;
+                select_f32<W, VPT, true>(R2, m, tid, lane, warp, sRed + (nu & 1) * W, u, ru, &s2);
+                const float s1 = fabsf(ru);
+                if (first_close < 0 && !(s1 - s2 > a.cert_delta * s1)) first_close = nu;
+            } else {
+                select_f32<W, VPT>(R2, m, tid, lane, warp, sRed + (nu & 1) * W, u, ru);
+            }
             if (u < 0 || u >= a.K) {
                 if (tid == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
                 u = 0;
@@ -440,6 +474,7 @@ iterate_f32_kernel(const IterArgs a)
             }
         }
         if constexpr (W > 1) __syncthreads(); else __syncwarp();
+        if (CERT && tid == 0) a.cert_flag[b] = first_close;
         if (failed) break;
         if (a.log_u) continue;                  // the model kernel evaluates the model
 
@@ -542,14 +577,14 @@ __global__ void __launch_bounds__(256) model_f32_kernel(const IterArgs a)
         for (int nu = lane; nu < I; nu += 32) bd.sel_coef[nu] = static_cast<double>(lc[nu]);
 }
 
-template <int W, int VPT, int BPC>
+template <int W, int VPT, int BPC, bool CERT = false>
 cudaError_t launch_f32(const IterArgs &a, cudaStream_t st, int *launches)
 {
     constexpr int threads = 32 * W * BPC;
     if (a.Kp != 32 * W * VPT) return cudaErrorInvalidValue;
     const size_t smem = 16 * BPC + (SE_ITER_ASYNC ? sizeof(float) * BPC * a.Kp : 0) +
                         sizeof(Cand<float>) * 2 * W + (sizeof(float) + sizeof(int)) * BPC * a.I_max + 16;
-    auto kern = iterate_f32_kernel<W, VPT, BPC>;
+    auto kern = iterate_f32_kernel<W, VPT, BPC, CERT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -614,6 +649,14 @@ cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st)
 template <>
 cudaError_t launch_iterate_full<float>(const IterArgs &a, cudaStream_t st, int *launches, int variant)
 {
+    if (a.cert_flag) {   // certified form: one warp per block, K <= 2048
+        switch (a.Kp) {
+        case 512: return launch_f32<1, 16, 4, true>(a, st, launches);
+        case 1024: return launch_f32<1, 32, 4, true>(a, st, launches);
+        case 2048: return launch_f32<1, 64, 4, true>(a, st, launches);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     // variant 1: twice the warps per block with half the projections per
     // lane (same selections and updates, another occupancy / latency balance)
     switch (a.Kp) {
@@ -630,6 +673,11 @@ cudaError_t launch_iterate_full<float>(const IterArgs &a, cudaStream_t st, int *
 int iterate_variants(int Kp, bool fp64)
 {
     return !fp64 && (Kp == 2048 || Kp == 4096 || Kp == 8192) ? 2 : 1;
+}
+
+int iterate_cert_max_kp()
+{
+    return 2048;
 }
 
 template <>

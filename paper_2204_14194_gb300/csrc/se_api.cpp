@@ -153,6 +153,7 @@ PrecCfg prec_cfg(se_prec p)
     case SE_PREC_FP64:
         c.fp64 = true;
         break;
+    case SE_PREC_CERTIFIED:
     case SE_PREC_BF16X6: {
         c.nparts = 3;
         c.npairs = 6;
@@ -222,6 +223,11 @@ void se::route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::
     full.clear();
     *I_full = 0;
 }
+
+// Relative gap between the two largest |R'| below which a certified plan
+// recomputes the block in fp64 (about 10x the largest fp32 score error
+// measured against the fp64 form on the benchmark workloads).
+constexpr float kCertGap = 1.5e-5f;
 
 // Model and replacement after the fp32 iteration kernel wrote its log:
 // separable outer products for transform plans, gathered atom values else.
@@ -381,6 +387,10 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         SE_CUDA(cudaEventSynchronize(ws.ev_ws));
     const size_t need_logs = fp64 ? 16 : 8 * static_cast<size_t>(n) * I_max;
     if (ws.logs.bytes < need_logs) SE_CUDA(cudaEventSynchronize(ws.ev_ws));
+    if (pl->certified) {
+        if (ws.cert.bytes < sizeof(int) * static_cast<size_t>(n)) SE_CUDA(cudaEventSynchronize(ws.ev_ws));
+        SE_TRY(dev_alloc(ctx, ws.cert, sizeof(int) * static_cast<size_t>(n)));
+    }
     SE_TRY(dev_alloc(ctx, ws.desc, need_desc));
     SE_TRY(dev_alloc(ctx, ws.x, need_x));
     SE_TRY(dev_alloc(ctx, ws.r0, need_r0));
@@ -448,6 +458,10 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         a.log_u = ws.logs.as<int>();
         a.log_c = reinterpret_cast<float *>(ws.logs.as<int>() + static_cast<size_t>(n) * I_max);
     }
+    if (pl->certified) {
+        a.cert_flag = ws.cert.as<int>();
+        a.cert_delta = kCertGap;
+    }
     int launched = 0;
     tok = stage_begin(ctx, 3, st);
     const std::string ikey = std::string("iterate:") + (fp64 ? "f64:" : "f32:") + std::to_string(Kp);
@@ -467,6 +481,23 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     ctx->launches += launched;
     probe_end(ctx, pl, 1, n, probe, st);
     SE_CUDA(cudaEventRecord(ws.ev_ws, st));
+    if (pl->certified) {
+        // blocks with a selection inside the certification gap: recompute in fp64
+        std::vector<int> flag(n);
+        SE_CUDA(cudaMemcpyAsync(flag.data(), ws.cert.ptr, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+        SE_CUDA(cudaStreamSynchronize(st));
+        std::vector<BlockDesc> again;
+        int I_again = 0;
+        for (int i = 0; i < n; ++i)
+            if (flag[i] >= 0) {
+                again.push_back(hdesc[i]);
+                I_again = std::max(I_again, hdesc[i].iterations);
+            }
+        ctx->cert_blocks += n;
+        ctx->cert_recomputed += again.size();
+        if (!again.empty())
+            SE_TRY(run_batch(ctx, pl->shadow, ws, static_cast<int>(again.size()), again.data(), I_again, st));
+    }
     return SE_OK;
 }
 
@@ -580,8 +611,10 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return fail(SE_ERR_INVALID, "gamma must be in (0, 1]");
     if (d.iterations < 1) return fail(SE_ERR_INVALID, "iterations must be >= 1");
     if (d.prec != SE_PREC_FP64 && d.prec != SE_PREC_BF16X6 && d.prec != SE_PREC_BF16X3 &&
-        d.prec != SE_PREC_BF16)
+        d.prec != SE_PREC_BF16 && d.prec != SE_PREC_CERTIFIED)
         return fail(SE_ERR_INVALID, "unknown precision");
+    if (d.prec == SE_PREC_CERTIFIED && d.gram == SE_GRAM_LAZY)
+        return fail(SE_ERR_INVALID, "certified plans serve the plan's pattern (gram LAZY not supported)");
     if (d.gram < SE_GRAM_AUTO || d.gram > SE_GRAM_LAZY) return fail(SE_ERR_INVALID, "unknown table mode");
     if (d.products < SE_PRODUCTS_AUTO || d.products > SE_PRODUCTS_TRANSFORM)
         return fail(SE_ERR_INVALID, "unknown product mode");
@@ -603,6 +636,9 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     const int MN = pl->MN, K = pl->K;
     pl->Kp = iterate_kp(K, pl->pc.fp64);
     if (pl->Kp < 0) return fail(SE_ERR_INVALID, "K is larger than the iteration kernel supports (16384)");
+    pl->certified = d.prec == SE_PREC_CERTIFIED;
+    if (pl->certified && pl->Kp > iterate_cert_max_kp())
+        return fail(SE_ERR_INVALID, "certified plans support K <= " + std::to_string(iterate_cert_max_kp()));
     find_collinear(K, MN, pl->phi.data(), pl->dup);
 
     pl->pattern.assign(MN, 1);
@@ -710,6 +746,19 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     SE_TRY(dev_alloc(ctx, pl->d_nadm, 16));   // admissible count (int) + largest C_kk (8 bytes at +8)
     SE_CUDA(cudaEventCreateWithFlags(&pl->tables_ready, cudaEventDisableTiming));
     SE_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (pl->certified) {
+        // the internal FP64 plan that recomputes the flagged blocks; owned by
+        // this plan (not listed in the context)
+        se_plan_desc d64 = d;
+        d64.prec = SE_PREC_FP64;
+        se_plan_s *sh = nullptr;
+        SE_TRY(se_plan(ctx, &d64, &sh));
+        {
+            std::lock_guard<std::mutex> lk(ctx->smu);
+            ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), sh), ctx->plans.end());
+        }
+        pl->shadow = sh;
+    }
     se_plan_s *raw = pl.release();
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
@@ -727,6 +776,13 @@ se_status se_plan_destroy(se_plan_t *plan)
     cudaDeviceSynchronize();
     probes_poll(ctx, true, plan);
     graphs_drop_plan(ctx, plan);
+    if (plan->shadow) {
+        probes_poll(ctx, true, plan->shadow);
+        graphs_drop_plan(ctx, plan->shadow);
+        if (plan->shadow->tables_ready) cudaEventDestroy(plan->shadow->tables_ready);
+        delete plan->shadow;
+        plan->shadow = nullptr;
+    }
     {
         std::lock_guard<std::mutex> lk(ctx->smu);
         ctx->plans.erase(std::remove(ctx->plans.begin(), ctx->plans.end(), plan), ctx->plans.end());
@@ -758,6 +814,8 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, cons
     SE_TRY(resolve_blocks(pl, n, blocks, d, &I_max, &any_mask));
     if (any_mask && pl->desc.gram == SE_GRAM_FULL)
         return fail(SE_ERR_INVALID, "per-block support masks need the lazy table path (plan gram is FULL)");
+    if (any_mask && pl->certified)
+        return fail(SE_ERR_INVALID, "certified plans serve blocks on the plan's pattern only");
     // blocks on the plan's pattern use the full table (unless LAZY is forced);
     // blocks with their own mask use lazily computed columns
     std::vector<BlockDesc> full, lazy;
@@ -977,6 +1035,14 @@ se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_buil
     if (tunings) *tunings = ctx->tunings.load();
     if (graph_builds) *graph_builds = ctx->graph_builds.load();
     if (graph_replays) *graph_replays = ctx->graph_replays.load();
+    return SE_OK;
+}
+
+se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    if (blocks) *blocks = ctx->cert_blocks.load();
+    if (recomputed) *recomputed = ctx->cert_recomputed.load();
     return SE_OK;
 }
 

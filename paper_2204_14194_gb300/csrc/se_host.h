@@ -47,7 +47,7 @@ struct DevBuf {
 // Device workspace of one in-flight batch (descriptors, packed operands,
 // initial projections, host-call I/O) with its pinned descriptor staging.
 struct Workspace {
-    DevBuf desc, x, r0, io, logs;
+    DevBuf desc, x, r0, io, logs, cert;
     // per-block-mask (lazy) path
     DevBuf lz_R, lz_D, lz_diag, lz_slot, lz_nslots, lz_cache, lz_ulog, lz_clog, lz_cur, lz_miss,
         lz_x, lz_mk, lz_v;
@@ -188,6 +188,7 @@ struct se_ctx_s {
     std::vector<se::CachedGraph> graphs;
     uint64_t graph_clock = 0;
     std::atomic<uint64_t> graph_builds{0}, graph_replays{0};
+    std::atomic<uint64_t> cert_blocks{0}, cert_recomputed{0};
 
     // serving
     std::mutex smu;
@@ -207,6 +208,8 @@ struct se_plan_s {
     se_plan_desc desc{};
     int M = 0, N = 0, MN = 0, K = 0, Kp = 0;
     se::PrecCfg pc;
+    bool certified = false;               // SE_PREC_CERTIFIED: fp32 path + fp64 recomputation
+    se_plan_s *shadow = nullptr;          //   the internal FP64 plan of a certified plan (owned)
     std::vector<double> phi;              // host K x MN atoms (fp64)
     std::vector<uint8_t> dup;             // host K flags
     std::vector<uint8_t> pattern;         // host MN default support

@@ -110,12 +110,17 @@ struct IterArgs {
     int *err;
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
     float *log_c;           //   model kernel; NULL: the iteration kernel evaluates the model
+    int *cert_flag;         // certified fp32 form: [n] first iteration whose two best |R'| lie
+                            //   within cert_delta (relative) of each other, -1 if none; NULL: off
+    float cert_delta;
 };
 // variant < iterate_variants(Kp, fp64): launch shapes with identical results
 // (see launch_iterate_full<float>).
 template <typename T>
 cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launches, int variant = 0);
 int iterate_variants(int Kp, bool fp64);
+// Largest padded K of the certified fp32 form (one warp per block).
+int iterate_cert_max_kp();
 
 // ------------------------------------------------------------ lazy columns
 struct LazyArgs {
