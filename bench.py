@@ -307,9 +307,13 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     achieved = ops / it_avg_s / 1e12
     variant = max(ctx.tuned_variant("iterate:f32:%d" % K), 0)
-    roofline = {"kernel": ITERATE_SHAPES.get(variant, "iterate_f32_kernel"), "bound": "alu", "achieved": achieved,
+    if args.prec == "certified":   # one launch shape; the stage also holds the fp64 recomputation
+        it_kernel, it_traffic = "iterate_f32_kernel<1,64,4> certified form + fp64 recomputation", None
+    else:
+        it_kernel, it_traffic = ITERATE_SHAPES.get(variant, "iterate_f32_kernel"), TRAFFIC_ITERATE.get(variant)
+    roofline = {"kernel": it_kernel, "bound": "alu", "achieved": achieved,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                "traffic": TRAFFIC_ITERATE.get(variant),
+                "traffic": it_traffic,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
                 "l2_read_GBps": n * (I - 1) * K * 4 / it_avg_s / 1e9}
     pr_ms, pr_n = stages["projections"]
