@@ -130,6 +130,13 @@ typedef struct {
     se_prec prec;
     se_gram gram;
     se_products products;     /* scalar products of the shared-pattern path */
+    int T;                    /* frames of a 3-D (video) area, 1..64; 0 = 1 (a 2-D area).  A 3-D
+                                 area is M x N x T samples stored frame-major, index
+                                 (t M + m) N + n; eq. (5) takes the distance to the centre of
+                                 the block; DCT / WHT atoms are products of three 1-D rows,
+                                 k = (r M + p) N + q (WHT: T a power of two); the default pattern
+                                 loses the centred M/2 x N/2 box in frames T/4 .. T/4+max(T/2,1)-1.
+                                 M N T <= 65536.  3-D plans use the dense products. */
 } se_plan_desc;
 
 /* One concealment block for se_extrapolate_batch (all pointers device). */

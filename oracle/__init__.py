@@ -67,6 +67,12 @@ def _load():
         lib.or_dict_wht.restype = ip
         lib.or_dict_dct_wht.argtypes = [ip, ip, _dp]
         lib.or_dict_dct_wht.restype = ip
+        lib.or_weights3.argtypes = [ip, ip, ip, dbl, _u8, vp, _dp]
+        lib.or_dict_dct3.argtypes = [ip, ip, ip, _dp]
+        lib.or_dict_wht3.argtypes = [ip, ip, ip, _dp]
+        lib.or_dict_wht3.restype = ip
+        lib.or_dict_dct_wht3.argtypes = [ip, ip, ip, _dp]
+        lib.or_dict_dct_wht3.restype = ip
         lib.or_find_duplicates.argtypes = [ip, ip, _dp, _u8]
         lib.or_projection_state.argtypes = [ip, ip, _dp, _dp, _dp, vp, vp, vp, vp]
         lib.or_se_original.argtypes = [ip, ip, ip, _dp, _dp, vp, _dp, dbl, ip, ip,
@@ -135,6 +141,38 @@ def dictionary(basis: str, M: int, N: int, numeric: Optional[np.ndarray] = None)
     if basis == "numeric":
         return _f64(numeric)
     raise ValueError(basis)
+
+
+def weights3(M: int, N: int, T: int, rho_hat: float, support: np.ndarray,
+             rho: Optional[np.ndarray] = None) -> np.ndarray:
+    """eq. (4)-(5) for an M x N x T block (frame-major [T][M][N])."""
+    w = np.empty((T, M, N))
+    sup = np.ascontiguousarray(support, dtype=np.uint8)
+    rr = None if rho is None else _f64(rho)
+    _load().or_weights3(M, N, T, float(rho_hat), sup, _ptr(rr), w)
+    return w
+
+
+def dictionary3(basis: str, M: int, N: int, T: int) -> np.ndarray:
+    """3-D DCT / WHT / DCT u WHT atoms, shape (K, T, M, N), k = (r M + p) N + q."""
+    V = M * N * T
+    K = 2 * V if basis == "dct_wht" else V
+    phi = np.empty((K, T, M, N))
+    lib = _load()
+    if basis == "dct":
+        lib.or_dict_dct3(M, N, T, phi)
+        return phi
+    fn = {"wht": lib.or_dict_wht3, "dct_wht": lib.or_dict_dct_wht3}[basis]
+    if fn(M, N, T, phi) != 0:
+        raise ValueError("WHT needs power-of-two M, N and T")
+    return phi
+
+
+def flat(a: np.ndarray) -> np.ndarray:
+    """A 3-D block (or stack of atoms / blocks) as the 2-D area (T M) x N that
+    Alg. 1-3 run on unchanged (frame-major flattening)."""
+    a = np.ascontiguousarray(a)
+    return a.reshape(a.shape[:-3] + (a.shape[-3] * a.shape[-2], a.shape[-1]))
 
 
 def find_duplicates(phi: np.ndarray) -> np.ndarray:

@@ -13,6 +13,9 @@
  *   or_weights            eq. (4)-(5)   weighting function w = rho on A, 0 on B
  *   or_dict_dct/wht       Sec. I        example dictionaries (normalisation and
  *                                       ordering are this oracle's reading)
+ *   or_weights3, or_dict_*3             the same for M x N x T (video) blocks,
+ *                                       the 3-D extension the paper names in
+ *                                       its conclusion
  *   or_find_duplicates                  collinear atoms (reading: only the
  *                                       lowest index of a collinear group
  *                                       may be selected)
@@ -135,6 +138,84 @@ int or_dict_dct_wht(int M, int N, double *phi)
 {
     or_dict_dct(M, N, phi);
     return or_dict_wht(M, N, phi + (size_t)M * N * M * N);
+}
+
+/* ------------------------------------------------ 3-D areas (video blocks) */
+/* The method itself does not depend on the dimension of the area (Sec. II
+ * works on any set of sample positions); for an M x N x T block the samples
+ * are stored frame-major, index (t * M + m) * N + n, and the functions of
+ * Alg. 1-3 below run unchanged on the flattened area.  Only the weighting
+ * function and the example dictionaries need the third coordinate. */
+
+/* eq. (5) with the distance to the centre of the M x N x T block. */
+void or_weights3(int M, int N, int T, double rho_hat, const uint8_t *support, const double *rho,
+                 double *w)
+{
+    for (int t = 0; t < T; ++t)
+        for (int m = 0; m < M; ++m)
+            for (int n = 0; n < N; ++n) {
+                const size_t i = ((size_t)t * M + m) * N + n;
+                double dt = t - (T - 1) / 2.0, dm = m - (M - 1) / 2.0, dn = n - (N - 1) / 2.0;
+                double r = rho ? rho[i] : pow(rho_hat, sqrt(dt * dt + dm * dm + dn * dn));
+                w[i] = support[i] ? r : 0.0;
+            }
+}
+
+/* 3-D orthonormal DCT-II atom (r, p, q) at (t, m, n); k = (r * M + p) * N + q. */
+void or_dict_dct3(int M, int N, int T, double *phi)
+{
+    const double pi = 3.14159265358979323846;
+    const size_t V = (size_t)M * N * T;
+    for (int r = 0; r < T; ++r)
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < N; ++q) {
+                double ar = r == 0 ? sqrt(1.0 / T) : sqrt(2.0 / T);
+                double ap = p == 0 ? sqrt(1.0 / M) : sqrt(2.0 / M);
+                double aq = q == 0 ? sqrt(1.0 / N) : sqrt(2.0 / N);
+                double *a = phi + ((size_t)r * M * N + (size_t)p * N + q) * V;
+                for (int t = 0; t < T; ++t)
+                    for (int m = 0; m < M; ++m)
+                        for (int n = 0; n < N; ++n)
+                            a[((size_t)t * M + m) * N + n] =
+                                ar * ap * aq * cos(pi * (2 * t + 1) * r / (2.0 * T)) *
+                                cos(pi * (2 * m + 1) * p / (2.0 * M)) * cos(pi * (2 * n + 1) * q / (2.0 * N));
+            }
+}
+
+/* 3-D WHT atom (r, p, q) = wal_r[t] wal_p[m] wal_q[n] / sqrt(MNT), sequency
+ * order, k = (r * M + p) * N + q; M, N, T powers of two.  Returns 0 on success. */
+int or_dict_wht3(int M, int N, int T, double *phi)
+{
+    if (M <= 0 || N <= 0 || T <= 0 || (M & (M - 1)) || (N & (N - 1)) || (T & (T - 1))) return -1;
+    double *wm = malloc(sizeof(double) * M * M);
+    double *wn = malloc(sizeof(double) * N * N);
+    double *wt = malloc(sizeof(double) * T * T);
+    if (!wm || !wn || !wt) { free(wm); free(wn); free(wt); return -2; }
+    walsh_rows(M, wm);
+    walsh_rows(N, wn);
+    walsh_rows(T, wt);
+    const size_t V = (size_t)M * N * T;
+    double s = 1.0 / sqrt((double)V);
+    for (int r = 0; r < T; ++r)
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < N; ++q) {
+                double *a = phi + ((size_t)r * M * N + (size_t)p * N + q) * V;
+                for (int t = 0; t < T; ++t)
+                    for (int m = 0; m < M; ++m)
+                        for (int n = 0; n < N; ++n)
+                            a[((size_t)t * M + m) * N + n] = wt[r * T + t] * wm[p * M + m] * wn[q * N + n] * s;
+            }
+    free(wm);
+    free(wn);
+    free(wt);
+    return 0;
+}
+
+/* 3-D DCT atoms at k in [0, MNT), 3-D WHT atoms at k in [MNT, 2MNT). */
+int or_dict_dct_wht3(int M, int N, int T, double *phi)
+{
+    or_dict_dct3(M, N, T, phi);
+    return or_dict_wht3(M, N, T, phi + (size_t)M * N * T * M * N * T);
 }
 
 /* excluded[j] = 1 if atom j is collinear over L with an atom i < j:

@@ -44,7 +44,7 @@ class PlanDesc(C.Structure):
     _fields_ = [("M", C.c_int), ("N", C.c_int), ("basis", C.c_int), ("K", C.c_int),
                 ("dict", C.c_void_p), ("rho_hat", C.c_double), ("rho", C.c_void_p),
                 ("support", C.c_void_p), ("gamma", C.c_double), ("iterations", C.c_int),
-                ("prec", C.c_int), ("gram", C.c_int), ("products", C.c_int)]
+                ("prec", C.c_int), ("gram", C.c_int), ("products", C.c_int), ("T", C.c_int)]
 
 
 class Block(C.Structure):
@@ -198,9 +198,10 @@ class Context:
     def plan(self, M: int, N: int, basis: str, K: int, rho_hat: float, gamma: float,
              iterations: int, prec: str = "bf16x6", gram: str = "auto",
              dictionary: Optional[np.ndarray] = None, support: Optional[np.ndarray] = None,
-             rho: Optional[np.ndarray] = None, products: str = "auto") -> "Plan":
+             rho: Optional[np.ndarray] = None, products: str = "auto", T: int = 1) -> "Plan":
+        """T > 1: a video block of T frames (arrays frame-major, [T][M][N])."""
         return Plan(self, M, N, basis, K, rho_hat, gamma, iterations, prec, gram, dictionary,
-                    support, rho, products)
+                    support, rho, products, T)
 
     # serving -------------------------------------------------------------
     def submit(self, plan: "Plan", samples: np.ndarray, out: np.ndarray,
@@ -231,10 +232,11 @@ class Plan:
     """An se_plan_t.  Host arrays are copied by the library."""
 
     def __init__(self, ctx: Context, M, N, basis, K, rho_hat, gamma, iterations, prec, gram,
-                 dictionary, support, rho, products="auto"):
+                 dictionary, support, rho, products="auto", T=1):
         self.ctx = ctx
         self._lib = ctx._lib
         self.M, self.N, self.K, self.iterations = int(M), int(N), int(K), int(iterations)
+        self.T = int(T)
         self.prec = prec
         self.products = products
         d = None if dictionary is None else np.ascontiguousarray(dictionary, dtype=np.float64)
@@ -242,7 +244,7 @@ class Plan:
         rh = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
         desc = PlanDesc(int(M), int(N), BASIS[basis], int(K), _ptr(d), float(rho_hat), _ptr(rh),
                         _ptr(sup), float(gamma), int(iterations), PREC[prec], GRAM[gram],
-                        PRODUCTS[products])
+                        PRODUCTS[products], int(T))
         h = C.c_void_p()
         _check(self._lib.se_plan(ctx.handle, C.byref(desc), C.byref(h)), "se_plan")
         self.handle = h

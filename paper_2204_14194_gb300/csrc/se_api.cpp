@@ -607,6 +607,10 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     *out = nullptr;
     const se_plan_desc &d = *desc;
     if (d.M < 1 || d.N < 1 || d.M > 256 || d.N > 256) return fail(SE_ERR_INVALID, "M and N must be in [1, 256]");
+    const int T = d.T == 0 ? 1 : d.T;
+    if (T < 1 || T > 64) return fail(SE_ERR_INVALID, "T must be in [1, 64] (0 = 1)");
+    if (static_cast<long long>(d.M) * d.N * T > 65536)
+        return fail(SE_ERR_INVALID, "M N T must be at most 65536 samples");
     if (!(d.rho_hat > 0.0 && d.rho_hat <= 1.0)) return fail(SE_ERR_INVALID, "rho_hat must be in (0, 1]");
     if (!(d.gamma > 0.0 && d.gamma <= 1.0)) return fail(SE_ERR_INVALID, "gamma must be in (0, 1]");
     if (d.iterations < 1) return fail(SE_ERR_INVALID, "iterations must be >= 1");
@@ -628,11 +632,13 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     pl->desc.support = nullptr;
     pl->M = d.M;
     pl->N = d.N;
-    pl->MN = d.M * d.N;
+    pl->T = T;
+    pl->desc.T = T;
+    pl->MN = d.M * d.N * T;
     pl->K = d.K;
     pl->pc = prec_cfg(d.prec);
     std::string why;
-    if (!build_dictionary(d.M, d.N, d.basis, d.K, d.dict, pl->phi, &why)) return fail(SE_ERR_INVALID, why);
+    if (!build_dictionary(d.M, d.N, T, d.basis, d.K, d.dict, pl->phi, &why)) return fail(SE_ERR_INVALID, why);
     const int MN = pl->MN, K = pl->K;
     pl->Kp = iterate_kp(K, pl->pc.fp64);
     if (pl->Kp < 0) return fail(SE_ERR_INVALID, "K is larger than the iteration kernel supports (16384)");
@@ -645,19 +651,21 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     if (d.support) {
         for (int i = 0; i < MN; ++i) pl->pattern[i] = d.support[i] ? 1 : 0;
     } else {
-        for (int m = d.M / 4; m < d.M / 4 + d.M / 2; ++m)
-            for (int n = d.N / 4; n < d.N / 4 + d.N / 2; ++n) pl->pattern[m * d.N + n] = 0;
+        // the centred loss box: M/2 x N/2 samples in frames T/4 .. T/4 + max(T/2, 1) - 1
+        for (int t = T / 4; t < T / 4 + std::max(T / 2, 1); ++t)
+            for (int m = d.M / 4; m < d.M / 4 + d.M / 2; ++m)
+                for (int n = d.N / 4; n < d.N / 4 + d.N / 2; ++n) pl->pattern[(t * d.M + m) * d.N + n] = 0;
     }
     if (d.rho) pl->rho_map.assign(d.rho, d.rho + MN);
-    weighting(d.M, d.N, d.rho_hat, d.rho, pl->pattern.data(), pl->w);
+    weighting(d.M, d.N, T, d.rho_hat, d.rho, pl->pattern.data(), pl->w);
     for (int i = 0; i < MN; ++i) {
         if (pl->pattern[i] && !(pl->w[i] >= 0.0 && std::isfinite(pl->w[i])))
             return fail(SE_ERR_INVALID, "rho must be finite and non-negative");
         if (pl->pattern[i] && pl->w[i] > 0.0) pl->a_idx.push_back(i);
         else if (!pl->pattern[i]) pl->b_idx.push_back(i);
     }
-    pl->box[0] = d.M; pl->box[1] = 0; pl->box[2] = d.N; pl->box[3] = 0;
-    for (int m = 0; m < d.M; ++m)
+    pl->box[0] = d.M; pl->box[1] = 0; pl->box[2] = d.N; pl->box[3] = 0;   // (2-D areas only)
+    for (int m = 0; m < d.M && T == 1; ++m)
         for (int n = 0; n < d.N; ++n)
             if (!pl->pattern[m * d.N + n]) {
                 pl->box[0] = std::min(pl->box[0], m); pl->box[1] = std::max(pl->box[1], m + 1);

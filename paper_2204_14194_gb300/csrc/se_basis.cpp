@@ -44,23 +44,30 @@ void walsh_seq_rows(int L, std::vector<double> &T)
     }
 }
 
-static void separable(int M, int N, const std::vector<double> &Tm, const std::vector<double> &Tn,
-                      double scale, double *phi)
+// Atoms that are products of 1-D rows: atom (r, p, q) at k = (r M + p) N + q
+// holds tt_r[t] tm_p[m] tn_q[n] * scale at pixel (t M + m) N + n (frame-major;
+// T = 1 is the 2-D case).
+static void separable(int M, int N, int T, const std::vector<double> &Tm, const std::vector<double> &Tn,
+                      const std::vector<double> &Tt, double scale, double *phi)
 {
-    for (int p = 0; p < M; ++p)
-        for (int q = 0; q < N; ++q) {
-            double *a = phi + static_cast<size_t>(p * N + q) * M * N;
-            for (int m = 0; m < M; ++m) {
-                const double vm = Tm[static_cast<size_t>(p) * M + m] * scale;
-                for (int n = 0; n < N; ++n) a[m * N + n] = vm * Tn[static_cast<size_t>(q) * N + n];
+    const size_t V = static_cast<size_t>(M) * N * T;
+    for (int r = 0; r < T; ++r)
+        for (int p = 0; p < M; ++p)
+            for (int q = 0; q < N; ++q) {
+                double *a = phi + (static_cast<size_t>(r) * M * N + static_cast<size_t>(p) * N + q) * V;
+                for (int t = 0; t < T; ++t)
+                    for (int m = 0; m < M; ++m) {
+                        const double vm = Tt[static_cast<size_t>(r) * T + t] * Tm[static_cast<size_t>(p) * M + m] * scale;
+                        for (int n = 0; n < N; ++n)
+                            a[(static_cast<size_t>(t) * M + m) * N + n] = vm * Tn[static_cast<size_t>(q) * N + n];
+                    }
             }
-        }
 }
 
-bool build_dictionary(int M, int N, int basis, int K, const double *numeric,
+bool build_dictionary(int M, int N, int T, int basis, int K, const double *numeric,
                       std::vector<double> &phi, std::string *why)
 {
-    const size_t MN = static_cast<size_t>(M) * N;
+    const size_t MN = static_cast<size_t>(M) * N * T;   // samples of the (flattened) area
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
     switch (basis) {
     case 1:   // DCT
@@ -71,21 +78,23 @@ bool build_dictionary(int M, int N, int basis, int K, const double *numeric,
             *why = "K does not match the basis cardinality (" + std::to_string(expect) + ")";
             return false;
         }
-        if (basis != 1 && (!pow2(M) || !pow2(N))) {
-            *why = "the WHT needs power-of-two M and N";
+        if (basis != 1 && (!pow2(M) || !pow2(N) || !pow2(T))) {
+            *why = "the WHT needs power-of-two M, N (and T)";
             return false;
         }
         phi.assign(static_cast<size_t>(K) * MN, 0.0);
-        std::vector<double> Tm, Tn;
+        std::vector<double> Tm, Tn, Tt;
         if (basis == 1 || basis == 3) {
             dct_rows(M, Tm);
             dct_rows(N, Tn);
-            separable(M, N, Tm, Tn, 1.0, phi.data());
+            dct_rows(T, Tt);
+            separable(M, N, T, Tm, Tn, Tt, 1.0, phi.data());
         }
         if (basis == 2 || basis == 3) {
             walsh_seq_rows(M, Tm);
             walsh_seq_rows(N, Tn);
-            separable(M, N, Tm, Tn, 1.0 / std::sqrt(static_cast<double>(MN)),
+            walsh_seq_rows(T, Tt);
+            separable(M, N, T, Tm, Tn, Tt, 1.0 / std::sqrt(static_cast<double>(MN)),
                       phi.data() + (basis == 3 ? MN * MN : 0));
         }
         return true;
@@ -150,22 +159,24 @@ void find_collinear(int K, int MN, const double *phi, std::vector<uint8_t> &dup)
 }
 
 // eq. (4)-(5): w = rho on A (rho_hat ^ distance to the area centre unless a
-// rho map is given), 0 on B.
-void weighting(int M, int N, double rho_hat, const double *rho, const uint8_t *support,
+// rho map is given), 0 on B; an M x N x T area is frame-major and its
+// distance has a temporal term (T = 1: the 2-D weighting).
+void weighting(int M, int N, int T, double rho_hat, const double *rho, const uint8_t *support,
                std::vector<double> &w)
 {
-    w.assign(static_cast<size_t>(M) * N, 0.0);
-    for (int m = 0; m < M; ++m)
-        for (int n = 0; n < N; ++n) {
-            const size_t i = static_cast<size_t>(m) * N + n;
-            if (!support[i]) continue;
-            if (rho) {
-                w[i] = rho[i];
-            } else {
-                const double dm = m - 0.5 * (M - 1), dn = n - 0.5 * (N - 1);
-                w[i] = std::pow(rho_hat, std::sqrt(dm * dm + dn * dn));
+    w.assign(static_cast<size_t>(M) * N * T, 0.0);
+    for (int t = 0; t < T; ++t)
+        for (int m = 0; m < M; ++m)
+            for (int n = 0; n < N; ++n) {
+                const size_t i = (static_cast<size_t>(t) * M + m) * N + n;
+                if (!support[i]) continue;
+                if (rho) {
+                    w[i] = rho[i];
+                } else {
+                    const double dt = t - 0.5 * (T - 1), dm = m - 0.5 * (M - 1), dn = n - 0.5 * (N - 1);
+                    w[i] = std::pow(rho_hat, std::sqrt(dt * dt + dm * dm + dn * dn));
+                }
             }
-        }
 }
 
 }  // namespace se

@@ -22,13 +22,13 @@ struct se_ctx_s;
 
 namespace se {
 
-bool build_dictionary(int M, int N, int basis, int K, const double *numeric,
+bool build_dictionary(int M, int N, int T, int basis, int K, const double *numeric,
                       std::vector<double> &phi, std::string *why);
 void find_collinear(int K, int MN, const double *phi, std::vector<uint8_t> &dup);
 // 1-D bases: orthonormal DCT-II rows and +-1 Walsh rows in sequency order (L x L).
 void dct_rows(int L, std::vector<double> &T);
 void walsh_seq_rows(int L, std::vector<double> &T);
-void weighting(int M, int N, double rho_hat, const double *rho, const uint8_t *support,
+void weighting(int M, int N, int T, double rho_hat, const double *rho, const uint8_t *support,
                std::vector<double> &w);
 
 // A device allocation charged against the context's HBM budget.
@@ -207,6 +207,7 @@ struct se_plan_s {
     se_ctx_s *ctx = nullptr;
     se_plan_desc desc{};
     int M = 0, N = 0, MN = 0, K = 0, Kp = 0;
+    int T = 1;                            // frames of a 3-D (video) area; MN = M N T samples
     se::PrecCfg pc;
     bool certified = false;               // SE_PREC_CERTIFIED: fp32 path + fp64 recomputation
     se_plan_s *shadow = nullptr;          //   the internal FP64 plan of a certified plan (owned)

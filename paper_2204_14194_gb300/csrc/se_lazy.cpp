@@ -45,7 +45,7 @@ se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
     const int MNp = static_cast<int>(r64(MN));
     std::vector<uint8_t> all(MN, 1);
     std::vector<double> rho;
-    weighting(pl->M, pl->N, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
+    weighting(pl->M, pl->N, pl->T, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
               all.data(), rho);
     std::vector<double> phi(static_cast<size_t>(Kp) * MN, 0.0), ar(static_cast<size_t>(Kp) * MNp, 0.0),
         ad(static_cast<size_t>(Kp) * MNp, 0.0);
@@ -92,11 +92,11 @@ se_status se::ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl)
     const int basis = pl->desc.basis;
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
     const size_t smem = tsz * (2 * static_cast<size_t>(MN) + pl->M * pl->M + pl->N * pl->N);
-    if ((basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT) &&
+    if ((basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT) && pl->T == 1 &&
         smem <= 227 * 1024) {
         std::vector<uint8_t> all(MN, 1);
         std::vector<double> rho;
-        weighting(pl->M, pl->N, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
+        weighting(pl->M, pl->N, pl->T, pl->desc.rho_hat, pl->rho_map.empty() ? nullptr : pl->rho_map.data(),
                   all.data(), rho);
         LZ_TRY(upload_vec(ctx, pl->d_rho, rho));
         int t = 0;

@@ -116,6 +116,27 @@ def holes_support(M: int, N: int, rng: np.random.Generator) -> np.ndarray:
     return s
 
 
+def video_block(M: int, N: int, T: int, seed: int) -> np.ndarray:
+    """A ``T x M x N`` (frame-major) float64 block of a moving scene: frame t is
+    the ``M x N`` window at offset (t*vy, t*vx) of one larger generator draw,
+    with a velocity (vy, vx) in {0, 1, 2}^2 pixels per frame drawn from the seed."""
+    rng = np.random.default_rng(seed)
+    vy, vx = (int(v) for v in rng.integers(0, 3, size=2))
+    L = max(M, N) + 2 * T + 2
+    big = patch(L, seed + 7919)
+    return np.stack([big[t * vy:t * vy + M, t * vx:t * vx + N] for t in range(T)])
+
+
+def centred_support3(M: int, N: int, T: int) -> np.ndarray:
+    """Frame-major ``T x M x N`` support with the centred loss box of
+    ``M/2 x N/2`` pixels in frames T/4 .. T/4 + max(T/2, 1) - 1 (for T = 1
+    this is ``centred_support``)."""
+    s = np.ones((T, M, N), dtype=np.uint8)
+    t0, nt = T // 4, max(T // 2, 1)
+    s[t0:t0 + nt, M // 4: M // 4 + M // 2, N // 4: N // 4 + N // 2] = 0
+    return s
+
+
 def gaussian_dictionary(K: int, M: int, N: int, seed: int) -> np.ndarray:
     """``K`` i.i.d. N(0,1) atoms of size ``M x N`` (atom-major), each of unit l2 norm over L."""
     rng = np.random.default_rng(seed)

@@ -305,3 +305,76 @@ def test_table1_counts_reproduce_fig3():
         else:
             ops = opcount.total(opcount.table_ops(64, 64, 4096))
         assert math.log10(ops) == pytest.approx(v, abs=6e-7), (curve, I)
+
+
+# ------------------------------------------------------------- 3-D blocks
+# The paper names the extension to video (three-dimensional areas) in its
+# conclusion; the method runs unchanged on the flattened area, only the
+# weighting function and the dictionaries gain a third coordinate.
+@pytest.mark.parametrize("M,N,T", [(4, 6, 3), (8, 8, 4)])
+def test_dct3_atoms_are_scipy_inverse_dct_of_impulses(M, N, T):
+    phi = O.dictionary3("dct", M, N, T)
+    V = M * N * T
+    for k in [0, 1, N, M * N, M * N + N + 1, V // 2 + 3, V - 1]:
+        r, rest = divmod(k, M * N)
+        p, q = divmod(rest, N)
+        e = np.zeros((T, M, N))
+        e[r, p, q] = 1.0
+        np.testing.assert_allclose(phi[k], scipy.fft.idctn(e, norm="ortho"), atol=1e-14)
+
+
+def test_wht3_atoms_are_kronecker_products_of_sequency_rows():
+    M, N, T = 4, 8, 2
+    phi = O.dictionary3("wht", M, N, T).reshape(M * N * T, M * N * T)
+    ref = np.kron(np.kron(_sequency_hadamard(T), _sequency_hadamard(M)), _sequency_hadamard(N))
+    np.testing.assert_array_equal(phi, ref / math.sqrt(M * N * T))
+    u = O.dictionary3("dct_wht", M, N, T)
+    np.testing.assert_array_equal(u[M * N * T:], O.dictionary3("wht", M, N, T))
+
+
+def test_weights3_integer_distances_and_masking():
+    rho = 0.8
+    sup = np.ones((5, 5, 5), dtype=np.uint8)
+    sup[4, 4, 4] = 0
+    w = O.weights3(5, 5, 5, rho, sup)
+    assert w[2, 2, 2] == 1.0                                  # centre
+    assert w[2, 2, 4] == pytest.approx(rho ** 2, rel=1e-15)   # axis
+    assert w[3, 4, 4] == pytest.approx(rho ** 3, rel=1e-15)   # (1, 2, 2): distance 3
+    assert w[4, 4, 4] == 0.0
+    # T = 1 is the 2-D weighting and dictionary
+    s2 = W.centred_support(8, 8)
+    np.testing.assert_array_equal(O.weights3(8, 8, 1, rho, s2[None]), O.weights(8, 8, rho, s2)[None])
+    np.testing.assert_array_equal(O.dictionary3("dct_wht", 8, 8, 1)[:, 0], O.dict_dct_wht(8, 8))
+
+
+@pytest.mark.parametrize("basis,j", [("dct", 37), ("dct_wht", 300)])
+def test_single_atom_closed_form_3d(basis, j):
+    M, N, T = 8, 8, 4
+    phi = O.flat(O.dictionary3(basis, M, N, T))
+    dup = O.find_duplicates(phi)
+    assert not dup[j]
+    w = O.flat(O.weights3(M, N, T, 0.8, W.centred_support3(M, N, T)))
+    a, gamma, I = 21.0, 0.5, 30
+    r = O.se_original(phi, w, a * phi[j], gamma, I, dup)
+    assert np.all(r.u == j)
+    nu = np.arange(1, I + 1)
+    np.testing.assert_allclose(r.c, gamma * (1 - gamma) ** (nu - 1) * a, rtol=1e-11)
+    np.testing.assert_allclose(r.g, a * (1 - (1 - gamma) ** I) * phi[j], rtol=1e-11, atol=1e-12)
+
+
+def test_fase_equals_se_on_a_video_block():
+    M, N, T, I = 8, 8, 4, 40
+    phi = O.flat(O.dictionary3("dct_wht", M, N, T))
+    dup = O.find_duplicates(phi)
+    w = O.flat(O.weights3(M, N, T, 0.8, W.centred_support3(M, N, T)))
+    s = O.flat(W.video_block(M, N, T, 5))
+    a = O.se_original(phi, w, s, 0.5, I, dup)
+    Cm, D = O.fase_tables(phi, w)
+    f = O.fase(phi, w, Cm, D, s, 0.5, I, dup)
+    t = int(np.argmax(a.margin <= 1e-9)) if np.any(a.margin <= 1e-9) else I
+    assert t >= 10
+    np.testing.assert_array_equal(a.u[:t], f.u[:t])
+    np.testing.assert_allclose(f.c[:t], a.c[:t], rtol=1e-10)
+    # the energy drops monotonically, as in 2-D
+    assert np.all(np.diff(a.energy) <= 1e-9 * a.energy[0])
+
