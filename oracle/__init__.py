@@ -74,6 +74,18 @@ def _load():
         lib.or_dict_dct_wht3.argtypes = [ip, ip, ip, _dp]
         lib.or_dict_dct_wht3.restype = ip
         lib.or_find_duplicates.argtypes = [ip, ip, _dp, _u8]
+        lib.or_dict_dft.argtypes = [ip, ip, _dp, _dp]
+        lib.or_dict_bdft.argtypes = [ip, ip, _dp, _dp]
+        lib.or_dict_dft_bdft.argtypes = [ip, ip, _dp, _dp]
+        lib.or_find_duplicates_c.argtypes = [ip, ip, _dp, _dp, _u8]
+        lib.or_se_original_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip,
+                                         _dp, vp, vp, vp, vp, vp, vp]
+        lib.or_se_original_c.restype = ip
+        lib.or_fase_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip, _dp, vp, vp, vp, vp]
+        lib.or_fase_c.restype = ip
+        lib.or_se_original_c_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, ip, vp, _dp, dbl, ip,
+                                               _dp, vp, vp, vp, vp, ip]
+        lib.or_se_original_c_batch.restype = ip
         lib.or_projection_state.argtypes = [ip, ip, _dp, _dp, _dp, vp, vp, vp, vp]
         lib.or_se_original.argtypes = [ip, ip, ip, _dp, _dp, vp, _dp, dbl, ip, ip,
                                        _dp, vp, vp, vp, vp, vp, vp]
@@ -293,3 +305,83 @@ def fase_batch(phi, w, Cm, D, s, gamma, I, dup=None, nthreads: int = 0):
 
 def max_threads() -> int:
     return int(_load().or_max_threads())
+
+
+# ------------------------------------------------------------ complex atoms
+def dict_complex(basis: str, M: int, N: int) -> np.ndarray:
+    """DFT / binarised DFT / their union as complex128 atoms (K, M, N)."""
+    V = M * N
+    K = 2 * V if basis == "dft_bdft" else V
+    re, im = np.empty((K, M, N)), np.empty((K, M, N))
+    fn = {"dft": _load().or_dict_dft, "bdft": _load().or_dict_bdft, "dft_bdft": _load().or_dict_dft_bdft}[basis]
+    fn(M, N, re, im)
+    return re + 1j * im
+
+
+def _planes(phi: np.ndarray):
+    return np.ascontiguousarray(phi.real, dtype=np.float64), np.ascontiguousarray(phi.imag, dtype=np.float64)
+
+
+def find_duplicates_c(phi: np.ndarray) -> np.ndarray:
+    K = phi.shape[0]
+    MN = int(np.prod(phi.shape[1:]))
+    re, im = _planes(phi)
+    ex = np.zeros(K, dtype=np.uint8)
+    _load().or_find_duplicates_c(K, MN, re, im, ex)
+    return ex
+
+
+def se_original_c(phi: np.ndarray, w: np.ndarray, s: np.ndarray, gamma: float, I: int,
+                  dup: Optional[np.ndarray] = None) -> SEResult:
+    """Complex Alg. 1 for one block; ``s`` real or complex.  ``out`` and ``g`` are complex."""
+    K = phi.shape[0]
+    M, N = w.shape
+    re, im = _planes(phi)
+    s = np.asarray(s)
+    s_re, s_im = np.ascontiguousarray(s.real, dtype=np.float64), np.ascontiguousarray(np.imag(s), dtype=np.float64)
+    o_re, o_im = np.empty((M, N)), np.empty((M, N))
+    u = np.empty(I, dtype=np.int32)
+    cr, ci, e, mg = np.empty(I), np.empty(I), np.empty(I), np.empty(I)
+    d = None if dup is None else np.ascontiguousarray(dup, dtype=np.uint8)
+    rc = _load().or_se_original_c(M, N, K, re, im, _f64(w), _ptr(d), s_re, _ptr(s_im), float(gamma), int(I),
+                                  o_re, _ptr(o_im), _ptr(u), _ptr(cr), _ptr(ci), _ptr(e), _ptr(mg))
+    out = o_re + 1j * o_im
+    g = np.where(np.asarray(w) > 0, np.nan, out)
+    return SEResult(out, g, u, cr + 1j * ci, energy=e, margin=mg, status=rc)
+
+
+def fase_c(phi: np.ndarray, w: np.ndarray, s: np.ndarray, gamma: float, I: int,
+           dup: Optional[np.ndarray] = None) -> SEResult:
+    """Complex Alg. 2 + 3 for one block (tables built inside)."""
+    K = phi.shape[0]
+    M, N = w.shape
+    re, im = _planes(phi)
+    s = np.asarray(s)
+    s_re, s_im = np.ascontiguousarray(s.real, dtype=np.float64), np.ascontiguousarray(np.imag(s), dtype=np.float64)
+    o_re, o_im = np.empty((M, N)), np.empty((M, N))
+    u = np.empty(I, dtype=np.int32)
+    cr, ci = np.empty(I), np.empty(I)
+    d = None if dup is None else np.ascontiguousarray(dup, dtype=np.uint8)
+    rc = _load().or_fase_c(M, N, K, re, im, _f64(w), _ptr(d), s_re, _ptr(s_im), float(gamma), int(I),
+                           o_re, _ptr(o_im), _ptr(u), _ptr(cr), _ptr(ci))
+    return SEResult(o_re + 1j * o_im, None, u, cr + 1j * ci, status=rc)
+
+
+def se_original_c_batch(phi: np.ndarray, w: np.ndarray, s: np.ndarray, gamma: float, I: int,
+                        dup: Optional[np.ndarray] = None, nthreads: int = 0, margins: bool = False):
+    """Complex Alg. 1 over real blocks ``s[B, M, N]``; returns (Re out, u, complex c, status[, margins])."""
+    K = phi.shape[0]
+    B, M, N = s.shape
+    re, im = _planes(phi)
+    out = np.empty((B, M, N))
+    u = np.full((B, I), -1, dtype=np.int32)
+    cr, ci = np.full((B, I), np.nan), np.full((B, I), np.nan)
+    mg = np.full((B, I), np.nan) if margins else None
+    d = None if dup is None else np.ascontiguousarray(dup, dtype=np.uint8)
+    rc = _load().or_se_original_c_batch(B, M, N, K, re, im, _f64(w), int(w.ndim == 3), _ptr(d), _f64(s),
+                                        float(gamma), int(I), out, _ptr(u), _ptr(cr), _ptr(ci), _ptr(mg),
+                                        int(nthreads))
+    if margins:
+        return out, u, cr + 1j * ci, mg, rc
+    return out, u, cr + 1j * ci, rc
+

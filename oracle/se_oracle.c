@@ -16,6 +16,9 @@
  *   or_weights3, or_dict_*3             the same for M x N x T (video) blocks,
  *                                       the 3-D extension the paper names in
  *                                       its conclusion
+ *   or_dict_dft/bdft, or_*_c            complex-valued atoms (DFT, binarised
+ *                                       DFT) and Alg. 1-3 with conjugates,
+ *                                       the paper's general case
  *   or_find_duplicates                  collinear atoms (reading: only the
  *                                       lowest index of a collinear group
  *                                       may be selected)
@@ -514,6 +517,284 @@ int or_fase_batch(int B, int M, int N, int K, const double *phi, const double *w
                          out + (size_t)b * MN, NULL, NULL,
                          u_log ? u_log + (size_t)b * I : NULL,
                          c_log ? c_log + (size_t)b * I : NULL);
+        if (rc) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            if (!status) status = rc;
+        }
+    }
+    return status;
+}
+
+/* ----------------------------------------------- complex-valued atoms */
+/* The paper states SE and FaSE for complex-valued signals and atoms (Sec. II
+ * and III): the scalar products use the conjugated atom, the selection takes
+ * |R_k| D_k, the coefficient is complex and C is Hermitian.  Complex arrays
+ * are kept as separate real and imaginary planes ("_re", "_im").  Signals in
+ * the tests are real images or, for the closed-form pin, a complex atom. */
+
+/* 2-D DFT atom (mu, eta): exp(j 2 pi (mu m / M + eta n / N)) / sqrt(MN),
+ * k = mu * N + eta.  The phase is reduced exactly in integers,
+ * theta = 2 pi a / (MN) with a = (mu m N + eta n M) mod MN. */
+void or_dict_dft(int M, int N, double *re, double *im)
+{
+    const double pi = 3.14159265358979323846;
+    const long L = (long)M * N;
+    const double s = 1.0 / sqrt((double)L);
+    for (int mu = 0; mu < M; ++mu)
+        for (int eta = 0; eta < N; ++eta) {
+            const size_t k = (size_t)mu * N + eta;
+            for (int m = 0; m < M; ++m)
+                for (int n = 0; n < N; ++n) {
+                    long a = ((long)mu * m * N + (long)eta * n * M) % L;
+                    re[k * L + (size_t)m * N + n] = s * cos(2.0 * pi * a / L);
+                    im[k * L + (size_t)m * N + n] = s * sin(2.0 * pi * a / L);
+                }
+        }
+}
+
+/* Binarised DFT atom (reading of "a binarized version of DFT functions"):
+ * sgn(cos theta) + j sgn(sin theta) with sgn(0) = +1, decided exactly on the
+ * integer phase a of or_dict_dft (cos >= 0 iff 4a <= L or 4a >= 3L;
+ * sin >= 0 iff 2a <= L), scaled to unit norm by 1 / sqrt(2 MN). */
+void or_dict_bdft(int M, int N, double *re, double *im)
+{
+    const long L = (long)M * N;
+    const double s = 1.0 / sqrt(2.0 * (double)L);
+    for (int mu = 0; mu < M; ++mu)
+        for (int eta = 0; eta < N; ++eta) {
+            const size_t k = (size_t)mu * N + eta;
+            for (int m = 0; m < M; ++m)
+                for (int n = 0; n < N; ++n) {
+                    long a = ((long)mu * m * N + (long)eta * n * M) % L;
+                    re[k * L + (size_t)m * N + n] = (4 * a <= L || 4 * a >= 3 * L) ? s : -s;
+                    im[k * L + (size_t)m * N + n] = (2 * a <= L) ? s : -s;
+                }
+        }
+}
+
+/* DFT atoms at k in [0, MN), binarised DFT atoms at k in [MN, 2MN). */
+void or_dict_dft_bdft(int M, int N, double *re, double *im)
+{
+    const size_t V = (size_t)M * N;
+    or_dict_dft(M, N, re, im);
+    or_dict_bdft(M, N, re + V * V, im + V * V);
+}
+
+/* Complex collinearity: excluded[j] = 1 if |<phi_i, phi_j>| >= (1 - 1e-12)
+ * |phi_i| |phi_j| for some i < j, with <a, b> = sum conj(a) b (plain double
+ * loop over all pairs; the complex dictionaries of the tests are small). */
+void or_find_duplicates_c(int K, int MN, const double *re, const double *im, uint8_t *excluded)
+{
+    double *nrm = malloc(sizeof(double) * K);
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int p = 0; p < MN; ++p) {
+            const size_t i = (size_t)k * MN + p;
+            s += re[i] * re[i] + im[i] * im[i];
+        }
+        nrm[k] = sqrt(s);
+        excluded[k] = 0;
+    }
+    for (int j = 1; j < K; ++j) {
+        if (nrm[j] == 0.0) continue;
+        for (int i = 0; i < j && !excluded[j]; ++i) {
+            if (nrm[i] == 0.0) continue;
+            double dr = 0.0, di = 0.0;
+            for (int p = 0; p < MN; ++p) {
+                const size_t a = (size_t)i * MN + p, b = (size_t)j * MN + p;
+                dr += re[a] * re[b] + im[a] * im[b];
+                di += re[a] * im[b] - im[a] * re[b];
+            }
+            if (sqrt(dr * dr + di * di) >= (1.0 - OR_COLLINEAR_REL) * nrm[i] * nrm[j]) excluded[j] = 1;
+        }
+    }
+    free(nrm);
+}
+
+/* Alg. 1 with complex atoms (eqs. 2-10 with conjugates).  s is complex
+ * (s_im may be NULL for a real signal).  out_re/out_im: s on A, g on B;
+ * u_log, c_re/c_im (complex coefficient), margin_log as in or_se_original.
+ * Returns 0, or -5 if no atom is admissible. */
+int or_se_original_c(int M, int N, int K, const double *re, const double *im, const double *w,
+                     const uint8_t *dup, const double *s_re, const double *s_im, double gamma, int I,
+                     double *out_re, double *out_im, int32_t *u_log, double *c_re, double *c_im,
+                     double *e_log, double *margin_log)
+{
+    const int MN = M * N;
+    double *rr = malloc(sizeof(double) * MN), *ri = malloc(sizeof(double) * MN);
+    double *gr = calloc(MN, sizeof(double)), *gi = calloc(MN, sizeof(double));
+    double *ckk = malloc(sizeof(double) * K), *pr = malloc(sizeof(double) * K), *pi_ = malloc(sizeof(double) * K);
+    double *sc = malloc(sizeof(double) * K);
+    uint8_t *ok = malloc(K);
+    int rc = 0;
+
+    /* eq. (2): r^(0) = s on A (B never read) */
+    for (int i = 0; i < MN; ++i) {
+        rr[i] = w[i] > 0.0 ? s_re[i] : 0.0;
+        ri[i] = w[i] > 0.0 && s_im ? s_im[i] : 0.0;
+    }
+    /* denominator of eq. (3): sum conj(phi_k) w phi_k */
+    for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < MN; ++i) {
+            const size_t a = (size_t)k * MN + i;
+            acc += (re[a] * re[a] + im[a] * im[a]) * w[i];
+        }
+        ckk[k] = acc;
+    }
+    if (admissible(K, ckk, dup, ok) == 0) { rc = -5; goto done; }
+
+    for (int nu = 1; nu <= I; ++nu) {
+        /* eq. (3): p_k = sum r conj(phi_k) w / C_kk; eq. (7): score |p_k|^2 C_kk */
+        for (int k = 0; k < K; ++k) {
+            double nr = 0.0, ni = 0.0;
+            for (int i = 0; i < MN; ++i) {
+                const size_t a = (size_t)k * MN + i;
+                /* r * conj(phi) = (rr + j ri)(pr - j pi) */
+                nr += (rr[i] * re[a] + ri[i] * im[a]) * w[i];
+                ni += (ri[i] * re[a] - rr[i] * im[a]) * w[i];
+            }
+            pr[k] = ckk[k] > 0.0 ? nr / ckk[k] : 0.0;
+            pi_[k] = ckk[k] > 0.0 ? ni / ckk[k] : 0.0;
+            sc[k] = (pr[k] * pr[k] + pi_[k] * pi_[k]) * ckk[k];
+        }
+        int u = -1;
+        double best = 0.0;
+        for (int k = 0; k < K; ++k) {
+            if (!ok[k]) continue;
+            if (u < 0 || sc[k] > best) { best = sc[k]; u = k; }
+        }
+        if (margin_log) {
+            double s1 = -1.0, s2 = -1.0;
+            for (int k = 0; k < K; ++k) {
+                if (!ok[k]) continue;
+                if (sc[k] > s1) { s2 = s1; s1 = sc[k]; }
+                else if (sc[k] > s2) s2 = sc[k];
+            }
+            margin_log[nu - 1] = s1 > 0.0 ? (s1 - (s2 < 0.0 ? 0.0 : s2)) / s1 : 0.0;
+        }
+        /* eq. (8) */
+        const double cr = gamma * pr[u], ci = gamma * pi_[u];
+        /* eqs. (9)-(10): g += c phi_u, r -= c phi_u */
+        for (int i = 0; i < MN; ++i) {
+            const size_t a = (size_t)u * MN + i;
+            const double vr = cr * re[a] - ci * im[a], vi = cr * im[a] + ci * re[a];
+            gr[i] += vr; gi[i] += vi;
+            rr[i] -= vr; ri[i] -= vi;
+        }
+        if (u_log) u_log[nu - 1] = u;
+        if (c_re) c_re[nu - 1] = cr;
+        if (c_im) c_im[nu - 1] = ci;
+        if (e_log) {
+            double E = 0.0;
+            for (int i = 0; i < MN; ++i) E += w[i] * (rr[i] * rr[i] + ri[i] * ri[i]);
+            e_log[nu - 1] = E;
+        }
+    }
+done:
+    for (int i = 0; i < MN; ++i) {
+        out_re[i] = w[i] > 0.0 ? s_re[i] : gr[i];
+        if (out_im) out_im[i] = w[i] > 0.0 ? (s_im ? s_im[i] : 0.0) : gi[i];
+    }
+    free(rr); free(ri); free(gr); free(gi); free(ckk); free(pr); free(pi_); free(sc); free(ok);
+    return rc;
+}
+
+/* Alg. 2 + 3 with complex atoms: C_(k,l) = sum conj(phi_k) w phi_l (Hermitian),
+ * R_k^(0) = sum s conj(phi_k) w, u = argmax |R_k| D_k, c = gamma R_u D_u^2,
+ * R_k -= c C_(k,u).  Outputs as or_se_original_c (no energy / margins). */
+int or_fase_c(int M, int N, int K, const double *re, const double *im, const double *w,
+              const uint8_t *dup, const double *s_re, const double *s_im, double gamma, int I,
+              double *out_re, double *out_im, int32_t *u_log, double *c_re, double *c_im)
+{
+    const int MN = M * N;
+    double *Cr = malloc(sizeof(double) * K * K), *Ci = malloc(sizeof(double) * K * K);
+    double *Rr = malloc(sizeof(double) * K), *Ri = malloc(sizeof(double) * K);
+    double *D = malloc(sizeof(double) * K), *ckk = malloc(sizeof(double) * K);
+    double *gr = calloc(MN, sizeof(double)), *gi = calloc(MN, sizeof(double));
+    uint8_t *ok = malloc(K);
+    int rc = 0;
+    /* Alg. 2: eq. (16) on the upper triangle, Hermitian mirror; eq. (17) */
+    for (int k = 0; k < K; ++k)
+        for (int l = k; l < K; ++l) {
+            double ar = 0.0, ai = 0.0;
+            for (int i = 0; i < MN; ++i) {
+                const size_t a = (size_t)k * MN + i, b = (size_t)l * MN + i;
+                ar += (re[a] * re[b] + im[a] * im[b]) * w[i];
+                ai += (re[a] * im[b] - im[a] * re[b]) * w[i];
+            }
+            Cr[(size_t)k * K + l] = ar; Ci[(size_t)k * K + l] = ai;
+            Cr[(size_t)l * K + k] = ar; Ci[(size_t)l * K + k] = -ai;
+        }
+    for (int k = 0; k < K; ++k) {
+        ckk[k] = Cr[(size_t)k * K + k];
+        D[k] = ckk[k] > 0.0 ? 1.0 / sqrt(ckk[k]) : 0.0;
+    }
+    if (admissible(K, ckk, dup, ok) == 0) { rc = -5; goto done; }
+    /* eq. (12) */
+    for (int k = 0; k < K; ++k) {
+        double ar = 0.0, ai = 0.0;
+        for (int i = 0; i < MN; ++i) {
+            if (!(w[i] > 0.0)) continue;
+            const size_t a = (size_t)k * MN + i;
+            const double sr = s_re[i], si = s_im ? s_im[i] : 0.0;
+            ar += (sr * re[a] + si * im[a]) * w[i];
+            ai += (si * re[a] - sr * im[a]) * w[i];
+        }
+        Rr[k] = ar; Ri[k] = ai;
+    }
+    for (int nu = 1; nu <= I; ++nu) {
+        int u = -1;
+        double best = 0.0;
+        for (int k = 0; k < K; ++k) {   /* eq. (18) */
+            if (!ok[k]) continue;
+            double v = sqrt(Rr[k] * Rr[k] + Ri[k] * Ri[k]) * D[k];
+            if (u < 0 || v > best) { best = v; u = k; }
+        }
+        const double cr = gamma * Rr[u] * D[u] * D[u], ci = gamma * Ri[u] * D[u] * D[u];   /* eq. (19) */
+        for (int i = 0; i < MN; ++i) {   /* eq. (9) */
+            const size_t a = (size_t)u * MN + i;
+            gr[i] += cr * re[a] - ci * im[a];
+            gi[i] += cr * im[a] + ci * re[a];
+        }
+        for (int k = 0; k < K; ++k) {    /* eq. (20): R_k -= c C_(k,u) */
+            const double xr = Cr[(size_t)k * K + u], xi = Ci[(size_t)k * K + u];
+            Rr[k] -= cr * xr - ci * xi;
+            Ri[k] -= cr * xi + ci * xr;
+        }
+        if (u_log) u_log[nu - 1] = u;
+        if (c_re) c_re[nu - 1] = cr;
+        if (c_im) c_im[nu - 1] = ci;
+    }
+done:
+    for (int i = 0; i < MN; ++i) {
+        out_re[i] = w[i] > 0.0 ? s_re[i] : gr[i];
+        if (out_im) out_im[i] = w[i] > 0.0 ? (s_im ? s_im[i] : 0.0) : gi[i];
+    }
+    free(Cr); free(Ci); free(Rr); free(Ri); free(D); free(ckk); free(gr); free(gi); free(ok);
+    return rc;
+}
+
+/* Complex Alg. 1 over B real-valued blocks (one pattern or per-block w). */
+int or_se_original_c_batch(int B, int M, int N, int K, const double *re, const double *im,
+                           const double *w, int w_stride, const uint8_t *dup, const double *s,
+                           double gamma, int I, double *out_re, int32_t *u_log, double *c_re,
+                           double *c_im, double *margin_log, int nthreads)
+{
+    const int MN = M * N;
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int b = 0; b < B; ++b) {
+        int rc = or_se_original_c(M, N, K, re, im, w + (w_stride ? (size_t)b * MN : 0), dup,
+                                  s + (size_t)b * MN, NULL, gamma, I, out_re + (size_t)b * MN, NULL,
+                                  u_log ? u_log + (size_t)b * I : NULL, c_re ? c_re + (size_t)b * I : NULL,
+                                  c_im ? c_im + (size_t)b * I : NULL, NULL,
+                                  margin_log ? margin_log + (size_t)b * I : NULL);
         if (rc) {
 #ifdef _OPENMP
 #pragma omp critical

@@ -378,3 +378,86 @@ def test_fase_equals_se_on_a_video_block():
     # the energy drops monotonically, as in 2-D
     assert np.all(np.diff(a.energy) <= 1e-9 * a.energy[0])
 
+
+
+# ---------------------------------------------------------- complex atoms
+# The paper states SE and FaSE for complex-valued atoms (conjugated scalar
+# products, Hermitian C); DFT and binarised DFT atoms are its complex examples.
+@pytest.mark.parametrize("M,N", [(4, 4), (8, 6)])
+def test_dft_atoms_give_numpy_fft2(M, N):
+    phi = O.dict_complex("dft", M, N)
+    x = np.random.default_rng(M * N).standard_normal((M, N)) + 1j * np.random.default_rng(7).standard_normal((M, N))
+    R = np.einsum("kmn,mn->k", phi.conj(), x)          # sum x conj(phi_k)
+    np.testing.assert_allclose(R, np.fft.fft2(x).ravel() / math.sqrt(M * N), atol=1e-12)
+    G = np.einsum("kmn,lmn->kl", phi.conj(), phi)
+    np.testing.assert_allclose(G, np.eye(M * N), atol=1e-13)
+
+
+def test_binarised_dft_atoms_by_exact_phase():
+    from fractions import Fraction
+    M, N = 4, 6
+    phi = O.dict_complex("bdft", M, N)
+    s = 1.0 / math.sqrt(2 * M * N)
+    for k in range(M * N):
+        mu, eta = divmod(k, N)
+        for m in range(M):
+            for n in range(N):
+                f = (Fraction(mu * m, M) + Fraction(eta * n, N)) % 1
+                re = s if (f <= Fraction(1, 4) or f >= Fraction(3, 4)) else -s
+                im = s if f <= Fraction(1, 2) else -s
+                assert phi[k, m, n] == re + 1j * im, (k, m, n)
+    u = O.dict_complex("dft_bdft", M, N)
+    np.testing.assert_array_equal(u[M * N:], phi)
+
+
+def test_complex_duplicates_match_brute_force():
+    M = N = 8
+    phi = O.dict_complex("dft_bdft", M, N).reshape(2 * M * N, M * N)
+    nrm = np.linalg.norm(phi, axis=1)
+    G = np.abs(phi.conj() @ phi.T)
+    ref = np.zeros(len(phi), dtype=np.uint8)
+    for j in range(1, len(phi)):
+        ref[j] = np.any(G[:j, j] >= (1 - 1e-12) * nrm[:j] * nrm[j])
+    ex = O.find_duplicates_c(phi.reshape(-1, M, N))
+    np.testing.assert_array_equal(ex, ref)
+    assert ex[M * N] == 1          # the binarised DC atom is (1 + j) times the DFT DC atom
+
+
+@pytest.mark.parametrize("a", [37.5, 12.0 - 20.0j])
+def test_complex_single_atom_closed_form(a):
+    L, j, gamma, I = 16, 37, 0.5, 30
+    phi = O.dict_complex("dft", L, L)
+    w = O.weights(L, L, 0.8, W.centred_support(L, L))
+    r = O.se_original_c(phi, w, a * phi[j], gamma, I)
+    assert np.all(r.u == j)
+    nu = np.arange(1, I + 1)
+    np.testing.assert_allclose(r.c, gamma * (1 - gamma) ** (nu - 1) * a, rtol=1e-11)
+    loss = w == 0
+    np.testing.assert_allclose(r.out[loss], a * (1 - (1 - gamma) ** I) * phi[j][loss], rtol=1e-11, atol=1e-12)
+
+
+def test_complex_unweighted_is_best_I_term_of_fft2():
+    L, I = 8, 20
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
+    w = np.ones((L, L))
+    r = O.se_original_c(O.dict_complex("dft", L, L), w, s, 1.0, I)
+    coef = np.fft.fft2(s).ravel() / L
+    order = np.argsort(-np.abs(coef), kind="stable")[:I]
+    np.testing.assert_array_equal(r.u, order)
+    np.testing.assert_allclose(r.c, coef[order], rtol=1e-11)
+
+
+def test_complex_fase_equals_se_and_energy_drops():
+    L, I = 8, 40
+    phi = O.dict_complex("dft_bdft", L, L)
+    dup = O.find_duplicates_c(phi)
+    w = O.weights(L, L, 0.8, W.centred_support(L, L))
+    s = W.patch(L, 11)
+    a = O.se_original_c(phi, w, s, 0.5, I, dup)
+    f = O.fase_c(phi, w, s, 0.5, I, dup)
+    t = int(np.argmax(a.margin <= 1e-9)) if np.any(a.margin <= 1e-9) else I
+    assert t >= 10
+    np.testing.assert_array_equal(a.u[:t], f.u[:t])
+    np.testing.assert_allclose(f.c[:t], a.c[:t], rtol=1e-10)
+    assert np.all(np.diff(a.energy) <= 1e-9 * a.energy[0])
