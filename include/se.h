@@ -53,7 +53,18 @@ typedef enum {
     SE_BASIS_DCT = 1,
     SE_BASIS_WHT = 2,
     SE_BASIS_DCT_WHT = 3,
-    SE_BASIS_NUMERIC = 4
+    SE_BASIS_NUMERIC = 4,
+    /* Complex-valued atoms (the general case of Sec. II-III; conjugated scalar
+     * products, Hermitian table).  DFT: exp(j 2 pi (mu m / M + eta n / N)) /
+     * sqrt(MN), k = mu N + eta.  BDFT (binarised DFT, Sec. I): sgn(cos theta) +
+     * j sgn(sin theta) of the same phase, sgn(0) = +1, scaled by 1/sqrt(2MN).
+     * DFT_BDFT: DFT at [0, MN), BDFT at [MN, 2MN).  Samples stay real; the model
+     * is complex and its real part replaces the loss area; sel_coef receives
+     * (Re, Im) pairs (2 doubles per iteration).  2-D areas, FP64 or BF16X6,
+     * blocks on the plan's pattern, device entry points (batch, strided). */
+    SE_BASIS_DFT = 5,
+    SE_BASIS_BDFT = 6,
+    SE_BASIS_DFT_BDFT = 7
 } se_basis;
 
 /* Arithmetic of the scalar-product stage (tables C of eq. 16 and initial

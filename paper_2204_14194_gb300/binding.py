@@ -20,7 +20,7 @@ from . import build as _build
 SE_OK, SE_PENDING = 0, 1
 SE_ERR = {-1: "SE_ERR_INVALID", -2: "SE_ERR_NOMEM", -3: "SE_ERR_CUDA", -4: "SE_ERR_TIMEOUT",
           -5: "SE_ERR_EMPTY_SUPPORT", -6: "SE_ERR_CANCELLED", -7: "SE_ERR_UNKNOWN_TICKET"}
-BASIS = {"dct": 1, "wht": 2, "dct_wht": 3, "numeric": 4}
+BASIS = {"dct": 1, "wht": 2, "dct_wht": 3, "numeric": 4, "dft": 5, "bdft": 6, "dft_bdft": 7}
 PREC = {"fp64": 0, "bf16x6": 1, "bf16x3": 3, "bf16": 4, "certified": 5}
 GRAM = {"auto": 0, "full": 1, "lazy": 2}
 PRODUCTS = {"auto": 0, "dense": 1, "transform": 2}

@@ -263,6 +263,13 @@ std::string nclass(int n)
 
 se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 {
+    if (pl->cplx) {
+        SE_TRY(build_tables_complex(ctx, pl, st));
+        SE_CUDA(cudaEventRecord(pl->tables_ready, st));
+        pl->tables_valid = true;
+        ctx->table_builds++;
+        return SE_OK;
+    }
     const int Kp = pl->Kp;
     std::string why;
     unsigned long long *dmax = reinterpret_cast<unsigned long long *>(pl->d_nadm.as<char>() + 8);
@@ -382,7 +389,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     // the workspace of the previous call must be free before it is reused
     SE_CUDA(cudaStreamWaitEvent(st, ws.ev_ws, 0));
     const size_t need_desc = sizeof(BlockDesc) * n, need_x = pl->sep_full ? 16 : xrow * n,
-                 need_r0 = tsz * Kp * static_cast<size_t>(n);
+                 need_r0 = (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(n);
     if (ws.desc.bytes < need_desc || ws.x.bytes < need_x || ws.r0.bytes < need_r0)
         SE_CUDA(cudaEventSynchronize(ws.ev_ws));
     const size_t need_logs = fp64 ? 16 : 8 * static_cast<size_t>(n) * I_max;
@@ -423,6 +430,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         }
     }
 
+    if (pl->cplx) return run_complex(ctx, pl, ws, n, I_max, st);
     const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
     cudaEvent_t probe = probe_begin(ctx, st);
     int tok;
@@ -638,14 +646,26 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     pl->K = d.K;
     pl->pc = prec_cfg(d.prec);
     std::string why;
-    if (!build_dictionary(d.M, d.N, T, d.basis, d.K, d.dict, pl->phi, &why)) return fail(SE_ERR_INVALID, why);
+    pl->cplx = d.basis == SE_BASIS_DFT || d.basis == SE_BASIS_BDFT || d.basis == SE_BASIS_DFT_BDFT;
+    if (pl->cplx) {
+        if (T != 1) return fail(SE_ERR_INVALID, "complex atoms: 2-D areas only (T = 1)");
+        if (d.prec != SE_PREC_FP64 && d.prec != SE_PREC_BF16X6)
+            return fail(SE_ERR_INVALID, "complex atoms: precision FP64 or BF16X6");
+        if (d.gram == SE_GRAM_LAZY) return fail(SE_ERR_INVALID, "complex atoms: the plan's pattern only (gram LAZY)");
+        if (d.products == SE_PRODUCTS_TRANSFORM) return fail(SE_ERR_INVALID, "complex atoms use the dense products");
+        if (!build_complex_dictionary(d.M, d.N, d.basis, d.K, pl->phi, pl->phi_im, &why))
+            return fail(SE_ERR_INVALID, why);
+    } else if (!build_dictionary(d.M, d.N, T, d.basis, d.K, d.dict, pl->phi, &why)) {
+        return fail(SE_ERR_INVALID, why);
+    }
     const int MN = pl->MN, K = pl->K;
     pl->Kp = iterate_kp(K, pl->pc.fp64);
     if (pl->Kp < 0) return fail(SE_ERR_INVALID, "K is larger than the iteration kernel supports (16384)");
     pl->certified = d.prec == SE_PREC_CERTIFIED;
     if (pl->certified && pl->Kp > iterate_cert_max_kp())
         return fail(SE_ERR_INVALID, "certified plans support K <= " + std::to_string(iterate_cert_max_kp()));
-    find_collinear(K, MN, pl->phi.data(), pl->dup);
+    if (pl->cplx) find_collinear_complex(K, MN, pl->phi.data(), pl->phi_im.data(), pl->dup);
+    else find_collinear(K, MN, pl->phi.data(), pl->dup);
 
     pl->pattern.assign(MN, 1);
     if (d.support) {
@@ -680,8 +700,9 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         std::vector<double> dg(K, 0.0);
         for (int k = 0; k < K; ++k) {
             const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+            const double *b = pl->cplx ? pl->phi_im.data() + static_cast<size_t>(k) * MN : nullptr;
             double s = 0.0;
-            for (int i : pl->a_idx) s += a[i] * a[i] * pl->w[i];
+            for (int i : pl->a_idx) s += (a[i] * a[i] + (b ? b[i] * b[i] : 0.0)) * pl->w[i];
             dg[k] = s;
             if (!pl->dup[k]) mx = std::max(mx, s);
         }
@@ -692,15 +713,18 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     pl->ka_pad = static_cast<int>(round_up(pl->nA, 64));
     const int Kp = pl->Kp, ka = pl->ka_pad;
 
-    std::vector<double> G(static_cast<size_t>(Kp) * ka, 0.0), sqw(pl->nA);
+    std::vector<double> sqw(pl->nA);
     for (int j = 0; j < pl->nA; ++j) sqw[j] = std::sqrt(pl->w[pl->a_idx[j]]);
-    for (int k = 0; k < K; ++k) {
-        const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
-        for (int j = 0; j < pl->nA; ++j) G[static_cast<size_t>(k) * ka + j] = a[pl->a_idx[j]] * sqw[j];
+    if (!pl->cplx) {
+        std::vector<double> G(static_cast<size_t>(Kp) * ka, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const double *a = pl->phi.data() + static_cast<size_t>(k) * MN;
+            for (int j = 0; j < pl->nA; ++j) G[static_cast<size_t>(k) * ka + j] = a[pl->a_idx[j]] * sqw[j];
+        }
+        SE_TRY(upload(ctx, pl->d_G64, G));
     }
     std::vector<uint8_t> dupp(Kp, 1);
     for (int k = 0; k < K; ++k) dupp[k] = pl->dup[k];
-    SE_TRY(upload(ctx, pl->d_G64, G));
     SE_TRY(upload(ctx, pl->d_sqrtw, sqw));
 
     SE_TRY(upload(ctx, pl->d_a_idx, pl->a_idx));
@@ -708,7 +732,9 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
     SE_TRY(upload(ctx, pl->d_pattern, pl->pattern));
     SE_TRY(upload(ctx, pl->d_dup, dupp));
     const size_t nBa = std::max(pl->nB, 1);
-    if (pl->pc.fp64) {
+    if (pl->cplx) {
+        SE_TRY(setup_complex_plan(ctx, pl.get(), ctx->stream));
+    } else if (pl->pc.fp64) {
         std::vector<double> pb(static_cast<size_t>(Kp) * nBa, 0.0);
         for (int k = 0; k < K; ++k)
             for (int j = 0; j < pl->nB; ++j)
@@ -747,7 +773,7 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         pl->sep_full = pl->sep;
     }
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
-    SE_TRY(dev_alloc(ctx, pl->d_C, tsz * Kp * static_cast<size_t>(Kp)));
+    SE_TRY(dev_alloc(ctx, pl->d_C, (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(Kp)));
     SE_TRY(dev_alloc(ctx, pl->d_invC, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_Dk, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_diag, sizeof(double) * Kp));
@@ -822,8 +848,8 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, cons
     SE_TRY(resolve_blocks(pl, n, blocks, d, &I_max, &any_mask));
     if (any_mask && pl->desc.gram == SE_GRAM_FULL)
         return fail(SE_ERR_INVALID, "per-block support masks need the lazy table path (plan gram is FULL)");
-    if (any_mask && pl->certified)
-        return fail(SE_ERR_INVALID, "certified plans serve blocks on the plan's pattern only");
+    if (any_mask && (pl->certified || pl->cplx))
+        return fail(SE_ERR_INVALID, "certified and complex plans serve blocks on the plan's pattern only");
     // blocks on the plan's pattern use the full table (unless LAZY is forced);
     // blocks with their own mask use lazily computed columns
     std::vector<BlockDesc> full, lazy;
@@ -863,7 +889,7 @@ se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, co
         b[i].support = nullptr;
         b[i].out = out + MN * i;
         b[i].sel_idx = sel_idx ? sel_idx + static_cast<size_t>(I) * i : nullptr;
-        b[i].sel_coef = sel_coef ? sel_coef + static_cast<size_t>(I) * i : nullptr;
+        b[i].sel_coef = sel_coef ? sel_coef + static_cast<size_t>(plan->cplx ? 2 : 1) * I * i : nullptr;
         b[i].iterations = I;
     }
     return se_extrapolate_batch(ctx, plan, n, b.data(), cuda_stream);
@@ -889,6 +915,7 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
                               double *out, int32_t *sel_idx, double *sel_coef, int iterations)
 {
     if (!ctx || !plan || n < 0) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    if (plan->cplx) return fail(SE_ERR_INVALID, "complex plans: device entry points only");
     if (n == 0) return SE_OK;
     if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
     if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
@@ -973,6 +1000,8 @@ se_status se_plan_autotune(se_ctx_t *ctx, se_plan_t *plan, int n_probe, void *cu
     if (!ctx || !plan) return fail(SE_ERR_INVALID, "NULL context or plan");
     if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
     if (n_probe < 1 || n_probe > 65536) return fail(SE_ERR_INVALID, "n_probe must be in [1, 65536]");
+    if (plan->cplx || plan->certified)
+        return fail(SE_ERR_INVALID, "complex and certified plans have no lazy path to compare");
     SE_CUDA(cudaSetDevice(ctx->device));
     se_plan_s *pl = plan;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -211,7 +211,9 @@ struct se_plan_s {
     se::PrecCfg pc;
     bool certified = false;               // SE_PREC_CERTIFIED: fp32 path + fp64 recomputation
     se_plan_s *shadow = nullptr;          //   the internal FP64 plan of a certified plan (owned)
-    std::vector<double> phi;              // host K x MN atoms (fp64)
+    std::vector<double> phi;              // host K x MN atoms (fp64; real part for complex atoms)
+    std::vector<double> phi_im;           // host K x MN imaginary part (complex atoms only)
+    bool cplx = false;                    // complex-valued atoms (DFT, binarised DFT)
     std::vector<uint8_t> dup;             // host K flags
     std::vector<uint8_t> pattern;         // host MN default support
     std::vector<double> w;                // host MN weights of the default pattern
@@ -224,7 +226,9 @@ struct se_plan_s {
     se::DevBuf d_G64;                     // Kp x ka_pad fp64, G = phi_A sqrt(w)
     se::DevBuf d_Gbf;                     // Kp x nparts*ka_pad bf16 split of G (tables)
     se::DevBuf d_Gwbf;                    // Kp x nparts*ka_pad bf16 split of Phi_A w (projections)
-    se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels
+    se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels ([Kp][2][nB] complex)
+    // complex atoms: [Gi|-Gr] rows for Im C (fp64 / bf16 split), [phi_r w; -phi_i w] rows of eq. 12 (fp64)
+    se::DevBuf d_Gc64, d_Gcbf, d_P64;
     // tables (eqs. 16-17)
     se::DevBuf d_C, d_invC, d_Dk, d_diag, d_nadm;
     bool tables_valid = false;
@@ -284,6 +288,13 @@ struct NoTuneScope {
     NoTuneScope();
     ~NoTuneScope();
 };
+// Complex-valued atoms (se_complex.cpp).
+bool build_complex_dictionary(int M, int N, int basis, int K, std::vector<double> &re, std::vector<double> &im,
+                              std::string *why);
+void find_collinear_complex(int K, int MN, const double *re, const double *im, std::vector<uint8_t> &dup);
+se_status setup_complex_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
+se_status build_tables_complex(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
+se_status run_complex(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, int I_max, cudaStream_t st);
 // A transform-domain launch with the schedule chosen by the autotuner.
 cudaError_t run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st);
 // Move pattern blocks to the lazy list when the measured costs favour it.

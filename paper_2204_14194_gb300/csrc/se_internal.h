@@ -121,6 +121,10 @@ cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launche
 int iterate_variants(int Kp, bool fp64);
 // Largest padded K of the certified fp32 form (one warp per block).
 int iterate_cert_max_kp();
+// Iterations, model and replacement for complex-valued atoms (k_complex.cu):
+// R0 [n][2][Kp], C [Kp][2][Kp] (row u = C(., u)), invC [Kp], PhiB [Kp][2][nB];
+// sel_coef receives (Re, Im) pairs.
+template <typename T> cudaError_t launch_iterate_cplx(const IterArgs &a, cudaStream_t st);
 
 // ------------------------------------------------------------ lazy columns
 struct LazyArgs {

@@ -90,6 +90,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     if (!samples || !out) return set_error(SE_ERR_INVALID, "NULL samples or out");
     if (iterations < 0) return set_error(SE_ERR_INVALID, "iterations < 0");
     se_plan_s *pl = const_cast<se_plan_s *>(plan);
+    if (pl->cplx) return set_error(SE_ERR_INVALID, "se_extrapolate_noalloc: complex plans use se_extrapolate_strided");
     if (pl->certified)
         return set_error(SE_ERR_INVALID, "se_extrapolate_noalloc: certified plans recompute flagged blocks "
                                          "in fp64, which needs workspace; use se_extrapolate_strided");

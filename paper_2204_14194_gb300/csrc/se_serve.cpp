@@ -271,6 +271,7 @@ se_status se_submit(se_ctx_t *ctx, const se_plan_t *plan, const se_request *req,
     if (plan->ctx != ctx) return set_error(SE_ERR_INVALID, "plan belongs to another context");
     if (!req->samples || !req->out) return set_error(SE_ERR_INVALID, "NULL samples or out");
     if (req->iterations < 0) return set_error(SE_ERR_INVALID, "iterations < 0");
+    if (plan->cplx) return set_error(SE_ERR_INVALID, "complex plans: device entry points only");
     if (req->support && plan->desc.gram == SE_GRAM_FULL)
         return set_error(SE_ERR_INVALID, "per-request support masks need the lazy table path (plan gram is FULL)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(SE_ERR_CUDA, "cudaSetDevice failed");

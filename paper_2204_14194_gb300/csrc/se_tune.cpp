@@ -125,7 +125,7 @@ cudaError_t tune_run(se_ctx_s *ctx, const std::string &key, int n_cand, cudaStre
 bool choose_lazy_for_pattern(se_plan_s *pl, int n)
 {
     std::lock_guard<std::mutex> lk(pl->cmu);
-    if (pl->tables_valid || pl->desc.gram != SE_GRAM_AUTO || pl->certified) return false;
+    if (pl->tables_valid || pl->desc.gram != SE_GRAM_AUTO || pl->certified || pl->cplx) return false;
     if (!(pl->t_table_ms > 0.0 && pl->t_full_blk_ms > 0.0 && pl->t_lazy_blk_ms > 0.0)) return false;
     const double extra = pl->t_lazy_blk_ms - pl->t_full_blk_ms;
     if (extra <= 0.0) return true;
