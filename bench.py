@@ -401,7 +401,28 @@ def run_workload(args):
 
     # one context (and stream) per plan, so the three area sizes overlap on the device
     ctxs, streams, groups = [], [], []
-    if args.workload == "gauss1080":
+    if args.workload in ("dft64", "video"):
+        # complex DFT atoms on 64 x 64 areas (the processing-time scenario of the
+        # paper's Fig. 7: K = 4096, 32 x 32 loss) or 3-D video blocks 16 x 16 x 4
+        # with 3-D DCT atoms (K = 1024); I = 100, gamma = 0.5, rho_hat = 0.8
+        ctxs.append(B.Context(0))
+        streams.append(torch.cuda.Stream())
+        if args.workload == "dft64":
+            n = args.blocks or 1024
+            plan = ctxs[0].plan(64, 64, "dft", 4096, 0.8, 0.5, 100, prec=args.prec)
+            samples = W.tiled_image(2048, 2048, 64)
+            rng = np.random.default_rng(64)
+            corners = rng.integers(0, 2048 - 64, size=(n, 2))
+            samples = np.stack([samples[r:r + 64, c:c + 64] for r, c in corners])
+            name = "dft_64x64_K4096_I100_%dblk" % n
+        else:
+            n = args.blocks or 4096
+            plan = ctxs[0].plan(16, 16, "dct", 1024, 0.8, 0.5, 100, prec=args.prec, T=4)
+            samples = np.stack([W.video_block(16, 16, 4, 20000 + i) for i in range(n)])
+            name = "video_16x16x4_dct_K1024_I100_%dblk" % n
+        s = torch.from_numpy(np.ascontiguousarray(samples)).cuda()
+        groups.append((plan, s, torch.empty_like(s), None, 100))
+    elif args.workload == "gauss1080":
         wl = W.config3(args.blocks or None)
         ctxs.append(B.Context(0))
         streams.append(torch.cuda.Stream())
@@ -607,7 +628,8 @@ def main():
     ap.add_argument("--warm-s", type=float, default=1.0, help="serving: warm-up seconds")
     ap.add_argument("--gauss-share", type=float, default=0.5, help="serving: share of Gaussian dictionaries")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM budget")
-    ap.add_argument("--workload", default="img512", choices=["img512", "gauss1080", "mixed", "serve", "single"],
+    ap.add_argument("--workload", default="img512",
+                    choices=["img512", "gauss1080", "mixed", "serve", "single", "dft64", "video"],
                     help="img512 is the headline; the others are secondary measurements")
     ap.add_argument("--blocks", type=int, default=0, help="block count for --workload gauss1080/mixed")
     args = ap.parse_args()

@@ -773,7 +773,7 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
         pl->sep_full = pl->sep;
     }
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
-    SE_TRY(dev_alloc(ctx, pl->d_C, (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(Kp)));
+    SE_TRY(dev_alloc(ctx, pl->d_C, pl->dft_w ? 16 : (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(Kp)));
     SE_TRY(dev_alloc(ctx, pl->d_invC, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_Dk, tsz * Kp));
     SE_TRY(dev_alloc(ctx, pl->d_diag, sizeof(double) * Kp));

@@ -134,12 +134,52 @@ void find_collinear_complex(int K, int MN, const double *re, const double *im, s
     }
 }
 
+// The 2-D DFT of the weighting function, What[a][b] = sum w[m][n]
+// exp(-j 2 pi (a m / M + b n / N)) / MN (exact phase reduction, fp64): for DFT
+// atoms C(k,u) = What[(mu_k - mu_u) mod M][(eta_k - eta_u) mod N] (Sec. VI, the
+// product of an atom and a conjugated atom is the atom of the frequency
+// difference).
+static void dft_of_weights(int M, int N, const std::vector<double> &w, std::vector<double> &re,
+                           std::vector<double> &im)
+{
+    const long L = static_cast<long>(M) * N;
+    const double pi = 3.14159265358979323846;
+    re.assign(L, 0.0);
+    im.assign(L, 0.0);
+    for (int a = 0; a < M; ++a)
+        for (int b = 0; b < N; ++b) {
+            double sr = 0.0, si = 0.0;
+            for (int m = 0; m < M; ++m)
+                for (int n = 0; n < N; ++n) {
+                    const double v = w[static_cast<size_t>(m) * N + n];
+                    if (v == 0.0) continue;
+                    const long ph = (static_cast<long>(a) * m * N + static_cast<long>(b) * n * M) % L;
+                    const double t = 2.0 * pi * static_cast<double>(ph) / static_cast<double>(L);
+                    sr += v * std::cos(t);
+                    si -= v * std::sin(t);
+                }
+            re[static_cast<size_t>(a) * N + b] = sr / static_cast<double>(L);
+            im[static_cast<size_t>(a) * N + b] = si / static_cast<double>(L);
+        }
+}
+
 se_status setup_complex_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 {
     const int K = pl->K, Kp = pl->Kp, ka = pl->ka_pad, MN = pl->MN, nA = pl->nA, nB = pl->nB;
     const int ka2 = 2 * ka;
     const double *re = pl->phi.data(), *im = pl->phi_im.data();
     const bool fp64 = pl->pc.fp64;
+    pl->dft_w = pl->desc.basis == SE_BASIS_DFT;
+    if (pl->dft_w) {
+        std::vector<double> wr, wi;
+        dft_of_weights(pl->M, pl->N, pl->w, wr, wi);
+        std::vector<double> planes(wr);
+        planes.insert(planes.end(), wi.begin(), wi.end());
+        if (fp64) CX_TRY(upload_cx(ctx, pl->d_What, planes));
+        else CX_TRY(upload_cx(ctx, pl->d_What, std::vector<float>(planes.begin(), planes.end())));
+        pl->dft_invC.assign(Kp, 0.0);
+        for (int k = 0; k < K; ++k) pl->dft_invC[k] = wr[0] > 0.0 ? 1.0 / wr[0] : 0.0;
+    }
     std::vector<double> G(static_cast<size_t>(Kp) * ka2, 0.0), Gc(static_cast<size_t>(Kp) * ka2, 0.0),
         P(static_cast<size_t>(2) * Kp * ka, 0.0);
     for (int k = 0; k < K; ++k)
@@ -156,18 +196,22 @@ se_status setup_complex_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
             P[static_cast<size_t>(k) * ka + j] = re[src] * f;
             P[static_cast<size_t>(Kp + k) * ka + j] = -im[src] * f;
         }
-    CX_TRY(upload_cx(ctx, pl->d_G64, G));                   // the diagonal of eq. (16) is read from it
+    if (!pl->dft_w) CX_TRY(upload_cx(ctx, pl->d_G64, G));   // the diagonal of eq. (16) is read from it
     if (fp64) {
-        CX_TRY(upload_cx(ctx, pl->d_Gc64, Gc));
+        if (!pl->dft_w) CX_TRY(upload_cx(ctx, pl->d_Gc64, Gc));
         CX_TRY(upload_cx(ctx, pl->d_P64, P));
     } else {
-        DevBuf tmp;
-        CX_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka2 * 2));
-        CX_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka2, ka2, ka2, pl->pc.nparts, pl->d_Gbf.as<uint16_t>(), st));
-        CX_TRY(upload_cx(ctx, tmp, Gc));
-        CX_TRY(dev_alloc(ctx, pl->d_Gcbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka2 * 2));
-        CX_CUDA(launch_split_bf16(tmp.as<double>(), Kp, ka2, ka2, ka2, pl->pc.nparts, pl->d_Gcbf.as<uint16_t>(), st));
-        CX_CUDA(cudaStreamSynchronize(st));
+        if (!pl->dft_w) {
+            DevBuf tmp;
+            CX_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka2 * 2));
+            CX_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka2, ka2, ka2, pl->pc.nparts,
+                                      pl->d_Gbf.as<uint16_t>(), st));
+            CX_TRY(upload_cx(ctx, tmp, Gc));
+            CX_TRY(dev_alloc(ctx, pl->d_Gcbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka2 * 2));
+            CX_CUDA(launch_split_bf16(tmp.as<double>(), Kp, ka2, ka2, ka2, pl->pc.nparts,
+                                      pl->d_Gcbf.as<uint16_t>(), st));
+            CX_CUDA(cudaStreamSynchronize(st));
+        }
         DevBuf tp;
         CX_TRY(upload_cx(ctx, tp, P));
         CX_TRY(dev_alloc(ctx, pl->d_Gwbf, static_cast<size_t>(2) * Kp * pl->pc.nparts * ka * 2));
@@ -203,6 +247,18 @@ se_status setup_complex_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 se_status build_tables_complex(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
 {
     const int K = pl->K, Kp = pl->Kp, ka2 = 2 * pl->ka_pad;
+    if (pl->dft_w) {   // no table: the DFT of w is uploaded with the plan; 1/C_kk is uniform
+        if (pl->pc.fp64) {
+            CX_CUDA(cudaMemcpyAsync(pl->d_invC.ptr, pl->dft_invC.data(), sizeof(double) * Kp,
+                                    cudaMemcpyHostToDevice, st));
+        } else {
+            static thread_local std::vector<float> f;
+            f.assign(pl->dft_invC.begin(), pl->dft_invC.end());
+            CX_CUDA(cudaMemcpyAsync(pl->d_invC.ptr, f.data(), sizeof(float) * Kp, cudaMemcpyHostToDevice, st));
+            CX_CUDA(cudaStreamSynchronize(st));
+        }
+        return SE_OK;
+    }
     unsigned long long *dmax = reinterpret_cast<unsigned long long *>(pl->d_nadm.as<char>() + 8);
     CX_CUDA(launch_tables_diag(pl->d_G64.as<double>(), ka2, K, Kp, ka2, pl->d_dup.as<uint8_t>(),
                                pl->d_diag.as<double>(), dmax, pl->d_nadm.as<int>(), st));
@@ -296,6 +352,11 @@ se_status run_complex(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, int I_
     a.gamma = pl->desc.gamma;
     a.I_max = I_max;
     a.err = ctx->ws_err.as<int>();
+    if (pl->dft_w) {
+        a.What = pl->d_What.ptr;
+        a.Mdft = pl->M;
+        a.Ndft = pl->N;
+    }
     tok = stage_begin(ctx, 3, st);
     cudaError_t e = fp64 ? launch_iterate_cplx<double>(a, st) : launch_iterate_cplx<float>(a, st);
     stage_end(ctx, tok, st);

@@ -229,6 +229,11 @@ struct se_plan_s {
     se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels ([Kp][2][nB] complex)
     // complex atoms: [Gi|-Gr] rows for Im C (fp64 / bf16 split), [phi_r w; -phi_i w] rows of eq. 12 (fp64)
     se::DevBuf d_Gc64, d_Gcbf, d_P64;
+    // DFT atoms: the table is replaced by the 2-D DFT of w ([2][MN], scaled by 1/MN, Sec. VI);
+    // every atom has C_kk = What[0][0], so 1/C_kk is uniform (host copy for the table stage)
+    bool dft_w = false;
+    se::DevBuf d_What;
+    std::vector<double> dft_invC;
     // tables (eqs. 16-17)
     se::DevBuf d_C, d_invC, d_Dk, d_diag, d_nadm;
     bool tables_valid = false;

@@ -110,6 +110,10 @@ struct IterArgs {
     int *err;
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
     float *log_c;           //   model kernel; NULL: the iteration kernel evaluates the model
+    const void *What;       // complex DFT plans: [2][M*N] planes of the 2-D DFT of w (scaled by
+                            //   1/MN); C(k,u) = What[(mu_k - mu_u) mod M][(eta_k - eta_u) mod N]
+                            //   replaces the table (Sec. VI); NULL: the table C is used
+    int Mdft, Ndft;
     int *cert_flag;         // certified fp32 form: [n] first iteration whose two best |R'| lie
                             //   within cert_delta (relative) of each other, -1 if none; NULL: off
     float cert_delta;

@@ -30,10 +30,12 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("L,basis", [(16, "dft"), (16, "bdft"), (16, "dft_bdft"), (32, "dft")])
+@pytest.mark.parametrize("L,basis,n,I", [(16, "dft", 16, 60), (16, "bdft", 16, 60), (16, "dft_bdft", 16, 60),
+                                         (32, "dft", 16, 60),
+                                         (32, "dft_bdft", 6, 50),   # K = 2048: four warps per block
+                                         (64, "dft", 2, 25)])       # K = 4096, DFT of w instead of a table
 @pytest.mark.parametrize("prec", ["fp64", "bf16x6"])
-def test_complex_atoms_against_the_oracle(ctx, L, basis, prec):
-    n, I = 16, 60
+def test_complex_atoms_against_the_oracle(ctx, L, basis, n, I, prec):
     K = (2 if basis == "dft_bdft" else 1) * L * L
     samples = np.stack([W.patch(L, 8000 + 31 * L + i) for i in range(n)])
     sup = W.centred_support(L, L)
@@ -48,7 +50,9 @@ def test_complex_atoms_against_the_oracle(ctx, L, basis, prec):
     cz = c[..., 0] + 1j * c[..., 1]
 
     phi = O.dict_complex(basis, L, L)
-    dup = O.find_duplicates_c(phi)
+    # DFT atoms are orthonormal, so none is collinear with another (pinned on
+    # the CPU); the pairwise search is only needed with binarised atoms
+    dup = np.zeros(K, dtype=np.uint8) if basis == "dft" else O.find_duplicates_c(phi)
     w = O.weights(L, L, 0.8, sup)
     ro, ru, rc, rm, st = O.se_original_c_batch(phi, w, samples, 0.5, I, dup, margins=True)
     assert st == 0
