@@ -361,15 +361,11 @@ iterate_f32_kernel(const IterArgs a)
     uint64_t *sBar = reinterpret_cast<uint64_t *>(smem);                     // [BPC] (bulk copies)
     float *sT = reinterpret_cast<float *>(smem + 16 * BPC);                  // [BPC][Kp] if async
     Cand<float> *sRed = reinterpret_cast<Cand<float> *>(sT + (SE_ITER_ASYNC ? BPC * Kp : 0));
-    float *sC = reinterpret_cast<float *>(sRed + 2 * W);                      // [BPC][I_max]
-    int *sU = reinterpret_cast<int *>(sC + BPC * a.I_max);                    // [BPC][I_max]
 
     const int g = threadIdx.x / NT;
     const int tid = threadIdx.x % NT;
     const int lane = threadIdx.x & 31;
     const int warp = tid >> 5;
-    float *logC = sC + g * a.I_max;
-    int *logU = sU + g * a.I_max;
     float *myT = sT + g * Kp;
     uint64_t *myBar = sBar + 2 * g;
     if (SE_ITER_ASYNC == 2 && tid == 0) {
@@ -430,14 +426,9 @@ iterate_f32_kernel(const IterArgs a)
             if (SE_ITER_ASYNC == 2 && more && tid == 0)
                 bulk_row(myT, trow, static_cast<uint32_t>(Kp * sizeof(float)), myBar);
             const float c = gamma * ru * __ldg(Dk + u);
-            if (tid == 0) {
-                if (a.log_u) {
-                    a.log_u[static_cast<size_t>(b) * a.I_max + nu] = u;
-                    a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
-                } else {
-                    logU[nu] = u;
-                    logC[nu] = c;
-                }
+            if (tid == 0) {   // the selection log, read by the model kernel (eq. 9)
+                a.log_u[static_cast<size_t>(b) * a.I_max + nu] = u;
+                a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
             }
             if (!more) break;
 
@@ -476,33 +467,6 @@ iterate_f32_kernel(const IterArgs a)
         if constexpr (W > 1) __syncthreads(); else __syncwarp();
         if (CERT && tid == 0) a.cert_flag[b] = first_close;
         if (failed) break;
-        if (a.log_u) continue;                  // the model kernel evaluates the model
-
-        const double *smp = bd.samples;
-        double *out = bd.out;
-        const float *PhiB = static_cast<const float *>(a.PhiB);
-        // model on the loss pixels: each thread owns 8 pixels per pass and walks
-        // the selection log once, so every logged atom's row is read with 8
-        // independent coalesced loads in flight
-        for (int j0 = tid; j0 < a.nB; j0 += 8 * NT) {
-            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            for (int nu = 0; nu < I; ++nu) {
-                const float cn = logC[nu];
-                const float *row = PhiB + static_cast<size_t>(logU[nu]) * a.nB + j0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (j0 + q * NT < a.nB) acc[q] = fmaf(cn, __ldg(row + q * NT), acc[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (j0 + q * NT < a.nB) out[a.b_idx[j0 + q * NT]] = static_cast<double>(acc[q]);
-        }
-        for (int p = tid; p < a.MN; p += NT)
-            if (a.pat_support[p]) out[p] = smp[p];
-        if (bd.sel_idx)
-            for (int nu = tid; nu < I; nu += NT) bd.sel_idx[nu] = logU[nu];
-        if (bd.sel_coef)
-            for (int nu = tid; nu < I; nu += NT) bd.sel_coef[nu] = static_cast<double>(logC[nu]);
         if constexpr (W > 1) __syncthreads(); else __syncwarp();
     }
 }
@@ -582,8 +546,8 @@ cudaError_t launch_f32(const IterArgs &a, cudaStream_t st, int *launches)
 {
     constexpr int threads = 32 * W * BPC;
     if (a.Kp != 32 * W * VPT) return cudaErrorInvalidValue;
-    const size_t smem = 16 * BPC + (SE_ITER_ASYNC ? sizeof(float) * BPC * a.Kp : 0) +
-                        sizeof(Cand<float>) * 2 * W + (sizeof(float) + sizeof(int)) * BPC * a.I_max + 16;
+    if (!a.log_u || !a.log_c) return cudaErrorInvalidValue;   // the model kernel reads the log
+    const size_t smem = 16 * BPC + (SE_ITER_ASYNC ? sizeof(float) * BPC * a.Kp : 0) + sizeof(Cand<float>) * 2 * W + 16;
     auto kern = iterate_f32_kernel<W, VPT, BPC, CERT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

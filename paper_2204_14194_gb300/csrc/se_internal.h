@@ -109,7 +109,7 @@ struct IterArgs {
     int I_max;              // largest iteration count in the batch
     int *err;
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
-    float *log_c;           //   model kernel; NULL: the iteration kernel evaluates the model
+    float *log_c;           //   model kernel (required); the fp64 form evaluates the model itself
     const void *What;       // complex DFT plans: [2][M*N] planes of the 2-D DFT of w (scaled by
                             //   1/MN); C(k,u) = What[(mu_k - mu_u) mod M][(eta_k - eta_u) mod N]
                             //   replaces the table (Sec. VI); NULL: the table C is used
