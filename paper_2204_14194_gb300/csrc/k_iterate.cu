@@ -390,7 +390,11 @@ iterate_f32_kernel(const IterArgs a)
         float m[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) {
-            const float4 v = *reinterpret_cast<const float4 *>(R0 + ch * NT * 4 + tid * 4);
+            float4 v = *reinterpret_cast<const float4 *>(R0 + ch * NT * 4 + tid * 4);
+            if (a.r0_scale) {   // R^(0) stored unscaled: R'_k = R_k D_k here
+                const float4 d = *reinterpret_cast<const float4 *>(a.r0_scale + ch * NT * 4 + tid * 4);
+                v.x *= d.x; v.y *= d.y; v.z *= d.z; v.w *= d.w;
+            }
             R2[ch * 2 + 0] = make_float2(v.x, v.y);
             R2[ch * 2 + 1] = make_float2(v.z, v.w);
             m[0] = fmaxf(m[0], fabsf(v.x));

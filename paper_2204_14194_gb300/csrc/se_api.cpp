@@ -183,7 +183,7 @@ PrecCfg prec_cfg(se_prec p)
 // (eq. 12) of every block, mode 3 the rows of C (eq. 16).  In the fp32 form
 // both carry the factor D_k of the recurrence; padded atoms [K, Kp) read NaN
 // there (never selected) and 0 in the fp64 form (zero criterion).
-SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out)
+SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out, bool scaled)
 {
     SepArgs s{};
     s.M = pl->M;
@@ -197,7 +197,7 @@ SepArgs se::pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n
     s.mode = mode;
     s.blocks = dd;
     s.pattern = pl->d_pattern.as<uint8_t>();
-    s.scale = pl->pc.fp64 ? nullptr : pl->d_Dk.as<float>();
+    s.scale = pl->pc.fp64 || !scaled ? nullptr : pl->d_Dk.as<float>();
     s.rho = pl->d_rho.as<double>();
     s.img = pl->d_sep_img.as<float>();
     s.out = out;
@@ -417,15 +417,27 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
                             cudaMemcpyHostToDevice, st));
     SE_CUDA(cudaEventRecord(ws.ev_staging, st));
 
+    // The fp32 transform form computes R^(0) unscaled (the iteration kernel
+    // applies D_k when it loads them), so a table build does not have to come
+    // first: it runs on the context's second stream while R^(0) is computed, and
+    // the iterations wait for it.
+    const bool overlap = pl->sep_full && !fp64;
     {
         std::lock_guard<std::mutex> lk(pl->tmu);
         if (!pl->tables_valid) {
-            const int tok = stage_begin(ctx, 1, st);
-            cudaEvent_t pa = probe_begin(ctx, st);
-            SE_TRY(build_tables(ctx, pl, st));
-            probe_end(ctx, pl, 0, 0, pa, st);
-            stage_end(ctx, tok, st);
-        } else {
+            cudaStream_t ts = st;
+            if (overlap) {   // the second stream starts after the work already queued on st
+                std::lock_guard<std::mutex> al(ctx->amu);
+                SE_CUDA(cudaEventRecord(ctx->ev_fork, st));
+                SE_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+                ts = ctx->aux;
+            }
+            const int tok = stage_begin(ctx, 1, ts);
+            cudaEvent_t pa = probe_begin(ctx, ts);
+            SE_TRY(build_tables(ctx, pl, ts));
+            probe_end(ctx, pl, 0, 0, pa, ts);
+            stage_end(ctx, tok, ts);
+        } else if (!overlap) {
             SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
         }
     }
@@ -437,9 +449,10 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     if (pl->sep_full) {
         // eq. (12) as a separable transform of w s per block: no packing stage
         tok = stage_begin(ctx, 2, st);
-        SepArgs sa = pattern_sep_args(pl, 0, ddesc, n, ws.r0.ptr);
+        SepArgs sa = pattern_sep_args(pl, 0, ddesc, n, ws.r0.ptr, !overlap);
         SE_CUDA(run_sep(ctx, pl, sa, st));
         stage_end(ctx, tok, st);
+        if (overlap) SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));   // the (forked) table build
         ctx->launches += 1;
     } else {
         SE_TRY(dense_pattern_projections(ctx, pl, ws, ddesc, n, st));
@@ -462,6 +475,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     a.gamma = pl->desc.gamma;
     a.I_max = I_max;
     a.err = ctx->ws_err.as<int>();
+    if (overlap) a.r0_scale = pl->d_Dk.as<float>();
     if (!fp64) {
         a.log_u = ws.logs.as<int>();
         a.log_c = reinterpret_cast<float *>(ws.logs.as<int>() + static_cast<size_t>(n) * I_max);
@@ -569,6 +583,9 @@ se_status se_ctx_create(int device, size_t hbm_budget_bytes, se_ctx_t **out)
     c->budget = hbm_budget_bytes;
     c->tuner.load_env();
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = c->ws.init();
     if (e != cudaSuccess) {
         delete c;
@@ -605,6 +622,9 @@ se_status se_ctx_destroy(se_ctx_t *ctx)
     std::vector<se_plan_s *> plans = ctx->plans;
     for (auto *p : plans) se_plan_destroy(p);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
     return SE_OK;
 }

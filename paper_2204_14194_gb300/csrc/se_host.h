@@ -157,6 +157,9 @@ struct se_ctx_s {
     size_t budget = 0;
     std::atomic<size_t> used{0};
     cudaStream_t stream = nullptr;        // internal stream (host-buffer calls, serving)
+    cudaStream_t aux = nullptr;           // table builds that overlap a batch's projections
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::mutex amu;                       // orders the fork onto the second stream
     std::mutex mu;                        // serialises batch calls (shared workspace)
 
     // workspace of the batch entry points (grown on demand, reused)
@@ -271,7 +274,7 @@ se_status ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl);
 // Transform-domain products on the plan's pattern (needs pl->sep): mode 0
 // R^(0) of n blocks, mode 3 the first n rows of C, written to out with row
 // pitch Kp.
-SepArgs pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out);
+SepArgs pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, void *out, bool scaled = true);
 // Model (eq. 9) and replacement from the log of the fp32 iteration kernel
 // (a.log_u / a.log_c set), for blocks on the plan's pattern.
 cudaError_t launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st);

@@ -110,6 +110,8 @@ struct IterArgs {
     int *err;
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
     float *log_c;           //   model kernel (required); the fp64 form evaluates the model itself
+    const float *r0_scale;  // fp32 form: if set, R0 holds unscaled R_k and the kernel forms
+                            //   R'_k = R_k * r0_scale[k] (D_k) when it loads them
     const void *What;       // complex DFT plans: [2][M*N] planes of the 2-D DFT of w (scaled by
                             //   1/MN); C(k,u) = What[(mu_k - mu_u) mod M][(eta_k - eta_u) mod N]
                             //   replaces the table (Sec. VI); NULL: the table C is used
