@@ -40,6 +40,7 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # shape without a capture or once the kernel changes.
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
 TRAFFIC_ITERATE = {0: 46.35e6}
+TRAFFIC_ITERATE_SYM = None
 
 
 def _dist():
@@ -303,19 +304,27 @@ def run_ours(args):
     hbm_peak, tc_peak, peak_kind = measured_peaks()
     it_ms, it_n = stages["iterate"]
     it_avg_s = it_ms / max(it_n, 1) / 1000.0
-    ops = n * I * opcount.fase_iteration_ops(M, N, K)
     alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    achieved = ops / it_avg_s / 1e12
+    info = plan.info()
     variant = max(ctx.tuned_variant("iterate:f32:%d" % K), 0)
-    if args.prec == "certified":   # one launch shape; the stage also holds the fp64 recomputation
-        it_kernel, it_traffic = "iterate_f32_kernel<1,64,4> certified form + fp64 recomputation", None
+    if info.get("iterations") == "parity-classes":
+        # the kernel's own work: a quarter of the atoms per iteration (one class)
+        ops = n * I * opcount.fase_iteration_ops_classes(M, N, K, classes=4)
+        it_kernel, it_traffic = "iterate_sym_kernel<64> (parity classes)", TRAFFIC_ITERATE_SYM
+        row_bytes = K // 4 * 4
     else:
-        it_kernel, it_traffic = ITERATE_SHAPES.get(variant, "iterate_f32_kernel"), TRAFFIC_ITERATE.get(variant)
+        ops = n * I * opcount.fase_iteration_ops(M, N, K)
+        row_bytes = K * 4
+        if args.prec == "certified":   # one launch shape; the stage also holds the fp64 recomputation
+            it_kernel, it_traffic = "iterate_f32_kernel<1,64,4> certified form + fp64 recomputation", None
+        else:
+            it_kernel, it_traffic = ITERATE_SHAPES.get(variant, "iterate_f32_kernel"), TRAFFIC_ITERATE.get(variant)
+    achieved = ops / it_avg_s / 1e12
     roofline = {"kernel": it_kernel, "bound": "alu", "achieved": achieved,
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 "traffic": it_traffic,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
-                "l2_read_GBps": n * (I - 1) * K * 4 / it_avg_s / 1e9}
+                "l2_read_GBps": n * (I - 1) * row_bytes / it_avg_s / 1e9, "plan": info}
     pr_ms, pr_n = stages["projections"]
     pr_avg_s = pr_ms / max(pr_n, 1) / 1000.0
     na = int(np.sum(wl.support))

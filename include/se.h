@@ -330,6 +330,13 @@ se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_buil
  * because a selection was within the certification gap.  Either pointer may
  * be NULL. */
 se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed);
+/* Which forms a plan's shared-pattern batches use, as a short text into buf
+ * (NUL-terminated, truncated to len): products ("transform" / "dense"),
+ * table ("table" / "dft-of-weights"), iterations ("parity-classes" when the
+ * weighting function is symmetric and the atoms are DCT / WHT rows, see
+ * k_sym.cu; "general" otherwise; "complex"; "fp64"), certified or not.
+ * Example: "products=transform table=table iterations=parity-classes". */
+se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len);
 /* The variant the autotuner keeps for a shape key (e.g. "iterate:f32:2048",
  * "sep:32x32:t2:f32"), or -1 in *variant when that key has not been tuned. */
 se_status se_tuned_variant(se_ctx_t *ctx, const char *key, int *variant);

@@ -30,7 +30,7 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
-           "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats"]
+           "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats", "se_plan_info"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
             "se_cert_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], i32),
+            "se_plan_info": ([vp, C.c_char_p, C.c_size_t], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -256,6 +257,16 @@ class Plan:
 
     def reset_tables(self):
         _check(self._lib.se_plan_reset_tables(self.handle), "se_plan_reset_tables")
+
+    def info(self) -> dict:
+        """The forms this plan's batches use (se_plan_info), as a dict."""
+        buf = C.create_string_buffer(256)
+        _check(self._lib.se_plan_info(self.handle, buf, 256), "se_plan_info")
+        out = {}
+        for item in buf.value.decode().split():
+            k, _, v = item.partition("=")
+            out[k] = v or True
+        return out
 
     def autotune(self, n_probe: int = 256, stream=None):
         """Measure table / full / lazy costs on n_probe synthetic blocks (synchronous)."""

@@ -24,6 +24,7 @@
 #include <climits>
 #include <cmath>
 
+#include "k_device.cuh"
 #include "se_internal.h"
 
 #ifndef SE_ITER_ASYNC
@@ -32,6 +33,10 @@
 
 namespace se {
 namespace {
+
+using dev::bar_wait;
+using dev::bulk_row;
+using dev::max3_abs;
 
 template <typename T> struct Vec;
 template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
@@ -282,21 +287,6 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
     }
 }
 
-#ifndef SE_ITER_MAX3
-#define SE_ITER_MAX3 1       // 1: three-input max instruction, 0: two fmaxf
-#endif
-
-// max(m, |a|, |b|); NaN inputs are ignored (maxNum semantics).
-__device__ __forceinline__ float max3_abs(float m, float a, float b)
-{
-#if SE_ITER_MAX3
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(fabsf(a)), "f"(fabsf(b)));
-    return r;
-#else
-    return fmaxf(m, fmaxf(fabsf(a), fabsf(b)));
-#endif
-}
 
 // The row of T is copied global -> shared with cp.async (16 bytes per
 // thread and chunk, L1-allocating), so the in-flight row holds no registers;
@@ -312,34 +302,6 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// One bulk (TMA) copy of a whole row of T into shared memory, completing on
-// an mbarrier; waits are bounded by %globaltimer.
-__device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)
-{
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
-}
-
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
-    uint32_t ok = 0;
-    unsigned long long t0 = 0;
-    for (uint32_t i = 0;; ++i) {
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(ok) : "r"(m), "r"(parity) : "memory");
-        if (ok) return true;
-        unsigned long long t;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (i == 0) t0 = t;
-        else if (t - t0 > 2000000000ull) return false;
-    }
-}
 
 // Register budget: VPT projections (the row of T is staged in shared memory
 // when SE_ITER_ASYNC, in registers otherwise); the launch bound keeps at

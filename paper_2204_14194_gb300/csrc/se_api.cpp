@@ -1,8 +1,10 @@
 // se_api.cpp -- the C ABI of include/se.h: contexts, plans and the batched
 // extrapolation path (Alg. 2 table generation + Alg. 3 model generation).
 #include <algorithm>
+#include <random>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -224,6 +226,71 @@ void se::route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::
     *I_full = 0;
 }
 
+// Parity classes (see k_sym.cu).  Enabled for the fp32 transform form with
+// DCT / WHT atoms, even M and N, K = Kp in {512, 1024, 2048} and a weighting
+// function that is exactly symmetric in m and in n; the vanishing of C(k,u)
+// across classes is also checked on sampled atom pairs before it is used.
+se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
+{
+    const int M = pl->M, N = pl->N, MN = pl->MN, K = pl->K;
+    const int basis = pl->desc.basis;
+    if (!(pl->sep_full && !pl->pc.fp64 && !pl->certified && !pl->cplx && pl->T == 1)) return SE_OK;
+    if (!(basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT)) return SE_OK;
+    if (M % 2 || N % 2 || K != pl->Kp || (K != 512 && K != 1024 && K != 2048)) return SE_OK;
+    for (int m = 0; m < M; ++m)
+        for (int n = 0; n < N; ++n) {
+            const double v = pl->w[static_cast<size_t>(m) * N + n];
+            if (v != pl->w[static_cast<size_t>(M - 1 - m) * N + n] || v != pl->w[static_cast<size_t>(m) * N + N - 1 - n])
+                return SE_OK;
+        }
+    auto cls = [&](int k) {
+        const int kk = k >= MN ? k - MN : k;
+        return (((kk / N) & 1) << 1) | ((kk % N) & 1);
+    };
+    std::vector<int> perm;
+    perm.reserve(K);
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < K; ++k)
+            if (cls(k) == c) perm.push_back(k);
+    for (int c = 0; c < 4; ++c)
+        if (perm[static_cast<size_t>(c) * (K / 4)] < 0 || cls(perm[static_cast<size_t>(c) * (K / 4)]) != c) return SE_OK;
+    // sampled check: atoms of different classes have (numerically) no weighted overlap
+    std::mt19937 gen(7);
+    for (int t = 0; t < 64; ++t) {
+        int k = static_cast<int>(gen() % K), u = static_cast<int>(gen() % K);
+        if (cls(k) == cls(u)) u = (u + 1) % K;
+        if (cls(k) == cls(u)) continue;
+        const double *a = pl->phi.data() + static_cast<size_t>(k) * MN, *b = pl->phi.data() + static_cast<size_t>(u) * MN;
+        double x = 0.0, na = 0.0, nb = 0.0;
+        for (int i = 0; i < MN; ++i) {
+            x += a[i] * b[i] * pl->w[i];
+            na += a[i] * a[i] * pl->w[i];
+            nb += b[i] * b[i] * pl->w[i];
+        }
+        if (std::fabs(x) > 1e-12 * std::sqrt(na * nb) + 1e-300) return SE_OK;
+    }
+    SE_TRY(upload(ctx, pl->d_perm, perm));
+    SE_TRY(dev_alloc(ctx, pl->d_Cc, sizeof(float) * static_cast<size_t>(K) * (K / 4)));
+    SE_TRY(dev_alloc(ctx, pl->d_Dkp, sizeof(float) * static_cast<size_t>(K)));
+    pl->sym = true;
+    return SE_OK;
+}
+
+cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched)
+{
+    if (pl->sym && !a.cert_flag) {
+        a.perm = pl->d_perm.as<int>();
+        a.Cc = pl->d_Cc.as<float>();
+        a.Dkp = pl->d_Dkp.as<float>();
+        return launch_iterate_sym(a, st, launched);
+    }
+    const std::string ikey = "iterate:f32:" + std::to_string(pl->Kp);
+    return tune_run(ctx, ikey, iterate_variants(pl->Kp, false), st, [&](int v) {
+        *launched = 0;
+        return launch_iterate_full<float>(a, st, launched, v);
+    });
+}
+
 // Relative gap between the two largest |R'| below which a certified plan
 // recomputes the block in fp64 (about 10x the largest fp32 score error
 // measured against the fp64 form on the benchmark workloads).
@@ -290,6 +357,11 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         SepArgs sa = pattern_sep_args(pl, 3, nullptr, pl->K, pl->d_C.ptr);
         SE_CUDA(run_sep(ctx, pl, sa, st));
         ctx->launches += 3;
+        if (pl->sym) {   // compact rows of the parity classes
+            SE_CUDA(launch_sym_gather(pl->d_C.as<float>(), pl->d_Dk.as<float>(), pl->d_perm.as<int>(), pl->K, Kp,
+                                      pl->d_Cc.as<float>(), pl->d_Dkp.as<float>(), st));
+            ctx->launches += 1;
+        }
     } else if (pl->pc.fp64) {
         SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
                                                pl->K, Kp, pl->d_invC.as<double>(),
@@ -486,12 +558,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     }
     int launched = 0;
     tok = stage_begin(ctx, 3, st);
-    const std::string ikey = std::string("iterate:") + (fp64 ? "f64:" : "f32:") + std::to_string(Kp);
-    cudaError_t e = tune_run(ctx, ikey, iterate_variants(Kp, fp64), st, [&](int v) {
-        launched = 0;
-        return fp64 ? launch_iterate_full<double>(a, st, &launched, v)
-                    : launch_iterate_full<float>(a, st, &launched, v);
-    });
+    cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterations_f32(ctx, pl, a, st, &launched);
     stage_end(ctx, tok, st);
     if (e == cudaSuccess && !fp64) {
         tok = stage_begin(ctx, 4, st);
@@ -792,6 +859,7 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
                                         "transforms fit in shared memory");
         pl->sep_full = pl->sep;
     }
+    SE_TRY(setup_sym(ctx, pl.get()));
     const size_t tsz = pl->pc.fp64 ? 8 : 4;
     SE_TRY(dev_alloc(ctx, pl->d_C, pl->dft_w ? 16 : (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(Kp)));
     SE_TRY(dev_alloc(ctx, pl->d_invC, tsz * Kp));
@@ -1100,6 +1168,17 @@ se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed)
     if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
     if (blocks) *blocks = ctx->cert_blocks.load();
     if (recomputed) *recomputed = ctx->cert_recomputed.load();
+    return SE_OK;
+}
+
+se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len)
+{
+    if (!plan || !buf || len == 0) return fail(SE_ERR_INVALID, "NULL plan or buffer");
+    std::string t = std::string("products=") + (plan->sep_full ? "transform" : "dense") +
+                    " table=" + (plan->dft_w ? "dft-of-weights" : "table") + " iterations=" +
+                    (plan->cplx ? "complex" : plan->pc.fp64 ? "fp64" : plan->sym ? "parity-classes" : "general") +
+                    (plan->certified ? " certified" : "");
+    std::snprintf(buf, len, "%s", t.c_str());
     return SE_OK;
 }
 

@@ -235,6 +235,9 @@ struct se_plan_s {
     // DFT atoms: the table is replaced by the 2-D DFT of w ([2][MN], scaled by 1/MN, Sec. VI);
     // every atom has C_kk = What[0][0], so 1/C_kk is uniform (host copy for the table stage)
     bool dft_w = false;
+    // symmetric weighting with DCT / WHT atoms: parity classes (k_sym.cu)
+    bool sym = false;
+    se::DevBuf d_perm, d_Cc, d_Dkp;
     se::DevBuf d_What;
     std::vector<double> dft_invC;
     // tables (eqs. 16-17)
@@ -303,6 +306,11 @@ void find_collinear_complex(int K, int MN, const double *re, const double *im, s
 se_status setup_complex_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
 se_status build_tables_complex(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st);
 se_status run_complex(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, int I_max, cudaStream_t st);
+// Detect the parity-class structure (symmetric w, DCT / WHT atoms) and set up
+// the permutation and the compact table buffers; sets pl->sym.
+se_status setup_sym(se_ctx_s *ctx, se_plan_s *pl);
+// The fp32 iterations: the parity-class kernel when pl->sym, else the tuned shapes.
+cudaError_t launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched);
 // A transform-domain launch with the schedule chosen by the autotuner.
 cudaError_t run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st);
 // Move pattern blocks to the lazy list when the measured costs favour it.

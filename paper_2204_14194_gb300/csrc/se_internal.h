@@ -110,6 +110,12 @@ struct IterArgs {
     int *err;
     int *log_u;             // fp32 form: [n][I_max] selection log (workspace) read by the
     float *log_c;           //   model kernel (required); the fp64 form evaluates the model itself
+    // symmetric weighting with parity-structured atoms (the fp32 class kernel): atoms permuted
+    // so that the 4 parity classes are contiguous (perm[new] = original index), each row of the
+    // compact table holds only its class (Kp/4 entries), D in the permuted order
+    const int *perm;
+    const float *Cc;
+    const float *Dkp;
     const float *r0_scale;  // fp32 form: if set, R0 holds unscaled R_k and the kernel forms
                             //   R'_k = R_k * r0_scale[k] (D_k) when it loads them
     const void *What;       // complex DFT plans: [2][M*N] planes of the 2-D DFT of w (scaled by
@@ -127,6 +133,13 @@ cudaError_t launch_iterate_full(const IterArgs &a, cudaStream_t st, int *launche
 int iterate_variants(int Kp, bool fp64);
 // Largest padded K of the certified fp32 form (one warp per block).
 int iterate_cert_max_kp();
+// The parity-class form of the fp32 iterations (a.perm, a.Cc, a.Dkp set; Kp = K
+// in {512, 1024, 2048}): each update touches only the selected atom's class.
+cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches);
+// Compact table rows of the parity-class form: Cc[u][j] = C[perm[u]][perm[c(u) K/4 + j]]
+// with c(u) = u / (K/4), from the full D-scaled table; Dkp[j] = Dk[perm[j]].
+cudaError_t launch_sym_gather(const float *C, const float *Dk, const int *perm, int K, int Kp, float *Cc,
+                              float *Dkp, cudaStream_t st);
 // Iterations, model and replacement for complex-valued atoms (k_complex.cu):
 // R0 [n][2][Kp], C [Kp][2][Kp] (row u = C(., u)), invC [Kp], PhiB [Kp][2][nB];
 // sel_coef receives (Re, Im) pairs.

@@ -132,7 +132,8 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
 
     std::string why;
     if (pl->sep_full) {
-        const SepArgs sa = pattern_sep_args(pl, 0, d_desc, n, d_r0);
+        // the parity-class kernel applies D_k when it loads R^(0)
+        const SepArgs sa = pattern_sep_args(pl, 0, d_desc, n, d_r0, !pl->sym);
         e = run_sep(ctx, pl, sa, st);
     } else if (fp64) {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
@@ -187,7 +188,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
         a.log_c = reinterpret_cast<float *>(d_log + static_cast<size_t>(n) * I);
     }
     int launched = 0;
-    e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterate_full<float>(a, st, &launched);
+    e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterations_f32(ctx, pl, a, st, &launched);
     if (e == cudaSuccess && !fp64) {
         e = launch_model(pl, a, st);
         ++launched;

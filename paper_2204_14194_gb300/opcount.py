@@ -37,3 +37,11 @@ def total(d: dict) -> int:
 def fase_iteration_ops(M: int, N: int, K: int) -> int:
     """Per-iteration part of the FaSE count: 5K + 2MN + 1 operations."""
     return 5 * K + 2 * M * N + 1
+
+
+def fase_iteration_ops_classes(M: int, N: int, K: int, classes: int = 4) -> int:
+    """The same count when C(k,u) vanishes outside the selected atom's class
+    (symmetric weighting, parity-structured atoms): the update, the scores and
+    the maximum touch K / classes atoms per iteration, plus one comparison per
+    class for the overall maximum."""
+    return 5 * (K // classes) + classes + 2 * M * N + 1

@@ -240,6 +240,28 @@ def test_host_entry_point_matches_device_path(ctx):
     plan.close()
 
 
+@pytest.mark.parametrize("shift", [0, 1])
+def test_symmetric_and_shifted_patterns(ctx, shift):
+    """A centred loss box makes w symmetric (the parity-class iterations run);
+    shifting it by one column breaks the symmetry (the general iterations run).
+    Both must match the oracle."""
+    L, n, I = 32, 48, 80
+    sup = np.ones((L, L), dtype=np.uint8)
+    sup[8:24, 8 + shift:24 + shift] = 0
+    s = np.stack([W.patch(L, 900 + i) for i in range(n)])
+    o = OracleSetup("dct_wht", L, L, 0.8, sup, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, s, 0.5, I, o.dup, margins=True)
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec="bf16x6", support=sup)
+    out, u, c = gpu_run(plan, s)
+    for b in range(n):
+        t = first_near_tie(rm[b], 1e-4)
+        np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+        assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= 1e-3
+    loss = np.broadcast_to(sup == 0, out.shape)
+    assert abs(psnr(out, s, loss) - psnr(ro, s, loss)) <= 0.05
+    plan.close()
+
+
 def test_dense_and_transform_products_agree(ctx):
     """The two ways of forming the scalar products (tensor-core GEMMs on the
     support pixels vs separable transforms, Sec. VI) select the same atoms on
