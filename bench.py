@@ -39,8 +39,8 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # traffic was captured for (ncu on this workload, see profiles/); None for a
 # shape without a capture or once the kernel changes.
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
-TRAFFIC_ITERATE = {0: 46.35e6}
-TRAFFIC_ITERATE_SYM = None
+TRAFFIC_ITERATE = {}
+TRAFFIC_ITERATE_SYM = 36.92e6
 
 
 def _dist():
