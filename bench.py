@@ -40,7 +40,8 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # shape without a capture or once the kernel changes.
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
 TRAFFIC_ITERATE = {}
-TRAFFIC_ITERATE_SYM = 36.92e6
+SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>"}
+TRAFFIC_ITERATE_SYM = {0: 36.92e6}
 
 
 def _dist():
@@ -310,7 +311,10 @@ def run_ours(args):
     if info.get("iterations") == "parity-classes":
         # the kernel's own work: a quarter of the atoms per iteration (one class)
         ops = n * I * opcount.fase_iteration_ops_classes(M, N, K, classes=4)
-        it_kernel, it_traffic = "iterate_sym_kernel<64> (parity classes)", TRAFFIC_ITERATE_SYM
+        nb = 1 << max(n - 1, 0).bit_length()
+        sv = max(ctx.tuned_variant("sym:f32:%d:n%d" % (K, nb)), 0)
+        it_kernel, it_traffic = SYM_SHAPES.get(sv, "iterate_sym kernel") + " (parity classes)", \
+            TRAFFIC_ITERATE_SYM.get(sv)
         row_bytes = K // 4 * 4
     else:
         ops = n * I * opcount.fase_iteration_ops(M, N, K)
@@ -336,10 +340,16 @@ def run_ours(args):
         if args.prec == "fp64":
             roofline_gemm = None
         else:
-            tflops = n * ntr * 2.0 * M * N * (M + N) / pr_avg_s / 1e12
+            if info.get("iterations") == "parity-classes":
+                # folded into four quarter-size transforms per block: half the flops
+                flops, pk = ntr * M * N * (M + N), "sym_r0_kernel<%d,%d> (eq. 12, four folded quarter transforms)" \
+                    % (M // 2, N // 2)
+            else:
+                flops, pk = ntr * 2.0 * M * N * (M + N), "sep_warp_kernel<32,32,8,4> (eq. 12 as separable transforms, Sec. VI)"
+            tflops = n * flops / pr_avg_s / 1e12
             gbs = n * (16.0 * na + 4.0 * K) / pr_avg_s / 1e9
             roofline_gemm = {
-                "kernel": "sep_warp_kernel<32,32,8,4> (eq. 12 as separable transforms, Sec. VI)",
+                "kernel": pk,
                 "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": tflops / alu_peak, "hbm_GBps": gbs, "hbm_frac": gbs / hbm_peak,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz"}

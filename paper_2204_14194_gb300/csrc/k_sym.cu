@@ -9,8 +9,9 @@
 // classes keep their maxima.
 //
 // Atoms are permuted so that the classes are contiguous (perm[new] = original
-// index, original order kept inside a class); lane l of the warp that owns a
-// block holds, for each class c, the atoms c K/4 + ch 128 + 4 l + e.
+// index, original order kept inside a class); R^(0) and the compact table come
+// in this order from the folded transforms below.  Lane l of the warp that
+// owns a block holds, for each class c, the atoms c K/4 + ch 128 + 4 l + e.
 // Everything else follows iterate_f32_kernel: D-scaled projections in
 // registers, packed FMAs, three-input maxima, one redux for the maximum, a
 // scan of the winning lane's class for the smallest index, bounded TMA row
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
                 float v[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    v[e] = R0[__ldg(a.perm + j + e)] * __ldg(a.Dkp + j + e);
+                    v[e] = R0[j + e] * __ldg(a.Dkp + j + e);
                     m[c] = fmaxf(m[c], fabsf(v[e]));
                 }
                 R2[c][2 * ch] = make_float2(v[0], v[1]);
@@ -155,26 +156,590 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
     }
 }
 
-__global__ void sym_gather_kernel(const float *__restrict__ C, const float *__restrict__ Dk,
-                                  const int *__restrict__ perm, int K, int Kp, float *__restrict__ Cc,
-                                  float *__restrict__ Dkp)
+// The same iterations with the block's projections in shared memory instead of
+// registers: a warp still owns one block, lane l keeps its float4 chunks at
+// [c][ch][l] (a warp's accesses are 512 contiguous bytes), and the selected
+// class's compact row is read straight into registers (four 16-byte loads per
+// lane, no copy engine and no barrier).  With 8 KiB per block at K = 2048 and
+// few registers, 27 blocks fit on an SM instead of 16, which is what an
+// iteration chain bound by the row's L2 latency needs.  Every arithmetic step
+// (R0 scaling, packed FMAs, three-input maxima, selection order) is the one of
+// iterate_sym_kernel, so both give the same bits.
+template <int VPT, int BPC, int MINB>
+__global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const IterArgs a)
 {
-    const int Q = K / 4;
-    const int u = blockIdx.x;
-    const int cu = u / Q;
-    const float *row = C + static_cast<size_t>(perm[u]) * Kp;
-    for (int j = threadIdx.x; j < Q; j += blockDim.x) Cc[static_cast<size_t>(u) * Q + j] = row[perm[cu * Q + j]];
-    if (threadIdx.x == 0) Dkp[u] = Dk[perm[u]];
+    constexpr int NCH = VPT / 4;
+    constexpr int NCC = NCH / 4;
+    constexpr int Q = 32 * 4 * NCC;
+    static_assert(NCC >= 1 && NCH % 4 == 0, "whole chunks per class");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *myR = reinterpret_cast<float4 *>(smem) + static_cast<size_t>(g) * (4 * NCC * 32) + lane;
+    const float gamma = static_cast<float>(a.gamma);
+
+    for (int b = blockIdx.x * BPC + g; b < a.n; b += gridDim.x * BPC) {
+        const BlockDesc bd = a.blocks[b];
+        const int I = bd.iterations;
+        const float *R0 = static_cast<const float *>(a.R0) + static_cast<size_t>(b) * a.Kp;
+        float m[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float mm = 0.0f;
+#pragma unroll 1
+            for (int ch = 0; ch < NCC; ++ch) {
+                const int j = c * Q + ch * 128 + 4 * lane;
+                const float4 rj = *reinterpret_cast<const float4 *>(R0 + j);
+                const float4 dj = __ldg(reinterpret_cast<const float4 *>(a.Dkp + j));
+                const float v[4] = {rj.x * dj.x, rj.y * dj.y, rj.z * dj.z, rj.w * dj.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mm = fmaxf(mm, fabsf(v[e]));
+                myR[(c * NCC + ch) * 32] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+            m[c] = mm;
+        }
+
+        for (int nu = 0; nu < I; ++nu) {
+            const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+            const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+            int kc = INT_MAX;
+            float rc = 0.0f;
+            if (mx == M) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (m[c] != M) continue;
+#pragma unroll
+                    for (int ch = 0; ch < NCC; ++ch) {
+                        const float4 q = myR[(c * NCC + ch) * 32];
+                        const float r4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (fabsf(r4[e]) == M) {
+                                kc = c * Q + ch * 128 + 4 * lane + e;
+                                rc = r4[e];
+                                goto found;
+                            }
+                        }
+                    }
+                }
+            found:;
+            }
+            int u = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
+            const int owner = u == INT_MAX ? 0 : (u % Q) / 4 % 32;
+            float ru = __shfl_sync(0xffffffffu, rc, owner);
+            if (u < 0 || u >= a.K) {
+                if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+                u = 0;
+                ru = 0.0f;
+            }
+            const int cu = u / Q;
+            const bool more = nu + 1 < I;
+            float4 t[NCC];
+            if (more) {
+                const float4 *row = reinterpret_cast<const float4 *>(a.Cc + static_cast<size_t>(u) * Q) + lane;
+#pragma unroll
+                for (int ch = 0; ch < NCC; ++ch) t[ch] = __ldg(row + ch * 32);
+            }
+            const float c = gamma * ru * __ldg(a.Dkp + u);
+            if (lane == 0) {
+                a.log_u[static_cast<size_t>(b) * a.I_max + nu] = __ldg(a.perm + u);
+                a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
+            }
+            if (!more) break;
+            const float2 nc = make_float2(-c, -c);
+            float mc[2] = {0.0f, 0.0f};
+            float4 *Rc = myR + cu * NCC * 32;
+#pragma unroll
+            for (int ch = 0; ch < NCC; ++ch) {
+                const float4 x = Rc[ch * 32];
+                const float2 x0 = __ffma2_rn(nc, make_float2(t[ch].x, t[ch].y), make_float2(x.x, x.y));
+                const float2 x1 = __ffma2_rn(nc, make_float2(t[ch].z, t[ch].w), make_float2(x.z, x.w));
+                Rc[ch * 32] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                mc[0] = max3_abs(mc[0], x0.x, x0.y);
+                mc[1] = max3_abs(mc[1], x1.x, x1.y);
+            }
+            const float mn = fmaxf(mc[0], mc[1]);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) m[cc] = cc == cu ? mn : m[cc];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- folded transforms
+// With w symmetric and t_p[M-1-m] = (-1)^p t_p[m] (DCT-II and sequency-ordered
+// Walsh rows), the separable transform of Sec. VI splits into four
+// quarter-size ones: for p = 2i + a and q = 2j + b,
+//   Y[p][q] = sum_{m < M/2, n < N/2} t_p[m] X_ab[m][n] t'_q[n],
+//   X_ab[m][n] = x[m][n] + (-1)^a x[M-1-m][n] + (-1)^b x[m][N-1-n]
+//                + (-1)^(a+b) x[M-1-m][N-1-n].
+// For R^(0) (x = w s) all four classes are formed, half the multiply-adds of
+// the full transform.  For a table row (x = w phi_u) only the class (a, b) of
+// atom u is non-zero and X_ab = 4 x on the quadrant, so a compact row costs an
+// eighth of a full one.  Outputs are written in the class order of the
+// iteration kernel: class c = 2a + b, then transform t, then (i, j).
+//
+// One warp per item; per transform t the constants A_t[m][a][i] = t_{2i+a}[m]
+// (m, i < M/2) and B_t[n][b][j] = t'_{2j+b}[n] (n, j < N/2) sit in shared
+// memory, then the unmasked weights rho[MN].  Lane l handles column
+// l mod QN and rows h RI .. h RI + RI - 1 (h = l / QN) of each quarter product.
+template <int QM, int QN>
+struct Fold {
+    static constexpr int QMN = QM * QN;
+    static constexpr int G = 32 / QN;     // row groups
+    static constexpr int RI = QM / G;     // rows per lane
+    static constexpr int RO = QMN / 32;   // quadrant points per lane
+    static_assert(QN <= 32 && 32 % QN == 0 && QM % G == 0 && QMN % 32 == 0 && RI % 2 == 0, "fold shape");
+    static constexpr int cst = 2 * QM * QM + 2 * QN * QN;   // floats per transform
+};
+
+template <int Nv>
+__device__ __forceinline__ void lds_v(const float *p, float (&v)[Nv])
+{
+    if constexpr (Nv % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p + j);
+            v[j] = t.x; v[j + 1] = t.y; v[j + 2] = t.z; v[j + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p + j);
+            v[j] = t.x; v[j + 1] = t.y;
+        }
+    }
+}
+
+template <int Nv>
+__device__ __forceinline__ void sts_v(float *p, const float (&v)[Nv])
+{
+    if constexpr (Nv % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 4) *reinterpret_cast<float4 *>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < Nv; j += 2) *reinterpret_cast<float2 *>(p + j) = make_float2(v[j], v[j + 1]);
+    }
+}
+
+// The quarter product Y = A_a X B_b^T of one class and transform for this
+// lane: acc[r] = Y[h RI + r][lane mod QN].  UT is the warp's [QN][QM] buffer.
+template <int QM, int QN>
+__device__ __forceinline__ void fold_product(const float *Ct, int a, int b, const float *X, float *UT, int lane,
+                                             float (&acc)[Fold<QM, QN>::RI])
+{
+    using F = Fold<QM, QN>;
+    constexpr int RI = F::RI;
+    const int col = lane % QN, h = lane / QN;
+    const float *A = Ct + a * QM + h * RI;                  // A[m][a][h RI ..] at m 2QM
+    const float *B = Ct + 2 * QM * QM + b * QN + col;       // B[n][b][col] at n 2QN
+    float u[RI];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) u[r] = 0.0f;
+#pragma unroll 4
+    for (int m = 0; m < QM; ++m) {
+        float av[RI];
+        lds_v<RI>(A + m * 2 * QM, av);
+        const float xv = X[m * QN + col];
+#pragma unroll
+        for (int r = 0; r < RI; r += 2) {
+            const float2 o = __ffma2_rn(make_float2(av[r], av[r + 1]), make_float2(xv, xv), make_float2(u[r], u[r + 1]));
+            u[r] = o.x;
+            u[r + 1] = o.y;
+        }
+    }
+    __syncwarp();   // the previous product's reads of UT are done
+    sts_v<RI>(UT + col * QM + h * RI, u);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RI; ++r) acc[r] = 0.0f;
+#pragma unroll 4
+    for (int n = 0; n < QN; ++n) {
+        float uv[RI];
+        lds_v<RI>(UT + n * QM + h * RI, uv);
+        const float bv = B[n * 2 * QN];
+#pragma unroll
+        for (int r = 0; r < RI; r += 2) {
+            const float2 o = __ffma2_rn(make_float2(uv[r], uv[r + 1]), make_float2(bv, bv), make_float2(acc[r], acc[r + 1]));
+            acc[r] = o.x;
+            acc[r + 1] = o.y;
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_consts(const float *src, float *dst, int nfloats)
+{
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int e = threadIdx.x; e < nfloats / 4; e += blockDim.x) d4[e] = __ldg(s4 + e);
+}
+
+// The table of Alg. 2 for a parity-class plan in one launch.  Every CTA first
+// forms the diagonal of eq. (16) for all atoms as a folded separable sum of
+// non-negative terms, C_kk = 4 sum_{m < M/2, n < N/2} w t_p[m]^2 t'_q[n]^2
+// (no cancellation, so fp32 keeps its relative accuracy down to the
+// admissibility threshold), the largest C_kk of the non-duplicate atoms, and
+// D_k of eq. (17) (NaN for inadmissible atoms); CTA 0 also stores D_k and
+// 1/C_kk.  Then the compact rows: item u (class order) is atom perm[u];
+// Cc[u][j] = C(perm[c Q + j], perm[u]) D_{perm[c Q + j]}, Dkp[u] = D_{perm[u]}.
+template <int QM, int QN>
+__global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
+{
+    using F = Fold<QM, QN>;
+    constexpr int QMN = F::QMN, RI = F::RI, RO = F::RO;
+    constexpr int M = 2 * QM, N = 2 * QN, MN = M * N;
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ float red[32];
+    const int ncst = a.ntr * F::cst;
+    float *cst = fsm;                          // constants, then rho
+    const float *rho = cst + ncst;
+    float *Dsh = cst + ncst + MN;              // [K] C_kk, then D_k
+    float *V = Dsh + a.K;                      // [ntr][M][QN] stage 1 of the diagonal
+    float *X = V + a.ntr * M * QN + (threadIdx.x >> 5) * 2 * QMN;
+    float *UT = X + QMN;
+    stage_consts(a.img, cst, ncst + MN);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+    const int Q = a.K / 4;
+
+    for (int e = threadIdx.x; e < a.ntr * M * QN; e += blockDim.x) {
+        const int t = e / (M * QN), p = (e / QN) % M, n = e % QN;
+        const float *At = cst + t * F::cst + (p & 1) * QM + (p >> 1);
+        float v = 0.0f;
+        for (int m = 0; m < QM; ++m) {
+            const float tp = At[m * 2 * QM];
+            const float wv = a.pattern[m * N + n] ? rho[m * N + n] : 0.0f;
+            v = fmaf(tp * tp, wv, v);
+        }
+        V[e] = v;
+    }
+    __syncthreads();
+    float lmax = 0.0f;
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+        const int t = k / MN, p = (k % MN) / N, q = k % N;
+        const float *Bt = cst + t * F::cst + 2 * QM * QM + (q & 1) * QN + (q >> 1);
+        const float *Vp = V + (t * M + p) * QN;
+        float d = 0.0f;
+        for (int n = 0; n < QN; ++n) {
+            const float tq = Bt[n * 2 * QN];
+            d = fmaf(Vp[n], tq * tq, d);
+        }
+        d *= 4.0f;
+        Dsh[k] = d;
+        if (!a.dup[k]) lmax = fmaxf(lmax, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (lane == 0) red[threadIdx.x >> 5] = lmax;
+    __syncthreads();
+    float dmax = 0.0f;
+    for (int w = 0; w < wpc; ++w) dmax = fmaxf(dmax, red[w]);
+    for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+        const float d = Dsh[k];
+        const bool adm = !a.dup[k] && dmax > 0.0f && d > 1e-14f * dmax;
+        const float D = adm ? 1.0f / sqrtf(d) : NAN;
+        Dsh[k] = D;
+        if (blockIdx.x == 0) {
+            a.Dk[k] = D;
+            a.invC[k] = adm ? 1.0f / d : 0.0f;
+        }
+    }
+    __syncthreads();
+
+    for (int u = blockIdx.x * wpc + (threadIdx.x >> 5); u < a.K; u += gridDim.x * wpc) {
+        const int k = __ldg(a.perm + u);
+        const int t = k >= MN ? 1 : 0;
+        const int kk = k - t * MN, pu = kk / N, qu = kk % N;
+        const int ca = pu & 1, cb = qu & 1;
+        const float *Ct = cst + t * F::cst;
+        __syncwarp();   // the previous item's reads of X are done
+#pragma unroll
+        for (int r = 0; r < RO; ++r) {
+            const int o = lane + 32 * r, m = o / QN, n = o % QN;
+            const float ex = Ct[m * 2 * QM + ca * QM + (pu >> 1)] * Ct[2 * QM * QM + n * 2 * QN + cb * QN + (qu >> 1)];
+            const float v = a.pattern[m * N + n] ? rho[m * N + n] : 0.0f;
+            X[o] = v * ex;
+        }
+        __syncwarp();
+        float *row = a.Cc + static_cast<size_t>(u) * Q;
+        for (int to = 0; to < a.ntr; ++to) {
+            float acc[RI];
+            fold_product<QM, QN>(cst + to * F::cst, ca, cb, X, UT, lane, acc);
+            // entry (i, jj) is atom (to, 2 i + ca, 2 jj + cb) of the class order
+            const int i0 = (lane / QN) * RI, jj = lane % QN;
+            const int base = to * QMN + i0 * QN + jj;
+            const float *Dr = Dsh + to * MN + (2 * i0 + ca) * N + 2 * jj + cb;
+#pragma unroll
+            for (int r = 0; r < RI; ++r) row[base + r * QN] = 4.0f * acc[r] * Dr[2 * r * N];
+        }
+        if (lane == 0) a.Dkp[u] = Dsh[k];
+    }
+}
+
+// R^(0) of eq. (12) for pattern blocks, all four classes, unscaled, in class
+// order (R0[b][c Q + t QM QN + i QN + j]); also copies the support samples to
+// the block's output.
+template <int QM, int QN>
+__global__ void __launch_bounds__(256) sym_r0_kernel(const SymSepArgs a)
+{
+    using F = Fold<QM, QN>;
+    constexpr int QMN = F::QMN, RI = F::RI, RO = F::RO;
+    constexpr int M = 2 * QM, N = 2 * QN, MN = M * N;
+    extern __shared__ __align__(16) float fsm[];
+    const int ncst = a.ntr * F::cst;
+    float *cst = fsm;
+    const float *rho = cst + ncst;
+    float *X = cst + ncst + MN + (threadIdx.x >> 5) * 5 * QMN;   // X_00, X_01, X_10, X_11
+    float *UT = X + 4 * QMN;
+    stage_consts(a.img, cst, ncst + MN);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+    const int Q = a.K / 4;
+    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc) {
+        const BlockDesc bd = a.blocks[b];
+        const uint8_t *mask = bd.support ? bd.support : a.pattern;
+        const double *smp = bd.samples;
+        double *dst = a.copy_support ? bd.out : nullptr;
+        __syncwarp();   // the previous block's reads of X are done
+#pragma unroll 2
+        for (int r = 0; r < RO; ++r) {
+            const int o = lane + 32 * r, m = o / QN, n = o % QN;
+            const int p[4] = {m * N + n, (M - 1 - m) * N + n, m * N + N - 1 - n, (M - 1 - m) * N + N - 1 - n};
+            float x[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool on = mask[p[e]] != 0;
+                const double sv = on ? smp[p[e]] : 0.0;
+                x[e] = on ? rho[p[e]] * static_cast<float>(sv) : 0.0f;
+                if (dst && on) dst[p[e]] = sv;
+            }
+            const float s0 = x[0] + x[1], d0 = x[0] - x[1];   // fold in m
+            const float s1 = x[2] + x[3], d1 = x[2] - x[3];
+            X[o] = s0 + s1;                                     // (a, b) = (0, 0)
+            X[QMN + o] = s0 - s1;                               // (0, 1)
+            X[2 * QMN + o] = d0 + d1;                           // (1, 0)
+            X[3 * QMN + o] = d0 - d1;                           // (1, 1)
+        }
+        __syncwarp();
+        float *R = a.R0 + static_cast<size_t>(b) * a.K;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            for (int t = 0; t < a.ntr; ++t) {
+                float acc[RI];
+                fold_product<QM, QN>(cst + t * F::cst, c >> 1, c & 1, X + c * QMN, UT, lane, acc);
+                const int base = c * Q + t * QMN + (lane / QN) * RI * QN + lane % QN;
+#pragma unroll
+                for (int r = 0; r < RI; ++r) R[base + r * QN] = acc[r];
+            }
+        }
+    }
+}
+
+// The same R^(0) pass for 32 x 32 areas with the lane as the column: lane n
+// reads rows r and 31 - r of column n for all r < 16 at once (no load waits
+// on another), folds in m in its registers and in n with the lane 31 - n
+// (shuffle); lanes < 16 write X_00 and X_10, lanes >= 16 X_01 and X_11.  The
+// quarter products run two at a time, one per half-warp (column parity b =
+// half), in 4 x 4 register tiles: two 16-byte shared loads per 16
+// multiply-adds.  Every output is the same chain of fused multiply-adds
+// (same operands, same order) as in sym_r0_kernel<16, 16>, so both give the
+// same bits.
+constexpr int kR0Plane = 272;   // X_ab plane pitch: 256 + 16 (lanes >= 16 store to the other 16 banks)
+constexpr int kR0UT = 20;       // pitch of a row n of the transposed stage-1 result
+__global__ void __launch_bounds__(256, 3) sym_r0_32_kernel(const SymSepArgs a)
+{
+    constexpr int M = 32, N = 32, MN = 1024, QMN = 256, CST = 1024;   // floats of one transform's constants
+    extern __shared__ __align__(16) float fsm[];
+    const int ncst = a.ntr * CST;
+    float *cst = fsm;
+    const float *rho = cst + ncst;
+    float *X = cst + ncst + MN + (threadIdx.x >> 5) * (4 * kR0Plane + 2 * 16 * kR0UT);
+    float *UT = X + 4 * kR0Plane;   // per half-warp [n][kR0UT]: the transposed stage-1 result
+    stage_consts(a.img, cst, ncst + MN);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+    const int hw = lane >> 4, iq = (lane >> 2) & 3, jq = lane & 3;
+    const int Q = a.K / 4;
+    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc) {
+        const BlockDesc bd = a.blocks[b];
+        const uint8_t *mask = (bd.support ? bd.support : a.pattern) + lane;
+        const double *smp = bd.samples + lane;
+        double *dst = a.copy_support ? bd.out + lane : nullptr;
+        __syncwarp();   // the previous block's reads of X and UT are done
+#pragma unroll 1
+        for (int r0 = 0; r0 < M / 2; r0 += 8) {
+            double s0[8], s1[8];
+            bool o0[8], o1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {   // loss samples are read too and dropped by the select below
+                const int r = r0 + k;
+                o0[k] = mask[r * N] != 0;
+                o1[k] = mask[(M - 1 - r) * N] != 0;
+                s0[k] = smp[r * N];
+                s1[k] = smp[(M - 1 - r) * N];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                const float x0 = o0[k] ? rho[r * N + lane] * static_cast<float>(s0[k]) : 0.0f;
+                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * static_cast<float>(s1[k]) : 0.0f;
+                if (dst) {
+                    if (o0[k]) dst[r * N] = s0[k];
+                    if (o1[k]) dst[(M - 1 - r) * N] = s1[k];
+                }
+                const float sm = x0 + x1, dm = x0 - x1;
+                const float smo = __shfl_xor_sync(0xffffffffu, sm, 31), dmo = __shfl_xor_sync(0xffffffffu, dm, 31);
+                if (lane < 16) {
+                    X[r * 16 + lane] = sm + smo;                          // (0, 0)
+                    X[2 * kR0Plane + r * 16 + lane] = dm + dmo;           // (1, 0)
+                } else {
+                    X[kR0Plane + r * 16 + 31 - lane] = smo - sm;          // (0, 1)
+                    X[3 * kR0Plane + r * 16 + 31 - lane] = dmo - dm;      // (1, 1)
+                }
+            }
+        }
+        __syncwarp();
+        float *R = a.R0 + static_cast<size_t>(b) * a.K;
+        // pass (ca, t): half-warp hw takes column parity cb = hw; lane hl = 4 iq + jq
+        // holds the 4 x 4 tile rows 4 iq .., columns 4 jq ..
+        float *UTh = UT + hw * 16 * kR0UT;
+#pragma unroll 1
+        for (int ca = 0; ca < 2; ++ca) {
+#pragma unroll 1
+            for (int t = 0; t < a.ntr; ++t) {
+                const float *A = cst + t * CST + ca * 16 + 4 * iq;                 // A[m][ca][4 iq ..] at m 32
+                const float *Bt = cst + t * CST + 2 * 16 * 16 + hw * 16 + 4 * jq;  // B[n][cb][4 jq ..] at n 32
+                const float *Xp = X + (2 * ca + hw) * kR0Plane + 4 * jq;
+                float u[4][4];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) u[ii][k] = 0.0f;
+#pragma unroll 4
+                for (int m = 0; m < 16; ++m) {
+                    const float4 av = *reinterpret_cast<const float4 *>(A + m * 32);
+                    const float4 xv = *reinterpret_cast<const float4 *>(Xp + m * 16);
+                    const float ai[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        float2 o = __ffma2_rn(make_float2(ai[ii], ai[ii]), make_float2(xv.x, xv.y),
+                                              make_float2(u[ii][0], u[ii][1]));
+                        u[ii][0] = o.x;
+                        u[ii][1] = o.y;
+                        o = __ffma2_rn(make_float2(ai[ii], ai[ii]), make_float2(xv.z, xv.w),
+                                       make_float2(u[ii][2], u[ii][3]));
+                        u[ii][2] = o.x;
+                        u[ii][3] = o.y;
+                    }
+                }
+                __syncwarp();   // the previous pass is done reading UT
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    *reinterpret_cast<float4 *>(UTh + (4 * jq + k) * kR0UT + 4 * iq) =
+                        make_float4(u[0][k], u[1][k], u[2][k], u[3][k]);
+                __syncwarp();
+                float y[4][4];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) y[ii][k] = 0.0f;
+#pragma unroll 4
+                for (int n = 0; n < 16; ++n) {
+                    const float4 uv = *reinterpret_cast<const float4 *>(UTh + n * kR0UT + 4 * iq);
+                    const float4 bv = *reinterpret_cast<const float4 *>(Bt + n * 32);
+                    const float ui[4] = {uv.x, uv.y, uv.z, uv.w};
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        float2 o = __ffma2_rn(make_float2(ui[ii], ui[ii]), make_float2(bv.x, bv.y),
+                                              make_float2(y[ii][0], y[ii][1]));
+                        y[ii][0] = o.x;
+                        y[ii][1] = o.y;
+                        o = __ffma2_rn(make_float2(ui[ii], ui[ii]), make_float2(bv.z, bv.w),
+                                       make_float2(y[ii][2], y[ii][3]));
+                        y[ii][2] = o.x;
+                        y[ii][3] = o.y;
+                    }
+                }
+                float *Rc = R + (2 * ca + hw) * Q + t * QMN + 4 * jq;
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+                    *reinterpret_cast<float4 *>(Rc + (4 * iq + ii) * 16) = make_float4(y[ii][0], y[ii][1], y[ii][2], y[ii][3]);
+            }
+        }
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_sym_gather(const float *C, const float *Dk, const int *perm, int K, int Kp, float *Cc, float *Dkp,
-                              cudaStream_t st)
+template <int QM, int QN>
+static cudaError_t launch_fold(const SymSepArgs &a, bool rows, cudaStream_t st)
 {
-    if (K <= 0 || K % 4) return cudaErrorInvalidValue;
-    sym_gather_kernel<<<K, 128, 0, st>>>(C, Dk, perm, K, Kp, Cc, Dkp);
+    using F = Fold<QM, QN>;
+    constexpr int wpc = 8;
+    const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * F::cst + 4 * QM * QN +
+                                         (rows ? static_cast<size_t>(a.K) + a.ntr * 2 * QM * QN : 0) +
+                                         static_cast<size_t>(wpc) * (rows ? 2 : 5) * F::QMN);
+    const int items = rows ? a.K : a.n;
+    if (items <= 0) return cudaSuccess;
+    auto kern = rows ? sym_rows_kernel<QM, QN> : sym_r0_kernel<QM, QN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, smem)) != cudaSuccess) return e;
+    const int need = (items + wpc - 1) / wpc;
+    // the table kernel repeats the diagonal in every CTA: one CTA per SM
+    const int cap = rows ? sms : sms * (per_sm > 0 ? per_sm : 1);
+    kern<<<need < cap ? need : cap, 32 * wpc, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+bool sym_fold_supported(int M, int N)
+{
+    return (M == 16 || M == 32) && (N == 16 || N == 32);
+}
+
+static cudaError_t launch_fold_any(const SymSepArgs &a, bool rows, cudaStream_t st)
+{
+    if (a.K != a.ntr * a.M * a.N || a.K % 4 || !a.img || !a.perm) return cudaErrorInvalidValue;
+    if (a.M == 32 && a.N == 32) return launch_fold<16, 16>(a, rows, st);
+    if (a.M == 16 && a.N == 16) return launch_fold<8, 8>(a, rows, st);
+    if (a.M == 32 && a.N == 16) return launch_fold<16, 8>(a, rows, st);
+    if (a.M == 16 && a.N == 32) return launch_fold<8, 16>(a, rows, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sym_rows(const SymSepArgs &a, cudaStream_t st)
+{
+    if (!a.Dk || !a.invC || !a.dup || !a.Cc || !a.Dkp) return cudaErrorInvalidValue;
+    return launch_fold_any(a, true, st);
+}
+
+int sym_r0_variants(int M, int N) { return M == 32 && N == 32 ? 2 : 1; }
+
+cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant)
+{
+    if (!a.blocks || !a.R0) return cudaErrorInvalidValue;
+    if (variant == 1 && a.M == 32 && a.N == 32) {
+        if (a.K != a.ntr * 1024 || !a.img) return cudaErrorInvalidValue;
+        if (a.n <= 0) return cudaSuccess;
+        constexpr int wpc = 8;
+        const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 1024 + 1024 +
+                                             wpc * static_cast<size_t>(4 * kR0Plane + 2 * 16 * kR0UT));
+        cudaError_t e = cudaFuncSetAttribute(sym_r0_32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sym_r0_32_kernel, 32 * wpc, smem)) !=
+            cudaSuccess)
+            return e;
+        const int need = (a.n + wpc - 1) / wpc;
+        const int cap = sms * (per_sm > 0 ? per_sm : 1);
+        sym_r0_32_kernel<<<need < cap ? need : cap, 32 * wpc, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    return launch_fold_any(a, false, st);
 }
 
 template <int VPT>
@@ -198,9 +763,42 @@ static cudaError_t launch_sym_vpt(const IterArgs &a, cudaStream_t st, int *launc
     return cudaGetLastError();
 }
 
-cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches)
+template <int VPT, int BPC, int MINB>
+static cudaError_t launch_sym_smem(const IterArgs &a, cudaStream_t st, int *launches)
+{
+    constexpr int Q = 32 * VPT / 4;
+    if (a.K != 4 * Q || a.Kp != a.K || !a.log_u || !a.log_c || !a.perm || !a.Cc || !a.Dkp)
+        return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * static_cast<size_t>(BPC) * a.Kp;
+    auto kern = iterate_sym_smem_kernel<VPT, BPC, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * BPC, smem)) != cudaSuccess) return e;
+    const int need = (a.n + BPC - 1) / BPC;
+    const int cap = sms * (per_sm > 0 ? per_sm : 1);
+    kern<<<need < cap ? need : cap, 32 * BPC, smem, st>>>(a);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+int iterate_sym_variants() { return 2; }
+
+cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches, int variant)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (variant == 1) {   // projections in shared memory
+        switch (a.Kp) {
+        case 512: return launch_sym_smem<16, 4, 12>(a, st, launches);
+        case 1024: return launch_sym_smem<32, 4, 10>(a, st, launches);
+        case 2048: return launch_sym_smem<64, 3, 9>(a, st, launches);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.Kp) {
     case 512: return launch_sym_vpt<16>(a, st, launches);
     case 1024: return launch_sym_vpt<32>(a, st, launches);

@@ -227,16 +227,19 @@ void se::route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::
 }
 
 // Parity classes (see k_sym.cu).  Enabled for the fp32 transform form with
-// DCT / WHT atoms, even M and N, K = Kp in {512, 1024, 2048} and a weighting
-// function that is exactly symmetric in m and in n; the vanishing of C(k,u)
-// across classes is also checked on sampled atom pairs before it is used.
+// DCT / WHT atoms, M, N in {16, 32}, K = Kp in {512, 1024, 2048} and a
+// weighting function that is exactly symmetric in m and in n; every atom is
+// checked to be even or odd in each direction as its indices say, and the
+// vanishing of C(k,u) across classes is checked on sampled atom pairs.
 se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
 {
     const int M = pl->M, N = pl->N, MN = pl->MN, K = pl->K;
     const int basis = pl->desc.basis;
     if (!(pl->sep_full && !pl->pc.fp64 && !pl->certified && !pl->cplx && pl->T == 1)) return SE_OK;
     if (!(basis == SE_BASIS_DCT || basis == SE_BASIS_WHT || basis == SE_BASIS_DCT_WHT)) return SE_OK;
-    if (M % 2 || N % 2 || K != pl->Kp || (K != 512 && K != 1024 && K != 2048)) return SE_OK;
+    if (!sym_fold_supported(M, N) || K != pl->Kp || (K != 512 && K != 1024 && K != 2048)) return SE_OK;
+    if (K != pl->sep_ntr * MN || (pl->sep_ntr == 2 && pl->sep_koff[1] != MN) || pl->d_sep_img.ptr == nullptr)
+        return SE_OK;
     for (int m = 0; m < M; ++m)
         for (int n = 0; n < N; ++n) {
             const double v = pl->w[static_cast<size_t>(m) * N + n];
@@ -252,8 +255,30 @@ se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
     for (int c = 0; c < 4; ++c)
         for (int k = 0; k < K; ++k)
             if (cls(k) == c) perm.push_back(k);
+    // the class order the folded transforms write: class, transform, (p / 2, q / 2)
+    if (static_cast<int>(perm.size()) != K) return SE_OK;
+    const int QM = M / 2, QN = N / 2, Q = K / 4;
     for (int c = 0; c < 4; ++c)
-        if (perm[static_cast<size_t>(c) * (K / 4)] < 0 || cls(perm[static_cast<size_t>(c) * (K / 4)]) != c) return SE_OK;
+        for (int t = 0; t < pl->sep_ntr; ++t)
+            for (int i = 0; i < QM; ++i)
+                for (int j = 0; j < QN; ++j)
+                    if (perm[static_cast<size_t>(c) * Q + t * QM * QN + i * QN + j] !=
+                        t * MN + (2 * i + (c >> 1)) * N + 2 * j + (c & 1))
+                        return SE_OK;
+    // every atom even or odd in each direction as (p mod 2, q mod 2) says
+    double amax = 0.0;
+    for (size_t e = 0; e < static_cast<size_t>(K) * MN; ++e) amax = std::max(amax, std::fabs(pl->phi[e]));
+    for (int k = 0; k < K; ++k) {
+        const double sa = (cls(k) >> 1) ? -1.0 : 1.0, sb = (cls(k) & 1) ? -1.0 : 1.0;
+        const double *f = pl->phi.data() + static_cast<size_t>(k) * MN;
+        for (int m = 0; m < M; ++m)
+            for (int n = 0; n < N; ++n) {
+                const double v = f[m * N + n];
+                if (std::fabs(f[(M - 1 - m) * N + n] - sa * v) > 1e-12 * amax ||
+                    std::fabs(f[m * N + N - 1 - n] - sb * v) > 1e-12 * amax)
+                    return SE_OK;
+            }
+    }
     // sampled check: atoms of different classes have (numerically) no weighted overlap
     std::mt19937 gen(7);
     for (int t = 0; t < 64; ++t) {
@@ -269,11 +294,58 @@ se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
         }
         if (std::fabs(x) > 1e-12 * std::sqrt(na * nb) + 1e-300) return SE_OK;
     }
+    // constants of the folded transforms from the transform kernels' image
+    // (per transform t_p[m] at m M + p, t'_q[n] at n N + q; then rho)
+    const int ntr = pl->sep_ntr;
+    std::vector<float> img(static_cast<size_t>(ntr) * (M * M + N * N) + MN);
+    SE_CUDA(cudaMemcpy(img.data(), pl->d_sep_img.ptr, img.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    std::vector<float> fimg;
+    fimg.reserve(static_cast<size_t>(ntr) * (M * M + N * N) / 2 + MN);
+    for (int t = 0; t < ntr; ++t) {
+        const float *tm = img.data() + static_cast<size_t>(t) * (M * M + N * N), *tn = tm + M * M;
+        for (int m = 0; m < QM; ++m)
+            for (int a = 0; a < 2; ++a)
+                for (int i = 0; i < QM; ++i) fimg.push_back(tm[m * M + 2 * i + a]);
+        for (int n = 0; n < QN; ++n)
+            for (int b = 0; b < 2; ++b)
+                for (int j = 0; j < QN; ++j) fimg.push_back(tn[n * N + 2 * j + b]);
+    }
+    fimg.insert(fimg.end(), img.end() - MN, img.end());
+    SE_TRY(upload(ctx, pl->d_sym_img, fimg));
     SE_TRY(upload(ctx, pl->d_perm, perm));
     SE_TRY(dev_alloc(ctx, pl->d_Cc, sizeof(float) * static_cast<size_t>(K) * (K / 4)));
     SE_TRY(dev_alloc(ctx, pl->d_Dkp, sizeof(float) * static_cast<size_t>(K)));
     pl->sym = true;
     return SE_OK;
+}
+
+static SymSepArgs sym_sep_args(se_plan_s *pl)
+{
+    SymSepArgs s{};
+    s.M = pl->M;
+    s.N = pl->N;
+    s.ntr = pl->sep_ntr;
+    s.K = pl->K;
+    s.img = pl->d_sym_img.as<float>();
+    s.perm = pl->d_perm.as<int>();
+    s.pattern = pl->d_pattern.as<uint8_t>();
+    return s;
+}
+
+cudaError_t se::launch_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, const BlockDesc *dd, int n, void *r0,
+                                           bool scaled, cudaStream_t st)
+{
+    if (pl->sym) {
+        SymSepArgs s = sym_sep_args(pl);
+        s.blocks = dd;
+        s.n = n;
+        s.R0 = static_cast<float *>(r0);
+        s.copy_support = pl->nB > 0;
+        const std::string key = "symr0:" + std::to_string(pl->M) + "x" + std::to_string(pl->N) + ":t" +
+                                std::to_string(pl->sep_ntr);
+        return tune_run(ctx, key, sym_r0_variants(pl->M, pl->N), st, [&](int v) { return launch_sym_r0(s, st, v); });
+    }
+    return run_sep(ctx, pl, pattern_sep_args(pl, 0, dd, n, r0, scaled), st);
 }
 
 cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched)
@@ -282,7 +354,15 @@ cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a,
         a.perm = pl->d_perm.as<int>();
         a.Cc = pl->d_Cc.as<float>();
         a.Dkp = pl->d_Dkp.as<float>();
-        return launch_iterate_sym(a, st, launched);
+        // the faster shape depends on how many waves the batch fills: key by the
+        // batch size rounded up to a power of two
+        int nb = 1;
+        while (nb < a.n) nb <<= 1;
+        const std::string skey = "sym:f32:" + std::to_string(pl->Kp) + ":n" + std::to_string(nb);
+        return tune_run(ctx, skey, iterate_sym_variants(), st, [&](int v) {
+            *launched = 0;
+            return launch_iterate_sym(a, st, launched, v);
+        });
     }
     const std::string ikey = "iterate:f32:" + std::to_string(pl->Kp);
     return tune_run(ctx, ikey, iterate_variants(pl->Kp, false), st, [&](int v) {
@@ -339,6 +419,20 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
     }
     const int Kp = pl->Kp;
     std::string why;
+    if (pl->sym) {   // diagonal, D_k and the compact rows of the parity classes in one launch
+        SymSepArgs s = sym_sep_args(pl);
+        s.dup = pl->d_dup.as<uint8_t>();
+        s.Dk = pl->d_Dk.as<float>();
+        s.invC = pl->d_invC.as<float>();
+        s.Cc = pl->d_Cc.as<float>();
+        s.Dkp = pl->d_Dkp.as<float>();
+        SE_CUDA(launch_sym_rows(s, st));
+        ctx->launches += 1;
+        SE_CUDA(cudaEventRecord(pl->tables_ready, st));
+        pl->tables_valid = true;
+        ctx->table_builds++;
+        return SE_OK;
+    }
     unsigned long long *dmax = reinterpret_cast<unsigned long long *>(pl->d_nadm.as<char>() + 8);
     SE_CUDA(launch_tables_diag(pl->d_G64.as<double>(), pl->ka_pad, pl->K, Kp, pl->nA,
                                pl->d_dup.as<uint8_t>(), pl->d_diag.as<double>(), dmax,
@@ -357,11 +451,6 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         SepArgs sa = pattern_sep_args(pl, 3, nullptr, pl->K, pl->d_C.ptr);
         SE_CUDA(run_sep(ctx, pl, sa, st));
         ctx->launches += 3;
-        if (pl->sym) {   // compact rows of the parity classes
-            SE_CUDA(launch_sym_gather(pl->d_C.as<float>(), pl->d_Dk.as<float>(), pl->d_perm.as<int>(), pl->K, Kp,
-                                      pl->d_Cc.as<float>(), pl->d_Dkp.as<float>(), st));
-            ctx->launches += 1;
-        }
     } else if (pl->pc.fp64) {
         SE_CUDA(launch_tables_finalize<double>(pl->d_diag.as<double>(), pl->d_dup.as<uint8_t>(), dmax,
                                                pl->K, Kp, pl->d_invC.as<double>(),
@@ -521,8 +610,7 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     if (pl->sep_full) {
         // eq. (12) as a separable transform of w s per block: no packing stage
         tok = stage_begin(ctx, 2, st);
-        SepArgs sa = pattern_sep_args(pl, 0, ddesc, n, ws.r0.ptr, !overlap);
-        SE_CUDA(run_sep(ctx, pl, sa, st));
+        SE_CUDA(launch_pattern_projections(ctx, pl, ddesc, n, ws.r0.ptr, !overlap, st));
         stage_end(ctx, tok, st);
         if (overlap) SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));   // the (forked) table build
         ctx->launches += 1;

@@ -236,8 +236,10 @@ struct se_plan_s {
     // every atom has C_kk = What[0][0], so 1/C_kk is uniform (host copy for the table stage)
     bool dft_w = false;
     // symmetric weighting with DCT / WHT atoms: parity classes (k_sym.cu)
+    // (class order perm, compact table Cc [K][K/4], D in class order, constants of the folded
+    // transforms); R^(0) of such plans is stored in class order
     bool sym = false;
-    se::DevBuf d_perm, d_Cc, d_Dkp;
+    se::DevBuf d_perm, d_Cc, d_Dkp, d_sym_img;
     se::DevBuf d_What;
     std::vector<double> dft_invC;
     // tables (eqs. 16-17)
@@ -313,6 +315,11 @@ se_status setup_sym(se_ctx_s *ctx, se_plan_s *pl);
 cudaError_t launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched);
 // A transform-domain launch with the schedule chosen by the autotuner.
 cudaError_t run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st);
+// R^(0) of n pattern blocks in the transform form (needs pl->sep_full): the
+// folded class-order kernel for parity-class plans (unscaled), else the
+// separable transform (scaled by D_k when scaled); support samples copied to out.
+cudaError_t launch_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, const BlockDesc *dd, int n, void *r0,
+                                       bool scaled, cudaStream_t st);
 // Move pattern blocks to the lazy list when the measured costs favour it.
 void route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::vector<BlockDesc> &lazy,
                           int *I_full, int *I_lazy);

@@ -135,11 +135,39 @@ int iterate_variants(int Kp, bool fp64);
 int iterate_cert_max_kp();
 // The parity-class form of the fp32 iterations (a.perm, a.Cc, a.Dkp set; Kp = K
 // in {512, 1024, 2048}): each update touches only the selected atom's class.
-cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches);
-// Compact table rows of the parity-class form: Cc[u][j] = C[perm[u]][perm[c(u) K/4 + j]]
-// with c(u) = u / (K/4), from the full D-scaled table; Dkp[j] = Dk[perm[j]].
-cudaError_t launch_sym_gather(const float *C, const float *Dk, const int *perm, int K, int Kp, float *Cc,
-                              float *Dkp, cudaStream_t st);
+// variant < iterate_sym_variants(): 0 projections in registers, 1 in shared
+// memory (more blocks per SM); identical results.
+cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches, int variant = 0);
+int iterate_sym_variants();
+// Folded separable transforms of the parity-class form (M, N in {16, 32};
+// K = ntr M N, atoms k = t M N + p N + q; class c = 2 (p mod 2) + (q mod 2);
+// class order perm: class, then transform, then (p, q)).
+struct SymSepArgs {
+    int M, N, ntr, K;
+    const float *img;           // per transform A_t[M/2][2][M/2] (t_{2i+a}[m] at (m, a, i)),
+                                //   B_t[N/2][2][N/2]; then rho [MN] (unmasked weights)
+    const int *perm;            // [K] class order -> original atom
+    const uint8_t *pattern;     // [MN] 1 = support
+    // table: the diagonal of eq. (16) and D_k, 1/C_kk of eq. (17) (written to Dk, invC in
+    // atom order; dup marks collinear duplicates), the compact rows
+    // Cc[u][j] = C(perm[c Q + j], perm[u]) D_{perm[c Q + j]} (Q = K/4, c = u / Q), Dkp[u] = D_{perm[u]}
+    const uint8_t *dup;
+    float *Dk;
+    float *invC;
+    float *Cc;
+    float *Dkp;
+    // projections: R0[b][c Q + t (MN/4) + i (N/2) + j] = R_k of atom (t, 2i + a, 2j + b),
+    // unscaled; with copy_support the support samples go to the block's out
+    const BlockDesc *blocks;
+    int n;
+    float *R0;
+    int copy_support;
+};
+bool sym_fold_supported(int M, int N);
+cudaError_t launch_sym_rows(const SymSepArgs &a, cudaStream_t st);
+// variant < sym_r0_variants(M, N): identical results (0 generic, 1 the 32 x 32 kernel)
+cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant = 0);
+int sym_r0_variants(int M, int N);
 // Iterations, model and replacement for complex-valued atoms (k_complex.cu):
 // R0 [n][2][Kp], C [Kp][2][Kp] (row u = C(., u)), invC [Kp], PhiB [Kp][2][nB];
 // sel_coef receives (Re, Im) pairs.

@@ -133,8 +133,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     std::string why;
     if (pl->sep_full) {
         // the parity-class kernel applies D_k when it loads R^(0)
-        const SepArgs sa = pattern_sep_args(pl, 0, d_desc, n, d_r0, !pl->sym);
-        e = run_sep(ctx, pl, sa, st);
+        e = launch_pattern_projections(ctx, pl, d_desc, n, d_r0, !pl->sym, st);
     } else if (fp64) {
         e = launch_pack_x(d_desc, n, pl->d_a_idx.as<int>(), pl->d_sqrtw.as<double>(), pl->nA,
                           pl->ka_pad, 0, pl->MN, nullptr, static_cast<double *>(d_x), st);

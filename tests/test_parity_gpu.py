@@ -252,6 +252,7 @@ def test_symmetric_and_shifted_patterns(ctx, shift):
     o = OracleSetup("dct_wht", L, L, 0.8, sup, tables=False)
     ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, s, 0.5, I, o.dup, margins=True)
     plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec="bf16x6", support=sup)
+    assert plan.info().get("iterations") == ("general" if shift else "parity-classes")
     out, u, c = gpu_run(plan, s)
     for b in range(n):
         t = first_near_tie(rm[b], 1e-4)
@@ -259,6 +260,46 @@ def test_symmetric_and_shifted_patterns(ctx, shift):
         assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= 1e-3
     loss = np.broadcast_to(sup == 0, out.shape)
     assert abs(psnr(out, s, loss) - psnr(ro, s, loss)) <= 0.05
+    plan.close()
+
+
+@pytest.mark.parametrize("M,N,basis", [(16, 32, "dct_wht"), (32, 16, "dct_wht"), (32, 32, "dct"),
+                                       (16, 16, "dct_wht"), (32, 32, "wht")])
+def test_parity_class_plans(ctx, M, N, basis):
+    """Patterns symmetric in both directions (a box and four mirrored holes)
+    take the parity-class form: folded quarter-size transforms for R0 and the
+    compact table, one class updated per iteration.  Checked against the
+    oracle, and the allocation-free entry point against the batched one."""
+    K = {"dct_wht": 2 * M * N, "dct": M * N, "wht": M * N}[basis]
+    n, I = 40, 70
+    sup = np.ones((M, N), dtype=np.uint8)
+    sup[M // 4:3 * M // 4, N // 4:3 * N // 4] = 0
+    for (r, c) in ((1, 2), (2, N - 4)):
+        for rr, cc in ((r, c), (M - 2 - r, c), (r, N - 2 - c), (M - 2 - r, N - 2 - c)):
+            sup[rr:rr + 2, cc:cc + 2] = 0
+    assert (sup == sup[::-1]).all() and (sup == sup[:, ::-1]).all()
+    s = np.stack([np.ascontiguousarray(W.patch(32, 1300 + i)[:M, :N]) for i in range(n)])
+    o = OracleSetup(basis, M, N, 0.8, sup, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, s, 0.5, I, o.dup, margins=True)
+    plan = ctx.plan(M, N, basis, K, 0.8, 0.5, I, prec="bf16x6", support=sup)
+    assert plan.info().get("iterations") == "parity-classes"
+    out, u, c = gpu_run(plan, s)
+    for b in range(n):
+        t = first_near_tie(rm[b], 1e-4)
+        np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+        assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= 1e-3
+        np.testing.assert_array_equal(out[b][sup > 0], s[b][sup > 0])
+    loss = np.broadcast_to(sup == 0, out.shape)
+    assert abs(psnr(out, s, loss) - psnr(ro, s, loss)) <= 0.05
+    st_ = torch.from_numpy(s).cuda()
+    o2 = torch.empty_like(st_)
+    u2 = torch.full((n, I), -7, dtype=torch.int32, device="cuda")
+    c2 = torch.full((n, I), float("nan"), dtype=torch.float64, device="cuda")
+    plan.extrapolate_noalloc(st_, o2, u2, c2)
+    ctx.sync()
+    np.testing.assert_array_equal(o2.cpu().numpy(), out)
+    np.testing.assert_array_equal(u2.cpu().numpy(), u)
+    np.testing.assert_array_equal(c2.cpu().numpy(), c)
     plan.close()
 
 

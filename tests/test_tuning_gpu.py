@@ -62,6 +62,7 @@ CASES = [
     # (name, M, basis, K, I, n, prec)
     ("dctwht32", 32, "dct_wht", 2048, 60, 200, "bf16x6"),   # transform schedule, iterate Kp 2048
     ("dctwht16", 16, "dct_wht", 512, 60, 300, "bf16x6"),    # transform schedule 16 x 16
+    ("dct32", 32, "dct", 1024, 60, 200, "bf16x6"),         # parity classes at Kp 1024
     ("gauss32", 32, "numeric", 4096, 40, 300, "bf16x6"),    # GEMM tile, iterate Kp 4096
     ("dctwht64", 64, "dct_wht", 8192, 20, 40, "bf16x6"),    # iterate Kp 8192
 ]
@@ -74,7 +75,7 @@ def test_forced_variants_are_bitwise_identical(case):
     dic = W.gaussian_dictionary(K, L, L, 91) if basis == "numeric" else None
     res = []
     for v in (0, 1):
-        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},iterate:={v}")
+        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},iterate:={v},sym:={v},symr0:={v}")
         try:
             plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec, dictionary=dic)
             res.append(_run(ctx, plan, samples))
