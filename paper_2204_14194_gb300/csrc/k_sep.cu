@@ -562,7 +562,9 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
                 Etab[lane] = make_int4(t * cstride + (ku / N) * M, t * cstride + M * M + (ku % N) * N,
                                        __float_as_int(cf), 0);
                 __syncwarp();
-                const int cnt = min(32, I - nu0);
+                // padded entries (coefficient 0) add exact zeros: whole groups of 4
+                const int cnt = (min(32, I - nu0) + 3) & ~3;
+#pragma unroll 4
                 for (int k = 0; k < cnt; ++k) {
                     const int4 e = Etab[k];
                     const float c = __int_as_float(e.z);

@@ -382,7 +382,7 @@ __device__ __forceinline__ void stage_consts(const float *src, float *dst, int n
 // 1/C_kk.  Then the compact rows: item u (class order) is atom perm[u];
 // Cc[u][j] = C(perm[c Q + j], perm[u]) D_{perm[c Q + j]}, Dkp[u] = D_{perm[u]}.
 template <int QM, int QN>
-__global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
+__global__ void __launch_bounds__(512) sym_rows_kernel(const SymSepArgs a)
 {
     using F = Fold<QM, QN>;
     constexpr int QMN = F::QMN, RI = F::RI, RO = F::RO;
@@ -392,11 +392,17 @@ __global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
     const int ncst = a.ntr * F::cst;
     float *cst = fsm;                          // constants, then rho
     const float *rho = cst + ncst;
-    float *Dsh = cst + ncst + MN;              // [K] C_kk, then D_k
+    float *wq = cst + ncst + MN;               // [QM][QN] w on the first quadrant
+    float *Dsh = wq + QMN;                     // [K] C_kk, then D_k
     float *V = Dsh + a.K;                      // [ntr][M][QN] stage 1 of the diagonal
     float *X = V + a.ntr * M * QN + (threadIdx.x >> 5) * 2 * QMN;
     float *UT = X + QMN;
     stage_consts(a.img, cst, ncst + MN);
+    __syncthreads();
+    for (int o = threadIdx.x; o < QMN; o += blockDim.x) {
+        const int m = o / QN, n = o % QN;
+        wq[o] = a.pattern[m * N + n] ? rho[m * N + n] : 0.0f;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
     const int Q = a.K / 4;
@@ -405,10 +411,10 @@ __global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
         const int t = e / (M * QN), p = (e / QN) % M, n = e % QN;
         const float *At = cst + t * F::cst + (p & 1) * QM + (p >> 1);
         float v = 0.0f;
+#pragma unroll 4
         for (int m = 0; m < QM; ++m) {
             const float tp = At[m * 2 * QM];
-            const float wv = a.pattern[m * N + n] ? rho[m * N + n] : 0.0f;
-            v = fmaf(tp * tp, wv, v);
+            v = fmaf(tp * tp, wq[m * QN + n], v);
         }
         V[e] = v;
     }
@@ -419,6 +425,7 @@ __global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
         const float *Bt = cst + t * F::cst + 2 * QM * QM + (q & 1) * QN + (q >> 1);
         const float *Vp = V + (t * M + p) * QN;
         float d = 0.0f;
+#pragma unroll 4
         for (int n = 0; n < QN; ++n) {
             const float tq = Bt[n * 2 * QN];
             d = fmaf(Vp[n], tq * tq, d);
@@ -455,8 +462,7 @@ __global__ void __launch_bounds__(256) sym_rows_kernel(const SymSepArgs a)
         for (int r = 0; r < RO; ++r) {
             const int o = lane + 32 * r, m = o / QN, n = o % QN;
             const float ex = Ct[m * 2 * QM + ca * QM + (pu >> 1)] * Ct[2 * QM * QM + n * 2 * QN + cb * QN + (qu >> 1)];
-            const float v = a.pattern[m * N + n] ? rho[m * N + n] : 0.0f;
-            X[o] = v * ex;
+            X[o] = wq[o] * ex;
         }
         __syncwarp();
         float *row = a.Cc + static_cast<size_t>(u) * Q;
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(256) sym_r0_kernel(const SymSepArgs a)
 // same bits.
 constexpr int kR0Plane = 272;   // X_ab plane pitch: 256 + 16 (lanes >= 16 store to the other 16 banks)
 constexpr int kR0UT = 20;       // pitch of a row n of the transposed stage-1 result
-__global__ void __launch_bounds__(256, 3) sym_r0_32_kernel(const SymSepArgs a)
+__global__ void __launch_bounds__(288, 3) sym_r0_32_kernel(const SymSepArgs a)
 {
     constexpr int M = 32, N = 32, MN = 1024, QMN = 256, CST = 1024;   // floats of one transform's constants
     extern __shared__ __align__(16) float fsm[];
@@ -673,9 +679,9 @@ template <int QM, int QN>
 static cudaError_t launch_fold(const SymSepArgs &a, bool rows, cudaStream_t st)
 {
     using F = Fold<QM, QN>;
-    constexpr int wpc = 8;
+    const int wpc = rows ? 16 : 8;
     const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * F::cst + 4 * QM * QN +
-                                         (rows ? static_cast<size_t>(a.K) + a.ntr * 2 * QM * QN : 0) +
+                                         (rows ? F::QMN + static_cast<size_t>(a.K) + a.ntr * 2 * QM * QN : 0) +
                                          static_cast<size_t>(wpc) * (rows ? 2 : 5) * F::QMN);
     const int items = rows ? a.K : a.n;
     if (items <= 0) return cudaSuccess;
@@ -722,7 +728,7 @@ cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant)
     if (variant == 1 && a.M == 32 && a.N == 32) {
         if (a.K != a.ntr * 1024 || !a.img) return cudaErrorInvalidValue;
         if (a.n <= 0) return cudaSuccess;
-        constexpr int wpc = 8;
+        constexpr int wpc = 9;   // 3 CTAs of 9 warps per SM: 4104 blocks in one wave
         const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 1024 + 1024 +
                                              wpc * static_cast<size_t>(4 * kR0Plane + 2 * 16 * kR0UT));
         cudaError_t e = cudaFuncSetAttribute(sym_r0_32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

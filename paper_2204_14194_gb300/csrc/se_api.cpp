@@ -312,6 +312,7 @@ se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
     }
     fimg.insert(fimg.end(), img.end() - MN, img.end());
     SE_TRY(upload(ctx, pl->d_sym_img, fimg));
+
     SE_TRY(upload(ctx, pl->d_perm, perm));
     SE_TRY(dev_alloc(ctx, pl->d_Cc, sizeof(float) * static_cast<size_t>(K) * (K / 4)));
     SE_TRY(dev_alloc(ctx, pl->d_Dkp, sizeof(float) * static_cast<size_t>(K)));

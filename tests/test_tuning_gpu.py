@@ -86,6 +86,26 @@ def test_forced_variants_are_bitwise_identical(case):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("basis,K", [("dct_wht", 2048), ("dct", 1024), ("wht", 1024)])
+def test_projection_variants_of_parity_plans_are_bitwise_identical(basis, K):
+    """The two R0 kernels of a 32 x 32 parity-class plan (generic fold, 32 x 32
+    tiles) give the same bits."""
+    samples = np.stack([W.patch(32, 7000 + i) for i in range(300)])
+    res = []
+    for v in (0, 1):
+        ctx = _ctx(force=f"symr0:={v}")
+        try:
+            plan = ctx.plan(32, 32, basis, K, 0.8, 0.5, 50, prec="bf16x6")
+            assert plan.info().get("iterations") == "parity-classes"
+            res.append(_run(ctx, plan, samples))
+            plan.close()
+        finally:
+            ctx.close()
+    for r in res[1:]:
+        for x, y in zip(res[0], r):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_autotuner_times_each_shape_once_and_persists(tmp_path):
     f = str(tmp_path / "tune.txt")
     # an asymmetric loss box: the general iteration kernel (whose launch shape
