@@ -32,6 +32,32 @@ using dev::max3_abs;
 
 constexpr int kBPC = 4;   // blocks (warps) per CTA
 
+// Selection key of eq. (18): the atom index above the sign bit of its R'
+// (the winner's |R'| is the warp maximum M, so index and sign give R'_u), and
+// the warp minimum of the keys is the smallest index attaining M.
+__device__ __forceinline__ unsigned sel_key(int k, float r)
+{
+    return (static_cast<unsigned>(k) << 1) | (__float_as_uint(r) >> 31);
+}
+
+// The selection log, lane nu mod 32 holding entry nu: written 32 entries at a
+// time (and at the last iteration) in original atom indices.
+__device__ __forceinline__ void log_entry(const IterArgs &a, int b, int nu, bool more, int lane, int u, float c,
+                                          int &lu, float &lc)
+{
+    if (lane == (nu & 31)) {
+        lu = u;
+        lc = c;
+    }
+    if ((nu & 31) == 31 || !more) {
+        const size_t o = static_cast<size_t>(b) * a.I_max + (nu & ~31) + lane;
+        if (lane <= (nu & 31)) {
+            a.log_u[o] = __ldg(a.perm + lu);
+            a.log_c[o] = lc;
+        }
+    }
+}
+
 template <int VPT>
 __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArgs a)
 {
@@ -79,12 +105,13 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
             }
         }
 
+        int lu = 0;
+        float lc = 0.0f;
         for (int nu = 0; nu < I; ++nu) {
             // eq. (18): the maximum over the class maxima, then the smallest index
             const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
             const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
-            int kc = INT_MAX;
-            float rc = 0.0f;
+            unsigned key = 0xffffffffu;
             if (mx == M) {
                 // the first class holding the maximum, then its first atom holding it
                 // (k grows with c, ch and e, so this is the lane's smallest index)
@@ -98,8 +125,7 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
                             const float2 q = R2[c][2 * ch + (e >> 1)];
                             const float r = (e & 1) ? q.y : q.x;
                             if (fabsf(r) == M) {
-                                kc = c * Q + ch * 128 + 4 * lane + e;
-                                rc = r;
+                                key = sel_key(c * Q + ch * 128 + 4 * lane + e, r);
                                 goto found;
                             }
                         }
@@ -107,9 +133,9 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
                 }
             found:;
             }
-            int u = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
-            const int owner = u == INT_MAX ? 0 : (u % Q) / 4 % 32;
-            float ru = __shfl_sync(0xffffffffu, rc, owner);
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            int u = static_cast<int>(kmin >> 1);
+            float ru = (kmin & 1u) ? -M : M;   // the winner's R' is +-M: its sign rides in the key
             if (u < 0 || u >= a.K) {
                 if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
                 u = 0;
@@ -121,10 +147,7 @@ __global__ void __launch_bounds__(32 * kBPC, 4) iterate_sym_kernel(const IterArg
                 bulk_row(myT, a.Cc + static_cast<size_t>(u) * Q, static_cast<uint32_t>(Q * sizeof(float)), myBar);
             // eq. (19): c = gamma R'_u D_u
             const float c = gamma * ru * __ldg(a.Dkp + u);
-            if (lane == 0) {   // the selection log in original atom indices (model kernel, user logs)
-                a.log_u[static_cast<size_t>(b) * a.I_max + nu] = __ldg(a.perm + u);
-                a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
-            }
+            log_entry(a, b, nu, more, lane, u, c, lu, lc);
             if (!more) break;
             if (!bar_wait(myBar, phase)) {
                 if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_WAIT_TIMEOUT);
@@ -198,11 +221,12 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
             m[c] = mm;
         }
 
+        int lu = 0;
+        float lc = 0.0f;
         for (int nu = 0; nu < I; ++nu) {
             const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
             const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
-            int kc = INT_MAX;
-            float rc = 0.0f;
+            unsigned key = 0xffffffffu;
             if (mx == M) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
@@ -214,8 +238,7 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             if (fabsf(r4[e]) == M) {
-                                kc = c * Q + ch * 128 + 4 * lane + e;
-                                rc = r4[e];
+                                key = sel_key(c * Q + ch * 128 + 4 * lane + e, r4[e]);
                                 goto found;
                             }
                         }
@@ -223,9 +246,9 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
                 }
             found:;
             }
-            int u = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
-            const int owner = u == INT_MAX ? 0 : (u % Q) / 4 % 32;
-            float ru = __shfl_sync(0xffffffffu, rc, owner);
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            int u = static_cast<int>(kmin >> 1);
+            float ru = (kmin & 1u) ? -M : M;
             if (u < 0 || u >= a.K) {
                 if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
                 u = 0;
@@ -240,10 +263,7 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
                 for (int ch = 0; ch < NCC; ++ch) t[ch] = __ldg(row + ch * 32);
             }
             const float c = gamma * ru * __ldg(a.Dkp + u);
-            if (lane == 0) {
-                a.log_u[static_cast<size_t>(b) * a.I_max + nu] = __ldg(a.perm + u);
-                a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
-            }
+            log_entry(a, b, nu, more, lane, u, c, lu, lc);
             if (!more) break;
             const float2 nc = make_float2(-c, -c);
             float mc[2] = {0.0f, 0.0f};
