@@ -218,8 +218,9 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
     constexpr int NCH = VPT / 4;
     const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
     const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
-    int kc = INT_MAX;
-    float rc = 0.0f;
+    // key: the index above the sign bit of R' (the winner's |R'| is M, so the
+    // warp minimum of the keys gives both the smallest index and R'_u)
+    unsigned key = 0xffffffffu;
     if (mx == M) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -229,9 +230,8 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
                     const int k = ch * NT * 4 + tid * 4 + j;
                     const float2 q = R2[ch * 2 + (j >> 1)];
                     const float r = (j & 1) ? q.y : q.x;
-                    if (k < kc && fabsf(r) == M) {
-                        kc = k;
-                        rc = r;
+                    if (static_cast<unsigned>(k) < (key >> 1) && fabsf(r) == M) {
+                        key = (static_cast<unsigned>(k) << 1) | (__float_as_uint(r) >> 31);
 #if SE_ITER_SCAN_BREAK
                         break;   // k grows with ch: the first match is this chain's smallest index
 #endif
@@ -240,10 +240,11 @@ __device__ __forceinline__ void select_f32(const float2 (&R2)[VPT / 2], const fl
             }
         }
     }
-    const int kw = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(kc)));
-    const int owner = kw == INT_MAX ? 0 : (kw >> 2) % NT % 32;
-    const float rw = __shfl_sync(0xffffffffu, rc, owner);
+    const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+    const int kw = static_cast<int>(kmin >> 1);   // INT_MAX when no lane holds M
+    const float rw = (kmin & 1u) ? -M : M;
     if constexpr (CERT) {
+        const int owner = kw == INT_MAX ? 0 : (kw >> 2) % NT % 32;
         static_assert(W == 1, "the runner-up is formed within one warp");
         // runner-up: the largest |R'| over every atom but the winner (the other
         // chains of each lane by their maxima, the winner's own chain in full)
@@ -366,6 +367,8 @@ iterate_f32_kernel(const IterArgs a)
         }
 
         int first_close = -1;
+        int lu = 0;
+        float lc = 0.0f;
         for (int nu = 0; nu < I; ++nu) {
             int u;
             float ru;
@@ -392,9 +395,16 @@ iterate_f32_kernel(const IterArgs a)
             if (SE_ITER_ASYNC == 2 && more && tid == 0)
                 bulk_row(myT, trow, static_cast<uint32_t>(Kp * sizeof(float)), myBar);
             const float c = gamma * ru * __ldg(Dk + u);
-            if (tid == 0) {   // the selection log, read by the model kernel (eq. 9)
-                a.log_u[static_cast<size_t>(b) * a.I_max + nu] = u;
-                a.log_c[static_cast<size_t>(b) * a.I_max + nu] = c;
+            // the selection log, read by the model kernel (eq. 9): lane nu mod 32 of
+            // warp 0 holds entry nu, written 32 entries at a time
+            if (tid == (nu & 31)) {
+                lu = u;
+                lc = c;
+            }
+            if (((nu & 31) == 31 || !more) && tid <= (nu & 31)) {
+                const size_t o = static_cast<size_t>(b) * a.I_max + (nu & ~31) + tid;
+                a.log_u[o] = lu;
+                a.log_c[o] = lc;
             }
             if (!more) break;
 

@@ -504,7 +504,9 @@ __global__ void __launch_bounds__(32 * WPC) sep_warp_kernel(const SepArgs a)
     }
 }
 
-// Model (eq. 9) for separable dictionaries, one warp per block.  Shared
+// Model (eq. 9) for separable dictionaries, one warp per block (the launcher
+// requires a non-empty box, so the first pass over it always runs and also
+// writes the caller's copies of the log).  Shared
 // memory holds the 1-D rows of every transform, T_t[p][m] then T'_t[q][n];
 // a log entry u = koff[t] + p N + q contributes c t_p[m] t'_q[n].  The
 // entries of the log pass through a per-warp table (row offsets and c, one
@@ -551,10 +553,24 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
             float acc[RP];
 #pragma unroll
             for (int r = 0; r < RP; ++r) acc[r] = 0.0f;
+            // the log in rounds of 32 entries, the next round's loads in flight
+            // while this one is evaluated; the first pass over the box also
+            // writes the caller's copies of the log
+            int un = lane < I ? lu[lane] : -1;
+            float cn = lane < I ? lc[lane] : 0.0f;
             for (int nu0 = 0; nu0 < I; nu0 += 32) {
-                int u = nu0 + lane < I ? lu[nu0 + lane] : -1;
+                int u = un;
+                const float cl = cn;
+                if (nu0 + 32 + lane < I) {
+                    un = lu[nu0 + 32 + lane];
+                    cn = lc[nu0 + 32 + lane];
+                }
+                if (o0 == 0 && nu0 + lane < I) {
+                    if (bd.sel_idx) bd.sel_idx[nu0 + lane] = u;
+                    if (bd.sel_coef) bd.sel_coef[nu0 + lane] = static_cast<double>(cl);
+                }
                 float cf = 0.0f;                                   // padded entries add 0
-                if (u >= 0 && u < s.koff[s.ntr - 1] + MN) cf = lc[nu0 + lane];
+                if (nu0 + lane < I && u >= 0 && u < s.koff[s.ntr - 1] + MN) cf = cl;
                 else u = 0;
                 const int t = (s.ntr > 1 && u >= s.koff[1]) ? 1 : 0;
                 const int ku = u - s.koff[t];
@@ -588,10 +604,6 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
                 if (!a.pat_support[p]) bd.out[p] = static_cast<double>(acc[r]);
             }
         }
-        if (bd.sel_idx)
-            for (int nu = lane; nu < I; nu += 32) bd.sel_idx[nu] = lu[nu];
-        if (bd.sel_coef)
-            for (int nu = lane; nu < I; nu += 32) bd.sel_coef[nu] = static_cast<double>(lc[nu]);
     }
 }
 

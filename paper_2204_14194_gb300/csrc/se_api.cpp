@@ -550,6 +550,33 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
 
     // the workspace of the previous call must be free before it is reused
     SE_CUDA(cudaStreamWaitEvent(st, ws.ev_ws, 0));
+
+    // The fp32 transform form computes R^(0) unscaled (the iteration kernel
+    // applies D_k when it loads them), so a table build does not have to come
+    // first: it runs on the context's second stream, from here on (it reads no
+    // descriptor), while the descriptors are staged and R^(0) is computed, and
+    // the iterations wait for it.
+    const bool overlap = pl->sep_full && !fp64;
+    {
+        std::lock_guard<std::mutex> lk(pl->tmu);
+        if (!pl->tables_valid) {
+            cudaStream_t ts = st;
+            if (overlap) {   // the second stream starts after the work already queued on st
+                std::lock_guard<std::mutex> al(ctx->amu);
+                SE_CUDA(cudaEventRecord(ctx->ev_fork, st));
+                SE_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+                ts = ctx->aux;
+            }
+            const int tok = stage_begin(ctx, 1, ts);
+            cudaEvent_t pa = probe_begin(ctx, ts);
+            SE_TRY(build_tables(ctx, pl, ts));
+            probe_end(ctx, pl, 0, 0, pa, ts);
+            stage_end(ctx, tok, ts);
+        } else if (!overlap) {
+            SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
+        }
+    }
+
     const size_t need_desc = sizeof(BlockDesc) * n, need_x = pl->sep_full ? 16 : xrow * n,
                  need_r0 = (pl->cplx ? 2 : 1) * tsz * Kp * static_cast<size_t>(n);
     if (ws.desc.bytes < need_desc || ws.x.bytes < need_x || ws.r0.bytes < need_r0)
@@ -578,31 +605,6 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     SE_CUDA(cudaMemcpyAsync(ws.desc.ptr, ws.h_desc, sizeof(BlockDesc) * n,
                             cudaMemcpyHostToDevice, st));
     SE_CUDA(cudaEventRecord(ws.ev_staging, st));
-
-    // The fp32 transform form computes R^(0) unscaled (the iteration kernel
-    // applies D_k when it loads them), so a table build does not have to come
-    // first: it runs on the context's second stream while R^(0) is computed, and
-    // the iterations wait for it.
-    const bool overlap = pl->sep_full && !fp64;
-    {
-        std::lock_guard<std::mutex> lk(pl->tmu);
-        if (!pl->tables_valid) {
-            cudaStream_t ts = st;
-            if (overlap) {   // the second stream starts after the work already queued on st
-                std::lock_guard<std::mutex> al(ctx->amu);
-                SE_CUDA(cudaEventRecord(ctx->ev_fork, st));
-                SE_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-                ts = ctx->aux;
-            }
-            const int tok = stage_begin(ctx, 1, ts);
-            cudaEvent_t pa = probe_begin(ctx, ts);
-            SE_TRY(build_tables(ctx, pl, ts));
-            probe_end(ctx, pl, 0, 0, pa, ts);
-            stage_end(ctx, tok, ts);
-        } else if (!overlap) {
-            SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));
-        }
-    }
 
     if (pl->cplx) return run_complex(ctx, pl, ws, n, I_max, st);
     const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
