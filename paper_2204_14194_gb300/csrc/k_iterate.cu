@@ -525,17 +525,9 @@ cudaError_t launch_f32(const IterArgs &a, cudaStream_t st, int *launches)
     if (!a.log_u || !a.log_c) return cudaErrorInvalidValue;   // the model kernel reads the log
     const size_t smem = 16 * BPC + (SE_ITER_ASYNC ? sizeof(float) * BPC * a.Kp : 0) + sizeof(Cand<float>) * 2 * W + 16;
     auto kern = iterate_f32_kernel<W, VPT, BPC, CERT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(kern), threads, smem, (a.n + BPC - 1) / BPC, &grid);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int need = (a.n + BPC - 1) / BPC;
-    const int grid = need < sms * per_sm ? need : sms * per_sm;
     kern<<<grid, threads, smem, st>>>(a);
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -549,17 +541,9 @@ cudaError_t launch_cfg(const IterArgs &a, cudaStream_t st, int *launches)
     const size_t smem = sizeof(T) * 2 * a.Kp + sizeof(Cand<T>) * 2 * W +
                         (sizeof(T) + sizeof(int)) * BPC * a.I_max + 16;
     auto kern = iterate_full_kernel<T, W, VPT, BPC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(kern), threads, smem, (a.n + BPC - 1) / BPC, &grid);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int need = (a.n + BPC - 1) / BPC;
-    const int grid = need < sms * per_sm ? need : sms * per_sm;
     kern<<<grid, threads, smem, st>>>(a);
     if (launches) ++*launches;
     return cudaGetLastError();

@@ -619,23 +619,10 @@ cudaError_t launch_sep_group(const SepArgs &a, cudaStream_t st, bool *done)
     while (groups > 0 && cst + 8 * MN * groups > 227 * 1024) groups /= 2;
     if (groups == 0) return cudaSuccess;
     const size_t smem = cst + 8 * MN * groups;
-    static bool attr = false;
-    static int sms = 0;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sep_group_kernel<TS, MC, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        attr = true;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_group_kernel<TS, MC, NC>,
-                                                                  kSepGroup * groups, smem);
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_group_kernel<TS, MC, NC>), kSepGroup * groups, smem,
+                                (a.n + groups - 1) / groups, &grid);
     if (e != cudaSuccess) return e;
-    const int want = (a.n + groups - 1) / groups;
-    const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
     sep_group_kernel<TS, MC, NC><<<grid, kSepGroup * groups, smem, st>>>(a, groups);
     *done = true;
     return cudaGetLastError();
@@ -646,23 +633,10 @@ cudaError_t launch_sep_warp(const SepArgs &a, cudaStream_t st)
 {
     constexpr int wpc = 10;   // 2 CTAs of 10 warps per SM at 32 x 32 (shared memory bound)
     const size_t smem = 4 * (a.ntr * static_cast<size_t>(M * M + N * N) + M * N + 2 * M * N * wpc);
-    static bool attr = false;
-    static int sms = 0;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sep_warp_kernel<M, N, TP, TQ, wpc>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        attr = true;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_warp_kernel<M, N, TP, TQ, wpc>,
-                                                                  32 * wpc, smem);
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_warp_kernel<M, N, TP, TQ, wpc>), 32 * wpc, smem,
+                                (a.n + wpc - 1) / wpc, &grid);
     if (e != cudaSuccess) return e;
-    const int want = (a.n + wpc - 1) / wpc;
-    const int grid = std::max(1, std::min(want, sms * std::max(per_sm, 1)));
     sep_warp_kernel<M, N, TP, TQ, wpc><<<grid, 32 * wpc, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -697,13 +671,9 @@ cudaError_t launch_sep(const SepArgs &a, cudaStream_t st, int variant)
     }
     const size_t smem = sizeof(T) * (2 * static_cast<size_t>(a.M) * a.N + a.M * a.M + a.N * a.N);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sep_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    int unused = 0;   // one CTA per item; the call only raises the shared memory limit (per device)
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_kernel<T>), 256, smem, 1, &unused);
+    if (e != cudaSuccess) return e;
     sep_kernel<T><<<a.n, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -712,21 +682,10 @@ template <bool COL, int RP>
 cudaError_t launch_sep_model_t(const IterArgs &a, const SepArgs &s, int m0, int Mb, int n0, int Nb, size_t smem,
                                cudaStream_t st)
 {
-    static bool attr = false;
-    static int sms = 0;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sep_model_kernel<COL, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        attr = true;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sep_model_kernel<COL, RP>, 256, smem);
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_model_kernel<COL, RP>), 256, smem, (a.n + 7) / 8,
+                                &grid);
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min((a.n + 7) / 8, sms * std::max(per_sm, 1)));
     sep_model_kernel<COL, RP><<<grid, 256, smem, st>>>(a, s, m0, Mb, n0, Nb);
     return cudaGetLastError();
 }

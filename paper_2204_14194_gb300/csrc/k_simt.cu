@@ -364,4 +364,30 @@ cudaError_t launch_probe_samples(double *s, long long total, uint32_t seed, cuda
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void fill_desc_kernel(BlockDesc *d, int n, StridedSpec s, int MN)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    BlockDesc x;
+    x.samples = s.samples + static_cast<size_t>(MN) * b;
+    x.support = nullptr;
+    x.out = s.out + static_cast<size_t>(MN) * b;
+    x.sel_idx = s.sel_idx ? s.sel_idx + static_cast<size_t>(s.I) * b : nullptr;
+    x.sel_coef = s.sel_coef ? s.sel_coef + static_cast<size_t>(s.I) * s.coef * b : nullptr;
+    x.iterations = s.I;
+    x.pad_ = 0;
+    d[b] = x;
+}
+
+}  // namespace
+
+cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_desc_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, n, s, MN);
+    return cudaGetLastError();
+}
+
 }  // namespace se

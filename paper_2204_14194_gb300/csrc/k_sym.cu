@@ -693,6 +693,176 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32_kernel(const SymSepArgs a)
     }
 }
 
+// R^(0) of 32 x 32 parity-class blocks on the tensor cores: the sixteen
+// quarter products of a block (Y = A^T X_ab B per class and transform) as
+// mma.sync m16n8k8 products in split TF32: each fp32 operand x is
+// x_b = tf32(x) plus x_s = tf32(x - x_b), and a product accumulates
+// x_s y_b + x_b y_s + x_b y_b in fp32 (the dropped x_s y_s and the two
+// roundings leave about 2^-21 relative), accurate like the fp32 transforms.
+// The fold is the one of sym_r0_kernel (lane = column, shuffle across the
+// centre); the constant operands come as per-lane fragments from the plan's
+// table (conflict-free 16- and 8-byte loads).  Fragments of m16n8k8: g = lane / 4,
+// q = lane mod 4; A(16 x 8) {(g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4)},
+// B(8 x 8) {(q, g), (q + 4, g)}, C(16 x 8) {(g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)}.
+constexpr int kTcPlane = 272;   // X_ab plane pitch (rows of 16; lanes >= 16 store to the other banks)
+constexpr int kTcU = 20;        // pitch of the stage-1 result rows
+
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &b, uint32_t &sm)
+{
+    b = tf32_rna(x);
+    sm = tf32_rna(x - __uint_as_float(b));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B in split TF32 (three products, small ones first)
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ab)[4], const uint32_t (&as)[4], uint32_t bb0,
+                                     uint32_t bb1, uint32_t bs0, uint32_t bs1)
+{
+    mma_tf32(d, as, bb0, bb1);
+    mma_tf32(d, ab, bs0, bs1);
+    mma_tf32(d, ab, bb0, bb1);
+}
+
+__global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
+{
+    constexpr int M = 32, N = 32, MN = 1024, QMN = 256;
+    extern __shared__ __align__(16) float fsm[];
+    const int ntr = a.ntr;
+    // constants: AF[t][ca][ks][lane] float4, BF[t][cb][ks][nt][lane] float2, rho[MN]
+    const int nconst = ntr * 1024 + MN;
+    float *cst = fsm;
+    const float4 *AF = reinterpret_cast<const float4 *>(cst);
+    const float2 *BF = reinterpret_cast<const float2 *>(cst + ntr * 512);
+    const float *rho = cst + ntr * 1024;
+    float *X = cst + nconst + (threadIdx.x >> 5) * (4 * kTcPlane + 16 * kTcU);
+    float *U = X + 4 * kTcPlane;
+    for (int e = threadIdx.x; e < nconst / 4; e += blockDim.x)
+        reinterpret_cast<float4 *>(cst)[e] = __ldg(reinterpret_cast<const float4 *>(a.img) + e);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int Q = a.K / 4;
+    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc) {
+        const BlockDesc bd = a.blocks[b];
+        const uint8_t *mask = (bd.support ? bd.support : a.pattern) + lane;
+        const double *smp = bd.samples + lane;
+        double *dst = a.copy_support ? bd.out + lane : nullptr;
+        __syncwarp();   // the previous block's reads of X and U are done
+#pragma unroll 1
+        for (int r0 = 0; r0 < M / 2; r0 += 8) {
+            double s0[8], s1[8];
+            bool o0[8], o1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {   // loss samples are read too and dropped by the select below
+                const int r = r0 + k;
+                o0[k] = mask[r * N] != 0;
+                o1[k] = mask[(M - 1 - r) * N] != 0;
+                s0[k] = smp[r * N];
+                s1[k] = smp[(M - 1 - r) * N];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                const float x0 = o0[k] ? rho[r * N + lane] * static_cast<float>(s0[k]) : 0.0f;
+                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * static_cast<float>(s1[k]) : 0.0f;
+                if (dst) {
+                    if (o0[k]) dst[r * N] = s0[k];
+                    if (o1[k]) dst[(M - 1 - r) * N] = s1[k];
+                }
+                const float sm = x0 + x1, dm = x0 - x1;
+                const float smo = __shfl_xor_sync(0xffffffffu, sm, 31), dmo = __shfl_xor_sync(0xffffffffu, dm, 31);
+                if (lane < 16) {
+                    X[r * 16 + lane] = sm + smo;                          // (0, 0)
+                    X[2 * kTcPlane + r * 16 + lane] = dm + dmo;           // (1, 0)
+                } else {
+                    X[kTcPlane + r * 16 + 31 - lane] = smo - sm;          // (0, 1)
+                    X[3 * kTcPlane + r * 16 + 31 - lane] = dmo - dm;      // (1, 1)
+                }
+            }
+        }
+        __syncwarp();
+        float *R = a.R0 + static_cast<size_t>(b) * a.K;
+#pragma unroll 1
+        for (int t = 0; t < ntr; ++t) {
+#pragma unroll 1
+            for (int ca = 0; ca < 2; ++ca) {
+                // A^T fragments of this (t, ca) for both k-steps, split
+                uint32_t Ab[2][4], As[2][4];
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const float4 f = AF[((t * 2 + ca) * 2 + ks) * 32 + lane];
+                    split_tf32(f.x, Ab[ks][0], As[ks][0]);
+                    split_tf32(f.y, Ab[ks][1], As[ks][1]);
+                    split_tf32(f.z, Ab[ks][2], As[ks][2]);
+                    split_tf32(f.w, Ab[ks][3], As[ks][3]);
+                }
+#pragma unroll 1
+                for (int cb = 0; cb < 2; ++cb) {
+                    const float *Xp = X + (2 * ca + cb) * kTcPlane;
+                    // stage 1: U = A^T X_ab (16 x 16), two column tiles of 8
+                    float d[2][4];
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            uint32_t bb0, bs0, bb1, bs1;
+                            split_tf32(Xp[(8 * ks + q) * 16 + 8 * nt + g], bb0, bs0);
+                            split_tf32(Xp[(8 * ks + q + 4) * 16 + 8 * nt + g], bb1, bs1);
+                            mma3(d[nt], Ab[ks], As[ks], bb0, bb1, bs0, bs1);
+                        }
+                    }
+                    __syncwarp();   // the previous product is done reading U
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        *reinterpret_cast<float2 *>(U + g * kTcU + 8 * nt + 2 * q) = make_float2(d[nt][0], d[nt][1]);
+                        *reinterpret_cast<float2 *>(U + (g + 8) * kTcU + 8 * nt + 2 * q) = make_float2(d[nt][2], d[nt][3]);
+                    }
+                    __syncwarp();
+                    // stage 2: Y = U B (16 x 16)
+                    uint32_t Ub[2][4], Us[2][4];
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        split_tf32(U[g * kTcU + 8 * ks + q], Ub[ks][0], Us[ks][0]);
+                        split_tf32(U[(g + 8) * kTcU + 8 * ks + q], Ub[ks][1], Us[ks][1]);
+                        split_tf32(U[g * kTcU + 8 * ks + q + 4], Ub[ks][2], Us[ks][2]);
+                        split_tf32(U[(g + 8) * kTcU + 8 * ks + q + 4], Ub[ks][3], Us[ks][3]);
+                    }
+                    float *Rc = R + (2 * ca + cb) * Q + t * QMN;
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const float2 f = BF[(((t * 2 + cb) * 2 + ks) * 2 + nt) * 32 + lane];
+                            uint32_t bb0, bs0, bb1, bs1;
+                            split_tf32(f.x, bb0, bs0);
+                            split_tf32(f.y, bb1, bs1);
+                            mma3(y, Ub[ks], Us[ks], bb0, bb1, bs0, bs1);
+                        }
+                        *reinterpret_cast<float2 *>(Rc + g * 16 + 8 * nt + 2 * q) = make_float2(y[0], y[1]);
+                        *reinterpret_cast<float2 *>(Rc + (g + 8) * 16 + 8 * nt + 2 * q) = make_float2(y[2], y[3]);
+                    }
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 template <int QM, int QN>
@@ -706,16 +876,15 @@ static cudaError_t launch_fold(const SymSepArgs &a, bool rows, cudaStream_t st)
     const int items = rows ? a.K : a.n;
     if (items <= 0) return cudaSuccess;
     auto kern = rows ? sym_rows_kernel<QM, QN> : sym_r0_kernel<QM, QN>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, smem)) != cudaSuccess) return e;
     const int need = (items + wpc - 1) / wpc;
-    // the table kernel repeats the diagonal in every CTA: one CTA per SM
-    const int cap = rows ? sms : sms * (per_sm > 0 ? per_sm : 1);
-    kern<<<need < cap ? need : cap, 32 * wpc, smem, st>>>(a);
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(kern), 32 * wpc, smem, need, &grid);
+    if (e != cudaSuccess) return e;
+    if (rows) {   // the table kernel repeats the diagonal in every CTA: at most one CTA per SM
+        const int sms = sm_count();
+        grid = need < sms ? need : sms;
+    }
+    kern<<<grid, 32 * wpc, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -742,6 +911,23 @@ cudaError_t launch_sym_rows(const SymSepArgs &a, cudaStream_t st)
 
 int sym_r0_variants(int M, int N) { return M == 32 && N == 32 ? 2 : 1; }
 
+cudaError_t launch_sym_r0_tc(const SymSepArgs &a, cudaStream_t st)
+{
+    if (!a.blocks || !a.R0 || !a.tc_img || a.M != 32 || a.N != 32 || a.K != a.ntr * 1024) return cudaErrorInvalidValue;
+    if (a.n <= 0) return cudaSuccess;
+    constexpr int wpc = 9;   // 3 CTAs of 9 warps per SM: 4104 blocks in one wave
+    const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 1024 + 1024 +
+                                         wpc * static_cast<size_t>(4 * kTcPlane + 16 * kTcU));
+    SymSepArgs b = a;
+    b.img = a.tc_img;
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sym_r0_32tc_kernel), 32 * wpc, smem,
+                                (a.n + wpc - 1) / wpc, &grid);
+    if (e != cudaSuccess) return e;
+    sym_r0_32tc_kernel<<<grid, 32 * wpc, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant)
 {
     if (!a.blocks || !a.R0) return cudaErrorInvalidValue;
@@ -751,18 +937,11 @@ cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant)
         constexpr int wpc = 9;   // 3 CTAs of 9 warps per SM: 4104 blocks in one wave
         const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 1024 + 1024 +
                                              wpc * static_cast<size_t>(4 * kR0Plane + 2 * 16 * kR0UT));
-        cudaError_t e = cudaFuncSetAttribute(sym_r0_32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        int grid = 0;
+        cudaError_t e = launch_grid(reinterpret_cast<const void *>(sym_r0_32_kernel), 32 * wpc, smem,
+                                    (a.n + wpc - 1) / wpc, &grid);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sym_r0_32_kernel, 32 * wpc, smem)) !=
-            cudaSuccess)
-            return e;
-        const int need = (a.n + wpc - 1) / wpc;
-        const int cap = sms * (per_sm > 0 ? per_sm : 1);
-        sym_r0_32_kernel<<<need < cap ? need : cap, 32 * wpc, smem, st>>>(a);
+        sym_r0_32_kernel<<<grid, 32 * wpc, smem, st>>>(a);
         return cudaGetLastError();
     }
     return launch_fold_any(a, false, st);
@@ -776,15 +955,10 @@ static cudaError_t launch_sym_vpt(const IterArgs &a, cudaStream_t st, int *launc
         return cudaErrorInvalidValue;
     const size_t smem = 16 * kBPC + sizeof(float) * kBPC * Q + 16;
     auto kern = iterate_sym_kernel<VPT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(kern), 32 * kBPC, smem, (a.n + kBPC - 1) / kBPC, &grid);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kBPC, smem)) != cudaSuccess) return e;
-    const int need = (a.n + kBPC - 1) / kBPC;
-    const int cap = sms * (per_sm > 0 ? per_sm : 1);
-    kern<<<need < cap ? need : cap, 32 * kBPC, smem, st>>>(a);
+    kern<<<grid, 32 * kBPC, smem, st>>>(a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -797,17 +971,11 @@ static cudaError_t launch_sym_smem(const IterArgs &a, cudaStream_t st, int *laun
         return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * static_cast<size_t>(BPC) * a.Kp;
     auto kern = iterate_sym_smem_kernel<VPT, BPC, MINB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(kern), 32 * BPC, smem, (a.n + BPC - 1) / BPC, &grid,
+                                true);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * BPC, smem)) != cudaSuccess) return e;
-    const int need = (a.n + BPC - 1) / BPC;
-    const int cap = sms * (per_sm > 0 ? per_sm : 1);
-    kern<<<need < cap ? need : cap, 32 * BPC, smem, st>>>(a);
+    kern<<<grid, 32 * BPC, smem, st>>>(a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

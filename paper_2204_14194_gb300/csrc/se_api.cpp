@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -312,6 +313,39 @@ se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
     }
     fimg.insert(fimg.end(), img.end() - MN, img.end());
     SE_TRY(upload(ctx, pl->d_sym_img, fimg));
+    if (M == 32 && N == 32) {
+        // the same constants as per-lane m16n8k8 fragments for the tensor-core R^(0)
+        // kernel (g = lane / 4, q = lane mod 4); SE_R0_FFMA=1 keeps the fp32 kernels
+        std::vector<float> tc;
+        tc.reserve(static_cast<size_t>(ntr) * 1024 + MN);
+        for (int t = 0; t < ntr; ++t)
+            for (int a = 0; a < 2; ++a)
+                for (int ks = 0; ks < 2; ++ks)
+                    for (int l = 0; l < 32; ++l) {
+                        const int g = l >> 2, q = l & 3;
+                        auto At = [&](int i, int m) { return fimg[static_cast<size_t>(t) * 1024 + m * 32 + a * 16 + i]; };
+                        tc.push_back(At(g, 8 * ks + q));
+                        tc.push_back(At(g + 8, 8 * ks + q));
+                        tc.push_back(At(g, 8 * ks + q + 4));
+                        tc.push_back(At(g + 8, 8 * ks + q + 4));
+                    }
+        for (int t = 0; t < ntr; ++t)
+            for (int b = 0; b < 2; ++b)
+                for (int ks = 0; ks < 2; ++ks)
+                    for (int nt = 0; nt < 2; ++nt)
+                        for (int l = 0; l < 32; ++l) {
+                            const int g = l >> 2, q = l & 3;
+                            auto Bt = [&](int n, int j) {
+                                return fimg[static_cast<size_t>(t) * 1024 + 512 + n * 32 + b * 16 + j];
+                            };
+                            tc.push_back(Bt(8 * ks + q, 8 * nt + g));
+                            tc.push_back(Bt(8 * ks + q + 4, 8 * nt + g));
+                        }
+        tc.insert(tc.end(), img.end() - MN, img.end());
+        SE_TRY(upload(ctx, pl->d_sym_tc, tc));
+        const char *env = std::getenv("SE_R0_FFMA");
+        pl->sym_tc = !(env && env[0] == '1');
+    }
 
     SE_TRY(upload(ctx, pl->d_perm, perm));
     SE_TRY(dev_alloc(ctx, pl->d_Cc, sizeof(float) * static_cast<size_t>(K) * (K / 4)));
@@ -342,6 +376,10 @@ cudaError_t se::launch_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, const B
         s.n = n;
         s.R0 = static_cast<float *>(r0);
         s.copy_support = pl->nB > 0;
+        if (pl->sym_tc) {
+            s.tc_img = pl->d_sym_tc.as<float>();
+            return launch_sym_r0_tc(s, st);
+        }
         const std::string key = "symr0:" + std::to_string(pl->M) + "x" + std::to_string(pl->N) + ":t" +
                                 std::to_string(pl->sep_ntr);
         return tune_run(ctx, key, sym_r0_variants(pl->M, pl->N), st, [&](int v) { return launch_sym_r0(s, st, v); });
@@ -540,7 +578,7 @@ se_status dense_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws,
 // All blocks use the plan's pattern: Alg. 2 tables (cached), eq. (12) GEMM,
 // Alg. 3 iterations.
 se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
-                        int I_max, cudaStream_t st)
+                        int I_max, cudaStream_t st, cudaEvent_t inputs_ready, const StridedSpec *ss)
 {
     const int Kp = pl->Kp;
     const bool fp64 = pl->pc.fp64;
@@ -592,19 +630,25 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
     SE_TRY(dev_alloc(ctx, ws.r0, need_r0));
     SE_TRY(dev_alloc(ctx, ws.logs, need_logs));
 
-    // pinned staging of the descriptors: free once the previous copy landed
-    SE_CUDA(cudaEventSynchronize(ws.ev_staging));
-    if (ws.h_desc_cap < static_cast<size_t>(n)) {
-        if (ws.h_desc) cudaFreeHost(ws.h_desc);
-        ws.h_desc = nullptr;
-        ws.h_desc_cap = 0;
-        SE_CUDA(cudaMallocHost(&ws.h_desc, sizeof(BlockDesc) * n));
-        ws.h_desc_cap = n;
+    if (ss) {   // a contiguous batch: the descriptors are formed on the device
+        SE_CUDA(launch_fill_desc(ws.desc.as<BlockDesc>(), n, *ss, pl->MN, st));
+        ctx->launches += 1;
+    } else {
+        // pinned staging of the descriptors: free once the previous copy landed
+        SE_CUDA(cudaEventSynchronize(ws.ev_staging));
+        if (ws.h_desc_cap < static_cast<size_t>(n)) {
+            if (ws.h_desc) cudaFreeHost(ws.h_desc);
+            ws.h_desc = nullptr;
+            ws.h_desc_cap = 0;
+            SE_CUDA(cudaMallocHost(&ws.h_desc, sizeof(BlockDesc) * n));
+            ws.h_desc_cap = n;
+        }
+        std::memcpy(ws.h_desc, hdesc, sizeof(BlockDesc) * n);
+        SE_CUDA(cudaMemcpyAsync(ws.desc.ptr, ws.h_desc, sizeof(BlockDesc) * n,
+                                cudaMemcpyHostToDevice, st));
+        SE_CUDA(cudaEventRecord(ws.ev_staging, st));
     }
-    std::memcpy(ws.h_desc, hdesc, sizeof(BlockDesc) * n);
-    SE_CUDA(cudaMemcpyAsync(ws.desc.ptr, ws.h_desc, sizeof(BlockDesc) * n,
-                            cudaMemcpyHostToDevice, st));
-    SE_CUDA(cudaEventRecord(ws.ev_staging, st));
+    if (inputs_ready) SE_CUDA(cudaStreamWaitEvent(st, inputs_ready, 0));   // the samples have landed
 
     if (pl->cplx) return run_complex(ctx, pl, ws, n, I_max, st);
     const BlockDesc *ddesc = ws.desc.as<BlockDesc>();
@@ -670,8 +714,21 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         int I_again = 0;
         for (int i = 0; i < n; ++i)
             if (flag[i] >= 0) {
-                again.push_back(hdesc[i]);
-                I_again = std::max(I_again, hdesc[i].iterations);
+                BlockDesc x;
+                if (hdesc) {
+                    x = hdesc[i];
+                } else {
+                    const size_t MN = static_cast<size_t>(pl->MN);
+                    x.samples = ss->samples + MN * i;
+                    x.support = nullptr;
+                    x.out = ss->out + MN * i;
+                    x.sel_idx = ss->sel_idx ? ss->sel_idx + static_cast<size_t>(ss->I) * i : nullptr;
+                    x.sel_coef = ss->sel_coef ? ss->sel_coef + static_cast<size_t>(ss->I) * ss->coef * i : nullptr;
+                    x.iterations = ss->I;
+                    x.pad_ = 0;
+                }
+                again.push_back(x);
+                I_again = std::max(I_again, x.iterations);
             }
         ctx->cert_blocks += n;
         ctx->cert_recomputed += again.size();
@@ -780,6 +837,13 @@ se_status se_ctx_destroy(se_ctx_t *ctx)
     std::vector<se_plan_s *> plans = ctx->plans;
     for (auto *p : plans) se_plan_destroy(p);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    for (int i = 0; i < se_ctx_s::kPipe; ++i) {
+        if (ctx->pipe_st[i]) cudaStreamDestroy(ctx->pipe_st[i]);
+        if (ctx->pipe_ev_in[i]) cudaEventDestroy(ctx->pipe_ev_in[i]);
+        if (ctx->pipe_ev_done[i]) cudaEventDestroy(ctx->pipe_ev_done[i]);
+    }
+    if (ctx->pipe_in) cudaStreamDestroy(ctx->pipe_in);
+    if (ctx->pipe_out) cudaStreamDestroy(ctx->pipe_out);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -1013,6 +1077,62 @@ se_status se_plan_reset_tables(se_plan_t *plan)
     return SE_OK;
 }
 
+namespace {
+
+// Pattern blocks (routed to the table or the lazy columns) and mask blocks of
+// one call, on workspace ws and stream st; ctx->mu is held by the caller.
+se_status run_resolved(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, std::vector<BlockDesc> &full, int I_full,
+                       std::vector<BlockDesc> &lazy, int I_lazy, cudaStream_t st,
+                       cudaEvent_t inputs_ready = nullptr)
+{
+    probes_poll(ctx, false);
+    route_pattern_blocks(pl, full, lazy, &I_full, &I_lazy);
+    if (!full.empty())
+        SE_TRY(run_batch(ctx, pl, ws, static_cast<int>(full.size()), full.data(), I_full, st, inputs_ready));
+    if (!lazy.empty()) {
+        if (inputs_ready && full.empty()) SE_CUDA(cudaStreamWaitEvent(st, inputs_ready, 0));
+        SE_TRY(run_lazy(ctx, pl, ws, static_cast<int>(lazy.size()), lazy.data(), I_lazy, st));
+    }
+    return SE_OK;
+}
+
+// Descriptors of n contiguous pattern blocks (samples / out M x N each, logs
+// [b][I], complex coefficient logs [b][I][2]).
+void strided_desc(const se_plan_s *pl, int n, const double *samples, double *out, int32_t *sel_idx,
+                  double *sel_coef, int I, std::vector<BlockDesc> &d)
+{
+    const size_t MN = static_cast<size_t>(pl->MN);
+    d.resize(n);
+    for (int i = 0; i < n; ++i) {
+        d[i].samples = samples + MN * i;
+        d[i].support = nullptr;
+        d[i].out = out + MN * i;
+        d[i].sel_idx = sel_idx ? sel_idx + static_cast<size_t>(I) * i : nullptr;
+        d[i].sel_coef = sel_coef ? sel_coef + static_cast<size_t>(pl->cplx ? 2 : 1) * I * i : nullptr;
+        d[i].iterations = I;
+        d[i].pad_ = 0;
+    }
+}
+
+// A contiguous batch of pattern blocks on workspace ws and stream st (ctx->mu
+// held): the table path with descriptors formed on the device, or the lazy
+// columns when the plan (LAZY) or the measured costs (AUTO) say so.
+se_status run_strided(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const StridedSpec &ss, cudaStream_t st,
+                      cudaEvent_t inputs_ready = nullptr)
+{
+    probes_poll(ctx, false);
+    if (pl->desc.gram == SE_GRAM_LAZY || choose_lazy_for_pattern(pl, n)) {
+        std::vector<BlockDesc> d;
+        strided_desc(pl, n, ss.samples, ss.out, ss.sel_idx, ss.sel_coef, ss.I, d);
+        for (auto &x : d) x.support = pl->d_pattern.as<uint8_t>();
+        if (inputs_ready) SE_CUDA(cudaStreamWaitEvent(st, inputs_ready, 0));
+        return run_lazy(ctx, pl, ws, n, d.data(), ss.I, st);
+    }
+    return run_batch(ctx, pl, ws, n, nullptr, ss.I, st, inputs_ready, &ss);
+}
+
+}  // namespace
+
 se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, const se_block *blocks,
                                void *cuda_stream)
 {
@@ -1044,12 +1164,7 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n, cons
         }
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
-    probes_poll(ctx, false);
-    route_pattern_blocks(pl, full, lazy, &I_full, &I_lazy);
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (!full.empty()) SE_TRY(run_batch(ctx, pl, ctx->ws, static_cast<int>(full.size()), full.data(), I_full, st));
-    if (!lazy.empty()) SE_TRY(run_lazy(ctx, pl, ctx->ws, static_cast<int>(lazy.size()), lazy.data(), I_lazy, st));
-    return SE_OK;
+    return run_resolved(ctx, pl, ctx->ws, full, I_full, lazy, I_lazy, static_cast<cudaStream_t>(cuda_stream));
 }
 
 se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, const double *samples,
@@ -1060,18 +1175,12 @@ se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, co
     if (n == 0) return SE_OK;
     if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
     if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
+    if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
+    SE_CUDA(cudaSetDevice(ctx->device));
     const int I = iterations ? iterations : plan->desc.iterations;
-    std::vector<se_block> b(n);
-    const size_t MN = static_cast<size_t>(plan->MN);
-    for (int i = 0; i < n; ++i) {
-        b[i].samples = samples + MN * i;
-        b[i].support = nullptr;
-        b[i].out = out + MN * i;
-        b[i].sel_idx = sel_idx ? sel_idx + static_cast<size_t>(I) * i : nullptr;
-        b[i].sel_coef = sel_coef ? sel_coef + static_cast<size_t>(plan->cplx ? 2 : 1) * I * i : nullptr;
-        b[i].iterations = I;
-    }
-    return se_extrapolate_batch(ctx, plan, n, b.data(), cuda_stream);
+    const StridedSpec ss{samples, out, sel_idx, sel_coef, I, plan->cplx ? 2 : 1};
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return run_strided(ctx, const_cast<se_plan_s *>(plan), ctx->ws, n, ss, static_cast<cudaStream_t>(cuda_stream));
 }
 
 se_status se_sync(se_ctx_t *ctx, void *cuda_stream)
@@ -1098,37 +1207,73 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
     if (n == 0) return SE_OK;
     if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
     if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
+    if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
     SE_CUDA(cudaSetDevice(ctx->device));
+    se_plan_s *pl = const_cast<se_plan_s *>(plan);
     const int I = iterations ? iterations : plan->desc.iterations;
     const size_t MN = static_cast<size_t>(plan->MN);
     const size_t io_bytes = 2 * MN * n * sizeof(double) +
                             (sel_idx ? sizeof(int32_t) * I * static_cast<size_t>(n) : 0) +
                             (sel_coef ? sizeof(double) * I * static_cast<size_t>(n) : 0) + 64;
-    cudaStream_t st = ctx->stream;
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu);
-        if (ctx->ws.io.bytes < io_bytes) SE_CUDA(cudaStreamSynchronize(st));
-        SE_TRY(dev_alloc(ctx, ctx->ws.io, io_bytes));
+    // chunks of at least 512 blocks: the copies of one chunk overlap the
+    // computation of the others
+    const int S = std::max(1, std::min(se_ctx_s::kPipe, n / 512));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->pipe_ready) {
+        for (int i = 0; i < se_ctx_s::kPipe; ++i) {
+            SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_st[i], cudaStreamNonBlocking));
+            SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_in[i], cudaEventDisableTiming));
+            SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_done[i], cudaEventDisableTiming));
+            SE_CUDA(ctx->pipe_ws[i].init());
+        }
+        SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_in, cudaStreamNonBlocking));
+        SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_out, cudaStreamNonBlocking));
+        ctx->pipe_ready = true;
     }
+    // the previous call has finished (it synchronised), so the I/O buffer is free
+    SE_TRY(dev_alloc(ctx, ctx->ws.io, io_bytes));
     double *d_s = ctx->ws.io.as<double>();
     double *d_o = d_s + MN * n;
     char *tail = reinterpret_cast<char *>(d_o + MN * n);
     int32_t *d_i = sel_idx ? reinterpret_cast<int32_t *>(tail) : nullptr;
     double *d_c = nullptr;
     if (sel_coef) {
-        size_t off = sel_idx ? round_up(sizeof(int32_t) * I * static_cast<size_t>(n), 16) : 0;
+        const size_t off = sel_idx ? round_up(sizeof(int32_t) * I * static_cast<size_t>(n), 16) : 0;
         d_c = reinterpret_cast<double *>(tail + off);
     }
-    SE_CUDA(cudaMemcpyAsync(d_s, samples, MN * n * sizeof(double), cudaMemcpyHostToDevice, st));
-    SE_TRY(se_extrapolate_strided(ctx, plan, n, d_s, d_o, d_i, d_c, I, st));
-    SE_CUDA(cudaMemcpyAsync(out, d_o, MN * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (sel_idx)
-        SE_CUDA(cudaMemcpyAsync(sel_idx, d_i, sizeof(int32_t) * I * static_cast<size_t>(n),
-                                cudaMemcpyDeviceToHost, st));
-    if (sel_coef)
-        SE_CUDA(cudaMemcpyAsync(sel_coef, d_c, sizeof(double) * I * static_cast<size_t>(n),
-                                cudaMemcpyDeviceToHost, st));
-    return se_sync(ctx, st);
+    for (int c = 0; c < S; ++c) {
+        const int b0 = static_cast<int>(static_cast<long long>(n) * c / S);
+        const int nc = static_cast<int>(static_cast<long long>(n) * (c + 1) / S) - b0;
+        const size_t o = MN * b0;
+        cudaStream_t st = ctx->pipe_st[c];
+        SE_CUDA(cudaMemcpyAsync(d_s + o, samples + o, MN * nc * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->pipe_in));
+        SE_CUDA(cudaEventRecord(ctx->pipe_ev_in[c], ctx->pipe_in));
+        const StridedSpec ss{d_s + o, d_o + o, d_i ? d_i + static_cast<size_t>(I) * b0 : nullptr,
+                             d_c ? d_c + static_cast<size_t>(I) * b0 : nullptr, I, 1};
+        // the chunk's kernels wait for its copy; a table build (first chunk) does not
+        SE_TRY(run_strided(ctx, pl, ctx->pipe_ws[c], nc, ss, st, ctx->pipe_ev_in[c]));
+        SE_CUDA(cudaEventRecord(ctx->pipe_ev_done[c], st));
+        SE_CUDA(cudaStreamWaitEvent(ctx->pipe_out, ctx->pipe_ev_done[c], 0));
+        SE_CUDA(cudaMemcpyAsync(out + o, d_o + o, MN * nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->pipe_out));
+        if (sel_idx)
+            SE_CUDA(cudaMemcpyAsync(sel_idx + static_cast<size_t>(I) * b0, d_i + static_cast<size_t>(I) * b0,
+                                    sizeof(int32_t) * I * static_cast<size_t>(nc), cudaMemcpyDeviceToHost,
+                                    ctx->pipe_out));
+        if (sel_coef)
+            SE_CUDA(cudaMemcpyAsync(sel_coef + static_cast<size_t>(I) * b0, d_c + static_cast<size_t>(I) * b0,
+                                    sizeof(double) * I * static_cast<size_t>(nc), cudaMemcpyDeviceToHost,
+                                    ctx->pipe_out));
+    }
+    SE_CUDA(cudaStreamSynchronize(ctx->pipe_out));
+    int bits = 0;
+    SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) {
+        SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
+        const se_status code = bits == (1 << DEV_ERR_EMPTY_SUPPORT) ? SE_ERR_EMPTY_SUPPORT : SE_ERR_CUDA;
+        return fail(code, std::string("device status: ") + dev_err_text(bits));
+    }
+    return SE_OK;
 }
 
 se_status se_set_profiling(se_ctx_t *ctx, int enable)
@@ -1268,7 +1413,7 @@ se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len)
     std::string t = std::string("products=") + (plan->sep_full ? "transform" : "dense") +
                     " table=" + (plan->dft_w ? "dft-of-weights" : "table") + " iterations=" +
                     (plan->cplx ? "complex" : plan->pc.fp64 ? "fp64" : plan->sym ? "parity-classes" : "general") +
-                    (plan->certified ? " certified" : "");
+                    (plan->sym_tc ? " projections=split-tf32" : "") + (plan->certified ? " certified" : "");
     std::snprintf(buf, len, "%s", t.c_str());
     return SE_OK;
 }

@@ -164,6 +164,14 @@ struct se_ctx_s {
 
     // workspace of the batch entry points (grown on demand, reused)
     se::Workspace ws;
+    // host-buffer calls in chunks: copies in on pipe_in, each chunk on its own stream
+    // and workspace (chunks overlap on the device), copies out on pipe_out
+    static constexpr int kPipe = 4;
+    se::Workspace pipe_ws[kPipe];
+    cudaStream_t pipe_st[kPipe] = {};
+    cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+    cudaEvent_t pipe_ev_in[kPipe] = {}, pipe_ev_done[kPipe] = {};
+    bool pipe_ready = false;
     se::DevBuf ws_err;                    // device status word shared by all kernels
 
     // per-stage timing (se_set_profiling)
@@ -240,6 +248,8 @@ struct se_plan_s {
     // transforms); R^(0) of such plans is stored in class order
     bool sym = false;
     se::DevBuf d_perm, d_Cc, d_Dkp, d_sym_img;
+    se::DevBuf d_sym_tc;         // 32 x 32: the folded constants as tensor-core fragments
+    bool sym_tc = false;         // R^(0) by split-TF32 tensor-core products
     se::DevBuf d_What;
     std::vector<double> dft_invC;
     // tables (eqs. 16-17)
@@ -268,9 +278,13 @@ struct se_plan_s {
 
 namespace se {
 // One batch of blocks of one plan, all on the plan's pattern: tables of
-// Alg. 2 if not cached, eq. (12) GEMM, Alg. 3 iterations, on stream st.
+// Alg. 2 if not cached, eq. (12) GEMM, Alg. 3 iterations, on stream st.  The
+// descriptors come from hdesc (host) or, for a contiguous batch, from ss
+// (formed on the device; hdesc may then be NULL); the kernels that read the
+// samples wait for inputs_ready when it is given.
 se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
-                    int I_max, cudaStream_t st);
+                    int I_max, cudaStream_t st, cudaEvent_t inputs_ready = nullptr,
+                    const StridedSpec *ss = nullptr);
 // Blocks with their own masks (desc.support set for every block): lazy columns.
 // Upload the transform-domain operands (weights without mask, 1-D basis
 // rows) when the plan's dictionary is separable; sets pl->sep.  Idempotent;

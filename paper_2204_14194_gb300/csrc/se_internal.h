@@ -91,6 +91,27 @@ cudaError_t launch_tables_finalize(const double *diag, const uint8_t *dup,
                                    const unsigned long long *dmax, int K, int Kp, T *invC, T *Dk,
                                    int *n_admissible, cudaStream_t st);
 
+// A contiguous batch: block b has samples / out at b MN, sel_idx at b I and
+// sel_coef at b I coef (coef = 2 for complex plans); NULL logs stay NULL.
+struct StridedSpec {
+    const double *samples;
+    double *out;
+    int32_t *sel_idx;
+    double *sel_coef;
+    int I;
+    int coef;
+};
+// Descriptors of such a batch, written on the device.
+cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, cudaStream_t st);
+
+// Grid of a persistent launch: min(want, SMs x resident CTAs per SM) for
+// kernel kern at this block size and dynamic shared memory; the first call for
+// a kernel raises its dynamic shared memory limit (and, with max_shared,
+// prefers the largest shared-memory carveout).  Cached per device.
+cudaError_t launch_grid(const void *kern, int threads, size_t smem, int want, int *grid, bool max_shared = false);
+// SMs of the current device (cached).
+int sm_count();
+
 // ------------------------------------------------------------------ iterate
 struct IterArgs {
     const BlockDesc *blocks;
@@ -146,6 +167,9 @@ struct SymSepArgs {
     int M, N, ntr, K;
     const float *img;           // per transform A_t[M/2][2][M/2] (t_{2i+a}[m] at (m, a, i)),
                                 //   B_t[N/2][2][N/2]; then rho [MN] (unmasked weights)
+    const float *tc_img;        // 32 x 32 only: the same constants as m16n8k8 fragments per lane,
+                                //   AF[t][a][ks][lane] (4 floats: A^T rows g, g + 8, columns
+                                //   8 ks + q, + 4), BF[t][b][ks][nt][lane] (2 floats), then rho
     const int *perm;            // [K] class order -> original atom
     const uint8_t *pattern;     // [MN] 1 = support
     // table: the diagonal of eq. (16) and D_k, 1/C_kk of eq. (17) (written to Dk, invC in
@@ -168,6 +192,9 @@ cudaError_t launch_sym_rows(const SymSepArgs &a, cudaStream_t st);
 // variant < sym_r0_variants(M, N): identical results (0 generic, 1 the 32 x 32 kernel)
 cudaError_t launch_sym_r0(const SymSepArgs &a, cudaStream_t st, int variant = 0);
 int sym_r0_variants(int M, int N);
+// R^(0) of 32 x 32 parity-class blocks with split-TF32 tensor-core products (a.tc_img set);
+// accurate like the fp32 transforms but not bitwise equal to them.
+cudaError_t launch_sym_r0_tc(const SymSepArgs &a, cudaStream_t st);
 // Iterations, model and replacement for complex-valued atoms (k_complex.cu):
 // R0 [n][2][Kp], C [Kp][2][Kp] (row u = C(., u)), invC [Kp], PhiB [Kp][2][nB];
 // sel_coef receives (Re, Im) pairs.

@@ -42,24 +42,6 @@ void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t r256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Block descriptors of a contiguous batch: samples[b], out[b] are M x N,
-// the logs are [b][iterations].
-__global__ void fill_desc_kernel(se::BlockDesc *d, int n, const double *samples, double *out,
-                                 int32_t *sel_idx, double *sel_coef, int iterations, int MN)
-{
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    se::BlockDesc x;
-    x.samples = samples + static_cast<size_t>(MN) * b;
-    x.support = nullptr;
-    x.out = out + static_cast<size_t>(MN) * b;
-    x.sel_idx = sel_idx ? sel_idx + static_cast<size_t>(iterations) * b : nullptr;
-    x.sel_coef = sel_coef ? sel_coef + static_cast<size_t>(iterations) * b : nullptr;
-    x.iterations = iterations;
-    x.pad_ = 0;
-    d[b] = x;
-}
-
 se_status scratch_address(int device, unsigned char **out)
 {
     if (device < 0 || device >= kMaxDevices)
@@ -123,9 +105,8 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     int *d_log = reinterpret_cast<int *>(base + desc_b + x_b + r_b);
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-    fill_desc_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_desc, n, samples, out, sel_idx, sel_coef, I,
-                                                      pl->MN);
-    cudaError_t e = cudaGetLastError();
+    const StridedSpec spec{samples, out, sel_idx, sel_coef, I, 1};
+    cudaError_t e = launch_fill_desc(d_desc, n, spec, pl->MN, st);
     if (e != cudaSuccess) return set_error(SE_ERR_CUDA, std::string("descriptors: ") + cudaGetErrorString(e));
     s = ensure_tables(ctx, pl, st);
     if (s != SE_OK) return s;

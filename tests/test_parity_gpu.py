@@ -240,6 +240,30 @@ def test_host_entry_point_matches_device_path(ctx):
     plan.close()
 
 
+@pytest.mark.parametrize("n,shift,prec,logs", [(2500, 0, "bf16x6", "both"), (1100, 1, "bf16x6", "idx"),
+                                              (1300, 0, "certified", "coef"), (2048, 0, "bf16x6", "none")])
+def test_pipelined_host_entry_point_matches_device_path(ctx, n, shift, prec, logs):
+    """Host-buffer calls of 1024 blocks and more run in chunks (copies in, each
+    chunk on its own stream, copies out); the results equal one device call."""
+    L, I = 32, 60
+    sup = np.ones((L, L), dtype=np.uint8)
+    sup[8:24, 8 + shift:24 + shift] = 0
+    s = np.stack([W.patch(L, 3000 + i) for i in range(n)])
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec=prec, support=sup)
+    dev, ud, cd = gpu_run(plan, s)
+    out = np.empty_like(s)
+    u = np.empty((n, I), dtype=np.int32) if logs in ("both", "idx") else None
+    c = np.empty((n, I)) if logs in ("both", "coef") else None
+    plan.reset_tables()
+    plan.extrapolate_host(s, out, u, c)
+    np.testing.assert_array_equal(out, dev)
+    if u is not None:
+        np.testing.assert_array_equal(u, ud)
+    if c is not None:
+        np.testing.assert_array_equal(c, cd)
+    plan.close()
+
+
 @pytest.mark.parametrize("shift", [0, 1])
 def test_symmetric_and_shifted_patterns(ctx, shift):
     """A centred loss box makes w symmetric (the parity-class iterations run);

@@ -92,18 +92,54 @@ def test_projection_variants_of_parity_plans_are_bitwise_identical(basis, K):
     tiles) give the same bits."""
     samples = np.stack([W.patch(32, 7000 + i) for i in range(300)])
     res = []
-    for v in (0, 1):
-        ctx = _ctx(force=f"symr0:={v}")
-        try:
-            plan = ctx.plan(32, 32, basis, K, 0.8, 0.5, 50, prec="bf16x6")
-            assert plan.info().get("iterations") == "parity-classes"
-            res.append(_run(ctx, plan, samples))
-            plan.close()
-        finally:
-            ctx.close()
+    os.environ["SE_R0_FFMA"] = "1"   # the fp32 kernels instead of the tensor-core one
+    try:
+        for v in (0, 1):
+            ctx = _ctx(force=f"symr0:={v}")
+            try:
+                plan = ctx.plan(32, 32, basis, K, 0.8, 0.5, 50, prec="bf16x6")
+                info = plan.info()
+                assert info.get("iterations") == "parity-classes" and "projections" not in info
+                res.append(_run(ctx, plan, samples))
+                plan.close()
+            finally:
+                ctx.close()
+    finally:
+        os.environ.pop("SE_R0_FFMA", None)
     for r in res[1:]:
         for x, y in zip(res[0], r):
             np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("basis,K", [("dct_wht", 2048), ("dct", 1024), ("wht", 1024)])
+def test_tensor_core_projections_match_the_fp32_transforms(basis, K):
+    """Split-TF32 tensor-core R0 (the 32 x 32 default) against the fp32 kernels:
+    the same selections up to near ties, coefficients and outputs within the
+    fp32 form's tolerance."""
+    from helpers import coef_rel_err
+    samples = np.stack([W.patch(32, 7300 + i) for i in range(300)])
+    res = []
+    for ffma in (False, True):
+        if ffma:
+            os.environ["SE_R0_FFMA"] = "1"
+        try:
+            ctx = _ctx()
+            try:
+                plan = ctx.plan(32, 32, basis, K, 0.8, 0.5, 60, prec="bf16x6")
+                assert (plan.info().get("projections") == "split-tf32") != ffma
+                res.append(_run(ctx, plan, samples))
+                plan.close()
+            finally:
+                ctx.close()
+        finally:
+            os.environ.pop("SE_R0_FFMA", None)
+    (o1, u1, c1), (o2, u2, c2) = res
+    same = np.all(u1 == u2, axis=1)
+    assert same.mean() >= 0.97, same.mean()
+    for b in np.where(same)[0]:   # both within 1e-3 of the fp64 values
+        assert coef_rel_err(c1[b], c2[b]).max() <= 2e-3
+    d = np.abs(o1 - o2)[same]
+    assert d.mean() <= 0.01 and d.max() <= 0.5, (d.mean(), d.max())
 
 
 def test_autotuner_times_each_shape_once_and_persists(tmp_path):
