@@ -243,9 +243,14 @@ se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
                                  const double *samples, double *out, int32_t *sel_idx,
                                  double *sel_coef, int iterations, void *cuda_stream);
 
-/* Same as se_extrapolate_strided but with HOST buffers: copies samples to
- * the device, runs the batch and copies out (and the optional logs) back
- * before returning.  Uses pinned staging owned by the context. */
+/* Same as se_extrapolate_strided but with HOST buffers; returns when out (and
+ * the optional logs) hold the results.  Buffers the GPU can address (pinned /
+ * page-locked memory: cudaHostAlloc, cudaHostRegister, torch pin_memory) are
+ * read and written by the kernels directly over the host link, so the transfers
+ * overlap the computation; other (pageable) buffers are copied through the
+ * context's device buffer in chunks of at least 512 blocks, the copies of one
+ * chunk overlapping the computation of the others.  Serialised with the other
+ * batch calls of the context. */
 se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
                               const double *samples, double *out,
                               int32_t *sel_idx, double *sel_coef, int iterations);

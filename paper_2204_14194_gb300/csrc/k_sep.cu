@@ -550,9 +550,10 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
                 mo[r] = COL ? mb + r : m0 + oc / Nb;
                 no[r] = COL ? n0 + lane % Nb : n0 + oc % Nb;
             }
-            float acc[RP];
+            static_assert(RP % 2 == 0, "outputs in pairs");
+            float2 acc2[RP / 2];
 #pragma unroll
-            for (int r = 0; r < RP; ++r) acc[r] = 0.0f;
+            for (int r = 0; r < RP / 2; ++r) acc2[r] = make_float2(0.0f, 0.0f);
             // the log in rounds of 32 entries, the next round's loads in flight
             // while this one is evaluated; the first pass over the box also
             // writes the caller's copies of the log
@@ -589,10 +590,14 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
                         float tv[RP];
                         lds_vec<RP>(Ts + e.x + mb, tv);
 #pragma unroll
-                        for (int r = 0; r < RP; ++r) acc[r] = fmaf(cb, tv[r], acc[r]);
+                        for (int r = 0; r < RP; r += 2)   // paired: the same fma per output
+                            acc2[r / 2] = __ffma2_rn(make_float2(cb, cb), make_float2(tv[r], tv[r + 1]), acc2[r / 2]);
                     } else {
 #pragma unroll
-                        for (int r = 0; r < RP; ++r) acc[r] = fmaf(c * Ts[e.y + no[r]], Ts[e.x + mo[r]], acc[r]);
+                        for (int r = 0; r < RP; ++r) {
+                            float &x = (r & 1) ? acc2[r / 2].y : acc2[r / 2].x;
+                            x = fmaf(c * Ts[e.y + no[r]], Ts[e.x + mo[r]], x);
+                        }
                     }
                 }
             }
@@ -601,7 +606,7 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
                 const int o = o0 + lane + 32 * r;
                 if (o >= nbox) continue;
                 const int p = mo[r] * N + no[r];
-                if (!a.pat_support[p]) bd.out[p] = static_cast<double>(acc[r]);
+                if (!a.pat_support[p]) bd.out[p] = static_cast<double>((r & 1) ? acc2[r / 2].y : acc2[r / 2].x);
             }
         }
     }

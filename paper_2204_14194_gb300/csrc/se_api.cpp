@@ -1215,8 +1215,41 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
     const size_t io_bytes = 2 * MN * n * sizeof(double) +
                             (sel_idx ? sizeof(int32_t) * I * static_cast<size_t>(n) : 0) +
                             (sel_coef ? sizeof(double) * I * static_cast<size_t>(n) : 0) + 64;
-    // chunks of at least 512 blocks: the copies of one chunk overlap the
-    // computation of the others
+    // Pinned (page-locked) caller buffers are read and written by the kernels
+    // themselves over the host link (no staging copies: the transfers overlap the
+    // computation); pageable ones are staged in chunks of at least 512 blocks, the
+    // copies of one chunk overlapping the computation of the others.
+    auto host_mapped = [](const void *p, void **dev) {
+        if (!p) {
+            *dev = nullptr;
+            return true;
+        }
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer) return false;
+        *dev = at.devicePointer;
+        return true;
+    };
+    void *z_s = nullptr, *z_o = nullptr, *z_i = nullptr, *z_c = nullptr;
+    if (host_mapped(samples, &z_s) && host_mapped(out, &z_o) && host_mapped(sel_idx, &z_i) &&
+        host_mapped(sel_coef, &z_c)) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        const StridedSpec ss{static_cast<const double *>(z_s), static_cast<double *>(z_o),
+                             static_cast<int32_t *>(z_i), static_cast<double *>(z_c), I, 1};
+        SE_TRY(run_strided(ctx, pl, ctx->ws, n, ss, ctx->stream));
+        SE_CUDA(cudaStreamSynchronize(ctx->stream));
+        int bits = 0;
+        SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (bits) {
+            SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
+            const se_status code = bits == (1 << DEV_ERR_EMPTY_SUPPORT) ? SE_ERR_EMPTY_SUPPORT : SE_ERR_CUDA;
+            return fail(code, std::string("device status: ") + dev_err_text(bits));
+        }
+        return SE_OK;
+    }
     const int S = std::max(1, std::min(se_ctx_s::kPipe, n / 512));
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (!ctx->pipe_ready) {

@@ -166,7 +166,7 @@ struct se_ctx_s {
     se::Workspace ws;
     // host-buffer calls in chunks: copies in on pipe_in, each chunk on its own stream
     // and workspace (chunks overlap on the device), copies out on pipe_out
-    static constexpr int kPipe = 4;
+    static constexpr int kPipe = 8;
     se::Workspace pipe_ws[kPipe];
     cudaStream_t pipe_st[kPipe] = {};
     cudaStream_t pipe_in = nullptr, pipe_out = nullptr;

@@ -264,6 +264,26 @@ def test_pipelined_host_entry_point_matches_device_path(ctx, n, shift, prec, log
     plan.close()
 
 
+@pytest.mark.parametrize("n,logs", [(2100, True), (300, False)])
+def test_host_entry_point_with_pinned_buffers(ctx, n, logs):
+    """Pinned host buffers are read and written by the kernels directly."""
+    L, I = 32, 60
+    s = np.stack([W.patch(L, 3500 + i) for i in range(n)])
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec="bf16x6")
+    dev, ud, cd = gpu_run(plan, s)
+    s_h = torch.from_numpy(s).pin_memory()
+    o_h = torch.full_like(s_h, float("nan")).pin_memory()
+    u_h = torch.full((n, I), -1, dtype=torch.int32).pin_memory() if logs else None
+    c_h = torch.zeros((n, I), dtype=torch.float64).pin_memory() if logs else None
+    plan.reset_tables()
+    plan.extrapolate_host(s_h, o_h, u_h, c_h)
+    np.testing.assert_array_equal(o_h.numpy(), dev)
+    if logs:
+        np.testing.assert_array_equal(u_h.numpy(), ud)
+        np.testing.assert_array_equal(c_h.numpy(), cd)
+    plan.close()
+
+
 @pytest.mark.parametrize("shift", [0, 1])
 def test_symmetric_and_shifted_patterns(ctx, shift):
     """A centred loss box makes w symmetric (the parity-class iterations run);
