@@ -41,7 +41,7 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
 TRAFFIC_ITERATE = {}
 SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>"}
-TRAFFIC_ITERATE_SYM = {0: 36.92e6}
+TRAFFIC_ITERATE_SYM = {1: 36.91e6}
 
 
 def _dist():
@@ -329,6 +329,13 @@ def run_ours(args):
                 "traffic": it_traffic,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
                 "l2_read_GBps": n * (I - 1) * row_bytes / it_avg_s / 1e9, "plan": info}
+    if info.get("iterations") == "parity-classes" and sv == 1:
+        # the on-chip roof the kernel actually meets: per block-iteration the row
+        # (L2 -> registers) and one class of R' read and written in shared memory
+        onchip = n * (I - 1) * (row_bytes + 2 * K // 4 * 4) / it_avg_s / 1e9
+        lsu_peak = 152 * 128 * 2.07e9 / 1e9
+        roofline["onchip"] = {"achieved": onchip, "peak": lsu_peak, "unit": "GB/s", "frac": onchip / lsu_peak,
+                              "peak_kind": "derived: 152 SMs x 128 B per cycle (L1/shared data pipe) x 2.07 GHz"}
     pr_ms, pr_n = stages["projections"]
     pr_avg_s = pr_ms / max(pr_n, 1) / 1000.0
     na = int(np.sum(wl.support))
@@ -340,19 +347,30 @@ def run_ours(args):
         if args.prec == "fp64":
             roofline_gemm = None
         else:
-            if info.get("iterations") == "parity-classes":
-                # folded into four quarter-size transforms per block: half the flops
-                flops, pk = ntr * M * N * (M + N), "sym_r0_kernel<%d,%d> (eq. 12, four folded quarter transforms)" \
-                    % (M // 2, N // 2)
-            else:
-                flops, pk = ntr * 2.0 * M * N * (M + N), "sep_warp_kernel<32,32,8,4> (eq. 12 as separable transforms, Sec. VI)"
-            tflops = n * flops / pr_avg_s / 1e12
             gbs = n * (16.0 * na + 4.0 * K) / pr_avg_s / 1e9
-            roofline_gemm = {
-                "kernel": pk,
-                "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": tflops / alu_peak, "hbm_GBps": gbs, "hbm_frac": gbs / hbm_peak,
-                "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz"}
+            if info.get("projections") == "split-tf32":
+                # four folded quarter transforms per block as m16n8k8 tensor products in
+                # split TF32 (3 products each): bound by the block's bytes, not its flops
+                tflops = n * 3 * ntr * M * N * (M + N) / pr_avg_s / 1e12
+                roofline_gemm = {
+                    "kernel": "sym_r0_32tc_kernel (eq. 12, folded quarter transforms, mma.sync split TF32)",
+                    "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "tensor_tflops": tflops, "peak_kind": peak_kind + " HBM copy",
+                    "bytes_per_block": "16 |A| (samples read, support copied to out) + 4 K (R0 written)"}
+            else:
+                if info.get("iterations") == "parity-classes":
+                    # folded into four quarter-size transforms per block: half the flops
+                    flops, pk = ntr * M * N * (M + N), \
+                        "sym_r0_kernel<%d,%d> (eq. 12, four folded quarter transforms)" % (M // 2, N // 2)
+                else:
+                    flops, pk = ntr * 2.0 * M * N * (M + N), \
+                        "sep_warp_kernel<32,32,8,4> (eq. 12 as separable transforms, Sec. VI)"
+                tflops = n * flops / pr_avg_s / 1e12
+                roofline_gemm = {
+                    "kernel": pk,
+                    "bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": tflops / alu_peak, "hbm_GBps": gbs, "hbm_frac": gbs / hbm_peak,
+                    "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz"}
     else:
         npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(args.prec, 0)
         tflops = 2.0 * K * n * na * npairs / pr_avg_s / 1e12 if npairs else None
