@@ -255,6 +255,15 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
                               const double *samples, double *out,
                               int32_t *sel_idx, double *sel_coef, int iterations);
 
+/* Exercises the device failure path: queues on `cuda_stream` one CTA that
+ * waits on an mbarrier nothing arrives at.  Like every wait in the library's
+ * kernels the wait is bounded (%globaltimer); after limit_us microseconds
+ * (1000 .. 2000000) it gives up, records the timeout in the context's status
+ * word and returns, so the context stays usable; the next se_sync on that
+ * stream returns SE_ERR_CUDA with the message and clears the word.  For tests
+ * and health checks of a deployment. */
+se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_stream);
+
 /* Wait for the work this context queued on `cuda_stream` and report
  * errors that its kernels recorded in the device status word (SE_ERR_CUDA
  * with a message, e.g. a bounded wait that ran out).  Clears the word. */

@@ -30,7 +30,8 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_extrapolate_batch", "se_extrapolate_strided", "se_extrapolate_host", "se_sync",
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
-           "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats", "se_plan_info"]
+           "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats", "se_plan_info",
+           "se_check_wait_timeout"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = True):
             "se_set_graphs": ([vp, i32], i32),
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
+            "se_check_wait_timeout": ([vp, C.c_uint32, vp], i32),
             "se_cert_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], i32),
             "se_plan_info": ([vp, C.c_char_p, C.c_size_t], i32),
         }
@@ -176,6 +178,11 @@ class Context:
         a, b = C.c_uint64(), C.c_uint64()
         _check(self._lib.se_cert_stats(self.handle, C.byref(a), C.byref(b)), "se_cert_stats")
         return {"blocks": a.value, "recomputed": b.value}
+
+    def check_wait_timeout(self, limit_us: int = 200_000, stream=None):
+        """Queue a device wait that runs out after limit_us (se_check_wait_timeout)."""
+        _check(self._lib.se_check_wait_timeout(self.handle, int(limit_us), _stream_handle(stream)),
+               "se_check_wait_timeout")
 
     def tuned_variant(self, key: str) -> int:
         """The autotuner's kept variant for a shape key, -1 if not tuned."""

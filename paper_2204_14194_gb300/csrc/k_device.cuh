@@ -25,7 +25,7 @@ __device__ __forceinline__ float max3_abs(float m, float a, float b)
 }
 
 // One bulk (TMA) copy of a whole row of T into shared memory, completing on
-// an mbarrier; waits are bounded by %globaltimer.
+// an mbarrier; waits are bounded by %globaltimer (2 s unless given).
 __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)
 {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
@@ -36,7 +36,7 @@ __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t 
                  ::"r"(d), "l"(src), "r"(bytes), "r"(m) : "memory");
 }
 
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns = 2000000000ull)
 {
     const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(bar));
     uint32_t ok = 0;
@@ -49,7 +49,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         if (i == 0) t0 = t;
-        else if (t - t0 > 2000000000ull) return false;
+        else if (t - t0 > limit_ns) return false;
     }
 }
 

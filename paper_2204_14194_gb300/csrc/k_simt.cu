@@ -5,6 +5,7 @@
 
 #include <cmath>
 
+#include "k_device.cuh"
 #include "se_internal.h"
 
 namespace se {
@@ -387,6 +388,29 @@ cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, 
 {
     if (n <= 0) return cudaSuccess;
     fill_desc_kernel<<<(n + 255) / 256, 256, 0, st>>>(d, n, s, MN);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// The device failure path, exercised on purpose: one thread waits on an
+// mbarrier that nothing arrives at; the bounded wait gives up after limit_ns,
+// the kernel records the timeout in the status word and returns.
+__global__ void wait_probe_kernel(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t m = static_cast<uint32_t>(__cvta_generic_to_shared(&bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!dev::bar_wait(&bar, 0, limit_ns)) atomicOr(err, 1 << DEV_ERR_WAIT_TIMEOUT);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(err, limit_ns);
     return cudaGetLastError();
 }
 

@@ -742,12 +742,13 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
     constexpr int M = 32, N = 32, MN = 1024, QMN = 256;
     extern __shared__ __align__(16) float fsm[];
     const int ntr = a.ntr;
-    // constants: AF[t][ca][ks][lane] float4, BF[t][cb][ks][nt][lane] float2, rho[MN]
-    const int nconst = ntr * 1024 + MN;
+    // constants, split into TF32 parts by the plan: AF[t][ca][ks][lane] (uint4 large,
+    // uint4 small), BF[t][cb][ks][nt][lane] (b0, b1 large, b0, b1 small), rho[MN]
+    const int nconst = ntr * 2048 + MN;
     float *cst = fsm;
-    const float4 *AF = reinterpret_cast<const float4 *>(cst);
-    const float2 *BF = reinterpret_cast<const float2 *>(cst + ntr * 512);
-    const float *rho = cst + ntr * 1024;
+    const uint4 *AF = reinterpret_cast<const uint4 *>(cst);
+    const uint4 *BF = reinterpret_cast<const uint4 *>(cst + ntr * 1024);
+    const float *rho = cst + ntr * 2048;
     float *X = cst + nconst + (threadIdx.x >> 5) * (4 * kTcPlane + 16 * kTcU);
     float *U = X + 4 * kTcPlane;
     for (int e = threadIdx.x; e < nconst / 4; e += blockDim.x)
@@ -804,11 +805,10 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
                 uint32_t Ab[2][4], As[2][4];
 #pragma unroll
                 for (int ks = 0; ks < 2; ++ks) {
-                    const float4 f = AF[((t * 2 + ca) * 2 + ks) * 32 + lane];
-                    split_tf32(f.x, Ab[ks][0], As[ks][0]);
-                    split_tf32(f.y, Ab[ks][1], As[ks][1]);
-                    split_tf32(f.z, Ab[ks][2], As[ks][2]);
-                    split_tf32(f.w, Ab[ks][3], As[ks][3]);
+                    const uint4 fb = AF[(((t * 2 + ca) * 2 + ks) * 2 + 0) * 32 + lane];
+                    const uint4 fs = AF[(((t * 2 + ca) * 2 + ks) * 2 + 1) * 32 + lane];
+                    Ab[ks][0] = fb.x; Ab[ks][1] = fb.y; Ab[ks][2] = fb.z; Ab[ks][3] = fb.w;
+                    As[ks][0] = fs.x; As[ks][1] = fs.y; As[ks][2] = fs.z; As[ks][3] = fs.w;
                 }
 #pragma unroll 1
                 for (int cb = 0; cb < 2; ++cb) {
@@ -848,11 +848,8 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
                         float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                         for (int ks = 0; ks < 2; ++ks) {
-                            const float2 f = BF[(((t * 2 + cb) * 2 + ks) * 2 + nt) * 32 + lane];
-                            uint32_t bb0, bs0, bb1, bs1;
-                            split_tf32(f.x, bb0, bs0);
-                            split_tf32(f.y, bb1, bs1);
-                            mma3(y, Ub[ks], Us[ks], bb0, bb1, bs0, bs1);
+                            const uint4 f = BF[(((t * 2 + cb) * 2 + ks) * 2 + nt) * 32 + lane];
+                            mma3(y, Ub[ks], Us[ks], f.x, f.y, f.z, f.w);
                         }
                         *reinterpret_cast<float2 *>(Rc + g * 16 + 8 * nt + 2 * q) = make_float2(y[0], y[1]);
                         *reinterpret_cast<float2 *>(Rc + (g + 8) * 16 + 8 * nt + 2 * q) = make_float2(y[2], y[3]);
@@ -916,7 +913,7 @@ cudaError_t launch_sym_r0_tc(const SymSepArgs &a, cudaStream_t st)
     if (!a.blocks || !a.R0 || !a.tc_img || a.M != 32 || a.N != 32 || a.K != a.ntr * 1024) return cudaErrorInvalidValue;
     if (a.n <= 0) return cudaSuccess;
     constexpr int wpc = 9;   // 3 CTAs of 9 warps per SM: 4104 blocks in one wave
-    const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 1024 + 1024 +
+    const size_t smem = sizeof(float) * (static_cast<size_t>(a.ntr) * 2048 + 1024 +
                                          wpc * static_cast<size_t>(4 * kTcPlane + 16 * kTcU));
     SymSepArgs b = a;
     b.img = a.tc_img;

@@ -81,7 +81,7 @@ se_status upload(se_ctx_s *ctx, DevBuf &b, const std::vector<V> &h)
 
 const char *dev_err_text(int bits)
 {
-    if (bits & (1 << DEV_ERR_WAIT_TIMEOUT)) return "a tensor-core pipeline wait timed out";
+    if (bits & (1 << DEV_ERR_WAIT_TIMEOUT)) return "a bounded device wait (mbarrier) ran out of time";
     if (bits & (1 << DEV_ERR_BAD_INDEX)) return "no admissible atom could be selected";
     if (bits & (1 << DEV_ERR_TMEM)) return "tensor memory allocation failed";
     if (bits & (1 << DEV_ERR_LAZY_CACHE)) return "lazy column cache overflow";
@@ -316,30 +316,48 @@ se_status se::setup_sym(se_ctx_s *ctx, se_plan_s *pl)
     if (M == 32 && N == 32) {
         // the same constants as per-lane m16n8k8 fragments for the tensor-core R^(0)
         // kernel (g = lane / 4, q = lane mod 4); SE_R0_FFMA=1 keeps the fp32 kernels
+        // TF32 parts of x: large = x rounded to 10 mantissa bits (nearest, ties away from
+        // zero, on the bit pattern: the 13 dropped bits decide), small = the same rounding
+        // of the exact remainder x - large
+        auto tf32 = [](float x) {
+            uint32_t u;
+            std::memcpy(&u, &x, 4);
+            u = (u + 0x1000u) & 0xffffe000u;
+            float r;
+            std::memcpy(&r, &u, 4);
+            return r;
+        };
         std::vector<float> tc;
-        tc.reserve(static_cast<size_t>(ntr) * 1024 + MN);
+        tc.reserve(static_cast<size_t>(ntr) * 2048 + MN);
         for (int t = 0; t < ntr; ++t)
             for (int a = 0; a < 2; ++a)
                 for (int ks = 0; ks < 2; ++ks)
-                    for (int l = 0; l < 32; ++l) {
-                        const int g = l >> 2, q = l & 3;
-                        auto At = [&](int i, int m) { return fimg[static_cast<size_t>(t) * 1024 + m * 32 + a * 16 + i]; };
-                        tc.push_back(At(g, 8 * ks + q));
-                        tc.push_back(At(g + 8, 8 * ks + q));
-                        tc.push_back(At(g, 8 * ks + q + 4));
-                        tc.push_back(At(g + 8, 8 * ks + q + 4));
-                    }
+                    for (int part = 0; part < 2; ++part)
+                        for (int l = 0; l < 32; ++l) {
+                            const int g = l >> 2, q = l & 3;
+                            auto At = [&](int i, int m) {
+                                const float x = fimg[static_cast<size_t>(t) * 1024 + m * 32 + a * 16 + i];
+                                const float xb = tf32(x);
+                                return part ? tf32(x - xb) : xb;
+                            };
+                            tc.push_back(At(g, 8 * ks + q));
+                            tc.push_back(At(g + 8, 8 * ks + q));
+                            tc.push_back(At(g, 8 * ks + q + 4));
+                            tc.push_back(At(g + 8, 8 * ks + q + 4));
+                        }
         for (int t = 0; t < ntr; ++t)
             for (int b = 0; b < 2; ++b)
                 for (int ks = 0; ks < 2; ++ks)
                     for (int nt = 0; nt < 2; ++nt)
                         for (int l = 0; l < 32; ++l) {
                             const int g = l >> 2, q = l & 3;
-                            auto Bt = [&](int n, int j) {
-                                return fimg[static_cast<size_t>(t) * 1024 + 512 + n * 32 + b * 16 + j];
-                            };
-                            tc.push_back(Bt(8 * ks + q, 8 * nt + g));
-                            tc.push_back(Bt(8 * ks + q + 4, 8 * nt + g));
+                            const float b0 = fimg[static_cast<size_t>(t) * 1024 + 512 + (8 * ks + q) * 32 + b * 16 + 8 * nt + g];
+                            const float b1 =
+                                fimg[static_cast<size_t>(t) * 1024 + 512 + (8 * ks + q + 4) * 32 + b * 16 + 8 * nt + g];
+                            tc.push_back(tf32(b0));
+                            tc.push_back(tf32(b1));
+                            tc.push_back(tf32(b0 - tf32(b0)));
+                            tc.push_back(tf32(b1 - tf32(b1)));
                         }
         tc.insert(tc.end(), img.end() - MN, img.end());
         SE_TRY(upload(ctx, pl->d_sym_tc, tc));
@@ -1181,6 +1199,16 @@ se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n, co
     const StridedSpec ss{samples, out, sel_idx, sel_coef, I, plan->cplx ? 2 : 1};
     std::lock_guard<std::mutex> lk(ctx->mu);
     return run_strided(ctx, const_cast<se_plan_s *>(plan), ctx->ws, n, ss, static_cast<cudaStream_t>(cuda_stream));
+}
+
+se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_stream)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    if (limit_us < 1000 || limit_us > 2000000) return fail(SE_ERR_INVALID, "limit_us outside [1000, 2000000]");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    SE_CUDA(launch_wait_probe(ctx->ws_err.as<int>(), 1000ull * limit_us, static_cast<cudaStream_t>(cuda_stream)));
+    ctx->launches += 1;
+    return SE_OK;
 }
 
 se_status se_sync(se_ctx_t *ctx, void *cuda_stream)

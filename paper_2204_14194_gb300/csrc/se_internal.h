@@ -104,6 +104,10 @@ struct StridedSpec {
 // Descriptors of such a batch, written on the device.
 cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, cudaStream_t st);
 
+// One CTA that waits on an mbarrier nothing arrives at, bounded by limit_ns;
+// it sets DEV_ERR_WAIT_TIMEOUT in *err and returns (the failure path, on purpose).
+cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_t st);
+
 // Grid of a persistent launch: min(want, SMs x resident CTAs per SM) for
 // kernel kern at this block size and dynamic shared memory; the first call for
 // a kernel raises its dynamic shared memory limit (and, with max_shared,
@@ -168,8 +172,9 @@ struct SymSepArgs {
     const float *img;           // per transform A_t[M/2][2][M/2] (t_{2i+a}[m] at (m, a, i)),
                                 //   B_t[N/2][2][N/2]; then rho [MN] (unmasked weights)
     const float *tc_img;        // 32 x 32 only: the same constants as m16n8k8 fragments per lane,
-                                //   AF[t][a][ks][lane] (4 floats: A^T rows g, g + 8, columns
-                                //   8 ks + q, + 4), BF[t][b][ks][nt][lane] (2 floats), then rho
+                                //   split into TF32 parts x_b + x_s: AF[t][a][ks][part][lane] (4 words:
+                                //   A^T rows g, g + 8, columns 8 ks + q, + 4), BF[t][b][ks][nt][lane]
+                                //   (b0, b1 large, b0, b1 small), then rho (fp32)
     const int *perm;            // [K] class order -> original atom
     const uint8_t *pattern;     // [MN] 1 = support
     // table: the diagonal of eq. (16) and D_k, 1/C_kk of eq. (17) (written to Dk, invC in
