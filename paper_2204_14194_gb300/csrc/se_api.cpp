@@ -596,7 +596,8 @@ se_status dense_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws,
 // All blocks use the plan's pattern: Alg. 2 tables (cached), eq. (12) GEMM,
 // Alg. 3 iterations.
 se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
-                        int I_max, cudaStream_t st, cudaEvent_t inputs_ready, const StridedSpec *ss)
+                        int I_max, cudaStream_t st, cudaEvent_t inputs_ready, const StridedSpec *ss,
+                        cudaEvent_t r0_done)
 {
     const int Kp = pl->Kp;
     const bool fp64 = pl->pc.fp64;
@@ -677,10 +678,12 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         tok = stage_begin(ctx, 2, st);
         SE_CUDA(launch_pattern_projections(ctx, pl, ddesc, n, ws.r0.ptr, !overlap, st));
         stage_end(ctx, tok, st);
+        if (r0_done) SE_CUDA(cudaEventRecord(r0_done, st));
         if (overlap) SE_CUDA(cudaStreamWaitEvent(st, pl->tables_ready, 0));   // the (forked) table build
         ctx->launches += 1;
     } else {
         SE_TRY(dense_pattern_projections(ctx, pl, ws, ddesc, n, st));
+        if (r0_done) SE_CUDA(cudaEventRecord(r0_done, st));
     }
 
     IterArgs a{};
@@ -1132,11 +1135,27 @@ void strided_desc(const se_plan_s *pl, int n, const double *samples, double *out
     }
 }
 
+// Streams, events and workspaces of the chunked host-buffer calls (ctx->mu held).
+se_status pipe_init(se_ctx_s *ctx)
+{
+    if (ctx->pipe_ready) return SE_OK;
+    for (int i = 0; i < se_ctx_s::kPipe; ++i) {
+        SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_st[i], cudaStreamNonBlocking));
+        SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_in[i], cudaEventDisableTiming));
+        SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_done[i], cudaEventDisableTiming));
+        SE_CUDA(ctx->pipe_ws[i].init());
+    }
+    SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_in, cudaStreamNonBlocking));
+    SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_out, cudaStreamNonBlocking));
+    ctx->pipe_ready = true;
+    return SE_OK;
+}
+
 // A contiguous batch of pattern blocks on workspace ws and stream st (ctx->mu
 // held): the table path with descriptors formed on the device, or the lazy
 // columns when the plan (LAZY) or the measured costs (AUTO) say so.
 se_status run_strided(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const StridedSpec &ss, cudaStream_t st,
-                      cudaEvent_t inputs_ready = nullptr)
+                      cudaEvent_t inputs_ready = nullptr, cudaEvent_t r0_done = nullptr)
 {
     probes_poll(ctx, false);
     if (pl->desc.gram == SE_GRAM_LAZY || choose_lazy_for_pattern(pl, n)) {
@@ -1144,9 +1163,11 @@ se_status run_strided(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const 
         strided_desc(pl, n, ss.samples, ss.out, ss.sel_idx, ss.sel_coef, ss.I, d);
         for (auto &x : d) x.support = pl->d_pattern.as<uint8_t>();
         if (inputs_ready) SE_CUDA(cudaStreamWaitEvent(st, inputs_ready, 0));
-        return run_lazy(ctx, pl, ws, n, d.data(), ss.I, st);
+        SE_TRY(run_lazy(ctx, pl, ws, n, d.data(), ss.I, st));
+        if (r0_done) SE_CUDA(cudaEventRecord(r0_done, st));
+        return SE_OK;
     }
-    return run_batch(ctx, pl, ws, n, nullptr, ss.I, st, inputs_ready, &ss);
+    return run_batch(ctx, pl, ws, n, nullptr, ss.I, st, inputs_ready, &ss, r0_done);
 }
 
 }  // namespace
@@ -1262,13 +1283,28 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
         return true;
     };
     void *z_s = nullptr, *z_o = nullptr, *z_i = nullptr, *z_c = nullptr;
+    const int S = std::max(1, std::min(se_ctx_s::kPipe, n / 512));
     if (host_mapped(samples, &z_s) && host_mapped(out, &z_o) && host_mapped(sel_idx, &z_i) &&
         host_mapped(sel_coef, &z_c)) {
+        // chunks on their own streams; their projection passes (the readers of the
+        // host samples) run one after another, so each has the link to itself
+        // while the earlier chunks iterate
         std::lock_guard<std::mutex> lk(ctx->mu);
-        const StridedSpec ss{static_cast<const double *>(z_s), static_cast<double *>(z_o),
-                             static_cast<int32_t *>(z_i), static_cast<double *>(z_c), I, 1};
-        SE_TRY(run_strided(ctx, pl, ctx->ws, n, ss, ctx->stream));
-        SE_CUDA(cudaStreamSynchronize(ctx->stream));
+        SE_TRY(pipe_init(ctx));
+        const int Sz = std::max(1, std::min(4, n / 1024));
+        for (int c = 0; c < Sz; ++c) {
+            const int b0 = static_cast<int>(static_cast<long long>(n) * c / Sz);
+            const int nc = static_cast<int>(static_cast<long long>(n) * (c + 1) / Sz) - b0;
+            const size_t o = MN * b0;
+            const StridedSpec ss{static_cast<const double *>(z_s) + o, static_cast<double *>(z_o) + o,
+                                 z_i ? static_cast<int32_t *>(z_i) + static_cast<size_t>(I) * b0 : nullptr,
+                                 z_c ? static_cast<double *>(z_c) + static_cast<size_t>(I) * b0 : nullptr, I, 1};
+            SE_TRY(run_strided(ctx, pl, ctx->pipe_ws[c], nc, ss, ctx->pipe_st[c], c ? ctx->pipe_ev_in[c - 1] : nullptr,
+                               ctx->pipe_ev_in[c]));
+            SE_CUDA(cudaEventRecord(ctx->pipe_ev_done[c], ctx->pipe_st[c]));
+            SE_CUDA(cudaStreamWaitEvent(ctx->pipe_out, ctx->pipe_ev_done[c], 0));
+        }
+        SE_CUDA(cudaStreamSynchronize(ctx->pipe_out));
         int bits = 0;
         SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
         if (bits) {
@@ -1278,19 +1314,8 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
         }
         return SE_OK;
     }
-    const int S = std::max(1, std::min(se_ctx_s::kPipe, n / 512));
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (!ctx->pipe_ready) {
-        for (int i = 0; i < se_ctx_s::kPipe; ++i) {
-            SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_st[i], cudaStreamNonBlocking));
-            SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_in[i], cudaEventDisableTiming));
-            SE_CUDA(cudaEventCreateWithFlags(&ctx->pipe_ev_done[i], cudaEventDisableTiming));
-            SE_CUDA(ctx->pipe_ws[i].init());
-        }
-        SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_in, cudaStreamNonBlocking));
-        SE_CUDA(cudaStreamCreateWithFlags(&ctx->pipe_out, cudaStreamNonBlocking));
-        ctx->pipe_ready = true;
-    }
+    SE_TRY(pipe_init(ctx));
     // the previous call has finished (it synchronised), so the I/O buffer is free
     SE_TRY(dev_alloc(ctx, ctx->ws.io, io_bytes));
     double *d_s = ctx->ws.io.as<double>();

@@ -281,10 +281,11 @@ namespace se {
 // Alg. 2 if not cached, eq. (12) GEMM, Alg. 3 iterations, on stream st.  The
 // descriptors come from hdesc (host) or, for a contiguous batch, from ss
 // (formed on the device; hdesc may then be NULL); the kernels that read the
-// samples wait for inputs_ready when it is given.
+// samples wait for inputs_ready when it is given, and r0_done (if given) is
+// recorded once they are done (before the iterations).
 se_status run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                     int I_max, cudaStream_t st, cudaEvent_t inputs_ready = nullptr,
-                    const StridedSpec *ss = nullptr);
+                    const StridedSpec *ss = nullptr, cudaEvent_t r0_done = nullptr);
 // Blocks with their own masks (desc.support set for every block): lazy columns.
 // Upload the transform-domain operands (weights without mask, 1-D basis
 // rows) when the plan's dictionary is separable; sets pl->sep.  Idempotent;
