@@ -530,6 +530,9 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) Ts[t * cstride + M * M + e] = gn[e];
     }
     __syncthreads();
+    // launched as a programmatic dependent of the iteration kernel: the rows above
+    // are staged while it drains; its log is read only after it has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
     const int nbox = Mb * Nb;
     constexpr int CH = 32 * RP;   // outputs per chunk
@@ -691,8 +694,17 @@ cudaError_t launch_sep_model_t(const IterArgs &a, const SepArgs &s, int m0, int 
     cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_model_kernel<COL, RP>), 256, smem, (a.n + 7) / 8,
                                 &grid);
     if (e != cudaSuccess) return e;
-    sep_model_kernel<COL, RP><<<grid, 256, smem, st>>>(a, s, m0, Mb, n0, Nb);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // may start while the
+    attr[0].val.programmaticStreamSerializationAllowed = 1;             // previous kernel drains
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sep_model_kernel<COL, RP>, a, s, m0, Mb, n0, Nb);
 }
 
 cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,

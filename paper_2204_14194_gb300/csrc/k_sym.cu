@@ -199,6 +199,9 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4 *myR = reinterpret_cast<float4 *>(smem) + static_cast<size_t>(g) * (4 * NCC * 32) + lane;
     const float gamma = static_cast<float>(a.gamma);
+    // the model kernel (a programmatic dependent) may be scheduled now; it waits for
+    // this grid to complete before it reads the log
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     for (int b = blockIdx.x * BPC + g; b < a.n; b += gridDim.x * BPC) {
         const BlockDesc bd = a.blocks[b];
