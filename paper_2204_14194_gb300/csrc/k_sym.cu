@@ -287,6 +287,158 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
     }
 }
 
+// The same iterations with the block's projections in tensor memory: a CTA of
+// four warps allocates 64 TMEM columns, warp w keeps its block's R' in TMEM
+// lanes 32 w .. 32 w + 31 (lane l, column c 16 + ch 4 + e: the atom
+// c K/4 + ch 128 + 4 l + e, the layout of the other two forms).  An iteration
+// finds the class of the winner (the smallest class holding the maximum),
+// loads that class's 16 columns with tcgen05.ld, scans it, updates it with the
+// row and stores it back with tcgen05.st: the class traffic leaves the
+// shared-memory/L1 pipe, which then carries only the row.  The arithmetic and
+// the selection order are those of the other forms (same bits).  At most
+// eight CTAs (512 columns) fit on an SM: the launch bounds and a shared-memory
+// reservation guarantee it, so tcgen05.alloc never waits.
+constexpr int kTmemCols = 64;
+constexpr int kTmemGuard = 26 * 1024;   // dynamic shared memory that keeps an SM at <= 8 CTAs
+
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tm_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                   "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                   "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                   "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                   "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                   "r"(__float_as_uint(v[15]))
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 8) iterate_sym_tmem_kernel(const IterArgs a)
+{
+    constexpr int NCC = 4;       // float4 chunks per lane and class (K = 2048)
+    constexpr int Q = 512;       // atoms per class
+    __shared__ uint32_t tmem_base;
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (g == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(&tmem_base))), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tw = tmem_base + (static_cast<uint32_t>(g * 32) << 16);   // this warp's lane quarter
+    const float gamma = static_cast<float>(a.gamma);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    for (int b = blockIdx.x * 4 + g; b < a.n; b += gridDim.x * 4) {
+        const BlockDesc bd = a.blocks[b];
+        const int I = bd.iterations;
+        const float *R0 = static_cast<const float *>(a.R0) + static_cast<size_t>(b) * a.Kp;
+        float m[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float v[16];
+            float mm = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < NCC; ++ch) {
+                const int j = c * Q + ch * 128 + 4 * lane;
+                const float4 rj = *reinterpret_cast<const float4 *>(R0 + j);
+                const float4 dj = __ldg(reinterpret_cast<const float4 *>(a.Dkp + j));
+                v[4 * ch] = rj.x * dj.x;
+                v[4 * ch + 1] = rj.y * dj.y;
+                v[4 * ch + 2] = rj.z * dj.z;
+                v[4 * ch + 3] = rj.w * dj.w;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mm = fmaxf(mm, fabsf(v[4 * ch + e]));
+            }
+            m[c] = mm;
+            tm_st16(tw + c * 16, v);
+        }
+
+        int lu = 0;
+        float lc = 0.0f;
+        for (int nu = 0; nu < I; ++nu) {
+            const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+            const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+            // the class of the winner: the smallest class holding M (indices grow with the class)
+            int cl = 4;
+            if (mx == M) cl = m[0] == M ? 0 : m[1] == M ? 1 : m[2] == M ? 2 : 3;
+            const int cw = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<unsigned>(cl)));
+            float v[16];
+            tm_ld16(tw + (cw & 3) * 16, v);
+            unsigned key = 0xffffffffu;
+            if (cl == cw) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (fabsf(v[j]) == M) {
+                        key = sel_key(cw * Q + (j >> 2) * 128 + 4 * lane + (j & 3), v[j]);
+                        break;
+                    }
+            }
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            int u = static_cast<int>(kmin >> 1);
+            float ru = (kmin & 1u) ? -M : M;
+            if (u < 0 || u >= a.K) {
+                if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+                u = 0;
+                ru = 0.0f;
+            }
+            const int cu = u / Q;   // == cw for a valid selection
+            const bool more = nu + 1 < I;
+            float4 t[NCC];
+            if (more) {
+                const float4 *row = reinterpret_cast<const float4 *>(a.Cc + static_cast<size_t>(u) * Q) + lane;
+#pragma unroll
+                for (int ch = 0; ch < NCC; ++ch) t[ch] = __ldg(row + ch * 32);
+            }
+            const float c = gamma * ru * __ldg(a.Dkp + u);
+            log_entry(a, b, nu, more, lane, u, c, lu, lc);
+            if (!more) break;
+            if (cu != cw) tm_ld16(tw + cu * 16, v);   // only after a recorded bad index
+            const float2 nc = make_float2(-c, -c);
+            float mc[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int ch = 0; ch < NCC; ++ch) {
+                const float2 x0 = __ffma2_rn(nc, make_float2(t[ch].x, t[ch].y), make_float2(v[4 * ch], v[4 * ch + 1]));
+                const float2 x1 =
+                    __ffma2_rn(nc, make_float2(t[ch].z, t[ch].w), make_float2(v[4 * ch + 2], v[4 * ch + 3]));
+                v[4 * ch] = x0.x;
+                v[4 * ch + 1] = x0.y;
+                v[4 * ch + 2] = x1.x;
+                v[4 * ch + 3] = x1.y;
+                mc[0] = max3_abs(mc[0], x0.x, x0.y);
+                mc[1] = max3_abs(mc[1], x1.x, x1.y);
+            }
+            tm_st16(tw + cu * 16, v);
+            const float mn = fmaxf(mc[0], mc[1]);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) m[cc] = cc == cu ? mn : m[cc];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (g == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- folded transforms
 // With w symmetric and t_p[M-1-m] = (-1)^p t_p[m] (DCT-II and sequency-ordered
 // Walsh rows), the separable transform of Sec. VI splits into four
@@ -980,11 +1132,29 @@ static cudaError_t launch_sym_smem(const IterArgs &a, cudaStream_t st, int *laun
     return cudaGetLastError();
 }
 
-int iterate_sym_variants() { return 2; }
+int iterate_sym_variants(int Kp) { return Kp == 2048 ? 3 : 2; }
+
+static cudaError_t launch_sym_tmem(const IterArgs &a, cudaStream_t st, int *launches)
+{
+    if (a.K != 2048 || a.Kp != 2048 || !a.log_u || !a.log_c || !a.perm || !a.Cc || !a.Dkp)
+        return cudaErrorInvalidValue;
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(iterate_sym_tmem_kernel), 128, kTmemGuard,
+                                (a.n + 3) / 4, &grid, true);
+    if (e != cudaSuccess) return e;
+    // the registers (64 x 128 per CTA) and the shared-memory guard bound the
+    // residency at 8 CTAs per SM, which is also the TMEM limit (8 x 64 columns)
+    const int want = (a.n + 3) / 4, cap = 8 * sm_count();
+    grid = want < cap ? want : cap;
+    iterate_sym_tmem_kernel<<<grid, 128, kTmemGuard, st>>>(a);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches, int variant)
 {
     if (a.n <= 0) return cudaSuccess;
+    if (variant == 2 && a.Kp == 2048) return launch_sym_tmem(a, st, launches);   // projections in tensor memory
     if (variant == 1) {   // projections in shared memory
         switch (a.Kp) {
         case 512: return launch_sym_smem<16, 4, 12>(a, st, launches);

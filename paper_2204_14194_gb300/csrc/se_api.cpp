@@ -416,7 +416,7 @@ cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a,
         int nb = 1;
         while (nb < a.n) nb <<= 1;
         const std::string skey = "sym:f32:" + std::to_string(pl->Kp) + ":n" + std::to_string(nb);
-        return tune_run(ctx, skey, iterate_sym_variants(), st, [&](int v) {
+        return tune_run(ctx, skey, iterate_sym_variants(pl->Kp), st, [&](int v) {
             *launched = 0;
             return launch_iterate_sym(a, st, launched, v);
         });

@@ -86,6 +86,26 @@ def test_forced_variants_are_bitwise_identical(case):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("n", [300, 4096])
+def test_parity_class_iteration_variants_are_bitwise_identical(n):
+    """Projections in registers, in shared memory and in tensor memory: the
+    same selections, coefficients and outputs, bit for bit."""
+    samples = np.stack([W.patch(32, 7600 + i % 997) for i in range(n)])
+    res = []
+    for v in (0, 1, 2):
+        ctx = _ctx(force=f"sym:={v}")
+        try:
+            plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 80, prec="bf16x6")
+            assert plan.info().get("iterations") == "parity-classes"
+            res.append(_run(ctx, plan, samples))
+            plan.close()
+        finally:
+            ctx.close()
+    for r in res[1:]:
+        for x, y in zip(res[0], r):
+            np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("basis,K", [("dct_wht", 2048), ("dct", 1024), ("wht", 1024)])
 def test_projection_variants_of_parity_plans_are_bitwise_identical(basis, K):
     """The two R0 kernels of a 32 x 32 parity-class plan (generic fold, 32 x 32
