@@ -338,7 +338,10 @@ se_status se_set_graphs(se_ctx_t *ctx, int enable);
  * once), graphs captured, graph replays.  Any pointer may be NULL.  The
  * autotuner times interchangeable kernel variants (identical results) on
  * the first launch of a shape; SE_TUNE_FILE (environment) names a file that
- * stores the choices across processes. */
+ * stores the choices across processes, and SE_TUNE_FORCE ("prefix=variant,...")
+ * forces the variant of every shape key that starts with a prefix.  SE_R0_FFMA=1
+ * (read when a plan is created) keeps the fp32 CUDA-core projection kernels of
+ * 32 x 32 parity-class plans instead of the split-TF32 tensor-core one. */
 se_status se_tuning_stats(se_ctx_t *ctx, uint64_t *tunings, uint64_t *graph_builds, uint64_t *graph_replays);
 /* SE_PREC_CERTIFIED plans: blocks computed, and blocks computed again in fp64
  * because a selection was within the certification gap.  Either pointer may
@@ -348,11 +351,15 @@ se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed);
  * (NUL-terminated, truncated to len): products ("transform" / "dense"),
  * table ("table" / "dft-of-weights"), iterations ("parity-classes" when the
  * weighting function is symmetric and the atoms are DCT / WHT rows, see
- * k_sym.cu; "general" otherwise; "complex"; "fp64"), certified or not.
- * Example: "products=transform table=table iterations=parity-classes". */
+ * k_sym.cu; "general" otherwise; "complex"; "fp64"), "projections=split-tf32"
+ * when a 32 x 32 parity-class plan forms eq. (12) on the tensor cores, and
+ * "certified" for certified plans.  Example: "products=transform table=table
+ * iterations=parity-classes projections=split-tf32". */
 se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len);
 /* The variant the autotuner keeps for a shape key (e.g. "iterate:f32:2048",
- * "sep:32x32:t2:f32"), or -1 in *variant when that key has not been tuned. */
+ * "sep:32x32:t2:f32", "sym:f32:2048:n4096" for the parity-class iterations of
+ * a 4096-block batch, "symr0:32x32:t2"), or -1 in *variant when that key has
+ * not been tuned. */
 se_status se_tuned_variant(se_ctx_t *ctx, const char *key, int *variant);
 
 #ifdef __cplusplus
