@@ -12,10 +12,17 @@
 // index, original order kept inside a class); R^(0) and the compact table come
 // in this order from the folded transforms below.  Lane l of the warp that
 // owns a block holds, for each class c, the atoms c K/4 + ch 128 + 4 l + e.
-// Everything else follows iterate_f32_kernel: D-scaled projections in
-// registers, packed FMAs, three-input maxima, one redux for the maximum, a
-// scan of the winning lane's class for the smallest index, bounded TMA row
-// copies into shared memory.
+//
+// The file holds three forms of the iterations with identical results (the
+// tuner picks one per batch size): the projections in registers
+// (iterate_sym_kernel: the row by a bounded TMA copy into shared memory), in
+// shared memory (iterate_sym_smem_kernel: 27 blocks per SM, the row loaded
+// straight into registers) and in tensor memory (iterate_sym_tmem_kernel);
+// the folded transforms of the table (sym_rows_kernel: diagonal, D_k and the
+// compact rows) and of eq. (12) (sym_r0_kernel, sym_r0_32_kernel on the CUDA
+// cores, sym_r0_32tc_kernel on the tensor cores).  All forms share the
+// arithmetic of iterate_f32_kernel: D-scaled projections, packed FMAs,
+// three-input maxima, one redux for the maximum and one for the smallest index.
 #include <cuda_runtime.h>
 
 #include <climits>
