@@ -38,71 +38,83 @@ _u8 = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 _i32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile ``se_oracle.c`` into ``oracle/_build/libse_oracle.so`` with gcc."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if (not force and os.path.exists(_OUT)
-            and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
-        return _OUT
-    tmp = _OUT + f".tmp{os.getpid()}"
+def build(force: bool = False, src: str = _SRC, out: str = _OUT) -> str:
+    """Compile ``src`` (default ``se_oracle.c``) into the shared library ``out``
+    (default ``oracle/_build/libse_oracle.so``) with gcc."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(src)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-fopenmp", "-o", tmp, _SRC, "-lm"]
+           "-fopenmp", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _OUT)
-    return _OUT
+    os.replace(tmp, out)
+    return out
 
 
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build())
-        vp = C.c_void_p
-        ip = C.c_int
-        dbl = C.c_double
-        lib.or_weights.argtypes = [ip, ip, dbl, _u8, vp, _dp]
-        lib.or_dict_dct.argtypes = [ip, ip, _dp]
-        lib.or_dict_wht.argtypes = [ip, ip, _dp]
-        lib.or_dict_wht.restype = ip
-        lib.or_dict_dct_wht.argtypes = [ip, ip, _dp]
-        lib.or_dict_dct_wht.restype = ip
-        lib.or_weights3.argtypes = [ip, ip, ip, dbl, _u8, vp, _dp]
-        lib.or_dict_dct3.argtypes = [ip, ip, ip, _dp]
-        lib.or_dict_wht3.argtypes = [ip, ip, ip, _dp]
-        lib.or_dict_wht3.restype = ip
-        lib.or_dict_dct_wht3.argtypes = [ip, ip, ip, _dp]
-        lib.or_dict_dct_wht3.restype = ip
-        lib.or_find_duplicates.argtypes = [ip, ip, _dp, _u8]
-        lib.or_dict_dft.argtypes = [ip, ip, _dp, _dp]
-        lib.or_dict_bdft.argtypes = [ip, ip, _dp, _dp]
-        lib.or_dict_dft_bdft.argtypes = [ip, ip, _dp, _dp]
-        lib.or_find_duplicates_c.argtypes = [ip, ip, _dp, _dp, _u8]
-        lib.or_se_original_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip,
-                                         _dp, vp, vp, vp, vp, vp, vp]
-        lib.or_se_original_c.restype = ip
-        lib.or_fase_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip, _dp, vp, vp, vp, vp]
-        lib.or_fase_c.restype = ip
-        lib.or_se_original_c_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, ip, vp, _dp, dbl, ip,
-                                               _dp, vp, vp, vp, vp, ip]
-        lib.or_se_original_c_batch.restype = ip
-        lib.or_projection_state.argtypes = [ip, ip, _dp, _dp, _dp, vp, vp, vp, vp]
-        lib.or_se_original.argtypes = [ip, ip, ip, _dp, _dp, vp, _dp, dbl, ip, ip,
-                                       _dp, vp, vp, vp, vp, vp, vp]
-        lib.or_se_original.restype = ip
-        lib.or_fase_tables.argtypes = [ip, ip, ip, _dp, _dp, _dp, _dp]
-        lib.or_fase.argtypes = [ip, ip, ip, _dp, _dp, _dp, _dp, vp, _dp, dbl, ip,
-                                _dp, vp, vp, vp, vp]
-        lib.or_fase.restype = ip
-        lib.or_se_original_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, ip, vp, _dp, dbl,
-                                             ip, vp, _dp, vp, vp, vp, ip]
-        lib.or_se_original_batch.restype = ip
-        lib.or_fase_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, _dp, vp, _dp, dbl,
-                                      ip, _dp, vp, vp, ip]
-        lib.or_fase_batch.restype = ip
-        lib.or_max_threads.restype = ip
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _configure(C.CDLL(build()))
+        return _lib
+
+
+def use_library(path: str) -> None:
+    """Route every function of this module through the shared library at
+    ``path`` (a build of a modified copy of ``se_oracle.c``).  The pin tests use
+    it to check that they reject an oracle with a planted mistake."""
+    global _lib
+    with _lock:
+        _lib = _configure(C.CDLL(os.path.abspath(path)))
+
+
+def _configure(lib):
+    vp = C.c_void_p
+    ip = C.c_int
+    dbl = C.c_double
+    lib.or_weights.argtypes = [ip, ip, dbl, _u8, vp, _dp]
+    lib.or_dict_dct.argtypes = [ip, ip, _dp]
+    lib.or_dict_wht.argtypes = [ip, ip, _dp]
+    lib.or_dict_wht.restype = ip
+    lib.or_dict_dct_wht.argtypes = [ip, ip, _dp]
+    lib.or_dict_dct_wht.restype = ip
+    lib.or_weights3.argtypes = [ip, ip, ip, dbl, _u8, vp, _dp]
+    lib.or_dict_dct3.argtypes = [ip, ip, ip, _dp]
+    lib.or_dict_wht3.argtypes = [ip, ip, ip, _dp]
+    lib.or_dict_wht3.restype = ip
+    lib.or_dict_dct_wht3.argtypes = [ip, ip, ip, _dp]
+    lib.or_dict_dct_wht3.restype = ip
+    lib.or_find_duplicates.argtypes = [ip, ip, _dp, _u8]
+    lib.or_dict_dft.argtypes = [ip, ip, _dp, _dp]
+    lib.or_dict_bdft.argtypes = [ip, ip, _dp, _dp]
+    lib.or_dict_dft_bdft.argtypes = [ip, ip, _dp, _dp]
+    lib.or_find_duplicates_c.argtypes = [ip, ip, _dp, _dp, _u8]
+    lib.or_se_original_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip,
+                                     _dp, vp, vp, vp, vp, vp, vp]
+    lib.or_se_original_c.restype = ip
+    lib.or_fase_c.argtypes = [ip, ip, ip, _dp, _dp, _dp, vp, _dp, vp, dbl, ip, _dp, vp, vp, vp, vp]
+    lib.or_fase_c.restype = ip
+    lib.or_se_original_c_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, ip, vp, _dp, dbl, ip,
+                                           _dp, vp, vp, vp, vp, ip]
+    lib.or_se_original_c_batch.restype = ip
+    lib.or_projection_state.argtypes = [ip, ip, _dp, _dp, _dp, vp, vp, vp, vp]
+    lib.or_se_original.argtypes = [ip, ip, ip, _dp, _dp, vp, _dp, dbl, ip, ip,
+                                   _dp, vp, vp, vp, vp, vp, vp]
+    lib.or_se_original.restype = ip
+    lib.or_fase_tables.argtypes = [ip, ip, ip, _dp, _dp, _dp, _dp]
+    lib.or_fase.argtypes = [ip, ip, ip, _dp, _dp, _dp, _dp, vp, _dp, dbl, ip,
+                            _dp, vp, vp, vp, vp]
+    lib.or_fase.restype = ip
+    lib.or_se_original_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, ip, vp, _dp, dbl,
+                                         ip, vp, _dp, vp, vp, vp, ip]
+    lib.or_se_original_batch.restype = ip
+    lib.or_fase_batch.argtypes = [ip, ip, ip, ip, _dp, _dp, _dp, _dp, vp, _dp, dbl,
+                                  ip, _dp, vp, vp, ip]
+    lib.or_fase_batch.restype = ip
+    lib.or_max_threads.restype = ip
+    return lib
 
 
 def _ptr(a: Optional[np.ndarray]):

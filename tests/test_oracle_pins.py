@@ -11,6 +11,7 @@ Citations are to Seiler & Kaup, arXiv 2204.14194.  What pins what:
   Alg. 1 == Alg. 3 the paper's equivalence claim, and the R recurrence of
                    eq. (15) equals the scalar products of SE's own residual
   single atom      closed form c_nu = gamma (1-gamma)^(nu-1) a, exact model
+  three atoms      closed-form selection order, coefficients and tie margin
   energy           E drops by gamma (2-gamma) R_u^2 / C_uu per iteration
   w == 1, gamma=1  orthonormal case reduces to the best I-term approximation
                    from scipy's DCT / an independent fast WHT
@@ -194,6 +195,30 @@ def test_single_atom_closed_form(basis, j):
     nu = np.arange(1, I + 1)
     np.testing.assert_allclose(r.c, gamma * (1 - gamma) ** (nu - 1) * a, rtol=1e-11)
     np.testing.assert_allclose(r.g, a * (1 - (1 - gamma) ** I) * phi[j], rtol=1e-11, atol=1e-12)
+
+
+def test_three_atom_sequence_and_tie_margin_closed_form():
+    """With w == 1 and orthonormal atoms, C = I, so the projection of eq. (3) is the atom's
+    amplitude in the residual.  Eq. (8) multiplies the selected amplitude by (1 - gamma), so
+    the selected sequence, the coefficients and the gap (s1 - s2) / s1 between the two best
+    eq. (7) scores (the tie margin) follow in closed form.  The largest amplitude sits at
+    the highest index, so the score scan has to move the old best into second place."""
+    M = N = 8
+    phi = O.dict_dct(M, N)
+    w = O.weights(M, N, 0.8, np.ones((M, N), dtype=np.uint8), rho=np.ones((M, N)))
+    idx, amp = [40, 7, 23], [5.0, -3.0, 2.0]
+    s = sum(a * phi[k] for k, a in zip(idx, amp))
+    gamma, I = 0.5, 7
+    r = O.se_original(phi, w, s, gamma, I)
+    cur = dict(zip(idx, amp))
+    for nu in range(I):
+        order = sorted(cur, key=lambda k: -cur[k] ** 2)
+        s1, s2 = cur[order[0]] ** 2, cur[order[1]] ** 2
+        assert s1 - s2 > 1e-3 * s1                      # no near-tie in this schedule
+        assert r.u[nu] == order[0]
+        assert r.c[nu] == pytest.approx(gamma * cur[order[0]], rel=1e-12)
+        assert r.margin[nu] == pytest.approx((s1 - s2) / s1, rel=1e-9)
+        cur[order[0]] *= 1.0 - gamma
 
 
 # ------------------------------------------------------------------ energy
