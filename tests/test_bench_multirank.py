@@ -1,5 +1,6 @@
 """bench.py's multi-rank logic on CPU: two gloo ranks, max-over-ranks timing,
-weak-scaling throughput, and the reference arm's rank > 0 early exit."""
+weak-scaling throughput, and the reference arm (rank 0 prints one line,
+other ranks exit without work)."""
 import os
 import subprocess
 import sys
@@ -54,3 +55,27 @@ def test_single_rank_helpers():
     import bench
     assert bench.max_over_ranks(3.25) == 3.25
     assert bench.job_throughput(100, 1, 2, 0.5) == 400.0
+
+
+def test_reference_arm_line_on_rank0():
+    """Rank 0 of the reference arm times the oracle and prints one JSON line with the GPU
+    arm's metric, unit and workload, an e2e object with no host copies and a cpu_baseline."""
+    import json
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0", OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1", "--ref-sample", "2"], env=env,
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"]["workload"] == bench.WORKLOAD and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert "2 of the 4096 blocks" in cb["sample"]
