@@ -8,6 +8,8 @@ The device code must never end a wait by faulting, so:
   - no trap instruction and no failing device assert;
   - no NVLink multicast or multimem forms, since the library is one process
     on one GPU.
+  - every mbarrier wait is bounded by a timer, after which the kernel records an
+    error and returns.
 """
 import glob
 import os
@@ -46,3 +48,25 @@ def test_kernels_build_for_sm103a_only():
     with open(os.path.join(ROOT, "paper_2204_14194_gb300", "build.py")) as f:
         text = f.read()
     assert re.findall(r"arch=compute_\w+,code=sm_\w+", text) == ["arch=compute_103a,code=sm_103a"]
+
+
+def test_every_mbarrier_wait_goes_through_a_bounded_helper():
+    """mbarrier.try_wait appears only inside the two wait helpers, and both give up after a
+    %globaltimer limit; the raw try helper is called only by its bounded wait loop."""
+    found = {}
+    for name, text in _sources():
+        n = text.count("mbarrier.try_wait")
+        if n:
+            found[os.path.basename(name)] = n
+    assert found == {"k_device.cuh": 1, "k_gemm_tc.cu": 1}, found
+    for name, text in _sources():
+        if name.endswith(".cuh") and "mbarrier.try_wait" in text:
+            body = text[text.index("bool bar_wait("):]
+            body = body[:body.index("\n}\n")]
+            assert "%%globaltimer" in body and "return false" in body
+        if name.endswith("k_gemm_tc.cu"):
+            body = text[text.index("bool mbar_wait("):]
+            body = body[:body.index("\n}\n")]
+            assert "gtimer()" in body and "return false" in body
+            assert len(re.findall(r"\bmbar_try\(", text)) == 3      # definition + two calls in mbar_wait
+            assert len(re.findall(r"\bmbar_try\(", body)) == 2
