@@ -40,7 +40,8 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # shape without a capture or once the kernel changes.
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
 TRAFFIC_ITERATE = {}
-SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>"}
+SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>", 2: "iterate_sym_tmem_kernel",
+              3: "iterate_sym_hot_kernel<64,3,9>"}
 TRAFFIC_ITERATE_SYM = {1: 36.91e6}
 
 
@@ -329,7 +330,7 @@ def run_ours(args):
                 "traffic": it_traffic,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
                 "l2_read_GBps": n * (I - 1) * row_bytes / it_avg_s / 1e9, "plan": info}
-    if info.get("iterations") == "parity-classes" and sv == 1:
+    if info.get("iterations") == "parity-classes" and sv in (1, 3):
         # the on-chip roof the kernel actually meets: per block-iteration the row
         # (L2 -> registers) and one class of R' read and written in shared memory
         onchip = n * (I - 1) * (row_bytes + 2 * K // 4 * 4) / it_avg_s / 1e9

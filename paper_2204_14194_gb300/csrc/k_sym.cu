@@ -13,11 +13,13 @@
 // in this order from the folded transforms below.  Lane l of the warp that
 // owns a block holds, for each class c, the atoms c K/4 + ch 128 + 4 l + e.
 //
-// The file holds three forms of the iterations with identical results (the
+// The file holds four forms of the iterations with identical results (the
 // tuner picks one per batch size): the projections in registers
 // (iterate_sym_kernel: the row by a bounded TMA copy into shared memory), in
 // shared memory (iterate_sym_smem_kernel: 27 blocks per SM, the row loaded
-// straight into registers) and in tensor memory (iterate_sym_tmem_kernel);
+// straight into registers), in tensor memory (iterate_sym_tmem_kernel), and the
+// last-updated class in registers with the other three in shared memory
+// (iterate_sym_hot_kernel);
 // the folded transforms of the table (sym_rows_kernel: diagonal, D_k and the
 // compact rows) and of eq. (12) (sym_r0_kernel, sym_r0_32_kernel on the CUDA
 // cores, sym_r0_32tc_kernel on the tensor cores).  All forms share the
@@ -293,6 +295,161 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
         }
     }
 }
+
+// The same iterations with the class that was updated last ("hot") kept in
+// registers and the other three classes in three shared-memory slots per block
+// (6 KiB at K = 2048).  When the next selection falls in the hot class (about
+// a third of the iterations) the update touches no shared memory; otherwise
+// the selected class is read from its slot, the hot class is written into that
+// slot chunk by chunk, and the selected class becomes the hot one.  A packed
+// map (2 bits per class, the hot class in bits 8-9) tells which slot holds
+// which class; it is always a permutation of the three cold classes.  One
+// block per warp, the grid covering the batch.  Arithmetic and selection
+// order are those of the other forms (same bits).
+template <int VPT, int BPC, int MINB>
+__global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_hot_kernel(const IterArgs a)
+{
+    constexpr int NCH = VPT / 4;
+    constexpr int NCC = NCH / 4;
+    constexpr int Q = 32 * 4 * NCC;
+    static_assert(NCC >= 1 && NCH % 4 == 0, "whole chunks per class");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4 *myR = reinterpret_cast<float4 *>(smem) + static_cast<size_t>(g) * (3 * NCC * 32) + lane;
+    const float gamma = static_cast<float>(a.gamma);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+    {
+        const int b = blockIdx.x * BPC + g;
+        if (b >= a.n) return;
+        const BlockDesc bd = a.blocks[b];
+        const int I = bd.iterations;
+        const float *R0 = static_cast<const float *>(a.R0) + static_cast<size_t>(b) * a.Kp;
+        float4 H[NCC];
+        float m[4];
+        {
+            float mm = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < NCC; ++ch) {
+                const int j = ch * 128 + 4 * lane;
+                const float4 rj = *reinterpret_cast<const float4 *>(R0 + j);
+                const float4 dj = __ldg(reinterpret_cast<const float4 *>(a.Dkp + j));
+                const float v[4] = {rj.x * dj.x, rj.y * dj.y, rj.z * dj.z, rj.w * dj.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mm = fmaxf(mm, fabsf(v[e]));
+                H[ch] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+            m[0] = mm;
+        }
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+            float mm = 0.0f;
+#pragma unroll 1
+            for (int ch = 0; ch < NCC; ++ch) {
+                const int j = c * Q + ch * 128 + 4 * lane;
+                const float4 rj = *reinterpret_cast<const float4 *>(R0 + j);
+                const float4 dj = __ldg(reinterpret_cast<const float4 *>(a.Dkp + j));
+                const float v[4] = {rj.x * dj.x, rj.y * dj.y, rj.z * dj.z, rj.w * dj.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) mm = fmaxf(mm, fabsf(v[e]));
+                myR[((c - 1) * NCC + ch) * 32] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+            m[c] = mm;
+        }
+        // slot of class c at bits 2c; the class held in H at bits 8-9
+        unsigned smap = (0u << 2) | (1u << 4) | (2u << 6);
+
+        int lu = 0;
+        float lc = 0.0f;
+        for (int nu = 0; nu < I; ++nu) {
+            const float mx = fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3]));
+            const float M = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(mx)));
+            unsigned key = 0xffffffffu;
+            if (mx == M) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (m[c] != M) continue;
+                    if (c == static_cast<int>(smap >> 8)) {
+#pragma unroll
+                        for (int ch = 0; ch < NCC; ++ch) {
+                            const float r4[4] = {H[ch].x, H[ch].y, H[ch].z, H[ch].w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (fabsf(r4[e]) == M) {
+                                    key = sel_key(c * Q + ch * 128 + 4 * lane + e, r4[e]);
+                                    goto found;
+                                }
+                        }
+                    } else {
+                        const float4 *Rs = myR + ((smap >> (2 * c)) & 3u) * (NCC * 32);
+#pragma unroll
+                        for (int ch = 0; ch < NCC; ++ch) {
+                            const float4 q = Rs[ch * 32];
+                            const float r4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (fabsf(r4[e]) == M) {
+                                    key = sel_key(c * Q + ch * 128 + 4 * lane + e, r4[e]);
+                                    goto found;
+                                }
+                        }
+                    }
+                }
+            found:;
+            }
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, key);
+            int u = static_cast<int>(kmin >> 1);
+            float ru = (kmin & 1u) ? -M : M;
+            if (u < 0 || u >= a.K) {
+                if (lane == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+                u = 0;
+                ru = 0.0f;
+            }
+            const int cu = u / Q;
+            const bool more = nu + 1 < I;
+            float4 t[NCC];
+            if (more) {
+                const float4 *row = reinterpret_cast<const float4 *>(a.Cc + static_cast<size_t>(u) * Q) + lane;
+#pragma unroll
+                for (int ch = 0; ch < NCC; ++ch) t[ch] = __ldg(row + ch * 32);
+            }
+            const float c = gamma * ru * __ldg(a.Dkp + u);
+            log_entry(a, b, nu, more, lane, u, c, lu, lc);
+            if (!more) break;
+            const float2 nc = make_float2(-c, -c);
+            float mc[2] = {0.0f, 0.0f};
+            const unsigned hc = smap >> 8;
+            if (static_cast<unsigned>(cu) == hc) {
+#pragma unroll
+                for (int ch = 0; ch < NCC; ++ch) {
+                    const float2 x0 = __ffma2_rn(nc, make_float2(t[ch].x, t[ch].y), make_float2(H[ch].x, H[ch].y));
+                    const float2 x1 = __ffma2_rn(nc, make_float2(t[ch].z, t[ch].w), make_float2(H[ch].z, H[ch].w));
+                    H[ch] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    mc[0] = max3_abs(mc[0], x0.x, x0.y);
+                    mc[1] = max3_abs(mc[1], x1.x, x1.y);
+                }
+            } else {
+                const unsigned s = (smap >> (2 * cu)) & 3u;
+                float4 *Rs = myR + s * (NCC * 32);
+#pragma unroll
+                for (int ch = 0; ch < NCC; ++ch) {
+                    const float4 x = Rs[ch * 32];
+                    Rs[ch * 32] = H[ch];
+                    const float2 x0 = __ffma2_rn(nc, make_float2(t[ch].x, t[ch].y), make_float2(x.x, x.y));
+                    const float2 x1 = __ffma2_rn(nc, make_float2(t[ch].z, t[ch].w), make_float2(x.z, x.w));
+                    H[ch] = make_float4(x0.x, x0.y, x1.x, x1.y);
+                    mc[0] = max3_abs(mc[0], x0.x, x0.y);
+                    mc[1] = max3_abs(mc[1], x1.x, x1.y);
+                }
+                smap = ((smap & 0xffu & ~(3u << (2 * hc))) | (s << (2 * hc))) | (static_cast<unsigned>(cu) << 8);
+            }
+            const float mn = fmaxf(mc[0], mc[1]);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) m[cc] = cc == cu ? mn : m[cc];
+        }
+    }
+}
+
 
 // The same iterations with the block's projections in tensor memory: a CTA of
 // four warps allocates 64 TMEM columns, warp w keeps its block's R' in TMEM
@@ -1139,7 +1296,19 @@ static cudaError_t launch_sym_smem(const IterArgs &a, cudaStream_t st, int *laun
     return cudaGetLastError();
 }
 
-int iterate_sym_variants(int Kp) { return Kp == 2048 ? 3 : 2; }
+int iterate_sym_variants(int Kp) { return Kp == 2048 ? 4 : 2; }
+
+static cudaError_t launch_sym_hot(const IterArgs &a, cudaStream_t st, int *launches)
+{
+    constexpr int BPC = 3, Q = 512;
+    if (a.K != 4 * Q || a.Kp != a.K || !a.log_u || !a.log_c || !a.perm || !a.Cc || !a.Dkp)
+        return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * static_cast<size_t>(BPC) * 3 * Q;   // three class slots per block
+    const int grid = (a.n + BPC - 1) / BPC;                                   // one block per warp
+    iterate_sym_hot_kernel<64, BPC, 9><<<grid, 32 * BPC, smem, st>>>(a);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
 
 static cudaError_t launch_sym_tmem(const IterArgs &a, cudaStream_t st, int *launches)
 {
@@ -1162,6 +1331,7 @@ cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches
 {
     if (a.n <= 0) return cudaSuccess;
     if (variant == 2 && a.Kp == 2048) return launch_sym_tmem(a, st, launches);   // projections in tensor memory
+    if (variant == 3 && a.Kp == 2048) return launch_sym_hot(a, st, launches);    // hot class in registers
     if (variant == 1) {   // projections in shared memory
         switch (a.Kp) {
         case 512: return launch_sym_smem<16, 4, 12>(a, st, launches);

@@ -161,7 +161,8 @@ int iterate_cert_max_kp();
 // The parity-class form of the fp32 iterations (a.perm, a.Cc, a.Dkp set; Kp = K
 // in {512, 1024, 2048}): each update touches only the selected atom's class.
 // variant < iterate_sym_variants(Kp): 0 projections in registers, 1 in shared
-// memory (more blocks per SM), 2 (Kp = 2048) in tensor memory; identical results.
+// memory (more blocks per SM), 2 (Kp = 2048) in tensor memory, 3 (Kp = 2048) the
+// last-updated class in registers and the rest in shared memory; identical results.
 cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches, int variant = 0);
 int iterate_sym_variants(int Kp);
 // Folded separable transforms of the parity-class form (M, N in {16, 32};

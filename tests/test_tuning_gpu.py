@@ -88,11 +88,12 @@ def test_forced_variants_are_bitwise_identical(case):
 
 @pytest.mark.parametrize("n", [300, 4096])
 def test_parity_class_iteration_variants_are_bitwise_identical(n):
-    """Projections in registers, in shared memory and in tensor memory: the
-    same selections, coefficients and outputs, bit for bit."""
+    """Projections in registers, in shared memory, in tensor memory, and the
+    last-updated class in registers with the rest in shared memory: the same
+    selections, coefficients and outputs, bit for bit."""
     samples = np.stack([W.patch(32, 7600 + i % 997) for i in range(n)])
     res = []
-    for v in (0, 1, 2):
+    for v in (0, 1, 2, 3):
         ctx = _ctx(force=f"sym:={v}")
         try:
             plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 80, prec="bf16x6")
