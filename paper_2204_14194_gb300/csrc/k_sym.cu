@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
 // The same iterations with the class that was updated last ("hot") kept in
 // registers and the other three classes in three shared-memory slots per block
 // (6 KiB at K = 2048).  When the next selection falls in the hot class (about
-// a third of the iterations) the update touches no shared memory; otherwise
+// 30 % of the iterations) the update touches no shared memory; otherwise
 // the selected class is read from its slot, the hot class is written into that
 // slot chunk by chunk, and the selected class becomes the hot one.  A packed
 // map (2 bits per class, the hot class in bits 8-9) tells which slot holds
