@@ -86,8 +86,8 @@ def test_forced_variants_are_bitwise_identical(case):
         np.testing.assert_array_equal(a, b)
 
 
-@pytest.mark.parametrize("n", [300, 4096])
-def test_parity_class_iteration_variants_are_bitwise_identical(n):
+@pytest.mark.parametrize("n,I", [(300, 80), (4096, 80), (5, 33), (7, 1)])
+def test_parity_class_iteration_variants_are_bitwise_identical(n, I):
     """Projections in registers, in shared memory, in tensor memory, and the
     last-updated class in registers with the rest in shared memory: the same
     selections, coefficients and outputs, bit for bit."""
@@ -96,7 +96,7 @@ def test_parity_class_iteration_variants_are_bitwise_identical(n):
     for v in (0, 1, 2, 3):
         ctx = _ctx(force=f"sym:={v}")
         try:
-            plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, 80, prec="bf16x6")
+            plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, I, prec="bf16x6")
             assert plan.info().get("iterations") == "parity-classes"
             res.append(_run(ctx, plan, samples))
             plan.close()
