@@ -332,6 +332,17 @@ def test_table1_counts_reproduce_fig3():
         assert math.log10(ops) == pytest.approx(v, abs=6e-7), (curve, I)
 
 
+@pytest.mark.parametrize("M,N,K", [(32, 32, 2048), (64, 64, 4096), (16, 16, 512)])
+def test_per_iteration_count_is_the_slope_of_table1(M, N, K):
+    """The benchmark's per-iteration operation count is the I-slope of Table I's FaSE row
+    (which the Fig. 3 data pins); the parity-class count applies it to one class of K/4
+    atoms plus one comparison per class."""
+    slope = opcount.total(opcount.fase_ops(M, N, K, 101)) - opcount.total(opcount.fase_ops(M, N, K, 100))
+    assert opcount.fase_iteration_ops(M, N, K) == slope
+    q = opcount.total(opcount.fase_ops(M, N, K // 4, 2)) - opcount.total(opcount.fase_ops(M, N, K // 4, 1))
+    assert opcount.fase_iteration_ops_classes(M, N, K) == q + 4
+
+
 # ------------------------------------------------------------- 3-D blocks
 # The paper names the extension to video (three-dimensional areas) in its
 # conclusion; the method runs unchanged on the flattened area, only the
