@@ -275,8 +275,11 @@ se_status se_sync(se_ctx_t *ctx, void *cuda_stream);
  * slots and HBM budget free up, runs the iteration kernels in slices over
  * all admitted blocks (continuous batching: requests that arrive while
  * others run join at the next slice) and copies results into the caller's
- * out/sel buffers.  Returns SE_ERR_INVALID for a bad request,
- * SE_ERR_NOMEM if one block can never fit the budget. */
+ * out/sel buffers.  Each slot has its own stream and workspace.  The state it
+ * shares with the batch entry points is locked: tables, tuner, cost probes,
+ * graphs and the budget.  So requests may be submitted while other threads
+ * call those entry points on the same context.  Returns SE_ERR_INVALID for a
+ * bad request, SE_ERR_NOMEM if one block can never fit the budget. */
 se_status se_submit(se_ctx_t *ctx, const se_plan_t *plan, const se_request *req,
                     uint64_t *ticket);
 
