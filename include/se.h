@@ -233,9 +233,12 @@ se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n,
  * holds until exit; n is limited by it (for 32 x 32 blocks with K = 2048 and
  * I = 100: about 1800 with transform products, 1200 with dense split-bf16
  * products, 1000 in the fp64 form) and larger n returns SE_ERR_INVALID with
- * the limit in se_last_error().  The first call on a device looks up the
- * array's device address and should come before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU race, so
+ * the limit in se_last_error().  se_ctx_create looks up the array's device
+ * address on the context's device (which also loads the array, so its
+ * 16 MiB are held from context creation); the call itself allocates
+ * nothing and does no CUDA set-up.  Argument errors (complex or certified
+ * plans, iterations < 0) are reported whatever n is.  All calls share the
+ * array: calls whose work overlaps on the GPU race, so
  * serialise them.  The plan's table is built into plan memory on first use;
  * the autotuner times no candidates inside this call (it takes its kept
  * choice, else the first variant). */

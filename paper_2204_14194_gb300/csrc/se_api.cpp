@@ -829,6 +829,10 @@ se_status se_ctx_create(int device, size_t hbm_budget_bytes, se_ctx_t **out)
     }
     se_status s = dev_alloc(c, c->ws_err, sizeof(int));
     if (s != SE_OK) { delete c; return s; }
+    // the static scratch of se_extrapolate_noalloc: its address on this device
+    // (looked up here, with the device current, so that the calls need no set-up)
+    s = noalloc_scratch_address(&c->noalloc_scratch);
+    if (s != SE_OK) { delete c; return s; }
     e = cudaMemset(c->ws_err.ptr, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {

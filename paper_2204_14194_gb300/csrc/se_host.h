@@ -62,6 +62,10 @@ struct Workspace {
 // Record a failure for se_last_error() and return the status.
 se_status set_error(se_status s, const std::string &msg);
 
+// Device address (on the current device) of the static array that
+// se_extrapolate_noalloc uses as scratch (se_noalloc.cu).
+se_status noalloc_scratch_address(void **out);
+
 // Precision set-up derived from se_prec.
 struct PrecCfg {
     bool fp64 = false;
@@ -173,6 +177,7 @@ struct se_ctx_s {
     cudaEvent_t pipe_ev_in[kPipe] = {}, pipe_ev_done[kPipe] = {};
     bool pipe_ready = false;
     se::DevBuf ws_err;                    // device status word shared by all kernels
+    void *noalloc_scratch = nullptr;      // device address of se_extrapolate_noalloc's static array
 
     // per-stage timing (se_set_profiling)
     static constexpr int kStages = 5;

@@ -13,9 +13,12 @@
 // allocated when it was created.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// names a host-side stand-in).  So the first call on each device, with that
-// device current, looks the address up with cudaGetSymbolAddress and caches
-// it; that first call should therefore come before any stream capture.
+// names a host-side stand-in).  So se_ctx_create, with the context's device
+// current, looks the address up once with cudaGetSymbolAddress (through
+// noalloc_scratch_address below) and keeps it in the context.  The lookup
+// also makes the CUDA runtime load the module that holds the array, so the
+// 16 MiB are in place from context creation on, and the calls themselves do
+// no CUDA set-up of any kind.
 //
 // Every call shares the one array, and it keeps the last call's contents.
 // Nothing in it has to start at zero (every byte a call reads was written by
@@ -25,7 +28,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "se_host.h"
@@ -33,33 +35,25 @@
 namespace {
 
 constexpr size_t kScratchBytes = 16u << 20;   // 16 MiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
 size_t r256(size_t v) { return (v + 255) / 256 * 256; }
 
-se_status scratch_address(int device, unsigned char **out)
+}  // namespace
+
+// The device address of the static scratch on the current device; called by
+// se_ctx_create with the context's device current.
+se_status se::noalloc_scratch_address(void **out)
 {
-    if (device < 0 || device >= kMaxDevices)
-        return se::set_error(SE_ERR_INVALID, "device index out of range for the static scratch");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return se::set_error(SE_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") +
-                                                  cudaGetErrorString(e));
-        g_scratch_addr[device] = p;
-    }
-    *out = static_cast<unsigned char *>(g_scratch_addr[device]);
+    *out = nullptr;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(SE_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = p;
     return SE_OK;
 }
-
-}  // namespace
 
 extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
                                             const double *samples, double *out, int32_t *sel_idx,
@@ -68,14 +62,15 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     using namespace se;
     if (!ctx || !plan || n < 0) return set_error(SE_ERR_INVALID, "NULL argument or n < 0");
     if (plan->ctx != ctx) return set_error(SE_ERR_INVALID, "plan belongs to another context");
-    if (n == 0) return SE_OK;
-    if (!samples || !out) return set_error(SE_ERR_INVALID, "NULL samples or out");
     if (iterations < 0) return set_error(SE_ERR_INVALID, "iterations < 0");
     se_plan_s *pl = const_cast<se_plan_s *>(plan);
     if (pl->cplx) return set_error(SE_ERR_INVALID, "se_extrapolate_noalloc: complex plans use se_extrapolate_strided");
     if (pl->certified)
         return set_error(SE_ERR_INVALID, "se_extrapolate_noalloc: certified plans recompute flagged blocks "
                                          "in fp64, which needs workspace; use se_extrapolate_strided");
+    if (n == 0) return SE_OK;
+    if (!samples || !out) return set_error(SE_ERR_INVALID, "NULL samples or out");
+    if (!ctx->noalloc_scratch) return set_error(SE_ERR_CUDA, "the context has no static scratch address");
     const int I = iterations ? iterations : pl->desc.iterations;
     const bool fp64 = pl->pc.fp64;
     const int Kp = pl->Kp;
@@ -96,9 +91,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(SE_ERR_CUDA, "cudaSetDevice failed");
     NoTuneScope no_tune;   // no timing runs (and no events) inside this call
-    unsigned char *base = nullptr;
-    se_status s = scratch_address(ctx->device, &base);
-    if (s != SE_OK) return s;
+    unsigned char *base = static_cast<unsigned char *>(ctx->noalloc_scratch);
     BlockDesc *d_desc = reinterpret_cast<BlockDesc *>(base);
     void *d_x = base + desc_b;
     void *d_r0 = base + desc_b + x_b;
@@ -108,7 +101,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
     const StridedSpec spec{samples, out, sel_idx, sel_coef, I, 1};
     cudaError_t e = launch_fill_desc(d_desc, n, spec, pl->MN, st);
     if (e != cudaSuccess) return set_error(SE_ERR_CUDA, std::string("descriptors: ") + cudaGetErrorString(e));
-    s = ensure_tables(ctx, pl, st);
+    se_status s = ensure_tables(ctx, pl, st);
     if (s != SE_OK) return s;
 
     std::string why;
