@@ -43,6 +43,11 @@ TRAFFIC_ITERATE = {}
 SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>", 2: "iterate_sym_tmem_kernel",
               3: "iterate_sym_hot_kernel<64,3,9>"}
 TRAFFIC_ITERATE_SYM = {1: 36.91e6}
+# On-chip roofs of the parity-class iteration kernel as ncu measured them per
+# launch shape (fractions of peak; see profiles/).
+ONCHIP_ITERATE_SYM = {
+    1: {"l1tex_data_pipe_busy": 0.799, "source": "ncu --set full, profiles/iterate_sym_img512_4096blk.md"},
+}
 
 
 def _dist():
@@ -125,19 +130,54 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
-def cpu_baseline(wl, n_blocks: int, threads: int = 0):
-    """Time the FP64 oracle (Alg. 1) on the host cores over the first n_blocks blocks."""
+def _oracle_setup(wl):
     import oracle as O
     phi = O.dict_dct_wht(wl.M, wl.N)
-    dup = O.find_duplicates(phi)
-    w = O.weights(wl.M, wl.N, wl.rho_hat, wl.support)
+    return O, phi, O.find_duplicates(phi), O.weights(wl.M, wl.N, wl.rho_hat, wl.support)
+
+
+def cpu_baseline(wl, n_blocks: int, threads: int = 0, margins: bool = False):
+    """Time the FP64 oracle's original SE (Alg. 1) on the host cores over the
+    first n_blocks blocks: (blocks/s, cores, seconds[, (out, u, c, margin)])."""
+    O, phi, dup, w = _oracle_setup(wl)
     s = np.ascontiguousarray(wl.samples[:n_blocks])
     cores = threads if threads > 0 else O.max_threads()
     t0 = time.perf_counter()
-    out, u, c, st = O.se_original_batch(phi, w, s, wl.gamma, wl.iterations, dup, nthreads=cores)
+    res = O.se_original_batch(phi, w, s, wl.gamma, wl.iterations, dup, nthreads=cores, margins=margins)
     dt = time.perf_counter() - t0
-    assert st == 0
+    assert res[-1] == 0
+    if margins:
+        return n_blocks / dt, cores, dt, res[:4]
     return n_blocks / dt, cores, dt
+
+
+class FaseBaseline:
+    """The oracle's fast form on the host cores: Alg. 2 (the tables, once per
+    pattern, timed on its own) and Alg. 3 over the blocks (timed per batch)."""
+
+    def __init__(self, wl, threads: int = 0):
+        self.O, self.phi, self.dup, self.w = _oracle_setup(wl)
+        self.wl = wl
+        self.cores = threads if threads > 0 else self.O.max_threads()
+        t0 = time.perf_counter()
+        self.C, self.D = self.O.fase_tables(self.phi, self.w)
+        self.tables_s = time.perf_counter() - t0
+
+    def run(self, n_blocks: int):
+        """Alg. 3 over the first n_blocks blocks; returns (blocks/s, seconds)."""
+        s = np.ascontiguousarray(self.wl.samples[:n_blocks])
+        t0 = time.perf_counter()
+        _out, _u, _c, st = self.O.fase_batch(self.phi, self.w, self.C, self.D, s, self.wl.gamma,
+                                             self.wl.iterations, self.dup, nthreads=self.cores)
+        dt = time.perf_counter() - t0
+        assert st == 0
+        return n_blocks / dt, dt
+
+
+def _psnr_sub(est, truth, loss):
+    """PSNR pooled over the loss pixels of all blocks (10 log10(255^2 / MSE))."""
+    d = est[:, loss] - truth[:, loss]
+    return 10.0 * np.log10(255.0 ** 2 / float(np.mean(d * d)))
 
 
 def calibrated_sample(wl, seconds: float) -> int:
@@ -147,29 +187,33 @@ def calibrated_sample(wl, seconds: float) -> int:
 
 
 def run_reference(args):
+    """The reference arm: the oracle's fast form (Alg. 2 + 3, FP64 C) on all host
+    cores, the fair CPU baseline; each step is the whole 4096-block batch
+    through Alg. 3, the tables (Alg. 2) built once per pattern beforehand and
+    listed separately."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     from paper_2204_14194_gb300 import workloads as W
     wl = W.config2()
-    # each step a bounded sample: the whole run (warm-up steps at 1/8 size) takes about 2 minutes
-    sample = args.ref_sample or calibrated_sample(wl, 120.0 / (args.steps + args.warmup / 8.0))
+    nb = min(args.ref_sample or wl.B, wl.B)
+    fb = FaseBaseline(wl)
     for _ in range(args.warmup):
-        cpu_baseline(wl, max(1, sample // 8))
-    vals = []
-    cores = 0
+        fb.run(max(1, nb // 8))
+    secs = []
     for _ in range(args.steps):
-        v, cores, _dt = cpu_baseline(wl, sample)
-        vals.append(v)
-    value = statistics.mean(vals)
+        secs.append(fb.run(nb)[1])
+    value = nb * args.steps / sum(secs)
+    which = f"all {wl.B} blocks" if nb == wl.B else f"first {nb} of the {wl.B} blocks"
+    sample = f"{which} per step, FaSE (Alg. 3) in fp64 C; tables (Alg. 2) built once, {fb.tables_s:.2f} s"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(secs) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "blocks": 4096, "sample_blocks_per_step": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {sample} of the 4096 blocks per step, original SE (Alg. 1), fp64 C"},
+        "config": {"workload": WORKLOAD, "blocks": wl.B, "blocks_per_step": nb, "form": "fase (Alg. 2 + 3)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": fb.cores, "kind": "oracle",
+                         "sample": sample, "tables_s": fb.tables_s},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -238,6 +282,34 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(step_ms))
     value = job_throughput(n, ws, args.steps, total_ms / 1000.0)
 
+    # ---- sustained pass: the same step back to back for about --sustain-s
+    # seconds (L2 flushed between steps), with its own clock record, so that
+    # the clocks are sampled many times while the GPU is busy
+    sustained = None
+    if args.sustain_s > 0:
+        sus_steps = max(1, int(args.sustain_s * 1000.0 / max(total_ms / args.steps + 0.05, 1e-3)))
+        sus_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(sus_steps)]
+        clocks_s = ClockSampler(local)
+        clocks_s.start()
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(sus_steps):
+                flush.fill_(float(i))
+                sus_ev[i][0].record(stream)
+                step()
+                sus_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        clk_s = clocks_s.stop()
+        ctx.sync(stream)
+        sus_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in sus_ev))
+        sustained = {"steps": sus_steps, "seconds_wall": wall, "value": job_throughput(n, ws, sus_steps, sus_ms / 1000.0),
+                     "ms_per_step": sus_ms / sus_steps, "clocks": clk_s,
+                     "timing": "CUDA events around each step; the L2 flush between steps is outside them"}
+
     # ---- per-stage device times (CUDA events around each stage on the launching
     # stream), in a separate pass so that the events do not touch the timed steps
     prof_steps = min(args.steps, 100)
@@ -299,10 +371,12 @@ def run_ours(args):
         return 10.0 * np.log10(255.0 ** 2 / float(np.mean(d * d)))
 
     # ---- roofline of the dominant kernel (the iteration kernel, Alg. 3).  Its
-    # table C (16 MiB) stays in L2, so it is bound by arithmetic issue, not
-    # HBM: achieved = Table-I FaSE operations of the iterations (I*(5K + 2MN
-    # + 1) per block) / average launch time, peak = fp32 CUDA-core rate
-    # (152 SMs x 128 lanes x 2 flops x max SM clock).
+    # table stays in L2 and its projections on chip, so HBM does not bind it:
+    # achieved = the kernel's own Table-I operations (scores, maximum,
+    # coefficient, update: I*(5K/4 + 5) per block with parity classes) /
+    # average launch time, against the fp32 CUDA-core rate (152 SMs x 128
+    # lanes x 2 flops x max SM clock) as context; the binding roofs are the
+    # on-chip data paths, whose busy fractions come from the ncu capture.
     hbm_peak, tc_peak, peak_kind = measured_peaks()
     it_ms, it_n = stages["iterate"]
     it_avg_s = it_ms / max(it_n, 1) / 1000.0
@@ -310,15 +384,17 @@ def run_ours(args):
     info = plan.info()
     variant = max(ctx.tuned_variant("iterate:f32:%d" % K), 0)
     if info.get("iterations") == "parity-classes":
-        # the kernel's own work: a quarter of the atoms per iteration (one class)
-        ops = n * I * opcount.fase_iteration_ops_classes(M, N, K, classes=4)
+        # the kernel's own work: scores, maximum, coefficient and update of one
+        # class (a quarter of the atoms) per iteration; the model accumulate of
+        # eq. (9) runs in the model kernel
+        ops = n * I * opcount.fase_select_update_ops(M, N, K, classes=4)
         nb = 1 << max(n - 1, 0).bit_length()
         sv = max(ctx.tuned_variant("sym:f32:%d:n%d" % (K, nb)), 0)
         it_kernel, it_traffic = SYM_SHAPES.get(sv, "iterate_sym kernel") + " (parity classes)", \
             TRAFFIC_ITERATE_SYM.get(sv)
         row_bytes = K // 4 * 4
     else:
-        ops = n * I * opcount.fase_iteration_ops(M, N, K)
+        ops = n * I * opcount.fase_select_update_ops(M, N, K)
         row_bytes = K * 4
         if args.prec == "certified":   # one launch shape; the stage also holds the fp64 recomputation
             it_kernel, it_traffic = "iterate_f32_kernel<1,64,4> certified form + fp64 recomputation", None
@@ -330,13 +406,10 @@ def run_ours(args):
                 "traffic": it_traffic,
                 "peak_kind": "derived: 152 SMs x 128 fp32 lanes x 2 flops x 2.07 GHz",
                 "l2_read_GBps": n * (I - 1) * row_bytes / it_avg_s / 1e9, "plan": info}
-    if info.get("iterations") == "parity-classes" and sv in (1, 3):
-        # the on-chip roof the kernel actually meets: per block-iteration the row
-        # (L2 -> registers) and one class of R' read and written in shared memory
-        onchip = n * (I - 1) * (row_bytes + 2 * K // 4 * 4) / it_avg_s / 1e9
-        lsu_peak = 152 * 128 * 2.07e9 / 1e9
-        roofline["onchip"] = {"achieved": onchip, "peak": lsu_peak, "unit": "GB/s", "frac": onchip / lsu_peak,
-                              "peak_kind": "derived: 152 SMs x 128 B per cycle (L1/shared data pipe) x 2.07 GHz"}
+    if info.get("iterations") == "parity-classes" and sv in ONCHIP_ITERATE_SYM:
+        # the roofs the kernel meets on chip, as ncu measured them for this
+        # launch shape (busy fraction of the L1/shared data pipe, L2 throughput)
+        roofline["onchip"] = dict(ONCHIP_ITERATE_SYM[sv])
     pr_ms, pr_n = stages["projections"]
     pr_avg_s = pr_ms / max(pr_n, 1) / 1000.0
     na = int(np.sum(wl.support))
@@ -381,11 +454,39 @@ def run_ours(args):
             "peak_kind": peak_kind + " bf16 dense"}
 
     cpu = None
+    vs_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
+        # original SE (Alg. 1) on a bounded sample, with its tie margins: the
+        # parity of the measured outputs against the oracle on those blocks
         sample = args.ref_sample or calibrated_sample(wl, 15.0)
-        v, cores, dt = cpu_baseline(wl, sample)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {sample} of the 4096 blocks, original SE (Alg. 1), fp64 C, {dt:.1f} s"}
+        v_se, cores, dt, (ro, ru, rc, rm) = cpu_baseline(wl, sample, margins=True)
+        tie_free, errs, same_to_tie = 0, [], 0
+        for b in range(sample):
+            bad = np.nonzero(rm[b] <= 1e-4)[0]
+            t = int(bad[0]) if len(bad) else I
+            tie_free += t == I
+            same_to_tie += bool(np.all(u_m[b, :t] == ru[b, :t]))
+            if t:
+                ref = rc[b, :t]
+                errs.append(float(np.max(np.abs(c_m[b, :t] - ref) /
+                                         np.maximum(np.abs(ref), 1e-12 * np.max(np.abs(ref))))))
+        lm = wl.support == 0
+        d_or = ro[:, lm] - wl.samples[:sample][:, lm]
+        vs_oracle = {"blocks": sample, "tie_margin": 1e-4, "tie_free_frac": tie_free / sample,
+                     "index_identical_to_first_near_tie_frac": same_to_tie / sample,
+                     "max_rel_coef_err_to_first_near_tie": max(errs) if errs else 0.0,
+                     "psnr_db": _psnr_sub(out_m[:sample], wl.samples[:sample], lm),
+                     "psnr_oracle_db": 10.0 * np.log10(255.0 ** 2 / float(np.mean(d_or * d_or))),
+                     "what": "the fp32 results of the timed steps against the FP64 oracle (Alg. 1) "
+                             "on the first blocks of the batch"}
+        # the fast form (Alg. 2 + 3) on all cores, the fair CPU baseline
+        fb = FaseBaseline(wl)
+        v_fase, fase_s = fb.run(n)
+        cpu = {"value": v_fase, "unit": UNIT, "cores": fb.cores, "kind": "oracle",
+               "sample": f"FaSE (Alg. 3, fp64 C) over all {n} blocks, {fase_s:.2f} s; tables (Alg. 2) "
+                         f"once per pattern, {fb.tables_s:.2f} s, not counted; original SE (Alg. 1) "
+                         f"over the first {sample} blocks, {dt:.1f} s",
+               "value_fase": v_fase, "value_se": v_se, "tables_s": fb.tables_s}
 
     sorted_ms = sorted(step_ms)
     line = {
@@ -413,8 +514,17 @@ def run_ours(args):
                          "index_sequence_identical_frac": float(np.mean(same)),
                          "max_rel_coef_err_before_first_divergence": float(max(rel)) if rel else 0.0,
                          "psnr_db": _psnr(out_m), "psnr_fp64_db": _psnr(o64)},
+        "vs_oracle": vs_oracle,
         "cpu_baseline": cpu,
     }
+    if sustained is not None:
+        line["sustained"] = sustained
+    if rank == 0 and args.secondary and args.prec != "fp64":
+        # secondary measurements recorded in the same line: the Gaussian-dictionary
+        # workload and a short serving run at the mixed-size request stream
+        line["gauss1080"] = secondary_gauss1080(args.prec)
+        line["serving"] = serve_measure(args.rate, args.serve_s, 0.5, args.gauss_share, args.budget_gb,
+                                        args.prec)
     if args.prec == "certified":
         cs = ctx.cert_stats()
         line["certified"] = {"blocks": cs["blocks"], "recomputed_in_fp64": cs["recomputed"],
@@ -571,33 +681,34 @@ def run_single(args):
     return 0
 
 
-def run_serve(args):
+def serve_measure(rate: float, duration: float, warm_s: float, gauss_share: float, budget_gb: float,
+                  prec: str = "bf16x6"):
     """Serving measurement: open-loop Poisson arrivals of single-block requests of
     mixed area size (16/32/64), DCT u WHT or Gaussian dictionaries with K = 2MN,
     random per-request masks, I in [100, 300], under an HBM budget; latency is
-    completion minus the scheduled arrival time."""
+    completion minus the scheduled arrival time.  Returns the result as a dict."""
     import threading as th
     from paper_2204_14194_gb300 import binding as B
     from paper_2204_14194_gb300 import workloads as W
 
     rng = np.random.default_rng(5)
-    ctx = B.Context(0, hbm_budget_bytes=int(args.budget_gb * (1 << 30)))
+    ctx = B.Context(0, hbm_budget_bytes=int(budget_gb * (1 << 30)))
     plans = {}
     for L in (16, 32, 64):
-        plans[("dct_wht", L)] = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, 300, prec=args.prec)
-        if args.gauss_share > 0:
-            plans[("gauss", L)] = ctx.plan(L, L, "numeric", 2 * L * L, 0.8, 0.5, 300, prec=args.prec,
+        plans[("dct_wht", L)] = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, 300, prec=prec)
+        if gauss_share > 0:
+            plans[("gauss", L)] = ctx.plan(L, L, "numeric", 2 * L * L, 0.8, 0.5, 300, prec=prec,
                                            dictionary=W.gaussian_dictionary(2 * L * L, L, L, 900 + L))
     pool = 256
     samp = {L: [W.patch(L, 50000 + 1000 * L + i) for i in range(pool)] for L in (16, 32, 64)}
     mrng = np.random.default_rng(6)
     masks = {L: [W.rect_support(L, L, mrng) if i % 2 else W.holes_support(L, L, mrng) for i in range(pool)]
              for L in (16, 32, 64)}
-    total_t = args.warm_s + args.duration
-    n = int(args.rate * total_t)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n))
+    total_t = warm_s + duration
+    n = int(rate * total_t)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     sizes = rng.choice([16, 32, 64], size=n)
-    gauss = rng.random(n) < args.gauss_share
+    gauss = rng.random(n) < gauss_share
     iters = rng.integers(100, 301, size=n)
     pick = rng.integers(0, pool, size=n)
     outs = {L: np.empty((pool, L, L)) for L in (16, 32, 64)}   # results are not checked here
@@ -632,20 +743,124 @@ def run_serve(args):
         done += 1
     th_sub.join()
     t_end = time.perf_counter()
-    keep = arrivals >= args.warm_s
+    keep = arrivals >= warm_s
     L_ms = lat[keep] * 1000.0
-    line = {"metric": "serving latency and throughput", "workload":
-            "poisson %.0f req/s, %.0f s (+%.0f s warm-up), areas 16/32/64, K = 2MN, %d%% Gaussian, "
-            "per-request masks, I in [100,300], budget %.0f GB" % (args.rate, args.duration, args.warm_s,
-                                                                  100 * args.gauss_share, args.budget_gb),
-            "offered_rate": args.rate, "requests": int(keep.sum()),
-            "throughput_blocks_per_s": done / (t_end - start),
-            "latency_ms": {"p50": float(np.percentile(L_ms, 50)), "p99": float(np.percentile(L_ms, 99)),
-                           "max": float(L_ms.max())},
-            "serving_slices": ctx.stats()["serving_slices"], "precision": args.prec}
-    print(json.dumps(line), flush=True)
+    thr = done / (t_end - start)
+    res = {"workload": "poisson %.0f req/s, %.1f s (+%.1f s warm-up), areas 16/32/64, K = 2MN, %d%% Gaussian, "
+                       "per-request masks, I in [100,300], budget %.0f GB" % (rate, duration, warm_s,
+                                                                             100 * gauss_share, budget_gb),
+           "offered_rate": rate, "requests": int(keep.sum()),
+           "throughput_blocks_per_s": thr,
+           "latency_ms": {"p50": float(np.percentile(L_ms, 50)), "p99": float(np.percentile(L_ms, 99)),
+                          "max": float(L_ms.max())},
+           "sustained": bool(thr >= 0.97 * rate),
+           "serving_slices": ctx.stats()["serving_slices"], "precision": prec}
     ctx.close()
+    return res
+
+
+def run_serve(args):
+    """The serving measurement alone (--workload serve)."""
+    res = serve_measure(args.rate, args.duration, args.warm_s, args.gauss_share, args.budget_gb, args.prec)
+    print(json.dumps({"metric": "serving latency and throughput", **res}), flush=True)
     return 0
+
+
+def secondary_gauss1080(prec: str, steps: int = 5, warmup: int = 3, oracle_blocks: int = 24):
+    """The 1920x1080 Gaussian-dictionary workload (8160 blocks of 32 x 32, K = 4096
+    seeded Gaussian atoms, I = 200) as a secondary measurement: device-timed
+    blocks/s with the table rebuilt every step and L2 flushed between steps,
+    tensor-core throughput of the two product stages (split-bf16 products, six
+    per product), and the error against the FP64 oracle (Alg. 1) on the first
+    blocks."""
+    import torch
+    from paper_2204_14194_gb300 import binding as B
+    from paper_2204_14194_gb300 import workloads as W
+
+    wl = W.config3()
+    n, I, K = wl.B, wl.iterations, 4096
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream()
+    plan = ctx.plan(32, 32, "numeric", K, wl.rho_hat, wl.gamma, I, prec=prec, dictionary=wl.dictionary)
+    s_d = torch.from_numpy(wl.samples).cuda()
+    out = torch.empty_like(s_d)
+    u = torch.empty((n, I), dtype=torch.int32, device="cuda")
+    c = torch.empty((n, I), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        plan.reset_tables()
+        plan.extrapolate_strided(s_d, out, u, c, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.fill_(1.0)
+            step()
+    ctx.sync(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+    ctx.sync(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    ctx.set_profiling(True)
+    ctx.stage_times(reset=True)
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))
+            step()
+    ctx.sync(stream)
+    stages = {k: v[0] / steps for k, v in ctx.stage_times(reset=True).items()}
+    ctx.set_profiling(False)
+    o_m, u_m, c_m = out.cpu().numpy(), u.cpu().numpy(), c.cpu().numpy()
+    na = int(np.sum(wl.support))
+    _hbm, tc_peak, peak_kind = measured_peaks()
+    npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(prec, 0)
+    tensor = None
+    if npairs and stages.get("projections", 0) > 0 and stages.get("tables", 0) > 0:
+        proj = 2.0 * K * n * na * npairs / (stages["projections"] / 1e3) / 1e12
+        tab = 1.0 * K * (K + 1) * na * npairs / (stages["tables"] / 1e3) / 1e12
+        tensor = {"projections_tflops": proj, "tables_tflops": tab, "peak": tc_peak,
+                  "projections_frac": proj / tc_peak, "tables_frac": tab / tc_peak,
+                  "peak_kind": peak_kind + " bf16 dense",
+                  "flops": "split products counted: 2 K |A| n x %d (eq. 12), K (K + 1) |A| x %d "
+                           "(eq. 16, the symmetric half)" % (npairs, npairs)}
+    # error against the FP64 oracle on the first blocks
+    import oracle as O
+    phi = np.ascontiguousarray(wl.dictionary, dtype=np.float64)
+    dup = O.find_duplicates(phi)
+    w = O.weights(32, 32, wl.rho_hat, wl.support)
+    ro, ru, rc, rm, st = O.se_original_batch(phi, w, np.ascontiguousarray(wl.samples[:oracle_blocks]),
+                                             wl.gamma, I, dup, margins=True)
+    assert st == 0
+    tie_free, errs, same = 0, [], 0
+    for b in range(oracle_blocks):
+        bad = np.nonzero(rm[b] <= 1e-4)[0]
+        t = int(bad[0]) if len(bad) else I
+        tie_free += t == I
+        same += bool(np.all(u_m[b, :t] == ru[b, :t]))
+        if t:
+            ref = rc[b, :t]
+            errs.append(float(np.max(np.abs(c_m[b, :t] - ref) /
+                                     np.maximum(np.abs(ref), 1e-12 * np.max(np.abs(ref))))))
+    pm = wl.psnr_mask
+    d_g = (o_m[:oracle_blocks] - wl.samples[:oracle_blocks])[pm[:oracle_blocks]]
+    d_o = (ro - wl.samples[:oracle_blocks])[pm[:oracle_blocks]]
+    res = {"workload": wl.name, "blocks": n, "value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "precision": prec, "stages_ms_per_step": stages, "tensor": tensor,
+           "vs_oracle": {"blocks": oracle_blocks, "tie_margin": 1e-4, "tie_free_frac": tie_free / oracle_blocks,
+                         "index_identical_to_first_near_tie_frac": same / oracle_blocks,
+                         "max_rel_coef_err_to_first_near_tie": max(errs) if errs else 0.0,
+                         "psnr_db": 10.0 * np.log10(255.0 ** 2 / float(np.mean(d_g * d_g))),
+                         "psnr_oracle_db": 10.0 * np.log10(255.0 ** 2 / float(np.mean(d_o * d_o)))},
+           "timing": "CUDA events per step, table rebuilt every step, L2 flushed between steps"}
+    plan.close()
+    ctx.close()
+    return res
 
 
 def main():
@@ -661,8 +876,14 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=0,
                     help="oracle blocks per CPU measurement (0: sized from a calibration run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sustain-s", type=float, default=1.5,
+                    help="seconds of the sustained pass after the timed steps (0: none)")
     ap.add_argument("--rate", type=float, default=50000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: measured seconds")
+    ap.add_argument("--serve-s", type=float, default=2.0,
+                    help="serving seconds measured inside the headline run (its 'serving' key)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the Gaussian-dictionary and serving measurements of the headline run")
     ap.add_argument("--warm-s", type=float, default=1.0, help="serving: warm-up seconds")
     ap.add_argument("--gauss-share", type=float, default=0.5, help="serving: share of Gaussian dictionaries")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM budget")

@@ -45,3 +45,14 @@ def fase_iteration_ops_classes(M: int, N: int, K: int, classes: int = 4) -> int:
     the maximum touch K / classes atoms per iteration, plus one comparison per
     class for the overall maximum."""
     return 5 * (K // classes) + classes + 2 * M * N + 1
+
+
+def fase_select_update_ops(M: int, N: int, K: int, classes: int = 1) -> int:
+    """The part of the per-iteration count that the iteration kernels execute:
+    scores, maximum, coefficient and the update of eq. (20), without the 2MN
+    operations of the model accumulate g += c phi_u (eq. 9), which the model
+    kernel evaluates once from the selection log.  With parity classes the
+    scores and the update touch K / classes atoms, plus one comparison per class."""
+    if classes == 1:
+        return fase_iteration_ops(M, N, K) - 2 * M * N
+    return fase_iteration_ops_classes(M, N, K, classes) - 2 * M * N

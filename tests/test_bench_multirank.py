@@ -58,8 +58,9 @@ def test_single_rank_helpers():
 
 
 def test_reference_arm_line_on_rank0():
-    """Rank 0 of the reference arm times the oracle and prints one JSON line with the GPU
-    arm's metric, unit and workload, an e2e object with no host copies and a cpu_baseline."""
+    """Rank 0 of the reference arm times the oracle's fast form (Alg. 2 + 3) and prints one
+    JSON line with the GPU arm's metric, unit and workload, an e2e object with no host
+    copies and a cpu_baseline that lists the table time separately."""
     import json
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0", OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
@@ -78,4 +79,5 @@ def test_reference_arm_line_on_rank0():
                         "d2h_bytes_per_step": 0}
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
-    assert "2 of the 4096 blocks" in cb["sample"]
+    assert "2 of the 4096 blocks" in cb["sample"] and "FaSE" in cb["sample"]
+    assert cb["tables_s"] > 0

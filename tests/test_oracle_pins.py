@@ -341,6 +341,13 @@ def test_per_iteration_count_is_the_slope_of_table1(M, N, K):
     assert opcount.fase_iteration_ops(M, N, K) == slope
     q = opcount.total(opcount.fase_ops(M, N, K // 4, 2)) - opcount.total(opcount.fase_ops(M, N, K // 4, 1))
     assert opcount.fase_iteration_ops_classes(M, N, K) == q + 4
+    # the iteration kernels' own share: Table I's per-iteration count without the
+    # model accumulate (one multiply and one add per area pixel, eq. 9)
+    model = opcount.total(opcount.fase_ops(M, N, K, 101)) - opcount.total(opcount.fase_ops(M, N, K, 100)) \
+        - (opcount.total(opcount.fase_ops(1, 1, K, 101)) - opcount.total(opcount.fase_ops(1, 1, K, 100)))
+    assert model == 2 * (M * N - 1)
+    assert opcount.fase_select_update_ops(M, N, K) == 5 * K + 1
+    assert opcount.fase_select_update_ops(M, N, K, classes=4) == 5 * (K // 4) + 4 + 1
 
 
 # ------------------------------------------------------------- 3-D blocks
