@@ -1305,7 +1305,12 @@ static cudaError_t launch_sym_hot(const IterArgs &a, cudaStream_t st, int *launc
         return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * static_cast<size_t>(BPC) * 3 * Q;   // three class slots per block
     const int grid = (a.n + BPC - 1) / BPC;                                   // one block per warp
-    iterate_sym_hot_kernel<64, BPC, 9><<<grid, 32 * BPC, smem, st>>>(a);
+    auto kern = iterate_sym_hot_kernel<64, BPC, 9>;
+    // the carveout of the other parity-class forms: batches that run side by side on
+    // several streams (the chunks of a host-buffer call) can then share the SMs
+    cudaError_t e = prefer_max_shared(reinterpret_cast<const void *>(kern));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 32 * BPC, smem, st>>>(a);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

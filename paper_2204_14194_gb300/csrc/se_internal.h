@@ -115,6 +115,10 @@ cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_
 cudaError_t launch_grid(const void *kern, int threads, size_t smem, int want, int *grid, bool max_shared = false);
 // SMs of the current device (cached).
 int sm_count();
+// Ask for the largest shared-memory carveout for a kernel (once per device):
+// kernels launched side by side on several streams share SMs only when their
+// carveouts agree.
+cudaError_t prefer_max_shared(const void *kern);
 
 // ------------------------------------------------------------------ iterate
 struct IterArgs {

@@ -17,6 +17,7 @@ std::mutex g_mu;
 std::map<int, int> g_sms;                                        // device -> SMs
 std::map<std::tuple<int, const void *>, size_t> g_smem;          // (device, kernel) -> limit set
 std::map<std::tuple<int, const void *, int, size_t>, int> g_occ; // -> CTAs per SM
+std::map<std::tuple<int, const void *>, bool> g_carve;           // (device, kernel) -> carveout set
 
 }  // namespace
 
@@ -53,6 +54,19 @@ cudaError_t launch_grid(const void *kern, int threads, size_t smem, int want, in
     }
     const int cap = s->second * o->second;
     *grid = want < 1 ? 1 : (want < cap ? want : cap);
+    return cudaSuccess;
+}
+
+cudaError_t prefer_max_shared(const void *kern)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_carve.count({dev, kern})) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    g_carve[{dev, kern}] = true;
     return cudaSuccess;
 }
 
