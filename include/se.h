@@ -154,7 +154,8 @@ typedef struct {
 typedef struct {
     const double *samples;    /* M x N samples s; values on B are never read */
     const uint8_t *support;   /* M x N mask (1 = A, 0 = B), or NULL = the plan's pattern */
-    double *out;              /* M x N result: s on A, the model g on B (Alg. 1/3 last step) */
+    double *out;              /* M x N result: s on A, the model g on B (Alg. 1/3 last step);
+                                 out may be samples (in place: only B is written) */
     int32_t *sel_idx;         /* optional [iterations] selected atom index u per iteration */
     double *sel_coef;         /* optional [iterations] coefficient c_u per iteration */
     int iterations;           /* 0 = the plan's default I */
@@ -214,7 +215,8 @@ se_status se_extrapolate_batch(se_ctx_t *ctx, const se_plan_t *plan, int n,
 /* Convenience form of se_extrapolate_batch for n blocks stored contiguously
  * on the device: samples[n][M][N], out[n][M][N], optional sel_idx /
  * sel_coef [n][iterations] (iterations = 0: the plan's I), all blocks on
- * the plan's pattern. */
+ * the plan's pattern.  out may equal samples: then the call works in place,
+ * reading only the support samples and writing only the loss areas. */
 se_status se_extrapolate_strided(se_ctx_t *ctx, const se_plan_t *plan, int n,
                                  const double *samples, double *out,
                                  int32_t *sel_idx, double *sel_coef,
@@ -252,8 +254,11 @@ se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
  * read and written by the kernels directly over the host link, so the transfers
  * overlap the computation; other (pageable) buffers are copied through the
  * context's device buffer in chunks of at least 512 blocks, the copies of one
- * chunk overlapping the computation of the others.  Serialised with the other
- * batch calls of the context. */
+ * chunk overlapping the computation of the others.  out may equal samples (in
+ * place): each block's loss area is overwritten with its extrapolation, and
+ * with pinned buffers only the support samples cross the link inwards and
+ * only the loss areas outwards (half the bytes of separate buffers for a
+ * quarter loss area).  Serialised with the other batch calls of the context. */
 se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
                               const double *samples, double *out,
                               int32_t *sel_idx, double *sel_coef, int iterations);
@@ -266,6 +271,14 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
  * stream returns SE_ERR_CUDA with the message and clears the word.  For tests
  * and health checks of a deployment. */
 se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_stream);
+
+/* Applies, on `cuda_stream`, the fp64 -> fp32 conversion that the projection
+ * kernels use for the samples (eq. 12 in the fp32 form: w s with s rounded
+ * to fp32) to n device doubles `in`, writing n device floats `out`.  The
+ * conversion rounds to nearest, ties to even, as IEEE 754 defines it; most
+ * values take an integer-pipe path, so this lets a test check it bit for bit.
+ * SE_ERR_INVALID for NULL buffers with n > 0 or n < 0. */
+se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, int n, void *cuda_stream);
 
 /* Wait for the work this context queued on `cuda_stream` and report
  * errors that its kernels recorded in the device status word (SE_ERR_CUDA
@@ -359,8 +372,11 @@ se_status se_cert_stats(se_ctx_t *ctx, uint64_t *blocks, uint64_t *recomputed);
  * weighting function is symmetric and the atoms are DCT / WHT rows, see
  * k_sym.cu; "general" otherwise; "complex"; "fp64"), "projections=split-tf32"
  * when a 32 x 32 parity-class plan forms eq. (12) on the tensor cores, and
- * "certified" for certified plans.  Example: "products=transform table=table
- * iterations=parity-classes projections=split-tf32". */
+ * "certified" for certified plans, and "columns=f16x3" once a batch with
+ * per-block masks has prepared the lazy columns of eq. (16) of a numeric
+ * dictionary in the fp32 form as products of two-part fp16 splits (three
+ * partial products, about 2^-21 relative).  Example: "products=transform
+ * table=table iterations=parity-classes projections=split-tf32". */
 se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len);
 /* The variant the autotuner keeps for a shape key (e.g. "iterate:f32:2048",
  * "sep:32x32:t2:f32", "sym:f32:2048:n4096" for the parity-class iterations of

@@ -31,7 +31,7 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
            "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats", "se_plan_info",
-           "se_check_wait_timeout"]
+           "se_check_wait_timeout", "se_check_sample_conversion"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
             "se_check_wait_timeout": ([vp, C.c_uint32, vp], i32),
+            "se_check_sample_conversion": ([vp, vp, vp, i32, vp], i32),
             "se_cert_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], i32),
             "se_plan_info": ([vp, C.c_char_p, C.c_size_t], i32),
         }
@@ -183,6 +184,11 @@ class Context:
         """Queue a device wait that runs out after limit_us (se_check_wait_timeout)."""
         _check(self._lib.se_check_wait_timeout(self.handle, int(limit_us), _stream_handle(stream)),
                "se_check_wait_timeout")
+
+    def check_sample_conversion(self, x, out, stream=None):
+        """The projection kernels' fp64 -> fp32 sample conversion on device tensors."""
+        _check(self._lib.se_check_sample_conversion(self.handle, _ptr(x), _ptr(out), int(x.numel()),
+                                                    _stream_handle(stream)), "se_check_sample_conversion")
 
     def tuned_variant(self, key: str) -> int:
         """The autotuner's kept variant for a shape key, -1 if not tuned."""

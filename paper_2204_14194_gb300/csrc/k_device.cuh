@@ -24,6 +24,34 @@ __device__ __forceinline__ float max3_abs(float m, float a, float b)
 #endif
 }
 
+// The hardware conversion, kept out of line so that the common path below
+// carries no fp64-pipe instruction.
+static __device__ __noinline__ float f64_to_f32_hw(double x) { return __double2float_rn(x); }
+
+// fp64 -> fp32 with rounding to nearest, ties to even (IEEE 754), on the
+// integer pipe: the 52-bit significand is cut to 23 bits and the 29 dropped
+// bits decide the rounding; a carry out of the significand raises the
+// exponent (and gives infinity above the largest float).  Doubles whose
+// result is a normal float (biased exponents 897 .. 1150) take this path, and
+// zeros and double subnormals (below half the smallest float subnormal) give
+// a signed zero; the rest (subnormal float results, infinities, NaNs, values
+// beyond the float range) take the hardware conversion.  The projection
+// kernels convert every sample, and the fp64 pipe is narrow on this GPU.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+    const unsigned lo = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u < 254u) {
+        const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // kept significand bits
+        const unsigned r = lo & 0x1fffffffu;                       // dropped bits
+        const unsigned up = (r > 0x10000000u) | ((r == 0x10000000u) & (m & 1u));
+        return __uint_as_float(((((e - 896u) << 23) | m) + up) | (hi & 0x80000000u));
+    }
+    if (e == 0u) return __uint_as_float(hi & 0x80000000u);
+    return f64_to_f32_hw(x);
+}
+
 // One bulk (TMA) copy of a whole row of T into shared memory, completing on
 // an mbarrier; waits are bounded by %globaltimer (2 s unless given).
 __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)

@@ -18,6 +18,7 @@
 
 #include <cuda_runtime.h>
 
+#include "k_device.cuh"
 #include "se_internal.h"
 
 namespace se {
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(256) sep_kernel(const SepArgs a)
         const BlockDesc bd = a.blocks[b];
         mask = bd.support ? bd.support : a.pattern;
         smp = bd.samples;
-        if (a.mode == 0 && a.copy_support) dst = bd.out;
+        if (a.mode == 0 && a.copy_support && bd.out != bd.samples) dst = bd.out;   // none in place
     }
     if (a.mode >= 2) {
         const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
             const BlockDesc bd = a.blocks[b];
             mask = bd.support ? bd.support : a.pattern;
             smp = bd.samples;
-            if (a.mode == 0 && a.copy_support) dst = bd.out;
+            if (a.mode == 0 && a.copy_support && bd.out != bd.samples) dst = bd.out;   // none in place
         }
         if (a.mode >= 2) {
             const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
                 const int p = p0 + j * kSepGroup + tg;
                 if (p >= MN) continue;
                 float v = on[j] ? Wr[p] : 0.0f;
-                if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
+                if (a.mode == 0) v = on[j] ? v * dev::f64_to_f32_rn(sv[j]) : 0.0f;
                 else if (a.mode >= 2) v *= ex[j];
                 X[p] = v;
                 if (dst && on[j]) dst[p] = sv[j];
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(32 * WPC) sep_warp_kernel(const SepArgs a)
             const BlockDesc bd = a.blocks[b];
             mask = bd.support ? bd.support : a.pattern;
             smp = bd.samples;
-            if (a.mode == 0 && a.copy_support) dst = bd.out;
+            if (a.mode == 0 && a.copy_support && bd.out != bd.samples) dst = bd.out;   // none in place
         }
         if (a.mode >= 2) {
             const int u = a.mode == 3 ? i : a.cur_u[b];
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(32 * WPC) sep_warp_kernel(const SepArgs a)
             for (int j = 0; j < R; ++j) {
                 const int p = q0 + j * 32 + lane;
                 float v = on[j] ? Wr[p] : 0.0f;
-                if (a.mode == 0) v = on[j] ? v * static_cast<float>(sv[j]) : 0.0f;
+                if (a.mode == 0) v = on[j] ? v * dev::f64_to_f32_rn(sv[j]) : 0.0f;
                 else if (a.mode >= 2) v *= ex[j];
                 X[p] = v;
                 if (dst && on[j]) dst[p] = sv[j];

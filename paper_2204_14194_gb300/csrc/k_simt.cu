@@ -406,7 +406,22 @@ __global__ void wait_probe_kernel(int *err, unsigned long long limit_ns)
     if (!dev::bar_wait(&bar, 0, limit_ns)) atomicOr(err, 1 << DEV_ERR_WAIT_TIMEOUT);
 }
 
+// The projection kernels' fp64 -> fp32 sample conversion applied to n values.
+__global__ void convert_probe_kernel(const double *in, float *out, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = dev::f64_to_f32_rn(in[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_convert_probe(const double *in, float *out, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    convert_probe_kernel<<<grid, 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_t st)
 {

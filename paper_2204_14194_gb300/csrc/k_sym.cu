@@ -842,7 +842,8 @@ __global__ void __launch_bounds__(256) sym_r0_kernel(const SymSepArgs a)
         const BlockDesc bd = a.blocks[b];
         const uint8_t *mask = bd.support ? bd.support : a.pattern;
         const double *smp = bd.samples;
-        double *dst = a.copy_support ? bd.out : nullptr;
+        // in place (out is samples): the support samples are already there
+        double *dst = a.copy_support && bd.out != bd.samples ? bd.out : nullptr;
         __syncwarp();   // the previous block's reads of X are done
 #pragma unroll 2
         for (int r = 0; r < RO; ++r) {
@@ -853,7 +854,7 @@ __global__ void __launch_bounds__(256) sym_r0_kernel(const SymSepArgs a)
             for (int e = 0; e < 4; ++e) {
                 const bool on = mask[p[e]] != 0;
                 const double sv = on ? smp[p[e]] : 0.0;
-                x[e] = on ? rho[p[e]] * static_cast<float>(sv) : 0.0f;
+                x[e] = on ? rho[p[e]] * dev::f64_to_f32_rn(sv) : 0.0f;
                 if (dst && on) dst[p[e]] = sv;
             }
             const float s0 = x[0] + x[1], d0 = x[0] - x[1];   // fold in m
@@ -907,25 +908,29 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32_kernel(const SymSepArgs a)
         const BlockDesc bd = a.blocks[b];
         const uint8_t *mask = (bd.support ? bd.support : a.pattern) + lane;
         const double *smp = bd.samples + lane;
-        double *dst = a.copy_support ? bd.out + lane : nullptr;
+        double *dst = a.copy_support && bd.out != bd.samples ? bd.out + lane : nullptr;   // none in place
         __syncwarp();   // the previous block's reads of X and UT are done
 #pragma unroll 1
         for (int r0 = 0; r0 < M / 2; r0 += 8) {
             double s0[8], s1[8];
             bool o0[8], o1[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {   // loss samples are read too and dropped by the select below
+            for (int k = 0; k < 8; ++k) {   // the loss samples are not read
                 const int r = r0 + k;
                 o0[k] = mask[r * N] != 0;
                 o1[k] = mask[(M - 1 - r) * N] != 0;
-                s0[k] = smp[r * N];
-                s1[k] = smp[(M - 1 - r) * N];
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int r = r0 + k;
-                const float x0 = o0[k] ? rho[r * N + lane] * static_cast<float>(s0[k]) : 0.0f;
-                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * static_cast<float>(s1[k]) : 0.0f;
+                s0[k] = o0[k] ? smp[r * N] : 0.0;
+                s1[k] = o1[k] ? smp[(M - 1 - r) * N] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                const float x0 = o0[k] ? rho[r * N + lane] * dev::f64_to_f32_rn(s0[k]) : 0.0f;
+                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * dev::f64_to_f32_rn(s1[k]) : 0.0f;
                 if (dst) {
                     if (o0[k]) dst[r * N] = s0[k];
                     if (o1[k]) dst[(M - 1 - r) * N] = s1[k];
@@ -1080,25 +1085,29 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
         const BlockDesc bd = a.blocks[b];
         const uint8_t *mask = (bd.support ? bd.support : a.pattern) + lane;
         const double *smp = bd.samples + lane;
-        double *dst = a.copy_support ? bd.out + lane : nullptr;
+        double *dst = a.copy_support && bd.out != bd.samples ? bd.out + lane : nullptr;   // none in place
         __syncwarp();   // the previous block's reads of X and U are done
 #pragma unroll 1
         for (int r0 = 0; r0 < M / 2; r0 += 8) {
             double s0[8], s1[8];
             bool o0[8], o1[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {   // loss samples are read too and dropped by the select below
+            for (int k = 0; k < 8; ++k) {   // the loss samples are not read
                 const int r = r0 + k;
                 o0[k] = mask[r * N] != 0;
                 o1[k] = mask[(M - 1 - r) * N] != 0;
-                s0[k] = smp[r * N];
-                s1[k] = smp[(M - 1 - r) * N];
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int r = r0 + k;
-                const float x0 = o0[k] ? rho[r * N + lane] * static_cast<float>(s0[k]) : 0.0f;
-                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * static_cast<float>(s1[k]) : 0.0f;
+                s0[k] = o0[k] ? smp[r * N] : 0.0;
+                s1[k] = o1[k] ? smp[(M - 1 - r) * N] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = r0 + k;
+                const float x0 = o0[k] ? rho[r * N + lane] * dev::f64_to_f32_rn(s0[k]) : 0.0f;
+                const float x1 = o1[k] ? rho[(M - 1 - r) * N + lane] * dev::f64_to_f32_rn(s1[k]) : 0.0f;
                 if (dst) {
                     if (o0[k]) dst[r * N] = s0[k];
                     if (o1[k]) dst[(M - 1 - r) * N] = s1[k];

@@ -54,12 +54,18 @@ struct TcGemmArgs {
     const long long *out_rows;  // optional (non-symmetric): element (n, m) goes to out[out_rows[n] + m]
     const int *n_dev;    // optional device count: only rows n < min(N, *n_dev) of B are used
     int *err;            // device status word
+    int f16;             // 1: the parts are fp16 (kind::f16 with f16 operands), else bf16
+    float post;          // factor applied to every sum before the scale above (0: none); a power
+                         //   of two undoes the scaling of fp16 parts exactly
 };
-// variant (non-symmetric products only): 0 = 128 x 256 tiles, 1 = 128 x 128
-// tiles; both stream one partial product per stage, so they accumulate in the
-// same order and give identical results.
+// variant (non-symmetric products only): 0 = 128 x 256 tiles, 1 = 128 x 128,
+// 2 = 128 x 64; all stream one partial product per stage, so they accumulate
+// in the same order and give identical results.
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant = 0);
 int tc_gemm_variants(const TcGemmArgs &a);
+// The tile variant that fills the GPU for an M x N product: the widest tile
+// whose grid covers every SM at least once (128 x 64 if none does).
+int tc_gemm_fill_variant(int M, int N);
 
 // fp64 (or fp32) CUDA-core GEMM, same contraction with a single part:
 // D[m][n] = sum_k A[m][k] B[n][k]; output mode as above.
@@ -107,6 +113,8 @@ cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, 
 // One CTA that waits on an mbarrier nothing arrives at, bounded by limit_ns;
 // it sets DEV_ERR_WAIT_TIMEOUT in *err and returns (the failure path, on purpose).
 cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_t st);
+// The fp64 -> fp32 sample conversion of the projection kernels, on n values.
+cudaError_t launch_convert_probe(const double *in, float *out, int n, cudaStream_t st);
 
 // Grid of a persistent launch: min(want, SMs x resident CTAs per SM) for
 // kernel kern at this block size and dynamic shared memory; the first call for
@@ -238,7 +246,12 @@ cudaError_t launch_lazy_pack(const BlockDesc *blocks, int n, int MN, int MN_pad,
                              double *xd, uint16_t *mb, double *md, cudaStream_t st);
 cudaError_t launch_lazy_pack_cols(const BlockDesc *blocks, int n, const int *miss_n, const int *miss_blk,
                                   const int *cur_u, const double *Phi64, int MN, int MN_pad,
-                                  uint16_t *vb, double *vd, cudaStream_t st);
+                                  uint16_t *vb, double *vd, cudaStream_t st, uint16_t *vh = nullptr,
+                                  float hscale = 1.0f);
+// Rows of a plan operand (fp64 [rows][ld_in]) as two fp16 parts of x * scale:
+// out[r][part][ka_pad], zero past cols.
+cudaError_t launch_split_f16(const double *in, int rows, int cols, int ld_in, int ka_pad, float scale,
+                             uint16_t *out, cudaStream_t st);
 template <typename T> cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st);
 template <typename T> cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st);
 template <typename T> cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st);

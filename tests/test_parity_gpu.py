@@ -421,3 +421,56 @@ def test_invalid_arguments(ctx):
     plan.extrapolate_strided(torch.empty((0, 8, 8), dtype=torch.float64, device="cuda"),
                              torch.empty((0, 8, 8), dtype=torch.float64, device="cuda"))
     plan.close()
+
+
+@pytest.mark.parametrize("products,prec", [("auto", "bf16x6"), ("dense", "bf16x6"), ("auto", "fp64")])
+def test_in_place_calls_equal_separate_outputs(ctx, products, prec):
+    """out = samples: each block's loss area is overwritten with its extrapolation,
+    the support keeps its samples, and every result equals the call with a
+    separate output buffer (device strided call, pinned and pageable host calls,
+    per-block masks)."""
+    n, I = 1100, 60
+    wl = W.config2(n)
+    plan = ctx.plan(32, 32, "dct_wht", 2048, wl.rho_hat, wl.gamma, I, prec=prec, products=products)
+    ref, ur, cr = gpu_run(plan, wl.samples)
+    loss = wl.support == 0
+    # device buffers
+    s = torch.from_numpy(wl.samples.copy()).cuda()
+    u = torch.empty((n, I), dtype=torch.int32, device="cuda")
+    c = torch.empty((n, I), dtype=torch.float64, device="cuda")
+    plan.extrapolate_strided(s, s, u, c)
+    ctx.sync()
+    np.testing.assert_array_equal(s.cpu().numpy(), ref)
+    np.testing.assert_array_equal(u.cpu().numpy(), ur)
+    np.testing.assert_array_equal(c.cpu().numpy(), cr)
+    # pinned host buffers (the kernels read and write them over the host link)
+    # and pageable ones (staged copies); the loss area holds NaN before the call
+    for pinned in (True, False):
+        h = wl.samples.copy()
+        h[:, loss] = np.nan
+        if pinned:
+            ht = torch.from_numpy(h).pin_memory()
+            plan.extrapolate_host(ht, ht)
+            h = ht.numpy()
+        else:
+            plan.extrapolate_host(h, h)
+        np.testing.assert_array_equal(h, ref)
+    plan.close()
+
+
+def test_in_place_per_block_masks(ctx):
+    L, n, I = 32, 24, 60
+    rng = np.random.default_rng(77)
+    masks = np.stack([W.rect_support(L, L, rng) if i % 2 == 0 else W.holes_support(L, L, rng) for i in range(n)])
+    smp = np.stack([W.patch(L, 9100 + i) for i in range(n)])
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec="bf16x6")
+    s = torch.from_numpy(smp).cuda()
+    m = torch.from_numpy(masks).cuda()
+    out = torch.empty_like(s)
+    plan.extrapolate_batch([{"samples": s[b], "support": m[b], "out": out[b]} for b in range(n)])
+    ctx.sync()
+    s2 = torch.from_numpy(smp).cuda()
+    plan.extrapolate_batch([{"samples": s2[b], "support": m[b], "out": s2[b]} for b in range(n)])
+    ctx.sync()
+    np.testing.assert_array_equal(s2.cpu().numpy(), out.cpu().numpy())
+    plan.close()
