@@ -1,11 +1,14 @@
 // k_gemm_tc.cu -- tcgen05 tensor-core GEMM for the scalar-product stages.
 //
 // Computes D[m][n] = sum_pairs sum_k A[m][pa*ka + k] * B[n][pb*ka + k] with
-// bf16 operands (both K-major) and fp32 accumulation in tensor memory.  The
-// "pairs" implement split-precision products: an fp64 operand v is stored as
-// bf16 parts v = h + m + l, and the partial products h*h, h*m, m*h, ... are
+// bf16 or fp16 operands (both K-major) and fp32 accumulation in tensor memory.
+// The "pairs" implement split-precision products: an fp64 operand v is stored
+// as bf16 parts v = h + m + l, and the partial products h*h, h*m, m*h, ... are
 // accumulated into the same TMEM tile, so a 3-part split with 6 products
-// gives ~fp32 accuracy from the bf16 tensor pipe.
+// gives ~fp32 accuracy from the bf16 tensor pipe.  With fp16 parts (11
+// significant bits each) two parts v = h + l and the 3 products h*h, h*l,
+// l*h give about 2^-21 relative, half the tensor work; the operands are then
+// scaled by powers of two into the fp16 range and the epilogue undoes it.
 //
 // Used for
 //   * the table of eq. (16), C = G G^T with G = Phi_A diag(sqrt(w)) (Alg. 2;
@@ -189,7 +192,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // cross product, so the small terms are summed among themselves and added
     // to the large ones only once, in the epilogue.
     constexpr uint32_t TMEM_COLS = 2 * BN;
-    constexpr uint32_t IDESC = make_idesc(BM, BN);
+    // A and B formats (bits 7-9, 10-12): 1 = bf16, 0 = fp16
+    const uint32_t IDESC = p.f16 ? make_idesc(BM, BN) & ~((7u << 7) | (7u << 10)) : make_idesc(BM, BN);
 
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = saddr(smem_raw);
@@ -355,6 +359,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(q[j]) + __uint_as_float(r[j]));
         }
         if (!ok || m >= p.M) continue;
+        if (p.post != 0.0f) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) * p.post);
+        }
         const int n0 = tn * BN + c0;
         const float sm = p.scale ? p.scale[m] : 1.0f;
         if (!p.symmetric) {
@@ -406,7 +414,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn(std::string *why)
 }
 
 bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_elems, int box_rows,
-              std::string *why)
+              std::string *why, bool f16)
 {
     auto fn = encode_fn(why);
     if (!fn) return false;
@@ -418,7 +426,8 @@ bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch_elems) * 2};
     cuuint32_t box[2] = {static_cast<cuuint32_t>(BK), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+    CUresult r = fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -433,8 +442,8 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 {
     using Cfg = TcCfg<BN, NP, GROUPED>;
     CUtensorMap mA, mB;
-    if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why)) return cudaErrorInvalidValue;
-    if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why)) return cudaErrorInvalidValue;
+    if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why, a.f16 != 0)) return cudaErrorInvalidValue;
+    if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why, a.f16 != 0)) return cudaErrorInvalidValue;
     const int mt = (a.M + BM - 1) / BM;
     const int nt = (a.N + BN - 1) / BN;
     const int grid = a.symmetric ? mt * (mt + 1) / 2 : mt * nt;
@@ -454,7 +463,15 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 
 int tc_gemm_variants(const TcGemmArgs &a)
 {
-    return a.symmetric ? 1 : 2;
+    return a.symmetric ? 1 : 3;
+}
+
+int tc_gemm_fill_variant(int M, int N)
+{
+    const int mt = (M + BM - 1) / BM, sms = sm_count();
+    if (mt * ((N + 255) / 256) >= sms) return 0;
+    if (mt * ((N + 127) / 128) >= sms) return 1;
+    return 2;
 }
 
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant)
@@ -487,6 +504,8 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
         default: break;
         }
     } else if (np <= 3) {
+        // narrow products (few columns of B) fill more SMs with narrower tiles
+        if (variant == 2) return launch_bn<64, 1, false>(a, st, why);
         return variant == 1 ? launch_bn<128, 1, false>(a, st, why) : launch_bn<256, 1, false>(a, st, why);
     }
     if (why) *why = "tc gemm: more than 3 split parts";

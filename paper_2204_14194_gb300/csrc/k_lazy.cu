@@ -18,11 +18,13 @@
 // round.  Projections are kept D-scaled (R'_k = R_k D_b,k) as in the full
 // path.  The model on the block's loss pixels is evaluated at the end.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <climits>
 #include <cmath>
 
+#include "k_device.cuh"
 #include "se_internal.h"
 
 namespace se {
@@ -65,6 +67,19 @@ __device__ __forceinline__ void split3(double x, uint16_t (&p)[3])
     p[2] = bf16b((r - bf16f(p[1])) + lo);
 }
 
+// x 2^s (s a power of two chosen by the plan so that |x 2^s| <= 2^14) as two
+// fp16 parts h + l: y = fp32(x 2^s), h = fp16(y), l = fp16(y - h).  The two
+// parts keep 22 significant bits; the products h h', h l', l h' then carry a
+// relative error of about 2^-21 (the dropped l l' and the roundings).
+__device__ __forceinline__ void split2h(double x, float scale, uint16_t (&p)[2])
+{
+    const float y = dev::f64_to_f32_rn(x) * scale;
+    const __half h = __float2half_rn(y);
+    const __half l = __float2half_rn(y - __half2float(h));
+    p[0] = __half_as_ushort(h);
+    p[1] = __half_as_ushort(l);
+}
+
 // Masked samples x_b[p] = m_b[p] s_b[p] (as 3 bf16 parts or fp64) and the
 // mask itself as one exact bf16 part (1 or 0).  Rows are [part][MN_pad].
 __global__ void lazy_pack_kernel(const BlockDesc *__restrict__ blocks, int MN, int MN_pad,
@@ -88,11 +103,13 @@ __global__ void lazy_pack_kernel(const BlockDesc *__restrict__ blocks, int MN, i
     }
 }
 
-// Column requests: v_j[p] = m_b[p] phi_u[p] for request j (block b, atom u).
+// Column requests: v_j[p] = m_b[p] phi_u[p] for request j (block b, atom u),
+// as three bf16 parts (vb), two scaled fp16 parts (vh) or fp64 (vd).
 __global__ void lazy_pack_cols_kernel(const BlockDesc *__restrict__ blocks, const int *__restrict__ miss_n,
                                       const int *__restrict__ miss_blk, const int *__restrict__ cur_u,
                                       const double *__restrict__ Phi64, int MN, int MN_pad,
-                                      uint16_t *__restrict__ vb, double *__restrict__ vd)
+                                      uint16_t *__restrict__ vb, double *__restrict__ vd,
+                                      uint16_t *__restrict__ vh, float hscale)
 {
     const int j = blockIdx.x;
     if (j >= *miss_n) return;
@@ -107,7 +124,26 @@ __global__ void lazy_pack_cols_kernel(const BlockDesc *__restrict__ blocks, cons
             split3(v, q);
             for (int t = 0; t < 3; ++t) vb[(static_cast<size_t>(j) * 3 + t) * MN_pad + p] = q[t];
         }
+        if (vh) {
+            uint16_t q[2];
+            split2h(v, hscale, q);
+            vh[(static_cast<size_t>(j) * 2 + 0) * MN_pad + p] = q[0];
+            vh[(static_cast<size_t>(j) * 2 + 1) * MN_pad + p] = q[1];
+        }
         if (vd) vd[static_cast<size_t>(j) * MN_pad + p] = v;
+    }
+}
+
+// Rows of a plan operand as two scaled fp16 parts: out[r][t][ka_pad].
+__global__ void split_f16_kernel(const double *__restrict__ in, int cols, int ld_in, int ka_pad, float scale,
+                                 uint16_t *__restrict__ out)
+{
+    const int r = blockIdx.x;
+    for (int j = threadIdx.x; j < ka_pad; j += blockDim.x) {
+        uint16_t q[2];
+        split2h(j < cols ? in[static_cast<size_t>(r) * ld_in + j] : 0.0, scale, q);
+        out[(static_cast<size_t>(r) * 2 + 0) * ka_pad + j] = q[0];
+        out[(static_cast<size_t>(r) * 2 + 1) * ka_pad + j] = q[1];
     }
 }
 
@@ -263,10 +299,19 @@ cudaError_t launch_lazy_pack(const BlockDesc *blocks, int n, int MN, int MN_pad,
 
 cudaError_t launch_lazy_pack_cols(const BlockDesc *blocks, int n, const int *miss_n, const int *miss_blk,
                                   const int *cur_u, const double *Phi64, int MN, int MN_pad,
-                                  uint16_t *vb, double *vd, cudaStream_t st)
+                                  uint16_t *vb, double *vd, cudaStream_t st, uint16_t *vh, float hscale)
 {
     if (n <= 0) return cudaSuccess;
-    lazy_pack_cols_kernel<<<n, 256, 0, st>>>(blocks, miss_n, miss_blk, cur_u, Phi64, MN, MN_pad, vb, vd);
+    lazy_pack_cols_kernel<<<n, 256, 0, st>>>(blocks, miss_n, miss_blk, cur_u, Phi64, MN, MN_pad, vb, vd, vh,
+                                             hscale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_f16(const double *in, int rows, int cols, int ld_in, int ka_pad, float scale,
+                             uint16_t *out, cudaStream_t st)
+{
+    if (rows <= 0) return cudaSuccess;
+    split_f16_kernel<<<rows, 256, 0, st>>>(in, cols, ld_in, ka_pad, scale, out);
     return cudaGetLastError();
 }
 

@@ -1236,6 +1236,15 @@ se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_str
     return SE_OK;
 }
 
+se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, int n, void *cuda_stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!in || !out))) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    SE_CUDA(launch_convert_probe(in, out, n, static_cast<cudaStream_t>(cuda_stream)));
+    ctx->launches += n > 0;
+    return SE_OK;
+}
+
 se_status se_sync(se_ctx_t *ctx, void *cuda_stream)
 {
     if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
@@ -1503,7 +1512,8 @@ se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len)
     std::string t = std::string("products=") + (plan->sep_full ? "transform" : "dense") +
                     " table=" + (plan->dft_w ? "dft-of-weights" : "table") + " iterations=" +
                     (plan->cplx ? "complex" : plan->pc.fp64 ? "fp64" : plan->sym ? "parity-classes" : "general") +
-                    (plan->sym_tc ? " projections=split-tf32" : "") + (plan->certified ? " certified" : "");
+                    (plan->sym_tc ? " projections=split-tf32" : "") + (plan->certified ? " certified" : "") +
+                    (plan->f16_cols ? " columns=f16x3" : "");
     std::snprintf(buf, len, "%s", t.c_str());
     return SE_OK;
 }

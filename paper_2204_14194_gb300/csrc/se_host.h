@@ -265,6 +265,11 @@ struct se_plan_s {
     bool lazy_ready = false;
     int MN_pad = 0;
     se::DevBuf d_Phi64, d_PhiT, d_ArBf, d_AdBf, d_Ar64, d_Ad64;
+    // lazy columns of numeric dictionaries in the fp32 form: Phi rho as two
+    // fp16 parts scaled by f16_a_scale, the packed m_b phi_u by f16_v_scale
+    se::DevBuf d_ArH;
+    bool f16_cols = false;
+    float f16_a_scale = 1.0f, f16_v_scale = 1.0f;
     // transform-domain form for DCT / WHT dictionaries: 1-D bases and rho
     bool sep = false, sep_checked = false;
     bool sep_full = false;       // shared-pattern tables and projections by transforms

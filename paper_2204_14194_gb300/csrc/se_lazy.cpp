@@ -76,6 +76,27 @@ se_status ensure_lazy_plan(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         ctx->launches += 2;
     }
     LZ_TRY(se::ensure_sep_ops(ctx, pl));
+    if (!pl->pc.fp64 && !pl->sep) {
+        // the columns of eq. (16) for numeric dictionaries: two fp16 parts per
+        // operand, each scaled by a power of two that puts its largest entry
+        // at or below 2^14 (no overflow of either part, low parts normal)
+        double amax = 0.0, pmax = 0.0;
+        for (double v : ar) amax = std::max(amax, std::fabs(v));
+        for (double v : phi) pmax = std::max(pmax, std::fabs(v));
+        auto pow2_scale = [](double mx) {
+            return mx > 0.0 ? static_cast<float>(std::ldexp(1.0, 14 - static_cast<int>(std::ceil(std::log2(mx)))))
+                            : 1.0f;
+        };
+        pl->f16_a_scale = pow2_scale(amax);
+        pl->f16_v_scale = pow2_scale(pmax);
+        DevBuf tmp;
+        LZ_TRY(upload_vec(ctx, tmp, ar));
+        LZ_TRY(dev_alloc(ctx, pl->d_ArH, static_cast<size_t>(Kp) * 2 * MNp * 2));
+        LZ_CUDA(launch_split_f16(tmp.as<double>(), Kp, MNp, MNp, MNp, pl->f16_a_scale, pl->d_ArH.as<uint16_t>(), st));
+        LZ_CUDA(cudaStreamSynchronize(st));
+        ctx->launches += 1;
+        pl->f16_cols = true;
+    }
     pl->MN_pad = MNp;
     pl->lazy_ready = true;
     return SE_OK;
@@ -366,11 +387,23 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
                     if (e != cudaSuccess) return e;
                     continue;
                 }
+                const bool h = pl->f16_cols;
                 e = launch_lazy_pack_cols(dd, nw, req, miss_blk, cur_u, pl->d_Phi64.as<double>(), MN, MNp,
-                                          fp64 ? nullptr : ws.lz_v.as<uint16_t>(),
-                                          fp64 ? ws.lz_v.as<double>() : nullptr, s);
+                                          fp64 || h ? nullptr : ws.lz_v.as<uint16_t>(),
+                                          fp64 ? ws.lz_v.as<double>() : nullptr, s,
+                                          h ? ws.lz_v.as<uint16_t>() : nullptr, pl->f16_v_scale);
                 if (e != cudaSuccess) return e;
-                if (fp64) {
+                if (h) {
+                    // three products of the fp16 parts; the epilogue undoes both scales
+                    const int paH[3] = {0, 0, 1}, pbH[3] = {0, 1, 0};
+                    TcGemmArgs g = gemm_args(pl->d_ArH.ptr, ws.lz_v.ptr, Kp, nw, 2 * MNp, 2 * MNp, MNp, 3, paH,
+                                             pbH, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
+                    g.f16 = 1;
+                    g.post = 1.0f / (pl->f16_a_scale * pl->f16_v_scale);
+                    g.out_rows = miss_rows;
+                    g.n_dev = req;
+                    e = launch_tc_gemm(g, s, &why, tc_gemm_fill_variant(Kp, nw));
+                } else if (fp64) {
                     e = launch_simt_gemm_ex<double>(pl->d_Ar64.as<double>(), MNp, ws.lz_v.as<double>(), MNp, Kp,
                                                     nw, MNp, ws.lz_cache.as<double>(), Kp, miss_rows, req, s);
                 } else {
@@ -378,7 +411,7 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
                                              pb6, ws.lz_cache.as<float>(), Kp, ctx->ws_err.as<int>());
                     g.out_rows = miss_rows;
                     g.n_dev = req;
-                    e = launch_tc_gemm(g, s, &why);
+                    e = launch_tc_gemm(g, s, &why, tc_gemm_fill_variant(Kp, nw));
                 }
                 if (e != cudaSuccess) return e;
             }

@@ -155,3 +155,57 @@ def test_masked_requests_alone_equal_mixed(ctx):
     np.testing.assert_array_equal(o.cpu().numpy()[0], mixed[5][0])
     np.testing.assert_array_equal(ud.cpu().numpy(), mixed[5][1])
     p16.close()
+
+
+def test_gaussian_masked_requests_alone_equal_mixed_and_match_the_oracle(ctx):
+    """Requests on a numeric (Gaussian) dictionary with their own masks: the
+    lazy columns of eq. (16) come from two-part fp16 products.  A request gives
+    bitwise the same result alone and mixed with others, and every result
+    meets the parity bars against the FP64 oracle (Alg. 1)."""
+    import oracle as O
+    from helpers import coef_rel_err, first_near_tie, psnr
+
+    L, K, n = 32, 2048, 24
+    dic = W.gaussian_dictionary(K, L, L, 932)
+    p = ctx.plan(L, L, "numeric", K, 0.8, 0.5, 200, prec="bf16x6", dictionary=dic)
+    rng = np.random.default_rng(13)
+    samples = [W.patch(L, 1500 + i) for i in range(n)]
+    masks = [W.rect_support(L, L, rng) if i % 2 else W.holes_support(L, L, rng) for i in range(n)]
+    iters = [int(v) for v in rng.integers(100, 201, size=n)]
+
+    def run(indices):
+        tick = []
+        for i in indices:
+            out = np.empty((L, L))
+            u = np.empty(iters[i], dtype=np.int32)
+            c = np.empty(iters[i])
+            t = ctx.submit(p, samples[i], out, u, c, iterations=iters[i], support=masks[i])
+            tick.append((i, t, out, u, c))
+        res = {}
+        for i, t, out, u, c in tick:
+            st, _ = ctx.poll(t, timeout_us=120_000_000)
+            assert st == B.SE_OK
+            res[i] = (out, u, c)
+        return res
+
+    alone = run([7])
+    mixed = run(list(range(n)))
+    for j in range(3):
+        np.testing.assert_array_equal(alone[7][j], mixed[7][j])
+    assert p.info().get("columns") == "f16x3"
+    phi = np.ascontiguousarray(dic, dtype=np.float64)
+    dup = O.find_duplicates(phi)
+    s = np.stack(samples)
+    w = np.stack([O.weights(L, L, 0.8, m) for m in masks])
+    ro, ru, rc, rm, st = O.se_original_batch(phi, w, s, 0.5, max(iters), dup, iters=np.asarray(iters),
+                                             margins=True)
+    assert st == 0
+    for i in range(n):
+        t = first_near_tie(rm[i, :iters[i]], 1e-4)
+        np.testing.assert_array_equal(mixed[i][1][:t], ru[i, :t])
+        if t:
+            assert coef_rel_err(mixed[i][2][:t], rc[i, :t]).max() <= 1e-3
+    out = np.stack([mixed[i][0] for i in range(n)])
+    loss = np.stack(masks) == 0
+    assert abs(psnr(out, s, loss) - psnr(ro, s, loss)) <= 0.05
+    p.close()
