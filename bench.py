@@ -539,8 +539,8 @@ def run_ours(args):
         # secondary measurements recorded in the same line: the Gaussian-dictionary
         # workload and a short serving run at the mixed-size request stream
         line["gauss1080"] = secondary_gauss1080(args.prec)
-        line["serving"] = serve_measure(args.rate, args.serve_s, 0.5, args.gauss_share, args.budget_gb,
-                                        args.prec)
+        line["serving"] = [serve_measure(float(r), args.serve_s, 0.5, args.gauss_share, args.budget_gb, args.prec)
+                           for r in args.serve_rates.split(",")]
     if args.prec == "certified":
         cs = ctx.cert_stats()
         line["certified"] = {"blocks": cs["blocks"], "recomputed_in_fp64": cs["recomputed"],
@@ -720,6 +720,11 @@ def serve_measure(rate: float, duration: float, warm_s: float, gauss_share: floa
     mrng = np.random.default_rng(6)
     masks = {L: [W.rect_support(L, L, mrng) if i % 2 else W.holes_support(L, L, mrng) for i in range(pool)]
              for L in (16, 32, 64)}
+    # every plan is ready before the clock starts: one masked request each
+    # prepares the plan's lazy-column operands and the tuner's choices
+    for (kind, L), p in plans.items():
+        o = np.empty((L, L))
+        ctx.poll(ctx.submit(p, samp[L][0], o, iterations=300, support=masks[L][0]), timeout_us=-1)
     total_t = warm_s + duration
     n = int(rate * total_t)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
@@ -896,7 +901,9 @@ def main():
                     help="seconds of the sustained pass after the timed steps (0: none)")
     ap.add_argument("--rate", type=float, default=50000.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: measured seconds")
-    ap.add_argument("--serve-s", type=float, default=2.0,
+    ap.add_argument("--serve-rates", default="50000,45000",
+                    help="offered rates of the serving runs inside the headline run (its 'serving' key)")
+    ap.add_argument("--serve-s", type=float, default=3.0,
                     help="serving seconds measured inside the headline run (its 'serving' key)")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
                     help="skip the Gaussian-dictionary and serving measurements of the headline run")

@@ -52,6 +52,42 @@ __device__ __forceinline__ float f64_to_f32_rn(double x)
     return f64_to_f32_hw(x);
 }
 
+// Split-TF32 tensor-core products (mma.sync m16n8k8): each fp32 operand x is
+// x_b = tf32(x) plus x_s = tf32(x - x_b), and a product accumulates
+// x_s y_b + x_b y_s + x_b y_b in fp32 (the dropped x_s y_s and the roundings
+// leave about 2^-21 relative).  Fragments: g = lane / 4, q = lane mod 4;
+// A (16 x 8) {(g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4)}, B (8 x 8)
+// {(q, g), (q + 4, g)}, C (16 x 8) {(g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)}.
+__device__ __forceinline__ uint32_t tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &b, uint32_t &sm)
+{
+    b = tf32_rna(x);
+    sm = tf32_rna(x - __uint_as_float(b));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += A B in split TF32 (three products, small ones first)
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ab)[4], const uint32_t (&as)[4], uint32_t bb0,
+                                     uint32_t bb1, uint32_t bs0, uint32_t bs1)
+{
+    mma_tf32(d, as, bb0, bb1);
+    mma_tf32(d, ab, bs0, bs1);
+    mma_tf32(d, ab, bb0, bb1);
+}
+
 // One bulk (TMA) copy of a whole row of T into shared memory, completing on
 // an mbarrier; waits are bounded by %globaltimer (2 s unless given).
 __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)

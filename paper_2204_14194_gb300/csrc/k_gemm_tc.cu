@@ -170,23 +170,28 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N)
 // k-slice.  Otherwise a stage holds the A and B slices of one partial product
 // (pair-major), which needs less shared memory per stage and so allows a
 // deeper ring and wider BN.
-template <int BN, int NP, bool GROUPED>
+// CPS CTAs share an SM: the ring is sized to 200 KiB / CPS.  With two CTAs of
+// one stage each, one CTA's loads, prologue and epilogue overlap the other's
+// products (the grouped table layout needs 96 KiB per stage).
+template <int BN, int NP, bool GROUPED, int CPS = 1>
 struct TcCfg {
     static constexpr int A_PART = BM * BK * 2;
     static constexpr int B_PART = BN * BK * 2;
     static constexpr int STAGE = (GROUPED ? NP : 1) * (A_PART + B_PART);
-    static constexpr int STAGES = (200 * 1024) / STAGE < 2 ? 1 : ((200 * 1024) / STAGE > 6 ? 6 : (200 * 1024) / STAGE);
+    static constexpr int BUDGET = (200 * 1024) / CPS;
+    static constexpr int STAGES = BUDGET / STAGE < 2 ? 1 : (BUDGET / STAGE > 6 ? 6 : BUDGET / STAGE);
     static constexpr size_t SMEM = static_cast<size_t>(STAGES) * STAGE + 1024 + 256;
 };
 
-template <int BN, int NP, bool GROUPED>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int BN, int NP, bool GROUPED, int CPS = 1>
+__global__ void __launch_bounds__(THREADS, CPS)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                const __grid_constant__ TcGemmArgs p, int mt, int nt)
 {
-    using Cfg = TcCfg<BN, NP, GROUPED>;
+    using Cfg = TcCfg<BN, NP, GROUPED, CPS>;
     constexpr int STAGES = Cfg::STAGES;
-    static_assert(STAGES >= 2, "at least double buffering");
+    static_assert(STAGES >= (CPS > 1 ? 1 : 2), "double buffering, in the CTA or across the CTAs of an SM");
+    static_assert(STAGES * Cfg::STAGE >= 4 * 32 * 33 * 4, "the epilogue's transpose fits in the ring");
     // Two fp32 accumulators of BN columns: acc0 takes the leading product
     // (the pair of the two largest parts, main_pair), acc1 every smaller
     // cross product, so the small terms are summed among themselves and added
@@ -358,14 +363,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(q[j]) + __uint_as_float(r[j]));
         }
-        if (!ok || m >= p.M) continue;
+        if (!ok) continue;   // the same for every thread of the CTA
         if (p.post != 0.0f) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) * p.post);
         }
         const int n0 = tn * BN + c0;
-        const float sm = p.scale ? p.scale[m] : 1.0f;
+        const bool live = m < p.M;
+        const float sm = p.scale && live ? p.scale[m] : 1.0f;
         if (!p.symmetric) {
+            if (!live) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int n = n0 + j;
@@ -375,15 +382,30 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 }
             }
         } else {
-            float *row = p.out + static_cast<long long>(m) * p.ldo;
+            // the mirrored half out[n][m]: lanes hold consecutive m, so each store
+            // is one coalesced row segment
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int n = n0 + j;
-                if (n >= p.N || (diag_tile && n < m)) continue;
-                const float v = __uint_as_float(r[j]);
-                row[n] = p.scale ? v * p.scale[n] : v;
-                p.out[static_cast<long long>(n) * p.ldo + m] = v * sm;
+                if (live && n < p.N && !(diag_tile && n < m))
+                    p.out[static_cast<long long>(n) * p.ldo + m] = __uint_as_float(r[j]) * sm;
             }
+            // the direct half out[m][n]: through a 32 x 32 transpose in shared memory
+            // (the pipeline stages are free once the accumulator is complete), so
+            // that lanes hold consecutive n and each store is coalesced as well
+            float *tr = reinterpret_cast<float *>(gbase) + warp * (32 * 33);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tr[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const int n = n0 + lane;
+            const float sn = p.scale && n < p.N ? p.scale[n] : 1.0f;
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+                const int mi = tm * BM + warp * 32 + i;
+                if (mi < p.M && n < p.N && !(diag_tile && n < mi))
+                    p.out[static_cast<long long>(mi) * p.ldo + n] = tr[i * 33 + lane] * sn;
+            }
+            __syncwarp();
         }
     }
 
@@ -437,10 +459,10 @@ bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_
     return true;
 }
 
-template <int BN, int NP, bool GROUPED>
+template <int BN, int NP, bool GROUPED, int CPS = 1>
 cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 {
-    using Cfg = TcCfg<BN, NP, GROUPED>;
+    using Cfg = TcCfg<BN, NP, GROUPED, CPS>;
     CUtensorMap mA, mB;
     if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why, a.f16 != 0)) return cudaErrorInvalidValue;
     if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why, a.f16 != 0)) return cudaErrorInvalidValue;
@@ -449,13 +471,13 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
     const int grid = a.symmetric ? mt * (mt + 1) / 2 : mt * nt;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP, GROUPED>,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP, GROUPED, CPS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(Cfg::SMEM));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_gemm_kernel<BN, NP, GROUPED><<<grid, THREADS, Cfg::SMEM, st>>>(mA, mB, a, mt, nt);
+    tc_gemm_kernel<BN, NP, GROUPED, CPS><<<grid, THREADS, Cfg::SMEM, st>>>(mA, mB, a, mt, nt);
     return cudaGetLastError();
 }
 
@@ -463,7 +485,7 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 
 int tc_gemm_variants(const TcGemmArgs &a)
 {
-    return a.symmetric ? 1 : 3;
+    return a.symmetric ? 2 : 4;
 }
 
 int tc_gemm_fill_variant(int M, int N)
@@ -497,15 +519,17 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
     // partial product per stage (measured faster for the wide, short-K case).
     if (a.symmetric) {
         if (npa != npb) return cudaErrorInvalidValue;
+        // variant 1: two CTAs per SM (one stage each); same accumulation order
         switch (np) {
-        case 1: return launch_bn<128, 1, true>(a, st, why);
-        case 2: return launch_bn<128, 2, true>(a, st, why);
-        case 3: return launch_bn<128, 3, true>(a, st, why);
+        case 1: return variant == 1 ? launch_bn<128, 1, true, 2>(a, st, why) : launch_bn<128, 1, true>(a, st, why);
+        case 2: return variant == 1 ? launch_bn<128, 2, true, 2>(a, st, why) : launch_bn<128, 2, true>(a, st, why);
+        case 3: return variant == 1 ? launch_bn<128, 3, true, 2>(a, st, why) : launch_bn<128, 3, true>(a, st, why);
         default: break;
         }
     } else if (np <= 3) {
         // narrow products (few columns of B) fill more SMs with narrower tiles
         if (variant == 2) return launch_bn<64, 1, false>(a, st, why);
+        if (variant == 3) return launch_bn<128, 1, false, 2>(a, st, why);   // two CTAs per SM
         return variant == 1 ? launch_bn<128, 1, false>(a, st, why) : launch_bn<256, 1, false>(a, st, why);
     }
     if (why) *why = "tc gemm: more than 3 split parts";

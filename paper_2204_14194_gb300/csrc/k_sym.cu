@@ -36,6 +36,8 @@ namespace se {
 namespace {
 
 using dev::bar_wait;
+using dev::mma3;
+using dev::split_tf32;
 using dev::bulk_row;
 using dev::max3_abs;
 
@@ -1030,36 +1032,6 @@ __global__ void __launch_bounds__(288, 3) sym_r0_32_kernel(const SymSepArgs a)
 // B(8 x 8) {(q, g), (q + 4, g)}, C(16 x 8) {(g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1)}.
 constexpr int kTcPlane = 272;   // X_ab plane pitch (rows of 16; lanes >= 16 store to the other banks)
 constexpr int kTcU = 20;        // pitch of the stage-1 result rows
-
-__device__ __forceinline__ uint32_t tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t &b, uint32_t &sm)
-{
-    b = tf32_rna(x);
-    sm = tf32_rna(x - __uint_as_float(b));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-                 "{%8, %9}, {%0, %1, %2, %3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// d += A B in split TF32 (three products, small ones first)
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ab)[4], const uint32_t (&as)[4], uint32_t bb0,
-                                     uint32_t bb1, uint32_t bs0, uint32_t bs1)
-{
-    mma_tf32(d, as, bb0, bb1);
-    mma_tf32(d, ab, bs0, bs1);
-    mma_tf32(d, ab, bb0, bb1);
-}
 
 __global__ void __launch_bounds__(288, 3) sym_r0_32tc_kernel(const SymSepArgs a)
 {

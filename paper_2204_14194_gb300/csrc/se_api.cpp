@@ -534,7 +534,10 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
         g.symmetric = 1;
         g.err = ctx->ws_err.as<int>();
         g.scale = pl->d_Dk.as<float>();
-        cudaError_t e = launch_tc_gemm(g, st, &why);
+        const std::string key = "gemm_table:" + std::to_string(Kp) + ":" + std::to_string(pl->ka_pad) + ":p" +
+                                std::to_string(pl->pc.npairs);
+        cudaError_t e = tune_run(ctx, key, tc_gemm_variants(g), st,
+                                 [&](int v) { return launch_tc_gemm(g, st, &why, v); });
         if (e != cudaSuccess) return fail(SE_ERR_CUDA, "table GEMM: " + why + " " + cudaGetErrorString(e));
         ctx->launches += 3;
     }

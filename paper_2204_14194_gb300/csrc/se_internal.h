@@ -58,9 +58,12 @@ struct TcGemmArgs {
     float post;          // factor applied to every sum before the scale above (0: none); a power
                          //   of two undoes the scaling of fp16 parts exactly
 };
-// variant (non-symmetric products only): 0 = 128 x 256 tiles, 1 = 128 x 128,
-// 2 = 128 x 64; all stream one partial product per stage, so they accumulate
-// in the same order and give identical results.
+// variant: non-symmetric products 0 = 128 x 256 tiles, 1 = 128 x 128, 2 =
+// 128 x 64, 3 = 128 x 128 with two CTAs per SM (all stream one partial
+// product per stage, so they accumulate in the same order and give identical
+// results); symmetric products 0 = one CTA
+// per SM with a two-stage ring, 1 = two CTAs per SM of one stage each (the
+// same kernel and order, identical results).
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant = 0);
 int tc_gemm_variants(const TcGemmArgs &a);
 // The tile variant that fills the GPU for an M x N product: the widest tile

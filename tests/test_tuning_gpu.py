@@ -74,10 +74,10 @@ def test_forced_variants_are_bitwise_identical(case):
     samples = np.stack([W.patch(L, 4000 + i) for i in range(n)])
     dic = W.gaussian_dictionary(K, L, L, 91) if basis == "numeric" else None
     res = []
-    # variant 2 exists only for the projection GEMM (128 x 64 tiles); other keys
-    # take their last variant
-    for v in (0, 1, 2):
-        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},iterate:={v},sym:={v},symr0:={v}")
+    # variants 2 and 3 exist only for the projection GEMM (128 x 64 tiles, two
+    # CTAs per SM); other keys take their last variant
+    for v in (0, 1, 2, 3):
+        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},gemm_table:={v},iterate:={v},sym:={v},symr0:={v}")
         try:
             plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec, dictionary=dic)
             res.append(_run(ctx, plan, samples))
