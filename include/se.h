@@ -258,7 +258,10 @@ se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan, int n,
  * place): each block's loss area is overwritten with its extrapolation, and
  * with pinned buffers only the support samples cross the link inwards and
  * only the loss areas outwards (half the bytes of separate buffers for a
- * quarter loss area).  Serialised with the other batch calls of the context. */
+ * quarter loss area).  Pinned calls run as one chunk; SE_PINNED_CHUNKS
+ * (environment, 1 .. 4, read at each call) splits them into up to that many
+ * chunks of at least 1024 blocks on their own streams.
+ * Serialised with the other batch calls of the context. */
 se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
                               const double *samples, double *out,
                               int32_t *sel_idx, double *sel_coef, int iterations);
@@ -351,7 +354,9 @@ se_status se_plan_costs(const se_plan_t *plan, double *table_ms, double *full_ms
 
 /* CUDA graphs: the lock-step rounds of the lazy path are captured once per
  * (plan, wave size, iteration count, workspace) and replayed (default on;
- * at most 32 graphs per context, the least recently used dropped first). */
+ * at most 32 graphs per context, the least recently used dropped first).
+ * A shape is launched directly the first time it is seen and captured the
+ * second time, so one-off shapes (most serving batches) cost no capture. */
 se_status se_set_graphs(se_ctx_t *ctx, int enable);
 /* Autotuner and graph counters: shapes tuned (each timed its candidates
  * once), graphs captured, graph replays.  Any pointer may be NULL.  The

@@ -191,7 +191,8 @@ __global__ void lazy_init_kernel(LazyArgs a)
         const bool adm = k < a.K && !a.dup[k] && mx > T(0) && d > T(1e-14) * mx;
         const T Dv = adm ? T(1) / sqrt(d) : nan_of<T>();
         D[k] = Dv;
-        R[k] = R[k] * Dv;
+        if (a.R64) a.R64[static_cast<size_t>(b) * a.Kp + k] = static_cast<double>(R[k]) * static_cast<double>(Dv);
+        else R[k] = R[k] * Dv;
         a.slot_of[static_cast<size_t>(b) * a.Kp + k] = -1;
         cnt += adm;
     }
@@ -204,49 +205,55 @@ __global__ void lazy_init_kernel(LazyArgs a)
 
 // One round nu for every block: R' -= c_prev D col(u_prev); select u; record
 // c; request the column of u if it is not cached and another round follows.
-template <typename T>
+// TR is the type of the running recurrence: T, or double over fp32 columns
+// (the product col D of two floats is exact in double, so each update carries
+// only the columns' own fp32 error).
+template <typename T, typename TR>
 __global__ void lazy_round_kernel(LazyArgs a, int nu)
 {
-    __shared__ Cand<T> red[32];
+    __shared__ Cand<TR> red[32];
+    constexpr bool MIX = sizeof(TR) != sizeof(T);
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
     const int Ib = a.blocks[b].iterations;
     if (nu >= Ib || a.n_slots[b] < 0) return;
-    T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
+    TR *R = (MIX ? reinterpret_cast<TR *>(a.R64) : static_cast<TR *>(a.R)) + static_cast<size_t>(b) * a.Kp;
+    TR *cur_c = MIX ? reinterpret_cast<TR *>(a.cur_c64) : static_cast<TR *>(a.cur_c);
+    TR *c_log = MIX ? reinterpret_cast<TR *>(a.c_log64) : static_cast<TR *>(a.c_log);
     const T *D = static_cast<const T *>(a.Dk) + static_cast<size_t>(b) * a.Kp;
     int *slot_of = a.slot_of + static_cast<size_t>(b) * a.Kp;
     const T *col = nullptr;
-    T cprev = T(0);
+    TR cprev = TR(0);
     if (nu > 0) {
         const int up = a.cur_u[b];
-        cprev = static_cast<const T *>(a.cur_c)[b];
+        cprev = cur_c[b];
         col = static_cast<const T *>(a.cache) +
               (static_cast<size_t>(b) * a.slots + slot_of[up]) * a.Kp;
     }
-    T s = T(-1), rb = T(0);
+    TR s = TR(-1), rb = TR(0);
     int kb = INT_MAX;
     for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
-        T r = R[k];
+        TR r = R[k];
         if (col) {
-            r = fma(-cprev, col[k] * D[k], r);
+            r = fma(-cprev, static_cast<TR>(col[k]) * static_cast<TR>(D[k]), r);
             R[k] = r;
         }
-        const T sc = fabs(r);
+        const TR sc = fabs(r);
         if (sc > s) { s = sc; kb = k; rb = r; }
     }
-    block_argmax<T>(s, kb, rb, red);
+    block_argmax<TR>(s, kb, rb, red);
     int u = kb;
     if (u < 0 || u >= a.K) {
         if (threadIdx.x == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
         u = 0;
-        rb = T(0);
+        rb = TR(0);
     }
     if (threadIdx.x == 0) {
-        const T c = static_cast<T>(a.gamma) * rb * D[u];
+        const TR c = static_cast<TR>(a.gamma) * rb * static_cast<TR>(D[u]);
         a.cur_u[b] = u;
-        static_cast<T *>(a.cur_c)[b] = c;
+        cur_c[b] = c;
         a.u_log[static_cast<size_t>(b) * a.I_max + nu] = u;
-        static_cast<T *>(a.c_log)[static_cast<size_t>(b) * a.I_max + nu] = c;
+        c_log[static_cast<size_t>(b) * a.I_max + nu] = c;
         if (nu + 1 < Ib && slot_of[u] < 0) {
             const int sl = a.n_slots[b]++;
             if (sl >= a.slots) {
@@ -263,21 +270,24 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
 }
 
 // Model on the block's loss pixels (eq. 9) and replacement; logs out.
-template <typename T>
+template <typename T, typename TR>
 __global__ void lazy_model_kernel(LazyArgs a)
 {
+    constexpr bool MIX = sizeof(TR) != sizeof(T);
     const int b = blockIdx.x;
     const BlockDesc bd = a.blocks[b];
     const int I = a.n_slots[b] < 0 ? 0 : bd.iterations;
     const int *ul = a.u_log + static_cast<size_t>(b) * a.I_max;
-    const T *cl = static_cast<const T *>(a.c_log) + static_cast<size_t>(b) * a.I_max;
+    const TR *cl = (MIX ? reinterpret_cast<const TR *>(a.c_log64) : static_cast<const TR *>(a.c_log)) +
+                   static_cast<size_t>(b) * a.I_max;
     const T *Phi = static_cast<const T *>(a.Phi);
     for (int p = threadIdx.x; p < a.MN; p += blockDim.x) {
         if (bd.support[p]) {
-            bd.out[p] = bd.samples[p];
+            if (bd.out != bd.samples) bd.out[p] = bd.samples[p];
         } else {
-            T acc = T(0);
-            for (int nu = 0; nu < I; ++nu) acc = fma(cl[nu], Phi[static_cast<size_t>(ul[nu]) * a.MN + p], acc);
+            TR acc = TR(0);
+            for (int nu = 0; nu < I; ++nu)
+                acc = fma(cl[nu], static_cast<TR>(Phi[static_cast<size_t>(ul[nu]) * a.MN + p]), acc);
             bd.out[p] = static_cast<double>(acc);
         }
     }
@@ -325,14 +335,20 @@ cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st)
 template <typename T>
 cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st)
 {
-    lazy_round_kernel<T><<<a.n, 256, 0, st>>>(a, nu);
+    if (a.R64 && sizeof(T) == 4)
+        lazy_round_kernel<T, double><<<a.n, 256, 0, st>>>(a, nu);
+    else
+        lazy_round_kernel<T, T><<<a.n, 256, 0, st>>>(a, nu);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st)
 {
-    lazy_model_kernel<T><<<a.n, 256, 0, st>>>(a);
+    if (a.R64 && sizeof(T) == 4)
+        lazy_model_kernel<T, double><<<a.n, 256, 0, st>>>(a);
+    else
+        lazy_model_kernel<T, T><<<a.n, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

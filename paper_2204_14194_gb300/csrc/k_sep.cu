@@ -633,6 +633,10 @@ __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, con
     float *Ts = reinterpret_cast<float *>(smem);
     const int M = s.M, N = s.N, MN = M * N, cstride = M * M + N * N;
     int4 *Etab = reinterpret_cast<int4 *>(Ts + ((s.ntr * cstride + 3) & ~3)) + (threadIdx.x >> 5) * 32;
+    constexpr int GP = 8 * NT + 1;   // pitch of the warp's output tile (padded)
+    float *Gt = reinterpret_cast<float *>(reinterpret_cast<int4 *>(Ts + ((s.ntr * cstride + 3) & ~3)) +
+                                          (blockDim.x >> 5) * 32) +
+                (threadIdx.x >> 5) * (16 * MT * GP);
     for (int t = 0; t < s.ntr; ++t) {
         const float *gm = static_cast<const float *>(s.TM[t]);
         const float *gn = static_cast<const float *>(s.TN[t]);
@@ -710,18 +714,25 @@ __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, con
                 }
             }
         }
-        // C fragments: (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) of each tile
+        // C fragments (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) of each tile go
+        // through the warp's tile in shared memory, so that the stores to the output
+        // are whole row segments (consecutive lanes, consecutive columns): the output
+        // may be host memory reached over the host link, where short scattered
+        // writes are slow
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int i = 16 * mt + g + 8 * (k >> 1), j = 8 * nt + 2 * q + (k & 1);
-                    if (i >= Mb || j >= Nb) continue;
-                    const int p = (m0 + i) * N + n0 + j;
-                    if (!a.pat_support[p]) bd.out[p] = static_cast<double>(acc[mt][nt][k]);
-                }
+                for (int k = 0; k < 4; ++k)
+                    Gt[(16 * mt + g + 8 * (k >> 1)) * GP + 8 * nt + 2 * q + (k & 1)] = acc[mt][nt][k];
+        __syncwarp();
+        for (int e = lane; e < Mb * Nb; e += 32) {
+            const int i = e / Nb, j = e - i * Nb;
+            const int p = (m0 + i) * N + n0 + j;
+            if (!a.pat_support[p]) bd.out[p] = static_cast<double>(Gt[i * GP + j]);
+        }
+        __syncwarp();   // the tile is read before the next block overwrites it
     }
 }
 
@@ -818,9 +829,10 @@ cudaError_t launch_sep_model_t(const IterArgs &a, const SepArgs &s, int m0, int 
 }
 
 template <int MT, int NT>
-cudaError_t launch_sep_model_tc(const IterArgs &a, const SepArgs &s, int m0, int Mb, int n0, int Nb, size_t smem,
+cudaError_t launch_sep_model_tc(const IterArgs &a, const SepArgs &s, int m0, int Mb, int n0, int Nb, size_t smem0,
                                 cudaStream_t st)
 {
+    const size_t smem = smem0 + sizeof(float) * 8 * (16 * MT) * (8 * NT + 1);   // eight warps' output tiles
     int grid = 0;
     cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_model_tc_kernel<MT, NT>), 256, smem,
                                 (a.n + 7) / 8, &grid);

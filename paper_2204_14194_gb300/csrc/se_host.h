@@ -51,6 +51,7 @@ struct Workspace {
     // per-block-mask (lazy) path
     DevBuf lz_R, lz_D, lz_diag, lz_slot, lz_nslots, lz_cache, lz_ulog, lz_clog, lz_cur, lz_miss,
         lz_x, lz_mk, lz_v;
+    DevBuf lz_R64, lz_c64;   // fp64 running recurrence of long fp32 runs: R', current and logged c
     BlockDesc *h_desc = nullptr;
     size_t h_desc_cap = 0;
     cudaEvent_t ev_staging = nullptr;     // the staging copy of the last batch has landed
@@ -97,11 +98,11 @@ namespace se {
 struct GraphKey {
     const se_plan_s *plan = nullptr;
     int nw = 0, I_max = 0;
-    const void *ptr[8] = {};
+    const void *ptr[10] = {};
     bool operator==(const GraphKey &o) const
     {
         if (plan != o.plan || nw != o.nw || I_max != o.I_max) return false;
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 10; ++i)
             if (ptr[i] != o.ptr[i]) return false;
         return true;
     }
@@ -202,6 +203,7 @@ struct se_ctx_s {
     static constexpr size_t kGraphCache = 32;
     std::mutex gmu;
     std::vector<se::CachedGraph> graphs;
+    std::vector<se::GraphKey> graph_seen;   // shapes run once without a graph
     uint64_t graph_clock = 0;
     std::atomic<uint64_t> graph_builds{0}, graph_replays{0};
     std::atomic<uint64_t> cert_blocks{0}, cert_recomputed{0};

@@ -244,6 +244,12 @@ struct LazyArgs {
     long long *miss_rows;      // [n] element offset of the requested cache row
     double gamma;
     int *err;
+    // fp32 form with the fp64 running recurrence (long iteration counts): R' is
+    // kept in R64 (initialised from the fp32 R0 in R), and the coefficients in
+    // cur_c64 / c_log64; the columns, D and the diagonal stay fp32.  NULL: off.
+    double *R64;
+    double *cur_c64;
+    double *c_log64;
 };
 cudaError_t launch_lazy_pack(const BlockDesc *blocks, int n, int MN, int MN_pad, uint16_t *xb,
                              double *xd, uint16_t *mb, double *md, cudaStream_t st);

@@ -250,18 +250,27 @@ se_status dense_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const B
 
 }  // namespace
 
+// Iteration counts above which the fp32 form keeps the running recurrence of
+// eq. (20) in fp64: the fp32 recurrence's error is about constant in the scale of
+// the initial projections, so it grows relative to the projections as they decay;
+// on 16 x 16 blocks with scattered holes it passed a near tie of 1.5e-4 relative
+// at iteration 286 while the fp64 form followed the oracle to I = 500.
+constexpr int kLongRun = 256;
+
 se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                        int I_max, cudaStream_t st)
 {
     LZ_TRY(ensure_lazy_plan(ctx, pl, st));
     const bool fp64 = pl->pc.fp64;
+    const bool r64 = !fp64 && I_max > kLongRun;
     const size_t tsz = fp64 ? 8 : 4;
     const int Kp = pl->Kp, MN = pl->MN, MNp = pl->MN_pad;
     const int slots = std::max(1, I_max - 1);
     const size_t opnd = fp64 ? 8 * static_cast<size_t>(MNp) * 3 : 2 * static_cast<size_t>(MNp) * 7;
     const size_t per_block = tsz * Kp * 3 + 4 * static_cast<size_t>(Kp) +
                              static_cast<size_t>(slots) * Kp * tsz + static_cast<size_t>(I_max) * (4 + tsz) +
-                             opnd + sizeof(BlockDesc) + 64;
+                             opnd + sizeof(BlockDesc) + 64 +
+                             (r64 ? 8 * static_cast<size_t>(Kp) + 8 * static_cast<size_t>(I_max) + 8 : 0);
     size_t avail;
     if (ctx->budget) {
         avail = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
@@ -289,6 +298,10 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
     LZ_TRY(dev_alloc(ctx, ws.lz_clog, tsz * I_max * static_cast<size_t>(wave)));
     LZ_TRY(dev_alloc(ctx, ws.lz_cur, (4 + 8) * static_cast<size_t>(wave) + 16));
     LZ_TRY(dev_alloc(ctx, ws.lz_miss, 16 + (4 + 8) * static_cast<size_t>(wave) + 16));
+    if (r64) {
+        LZ_TRY(dev_alloc(ctx, ws.lz_R64, 8 * static_cast<size_t>(Kp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_c64, 8 * (static_cast<size_t>(I_max) + 1) * wave));
+    }
     if (fp64) {
         LZ_TRY(dev_alloc(ctx, ws.lz_x, 8 * static_cast<size_t>(MNp) * wave));
         LZ_TRY(dev_alloc(ctx, ws.lz_mk, 8 * static_cast<size_t>(MNp) * wave));
@@ -363,6 +376,11 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         a.miss_rows = miss_rows;
         a.gamma = pl->desc.gamma;
         a.err = ctx->ws_err.as<int>();
+        if (r64) {
+            a.R64 = ws.lz_R64.as<double>();
+            a.cur_c64 = ws.lz_c64.as<double>();
+            a.c_log64 = ws.lz_c64.as<double>() + wave;
+        }
 
         tok = stage_begin(ctx, 3, st);
         cudaEvent_t probe = probe_begin(ctx, st);
@@ -421,9 +439,10 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         gk.plan = pl;
         gk.nw = nw;
         gk.I_max = I_max;
-        const void *ptrs[8] = {ws.desc.ptr, ws.lz_R.ptr, ws.lz_cache.ptr, ws.lz_v.ptr,
-                               ws.lz_miss.ptr, ws.lz_cur.ptr, ws.lz_ulog.ptr, ws.lz_clog.ptr};
-        for (int i = 0; i < 8; ++i) gk.ptr[i] = ptrs[i];
+        const void *ptrs[10] = {ws.desc.ptr, ws.lz_R.ptr, ws.lz_cache.ptr, ws.lz_v.ptr,
+                                ws.lz_miss.ptr, ws.lz_cur.ptr, ws.lz_ulog.ptr, ws.lz_clog.ptr,
+                                r64 ? ws.lz_R64.ptr : nullptr, r64 ? ws.lz_c64.ptr : nullptr};
+        for (int i = 0; i < 10; ++i) gk.ptr[i] = ptrs[i];
         {
             cudaError_t e = graph_run(ctx, gk, st, rounds);
             if (e != cudaSuccess)

@@ -228,6 +228,16 @@ cudaError_t graph_run(se_ctx_s *ctx, const GraphKey &key, cudaStream_t st,
                 ctx->graph_replays++;
                 return cudaGraphLaunch(g.exec, st);
             }
+        // A shape seen for the first time runs directly; only a shape that comes
+        // back is captured.  Serving batches rarely repeat their shape, and a
+        // capture that is never replayed costs more than the launches it holds.
+        auto seen = std::find(ctx->graph_seen.begin(), ctx->graph_seen.end(), key);
+        if (seen == ctx->graph_seen.end()) {
+            if (ctx->graph_seen.size() >= 4 * se_ctx_s::kGraphCache) ctx->graph_seen.erase(ctx->graph_seen.begin());
+            ctx->graph_seen.push_back(key);
+            return record(st);
+        }
+        ctx->graph_seen.erase(seen);
     }
     // capture on a private stream ordered after the caller's work
     cudaStream_t cs = nullptr;
@@ -267,6 +277,7 @@ void graphs_clear(se_ctx_s *ctx)
     std::lock_guard<std::mutex> lk(ctx->gmu);
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
+    ctx->graph_seen.clear();
 }
 
 void graphs_drop_plan(se_ctx_s *ctx, const se_plan_s *pl)

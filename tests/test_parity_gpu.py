@@ -290,9 +290,13 @@ def test_pipelined_host_entry_point_matches_device_path(ctx, n, shift, prec, log
     plan.close()
 
 
-@pytest.mark.parametrize("n,logs", [(2100, True), (300, False)])
-def test_host_entry_point_with_pinned_buffers(ctx, n, logs):
-    """Pinned host buffers are read and written by the kernels directly."""
+@pytest.mark.parametrize("n,logs,chunks", [(2100, True, None), (300, False, None), (2100, True, "2"),
+                                           (4500, False, "4")])
+def test_host_entry_point_with_pinned_buffers(ctx, n, logs, chunks, monkeypatch):
+    """Pinned host buffers are read and written by the kernels directly, in one
+    chunk or (SE_PINNED_CHUNKS) in several chunks on their own streams."""
+    if chunks:
+        monkeypatch.setenv("SE_PINNED_CHUNKS", chunks)
     L, I = 32, 60
     s = np.stack([W.patch(L, 3500 + i) for i in range(n)])
     plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec="bf16x6")
