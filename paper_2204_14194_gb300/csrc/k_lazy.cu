@@ -191,8 +191,14 @@ __global__ void lazy_init_kernel(LazyArgs a)
         const bool adm = k < a.K && !a.dup[k] && mx > T(0) && d > T(1e-14) * mx;
         const T Dv = adm ? T(1) / sqrt(d) : nan_of<T>();
         D[k] = Dv;
-        if (a.R64) a.R64[static_cast<size_t>(b) * a.Kp + k] = static_cast<double>(R[k]) * static_cast<double>(Dv);
-        else R[k] = R[k] * Dv;
+        if (a.R64 && sizeof(T) == 4) {
+            // R' = R0 D as a pair of floats (hi + lo, the product's exact rounding error)
+            const float r0 = static_cast<float>(R[k]), dv = static_cast<float>(Dv);
+            const float hi = r0 * dv;
+            reinterpret_cast<float2 *>(a.R64)[static_cast<size_t>(b) * a.Kp + k] = make_float2(hi, fmaf(r0, dv, -hi));
+        } else {
+            R[k] = R[k] * Dv;
+        }
         a.slot_of[static_cast<size_t>(b) * a.Kp + k] = -1;
         cnt += adm;
     }
@@ -205,55 +211,94 @@ __global__ void lazy_init_kernel(LazyArgs a)
 
 // One round nu for every block: R' -= c_prev D col(u_prev); select u; record
 // c; request the column of u if it is not cached and another round follows.
-// TR is the type of the running recurrence: T, or double over fp32 columns
-// (the product col D of two floats is exact in double, so each update carries
-// only the columns' own fp32 error).
-template <typename T, typename TR>
+// The recurrence R'_k -= c_prev D_k col_k of eq. (20).  In T, or, for long
+// fp32 runs (a.R64 set), in double-float: R'_k = hi + lo and c = ch + cl as
+// pairs of floats, updated with exact products (fma) and exact sums (two-sum),
+// about 48 significant bits on the fp32 pipe; the product D_k col_k of two
+// floats enters with its exact rounding error.  The selection compares the hi
+// parts.
+__device__ __forceinline__ float2 df_update(float2 r, float2 c, float col, float d)
+{
+    const float v = col * d, ev = fmaf(col, d, -v);          // v + ev = col d exactly
+    const float p = c.x * v, pe = fmaf(c.x, v, -p);          // p + pe = ch v exactly
+    const float corr = pe + fmaf(c.x, ev, c.y * v);          // the small terms of c (col d)
+    const float s = r.x - p, bb = s - r.x;                    // two-sum of hi - p
+    const float err = (r.x - (s - bb)) + (-p - bb);
+    const float lo = (r.y - corr) + err;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+
+template <typename T>
 __global__ void lazy_round_kernel(LazyArgs a, int nu)
 {
-    __shared__ Cand<TR> red[32];
-    constexpr bool MIX = sizeof(TR) != sizeof(T);
+    __shared__ Cand<T> red[32];
+    const bool df = a.R64 != nullptr && sizeof(T) == 4;
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
     const int Ib = a.blocks[b].iterations;
     if (nu >= Ib || a.n_slots[b] < 0) return;
-    TR *R = (MIX ? reinterpret_cast<TR *>(a.R64) : static_cast<TR *>(a.R)) + static_cast<size_t>(b) * a.Kp;
-    TR *cur_c = MIX ? reinterpret_cast<TR *>(a.cur_c64) : static_cast<TR *>(a.cur_c);
-    TR *c_log = MIX ? reinterpret_cast<TR *>(a.c_log64) : static_cast<TR *>(a.c_log);
+    T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
+    float2 *R2 = df ? reinterpret_cast<float2 *>(a.R64) + static_cast<size_t>(b) * a.Kp : nullptr;
     const T *D = static_cast<const T *>(a.Dk) + static_cast<size_t>(b) * a.Kp;
     int *slot_of = a.slot_of + static_cast<size_t>(b) * a.Kp;
     const T *col = nullptr;
-    TR cprev = TR(0);
+    T cprev = T(0);
+    float2 c2 = make_float2(0.0f, 0.0f);
     if (nu > 0) {
         const int up = a.cur_u[b];
-        cprev = cur_c[b];
+        if (df) c2 = reinterpret_cast<const float2 *>(a.cur_c64)[b];
+        else cprev = static_cast<const T *>(a.cur_c)[b];
         col = static_cast<const T *>(a.cache) +
               (static_cast<size_t>(b) * a.slots + slot_of[up]) * a.Kp;
     }
-    TR s = TR(-1), rb = TR(0);
+    T s = T(-1), rb = T(0);
     int kb = INT_MAX;
     for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
-        TR r = R[k];
-        if (col) {
-            r = fma(-cprev, static_cast<TR>(col[k]) * static_cast<TR>(D[k]), r);
-            R[k] = r;
+        T r;
+        if (df) {
+            float2 r2 = R2[k];
+            if (col) {
+                r2 = df_update(r2, c2, static_cast<float>(col[k]), static_cast<float>(D[k]));
+                R2[k] = r2;
+            }
+            r = static_cast<T>(r2.x);
+        } else {
+            r = R[k];
+            if (col) {
+                r = fma(-cprev, col[k] * D[k], r);
+                R[k] = r;
+            }
         }
-        const TR sc = fabs(r);
+        const T sc = fabs(r);
         if (sc > s) { s = sc; kb = k; rb = r; }
     }
-    block_argmax<TR>(s, kb, rb, red);
+    block_argmax<T>(s, kb, rb, red);
     int u = kb;
     if (u < 0 || u >= a.K) {
         if (threadIdx.x == 0) atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
         u = 0;
-        rb = TR(0);
+        rb = T(0);
     }
     if (threadIdx.x == 0) {
-        const TR c = static_cast<TR>(a.gamma) * rb * static_cast<TR>(D[u]);
+        T c;
+        if (df) {
+            // c = gamma R'_u D_u from the pair (the winner's lo part is in global
+            // memory, written by this CTA before the barriers of the argmax)
+            const float2 ru = (u == kb) ? R2[u] : make_float2(0.0f, 0.0f);
+            const double cd = a.gamma * (static_cast<double>(ru.x) + static_cast<double>(ru.y)) *
+                              static_cast<double>(D[u]);
+            const float ch = static_cast<float>(cd);
+            reinterpret_cast<float2 *>(a.cur_c64)[b] = make_float2(ch, static_cast<float>(cd - ch));
+            a.c_log64[static_cast<size_t>(b) * a.I_max + nu] = cd;
+            c = static_cast<T>(ch);
+        } else {
+            c = static_cast<T>(a.gamma) * rb * D[u];
+            static_cast<T *>(a.cur_c)[b] = c;
+        }
         a.cur_u[b] = u;
-        cur_c[b] = c;
         a.u_log[static_cast<size_t>(b) * a.I_max + nu] = u;
-        c_log[static_cast<size_t>(b) * a.I_max + nu] = c;
+        static_cast<T *>(a.c_log)[static_cast<size_t>(b) * a.I_max + nu] = c;
         if (nu + 1 < Ib && slot_of[u] < 0) {
             const int sl = a.n_slots[b]++;
             if (sl >= a.slots) {
@@ -270,31 +315,31 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
 }
 
 // Model on the block's loss pixels (eq. 9) and replacement; logs out.
-template <typename T, typename TR>
+template <typename T>
 __global__ void lazy_model_kernel(LazyArgs a)
 {
-    constexpr bool MIX = sizeof(TR) != sizeof(T);
     const int b = blockIdx.x;
     const BlockDesc bd = a.blocks[b];
     const int I = a.n_slots[b] < 0 ? 0 : bd.iterations;
     const int *ul = a.u_log + static_cast<size_t>(b) * a.I_max;
-    const TR *cl = (MIX ? reinterpret_cast<const TR *>(a.c_log64) : static_cast<const TR *>(a.c_log)) +
-                   static_cast<size_t>(b) * a.I_max;
+    const T *cl = static_cast<const T *>(a.c_log) + static_cast<size_t>(b) * a.I_max;
     const T *Phi = static_cast<const T *>(a.Phi);
     for (int p = threadIdx.x; p < a.MN; p += blockDim.x) {
         if (bd.support[p]) {
             if (bd.out != bd.samples) bd.out[p] = bd.samples[p];
         } else {
-            TR acc = TR(0);
-            for (int nu = 0; nu < I; ++nu)
-                acc = fma(cl[nu], static_cast<TR>(Phi[static_cast<size_t>(ul[nu]) * a.MN + p]), acc);
+            T acc = T(0);
+            for (int nu = 0; nu < I; ++nu) acc = fma(cl[nu], Phi[static_cast<size_t>(ul[nu]) * a.MN + p], acc);
             bd.out[p] = static_cast<double>(acc);
         }
     }
     if (bd.sel_idx)
         for (int nu = threadIdx.x; nu < I; nu += blockDim.x) bd.sel_idx[nu] = ul[nu];
-    if (bd.sel_coef)
-        for (int nu = threadIdx.x; nu < I; nu += blockDim.x) bd.sel_coef[nu] = static_cast<double>(cl[nu]);
+    if (bd.sel_coef) {
+        const double *c64 = a.c_log64 ? a.c_log64 + static_cast<size_t>(b) * a.I_max : nullptr;
+        for (int nu = threadIdx.x; nu < I; nu += blockDim.x)
+            bd.sel_coef[nu] = c64 ? c64[nu] : static_cast<double>(cl[nu]);
+    }
 }
 
 }  // namespace
@@ -335,20 +380,14 @@ cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st)
 template <typename T>
 cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st)
 {
-    if (a.R64 && sizeof(T) == 4)
-        lazy_round_kernel<T, double><<<a.n, 256, 0, st>>>(a, nu);
-    else
-        lazy_round_kernel<T, T><<<a.n, 256, 0, st>>>(a, nu);
+    lazy_round_kernel<T><<<a.n, 256, 0, st>>>(a, nu);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_lazy_model(const LazyArgs &a, cudaStream_t st)
 {
-    if (a.R64 && sizeof(T) == 4)
-        lazy_model_kernel<T, double><<<a.n, 256, 0, st>>>(a);
-    else
-        lazy_model_kernel<T, T><<<a.n, 256, 0, st>>>(a);
+    lazy_model_kernel<T><<<a.n, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -244,9 +244,11 @@ struct LazyArgs {
     long long *miss_rows;      // [n] element offset of the requested cache row
     double gamma;
     int *err;
-    // fp32 form with the fp64 running recurrence (long iteration counts): R' is
-    // kept in R64 (initialised from the fp32 R0 in R), and the coefficients in
-    // cur_c64 / c_log64; the columns, D and the diagonal stay fp32.  NULL: off.
+    // fp32 form with a double-float running recurrence (long iteration counts):
+    // R' as (hi, lo) float pairs [n][Kp] in R64 (from the fp32 R0 in R), the
+    // current coefficient as a float pair [n] in cur_c64 and the logged
+    // coefficients in fp64 [n][I_max] in c_log64; the columns, D, the diagonal and
+    // the float log of the model stay fp32.  NULL: off.
     double *R64;
     double *cur_c64;
     double *c_log64;

@@ -251,10 +251,11 @@ se_status dense_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const B
 }  // namespace
 
 // Iteration counts above which the fp32 form keeps the running recurrence of
-// eq. (20) in fp64: the fp32 recurrence's error is about constant in the scale of
-// the initial projections, so it grows relative to the projections as they decay;
-// on 16 x 16 blocks with scattered holes it passed a near tie of 1.5e-4 relative
-// at iteration 286 while the fp64 form followed the oracle to I = 500.
+// eq. (20) at fp64-class precision (double-float pairs, see k_lazy.cu): the fp32
+// recurrence's error is about constant in the scale of the initial projections,
+// so it grows relative to the projections as they decay; on 16 x 16 blocks with
+// scattered holes it passed a near tie of 1.5e-4 relative at iteration 286 while
+// the fp64 form followed the oracle to I = 500.
 constexpr int kLongRun = 256;
 
 se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
