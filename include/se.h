@@ -277,11 +277,14 @@ se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_str
 
 /* Applies, on `cuda_stream`, the fp64 -> fp32 conversion that the projection
  * kernels use for the samples (eq. 12 in the fp32 form: w s with s rounded
- * to fp32) to n device doubles `in`, writing n device floats `out`.  The
- * conversion rounds to nearest, ties to even, as IEEE 754 defines it; most
- * values take an integer-pipe path, so this lets a test check it bit for bit.
- * SE_ERR_INVALID for NULL buffers with n > 0 or n < 0. */
-se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, int n, void *cuda_stream);
+ * to fp32) to n device doubles `in`, writing n device floats `out`, and, if
+ * `back` (n device doubles) is not NULL, the fp32 -> fp64 conversion that the
+ * model kernels use for their results (eq. 9) to those floats.  The first
+ * rounds to nearest, ties to even, the second is exact, as IEEE 754 defines
+ * them; most values take integer-pipe paths, so this lets a test check both
+ * bit for bit.  SE_ERR_INVALID for NULL in/out with n > 0 or n < 0. */
+se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, double *back, int n,
+                                     void *cuda_stream);
 
 /* Wait for the work this context queued on `cuda_stream` and report
  * errors that its kernels recorded in the device status word (SE_ERR_CUDA

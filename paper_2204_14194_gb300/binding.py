@@ -103,7 +103,7 @@ def load(build_if_missing: bool = True):
             "se_tuning_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], i32),
             "se_tuned_variant": ([vp, C.c_char_p, C.POINTER(i32)], i32),
             "se_check_wait_timeout": ([vp, C.c_uint32, vp], i32),
-            "se_check_sample_conversion": ([vp, vp, vp, i32, vp], i32),
+            "se_check_sample_conversion": ([vp, vp, vp, vp, i32, vp], i32),
             "se_cert_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], i32),
             "se_plan_info": ([vp, C.c_char_p, C.c_size_t], i32),
         }
@@ -185,9 +185,10 @@ class Context:
         _check(self._lib.se_check_wait_timeout(self.handle, int(limit_us), _stream_handle(stream)),
                "se_check_wait_timeout")
 
-    def check_sample_conversion(self, x, out, stream=None):
-        """The projection kernels' fp64 -> fp32 sample conversion on device tensors."""
-        _check(self._lib.se_check_sample_conversion(self.handle, _ptr(x), _ptr(out), int(x.numel()),
+    def check_sample_conversion(self, x, out, back=None, stream=None):
+        """The projection kernels' fp64 -> fp32 sample conversion on device tensors (and,
+        into back, the model kernels' fp32 -> fp64 conversion of the results)."""
+        _check(self._lib.se_check_sample_conversion(self.handle, _ptr(x), _ptr(out), _ptr(back), int(x.numel()),
                                                     _stream_handle(stream)), "se_check_sample_conversion")
 
     def tuned_variant(self, key: str) -> int:

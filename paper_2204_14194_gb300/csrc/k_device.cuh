@@ -88,6 +88,24 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ab)[4], con
     mma_tf32(d, ab, bb0, bb1);
 }
 
+// fp32 -> fp64 (exact) on the integer pipe: a normal float's exponent is
+// rebiased and its significand shifted into place, zeros keep their sign;
+// subnormals, infinities and NaNs take the hardware conversion (out of line).
+static __device__ __noinline__ double f32_to_f64_hw(float x) { return static_cast<double>(x); }
+
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned sign = b & 0x80000000u;
+    if (e - 1u < 254u) {
+        const unsigned m = b & 0x7fffffu;
+        return __hiloint2double(static_cast<int>(sign | ((e + 896u) << 20) | (m >> 3)), static_cast<int>(m << 29));
+    }
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double(static_cast<int>(sign), 0);
+    return f32_to_f64_hw(x);
+}
+
 // One bulk (TMA) copy of a whole row of T into shared memory, completing on
 // an mbarrier; waits are bounded by %globaltimer (2 s unless given).
 __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t bytes, uint64_t *bar)

@@ -435,8 +435,50 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn(std::string *why)
     return fn;
 }
 
+// Encoded tensor maps of recent operands: the lazy rounds launch the same
+// products (same operands, same shapes) hundreds of times per batch, and an
+// encoding costs host time on every launch that is not replayed from a graph.
+struct MapKey {
+    const void *base;
+    int rows, cols, pitch, box_rows;
+    bool f16;
+    bool operator==(const MapKey &o) const
+    {
+        return base == o.base && rows == o.rows && cols == o.cols && pitch == o.pitch && box_rows == o.box_rows &&
+               f16 == o.f16;
+    }
+};
+constexpr int kMapCache = 64;
+std::mutex g_map_mu;
+MapKey g_map_key[kMapCache];
+CUtensorMap g_map_val[kMapCache];
+int g_map_n = 0, g_map_next = 0;
+
+bool encode_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_elems, int box_rows,
+                std::string *why, bool f16);
+
 bool make_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_elems, int box_rows,
               std::string *why, bool f16)
+{
+    const MapKey k{base, rows, cols, pitch_elems, box_rows, f16};
+    {
+        std::lock_guard<std::mutex> lk(g_map_mu);
+        for (int i = 0; i < g_map_n; ++i)
+            if (g_map_key[i] == k) {
+                *map = g_map_val[i];
+                return true;
+            }
+    }
+    if (!encode_map(map, base, rows, cols, pitch_elems, box_rows, why, f16)) return false;
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    const int slot = g_map_n < kMapCache ? g_map_n++ : (g_map_next++ % kMapCache);
+    g_map_key[slot] = k;
+    g_map_val[slot] = *map;
+    return true;
+}
+
+bool encode_map(CUtensorMap *map, const void *base, int rows, int cols, int pitch_elems, int box_rows,
+                std::string *why, bool f16)
 {
     auto fn = encode_fn(why);
     if (!fn) return false;

@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, con
             }
             if (nu0 + lane < I) {
                 if (bd.sel_idx) bd.sel_idx[nu0 + lane] = u;
-                if (bd.sel_coef) bd.sel_coef[nu0 + lane] = static_cast<double>(cl);
+                if (bd.sel_coef) bd.sel_coef[nu0 + lane] = dev::f32_to_f64(cl);
             }
             float cf = 0.0f;                                   // padded entries add 0
             if (nu0 + lane < I && u >= 0 && u < s.koff[s.ntr - 1] + MN) cf = cl;
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, con
         for (int e = lane; e < Mb * Nb; e += 32) {
             const int i = e / Nb, j = e - i * Nb;
             const int p = (m0 + i) * N + n0 + j;
-            if (!a.pat_support[p]) bd.out[p] = static_cast<double>(Gt[i * GP + j]);
+            if (!a.pat_support[p]) bd.out[p] = dev::f32_to_f64(Gt[i * GP + j]);
         }
         __syncwarp();   // the tile is read before the next block overwrites it
     }

@@ -406,20 +406,25 @@ __global__ void wait_probe_kernel(int *err, unsigned long long limit_ns)
     if (!dev::bar_wait(&bar, 0, limit_ns)) atomicOr(err, 1 << DEV_ERR_WAIT_TIMEOUT);
 }
 
-// The projection kernels' fp64 -> fp32 sample conversion applied to n values.
-__global__ void convert_probe_kernel(const double *in, float *out, int n)
+// The projection kernels' fp64 -> fp32 sample conversion applied to n values,
+// and (back != NULL) the model kernels' fp32 -> fp64 output conversion of the
+// results.
+__global__ void convert_probe_kernel(const double *in, float *out, double *back, int n)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = dev::f64_to_f32_rn(in[i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float f = dev::f64_to_f32_rn(in[i]);
+        out[i] = f;
+        if (back) back[i] = dev::f32_to_f64(f);
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_convert_probe(const double *in, float *out, int n, cudaStream_t st)
+cudaError_t launch_convert_probe(const double *in, float *out, double *back, int n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
-    convert_probe_kernel<<<grid, 256, 0, st>>>(in, out, n);
+    convert_probe_kernel<<<grid, 256, 0, st>>>(in, out, back, n);
     return cudaGetLastError();
 }
 

@@ -1239,11 +1239,12 @@ se_status se_check_wait_timeout(se_ctx_t *ctx, uint32_t limit_us, void *cuda_str
     return SE_OK;
 }
 
-se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, int n, void *cuda_stream)
+se_status se_check_sample_conversion(se_ctx_t *ctx, const double *in, float *out, double *back, int n,
+                                     void *cuda_stream)
 {
     if (!ctx || n < 0 || (n > 0 && (!in || !out))) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
     SE_CUDA(cudaSetDevice(ctx->device));
-    SE_CUDA(launch_convert_probe(in, out, n, static_cast<cudaStream_t>(cuda_stream)));
+    SE_CUDA(launch_convert_probe(in, out, back, n, static_cast<cudaStream_t>(cuda_stream)));
     ctx->launches += n > 0;
     return SE_OK;
 }

@@ -312,6 +312,8 @@ SepArgs pattern_sep_args(se_plan_s *pl, int mode, const BlockDesc *dd, int n, vo
 cudaError_t launch_model(se_plan_s *pl, const IterArgs &a, cudaStream_t st);
 se_status run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                    int I_max, cudaStream_t st);
+// Device bytes one block of a lazy (per-block mask) wave needs at I_max iterations.
+size_t lazy_bytes_per_block(const se_plan_s *pl, int I_max);
 se_status dev_alloc(se_ctx_s *ctx, DevBuf &b, size_t bytes);
 // Build the plan's tables on stream st if they are not cached (plan memory
 // only, nothing is allocated), else make st wait for the cached build.

@@ -116,8 +116,9 @@ cudaError_t launch_fill_desc(BlockDesc *d, int n, const StridedSpec &s, int MN, 
 // One CTA that waits on an mbarrier nothing arrives at, bounded by limit_ns;
 // it sets DEV_ERR_WAIT_TIMEOUT in *err and returns (the failure path, on purpose).
 cudaError_t launch_wait_probe(int *err, unsigned long long limit_ns, cudaStream_t st);
-// The fp64 -> fp32 sample conversion of the projection kernels, on n values.
-cudaError_t launch_convert_probe(const double *in, float *out, int n, cudaStream_t st);
+// The fp64 -> fp32 sample conversion of the projection kernels, on n values,
+// and (back != NULL) the fp32 -> fp64 output conversion of the model kernels.
+cudaError_t launch_convert_probe(const double *in, float *out, double *back, int n, cudaStream_t st);
 
 // Grid of a persistent launch: min(want, SMs x resident CTAs per SM) for
 // kernel kern at this block size and dynamic shared memory; the first call for

@@ -258,6 +258,19 @@ se_status dense_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const B
 // the fp64 form followed the oracle to I = 500.
 constexpr int kLongRun = 256;
 
+size_t se::lazy_bytes_per_block(const se_plan_s *pl, int I_max)
+{
+    const bool fp64 = pl->pc.fp64;
+    const bool r64 = !fp64 && I_max > kLongRun;
+    const size_t tsz = fp64 ? 8 : 4;
+    const size_t Kp = static_cast<size_t>(pl->Kp);
+    const size_t MNp = (static_cast<size_t>(pl->MN) + 63) / 64 * 64;
+    const size_t slots = static_cast<size_t>(std::max(1, I_max - 1));
+    const size_t opnd = fp64 ? 8 * MNp * 3 : 2 * MNp * 7;
+    return tsz * Kp * 3 + 4 * Kp + slots * Kp * tsz + static_cast<size_t>(I_max) * (4 + tsz) + opnd +
+           sizeof(BlockDesc) + 64 + (r64 ? 8 * Kp + 8 * static_cast<size_t>(I_max) + 8 : 0);
+}
+
 se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
                        int I_max, cudaStream_t st)
 {
@@ -267,14 +280,16 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
     const size_t tsz = fp64 ? 8 : 4;
     const int Kp = pl->Kp, MN = pl->MN, MNp = pl->MN_pad;
     const int slots = std::max(1, I_max - 1);
-    const size_t opnd = fp64 ? 8 * static_cast<size_t>(MNp) * 3 : 2 * static_cast<size_t>(MNp) * 7;
-    const size_t per_block = tsz * Kp * 3 + 4 * static_cast<size_t>(Kp) +
-                             static_cast<size_t>(slots) * Kp * tsz + static_cast<size_t>(I_max) * (4 + tsz) +
-                             opnd + sizeof(BlockDesc) + 64 +
-                             (r64 ? 8 * static_cast<size_t>(Kp) + 8 * static_cast<size_t>(I_max) + 8 : 0);
+    const size_t per_block = lazy_bytes_per_block(pl, I_max);
     size_t avail;
     if (ctx->budget) {
-        avail = ctx->budget > ctx->used.load() ? ctx->budget - ctx->used.load() : 0;
+        // this workspace's own lazy buffers are reused (grown in place of the old ones)
+        const size_t held = ws.desc.bytes + ws.lz_R.bytes + ws.lz_D.bytes + ws.lz_diag.bytes + ws.lz_slot.bytes +
+                            ws.lz_nslots.bytes + ws.lz_cache.bytes + ws.lz_ulog.bytes + ws.lz_clog.bytes +
+                            ws.lz_cur.bytes + ws.lz_miss.bytes + ws.lz_x.bytes + ws.lz_mk.bytes + ws.lz_v.bytes +
+                            ws.lz_R64.bytes + ws.lz_c64.bytes;
+        const size_t used = ctx->used.load();
+        avail = ctx->budget + held > used ? ctx->budget + held - used : 0;
     } else {
         // no budget: a wave may use up to 45% of the free HBM (at most 96 GiB),
         // so even 64 x 64 blocks with K = 8192 and I = 500 run thousands per wave

@@ -209,8 +209,16 @@ void serve_loop(se_ctx_s *ctx)
                 if (!any_busy) break;
             } else if (free_lane && !ctx->queue.empty()) {
                 se_plan_s *pl = ctx->queue.front()->plan;
+                // a slice fits one lazy wave within a lane's share of the budget: a larger
+                // one would run as several waves in a row, each repeating every round, and
+                // the requests queued meanwhile would form ever larger slices
+                int cap = kMaxBatch;
+                if (ctx->budget) {
+                    const size_t per = lazy_bytes_per_block(pl, std::max(1, pl->desc.iterations));
+                    cap = static_cast<int>(std::max<size_t>(1, std::min<size_t>(kMaxBatch, ctx->budget / kLanes / per)));
+                }
                 for (auto it = ctx->queue.begin();
-                     it != ctx->queue.end() && static_cast<int>(take.size()) < kMaxBatch;) {
+                     it != ctx->queue.end() && static_cast<int>(take.size()) < cap;) {
                     if ((*it)->plan == pl) {
                         (*it)->state = 1;
                         take.push_back(*it);

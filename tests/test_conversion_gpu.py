@@ -1,4 +1,5 @@
-"""The projection kernels' fp64 -> fp32 sample conversion, bit for bit.
+"""The projection kernels' fp64 -> fp32 sample conversion (and the model
+kernels' fp32 -> fp64 widening of the results), bit for bit.
 
 In the fp32 form the samples enter eq. (12) rounded to fp32.  The kernels
 round them on the integer pipe (cut the significand, round to nearest with
@@ -68,9 +69,15 @@ def test_sample_conversion_is_ieee_round_to_nearest_even():
     try:
         xd = torch.from_numpy(x).cuda()
         out = torch.full(x.shape, float("nan"), dtype=torch.float32, device="cuda")
-        ctx.check_sample_conversion(xd, out)
+        back = torch.full(x.shape, float("nan"), dtype=torch.float64, device="cuda")
+        ctx.check_sample_conversion(xd, out, back)
         ctx.sync()
         got = out.cpu().numpy()
+        # the widening of the results back to fp64 is exact
+        wide = back.cpu().numpy()
+        fin = ~np.isnan(got)
+        np.testing.assert_array_equal(np.isnan(wide), ~fin)
+        np.testing.assert_array_equal(wide[fin].view(np.uint64), got[fin].astype(np.float64).view(np.uint64))
         with np.errstate(over="ignore"):
             want = x.astype(np.float32)
         hw = xd.to(torch.float32).cpu().numpy()
