@@ -41,7 +41,7 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
 TRAFFIC_ITERATE = {}
 SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>", 2: "iterate_sym_tmem_kernel",
-              3: "iterate_sym_hot_kernel<64,3,9>"}
+              3: "iterate_sym_hot_kernel<64,3,9>", 4: "iterate_sym_hot_kernel<64,3,9,1,2> with the model of eq. 9"}
 TRAFFIC_ITERATE_SYM = {1: 36.91e6, 3: 36.92e6}
 # On-chip roofs of the parity-class iteration kernel as ncu measured them per
 # launch shape (fractions of peak; see profiles/).
@@ -399,10 +399,17 @@ def run_ours(args):
     if info.get("iterations") == "parity-classes":
         # the kernel's own work: scores, maximum, coefficient and update of one
         # class (a quarter of the atoms) per iteration; the model accumulate of
-        # eq. (9) runs in the model kernel
+        # eq. (9) (2 flops per loss pixel and iteration) when the kernel
+        # evaluates the model itself, else the model kernel does
         ops = n * I * opcount.fase_select_update_ops(M, N, K, classes=4)
         nb = 1 << max(n - 1, 0).bit_length()
-        sv = max(ctx.tuned_variant("sym:f32:%d:n%d" % (K, nb)), 0)
+        rows, cols = np.nonzero(wl.support == 0)
+        mkey = "sym:f32:%d:n%d:model%dx%d" % (K, nb, rows.max() - rows.min() + 1, cols.max() - cols.min() + 1)
+        sv = ctx.tuned_variant(mkey)
+        if sv < 0:
+            sv = max(ctx.tuned_variant("sym:f32:%d:n%d" % (K, nb)), 0)
+        if sv == 4:
+            ops += n * I * 2 * int(np.sum(wl.support == 0))
         it_kernel, it_traffic = SYM_SHAPES.get(sv, "iterate_sym kernel") + " (parity classes)", \
             TRAFFIC_ITERATE_SYM.get(sv)
         row_bytes = K // 4 * 4

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "k_device.cuh"
+#include "k_model.cuh"
 #include "se_internal.h"
 
 namespace se {
@@ -617,26 +618,20 @@ __global__ void __launch_bounds__(256) sep_model_kernel(const IterArgs a, const 
     }
 }
 
-// The same model on the tensor cores.  On the loss box (Mb x Nb, at most 32 x 32)
-// the model is a matrix product G = A B^T over the log entries nu:
-// A[i][nu] = c_nu t_p[m0 + i] (p the atom's row index) and B[j][nu] = t'_q[n0 + j],
-// taken in steps of 8 entries as mma.sync m16n8k8 products in split TF32
-// (x_s y_b + x_b y_s + x_b y_b, about 2^-21 relative, like the fp32 sums).
-// One warp per block, MT x NT output tiles of 16 x 8; the log is read 32
-// entries at a time (the next 32 in flight) through a per-warp table, as in
-// the kernel above, which also writes the caller's copies of the log.
+// The same model on the tensor cores (the per-block body is dev::model_tc_block):
+// one warp per block, the 1-D rows of the transforms staged in shared memory
+// while the iteration kernel drains, a per-warp log table and output tile.
 template <int MT, int NT>
 __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, const SepArgs s, int m0, int Mb,
                                                            int n0, int Nb)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     float *Ts = reinterpret_cast<float *>(smem);
-    const int M = s.M, N = s.N, MN = M * N, cstride = M * M + N * N;
+    const int M = s.M, N = s.N, cstride = M * M + N * N;
     int4 *Etab = reinterpret_cast<int4 *>(Ts + ((s.ntr * cstride + 3) & ~3)) + (threadIdx.x >> 5) * 32;
-    constexpr int GP = 8 * NT + 1;   // pitch of the warp's output tile (padded)
     float *Gt = reinterpret_cast<float *>(reinterpret_cast<int4 *>(Ts + ((s.ntr * cstride + 3) & ~3)) +
                                           (blockDim.x >> 5) * 32) +
-                (threadIdx.x >> 5) * (16 * MT * GP);
+                (threadIdx.x >> 5) * dev::model_tile_floats(MT, NT);
     for (int t = 0; t < s.ntr; ++t) {
         const float *gm = static_cast<const float *>(s.TM[t]);
         const float *gn = static_cast<const float *>(s.TN[t]);
@@ -646,94 +641,9 @@ __global__ void __launch_bounds__(256) sep_model_tc_kernel(const IterArgs a, con
     __syncthreads();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
-    const int g = lane >> 2, q = lane & 3;
-    // rows of the A fragments and columns of the B fragments (clamped into the
-    // area; the clamped lanes compute values that are not stored)
-    int ra[MT][2], cb[NT];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) ra[mt][h] = min(m0 + 16 * mt + g + 8 * h, M - 1);
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) cb[nt] = min(n0 + 8 * nt + g, N - 1);
-    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc) {
-        const BlockDesc bd = a.blocks[b];
-        const int I = bd.iterations;
-        const int *lu = a.log_u + static_cast<size_t>(b) * a.I_max;
-        const float *lc = a.log_c + static_cast<size_t>(b) * a.I_max;
-        float acc[MT][NT][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.0f;
-        int un = lane < I ? lu[lane] : -1;
-        float cn = lane < I ? lc[lane] : 0.0f;
-        for (int nu0 = 0; nu0 < I; nu0 += 32) {
-            int u = un;
-            const float cl = cn;
-            if (nu0 + 32 + lane < I) {
-                un = lu[nu0 + 32 + lane];
-                cn = lc[nu0 + 32 + lane];
-            }
-            if (nu0 + lane < I) {
-                if (bd.sel_idx) bd.sel_idx[nu0 + lane] = u;
-                if (bd.sel_coef) bd.sel_coef[nu0 + lane] = dev::f32_to_f64(cl);
-            }
-            float cf = 0.0f;                                   // padded entries add 0
-            if (nu0 + lane < I && u >= 0 && u < s.koff[s.ntr - 1] + MN) cf = cl;
-            else u = 0;
-            const int t = (s.ntr > 1 && u >= s.koff[1]) ? 1 : 0;
-            const int ku = u - s.koff[t];
-            __syncwarp();   // the previous round's reads of the table are done
-            Etab[lane] = make_int4(t * cstride + (ku / N) * M, t * cstride + M * M + (ku % N) * N,
-                                   __float_as_int(cf), 0);
-            __syncwarp();
-            const int steps = (min(32, I - nu0) + 7) >> 3;
-#pragma unroll 1
-            for (int ks = 0; ks < steps; ++ks) {
-                const int4 e0 = Etab[8 * ks + q], e1 = Etab[8 * ks + q + 4];
-                const float c0 = __int_as_float(e0.z), c1 = __int_as_float(e1.z);
-                uint32_t bb[NT][2], bs[NT][2];
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    dev::split_tf32(Ts[e0.y + cb[nt]], bb[nt][0], bs[nt][0]);
-                    dev::split_tf32(Ts[e1.y + cb[nt]], bb[nt][1], bs[nt][1]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    uint32_t ab[4], as[4];
-                    dev::split_tf32(c0 * Ts[e0.x + ra[mt][0]], ab[0], as[0]);
-                    dev::split_tf32(c0 * Ts[e0.x + ra[mt][1]], ab[1], as[1]);
-                    dev::split_tf32(c1 * Ts[e1.x + ra[mt][0]], ab[2], as[2]);
-                    dev::split_tf32(c1 * Ts[e1.x + ra[mt][1]], ab[3], as[3]);
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-                        dev::mma3(acc[mt][nt], ab, as, bb[nt][0], bb[nt][1], bs[nt][0], bs[nt][1]);
-                }
-            }
-        }
-        // C fragments (g, 2q), (g, 2q + 1), (g + 8, 2q), (g + 8, 2q + 1) of each tile go
-        // through the warp's tile in shared memory, so that the stores to the output
-        // are whole row segments (consecutive lanes, consecutive columns): the output
-        // may be host memory reached over the host link, where short scattered
-        // writes are slow
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    Gt[(16 * mt + g + 8 * (k >> 1)) * GP + 8 * nt + 2 * q + (k & 1)] = acc[mt][nt][k];
-        __syncwarp();
-        for (int e = lane; e < Mb * Nb; e += 32) {
-            const int i = e / Nb, j = e - i * Nb;
-            const int p = (m0 + i) * N + n0 + j;
-            if (!a.pat_support[p]) bd.out[p] = dev::f32_to_f64(Gt[i * GP + j]);
-        }
-        __syncwarp();   // the tile is read before the next block overwrites it
-    }
+    const dev::ModelLayout L = dev::model_full_layout(M, N);
+    for (int b = blockIdx.x * wpc + (threadIdx.x >> 5); b < a.n; b += gridDim.x * wpc)
+        dev::model_tc_block<MT, NT>(a, s, Ts, L, Etab, Gt, b, m0, Mb, n0, Nb, lane);
 }
 
 }  // namespace
@@ -850,6 +760,16 @@ cudaError_t launch_sep_model_tc(const IterArgs &a, const SepArgs &s, int m0, int
     return cudaLaunchKernelEx(&cfg, sep_model_tc_kernel<MT, NT>, a, s, m0, Mb, n0, Nb);
 }
 
+// Boxes up to 32 x 32 take the tensor-core form (SE_MODEL_FFMA=1: the fp32 FMA kernel).
+bool sep_model_tc_box(int Mb, int Nb)
+{
+    static const bool ffma = [] {
+        const char *env = std::getenv("SE_MODEL_FFMA");
+        return env && env[0] == '1';
+    }();
+    return !ffma && Mb > 0 && Nb > 0 && Mb <= 32 && Nb <= 32;
+}
+
 cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,
                              cudaStream_t st)
 {
@@ -859,12 +779,7 @@ cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1
     const size_t smem = 4 * ((s.ntr * (static_cast<size_t>(s.M) * s.M + static_cast<size_t>(s.N) * s.N) + 3) & ~size_t(3)) +
                         8 * 32 * sizeof(int4);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    // boxes up to 32 x 32 on the tensor cores (SE_MODEL_FFMA=1: the fp32 FMA kernel below)
-    static const bool ffma = [] {
-        const char *env = std::getenv("SE_MODEL_FFMA");
-        return env && env[0] == '1';
-    }();
-    if (!ffma && Mb <= 32 && Nb <= 32) {
+    if (sep_model_tc_box(Mb, Nb)) {
         const int nt = Nb <= 8 ? 1 : Nb <= 16 ? 2 : 4;
         if (Mb <= 16)
             return nt == 1 ? launch_sep_model_tc<1, 1>(a, s, m0, Mb, n0, Nb, smem, st)

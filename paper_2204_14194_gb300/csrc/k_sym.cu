@@ -30,6 +30,7 @@
 #include <climits>
 
 #include "k_device.cuh"
+#include "k_model.cuh"
 #include "se_internal.h"
 
 namespace se {
@@ -308,8 +309,13 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_smem_kernel(const 
 // which class; it is always a permutation of the three cold classes.  One
 // block per warp, the grid covering the batch.  Arithmetic and selection
 // order are those of the other forms (same bits).
-template <int VPT, int BPC, int MINB>
-__global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_hot_kernel(const IterArgs a)
+//
+// With MT > 0 the kernel also evaluates the model of eq. (9) on the loss box
+// once a block's iterations are done (dev::model_tc_block, the body of the
+// tensor-core model kernel, so the same bits): the block's class slots are
+// free by then and hold the warp's log table and output tile.
+template <int VPT, int BPC, int MINB, int MT = 0, int NT = 0>
+__global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_hot_kernel(const IterArgs a, const FusedModel fm)
 {
     constexpr int NCH = VPT / 4;
     constexpr int NCC = NCH / 4;
@@ -448,6 +454,30 @@ __global__ void __launch_bounds__(32 * BPC, MINB) iterate_sym_hot_kernel(const I
             const float mn = fmaxf(mc[0], mc[1]);
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) m[cc] = cc == cu ? mn : m[cc];
+        }
+        if constexpr (MT > 0) {
+            static_assert(4 * 32 + dev::model_tile_floats(MT, NT) <= 3 * NCC * 32 * 4, "table and tile fit the slots");
+            __syncwarp();   // the log is stored and the slots are no longer read
+            float *base = reinterpret_cast<float *>(myR - lane);
+            if (fm.compact) {
+                // square area, box rows and columns from m0 = n0: the rows t_p[m0 .. m0 + RA)
+                // of every transform serve both factors; staged in the warp's slots
+                constexpr int RA = 16 * MT;
+                const int M = fm.s.M, cs = M * M + fm.s.N * fm.s.N, rows = fm.s.ntr * M;
+                for (int tp = lane / RA; tp < rows; tp += 32 / RA) {
+                    const int t = tp >= M ? 1 : 0, p = tp - t * M;
+                    base[tp * RA + lane % RA] = __ldg(fm.tab + t * cs + p * M + fm.m0 + lane % RA);
+                }
+                __syncwarp();
+                const dev::ModelLayout L{-fm.m0, M * RA, RA, -fm.n0, M * RA, RA};
+                int4 *Etab = reinterpret_cast<int4 *>(base + rows * RA);
+                dev::model_tc_block<MT, NT>(a, fm.s, base, L, Etab, reinterpret_cast<float *>(Etab + 32), b, fm.m0,
+                                            fm.Mb, fm.n0, fm.Nb, lane);
+            } else {
+                int4 *Etab = reinterpret_cast<int4 *>(base);
+                dev::model_tc_block<MT, NT>(a, fm.s, fm.tab, dev::model_full_layout(fm.s.M, fm.s.N), Etab,
+                                            reinterpret_cast<float *>(Etab + 32), b, fm.m0, fm.Mb, fm.n0, fm.Nb, lane);
+            }
         }
     }
 }
@@ -1279,21 +1309,37 @@ static cudaError_t launch_sym_smem(const IterArgs &a, cudaStream_t st, int *laun
 
 int iterate_sym_variants(int Kp) { return Kp == 2048 ? 4 : 2; }
 
-static cudaError_t launch_sym_hot(const IterArgs &a, cudaStream_t st, int *launches)
+template <int MT, int NT>
+static cudaError_t launch_sym_hot(const IterArgs &a, const FusedModel &fm, cudaStream_t st, int *launches)
 {
     constexpr int BPC = 3, Q = 512;
     if (a.K != 4 * Q || a.Kp != a.K || !a.log_u || !a.log_c || !a.perm || !a.Cc || !a.Dkp)
         return cudaErrorInvalidValue;
+    if (MT > 0 && (!fm.tab || fm.Mb <= 0 || fm.Nb <= 0 || fm.Mb > 16 * MT || fm.Nb > 8 * NT || fm.m0 < 0 ||
+                   fm.n0 < 0 || fm.m0 + fm.Mb > fm.s.M || fm.n0 + fm.Nb > fm.s.N || !a.pat_support))
+        return cudaErrorInvalidValue;
     const size_t smem = sizeof(float) * static_cast<size_t>(BPC) * 3 * Q;   // three class slots per block
     const int grid = (a.n + BPC - 1) / BPC;                                   // one block per warp
-    auto kern = iterate_sym_hot_kernel<64, BPC, 9>;
+    auto kern = iterate_sym_hot_kernel<64, BPC, 9, MT, NT>;
     // the carveout of the other parity-class forms: batches that run side by side on
     // several streams (the chunks of a host-buffer call) can then share the SMs
     cudaError_t e = prefer_max_shared(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return e;
-    kern<<<grid, 32 * BPC, smem, st>>>(a);
+    kern<<<grid, 32 * BPC, smem, st>>>(a, fm);
     if (launches) ++*launches;
     return cudaGetLastError();
+}
+
+bool sym_model_box(int Mb, int Nb) { return Mb > 0 && Nb > 0 && ((Mb <= 16 && Nb <= 16) || (Mb <= 32 && Nb <= 8)); }
+
+cudaError_t launch_iterate_sym_model(const IterArgs &a, const FusedModel &fm, cudaStream_t st, int *launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    if (!sym_model_box(fm.Mb, fm.Nb)) return cudaErrorInvalidValue;
+    // the tile shapes of the tensor-core model kernel for the same box (at most two
+    // tiles: the model's accumulators then fit the iteration kernel's registers)
+    if (fm.Mb > 16) return launch_sym_hot<2, 1>(a, fm, st, launches);
+    return fm.Nb <= 8 ? launch_sym_hot<1, 1>(a, fm, st, launches) : launch_sym_hot<1, 2>(a, fm, st, launches);
 }
 
 static cudaError_t launch_sym_tmem(const IterArgs &a, cudaStream_t st, int *launches)
@@ -1317,7 +1363,7 @@ cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches
 {
     if (a.n <= 0) return cudaSuccess;
     if (variant == 2 && a.Kp == 2048) return launch_sym_tmem(a, st, launches);   // projections in tensor memory
-    if (variant == 3 && a.Kp == 2048) return launch_sym_hot(a, st, launches);    // hot class in registers
+    if (variant == 3 && a.Kp == 2048) return launch_sym_hot<0, 0>(a, FusedModel{}, st, launches);   // hot class in registers
     if (variant == 1) {   // projections in shared memory
         switch (a.Kp) {
         case 512: return launch_sym_smem<16, 4, 12>(a, st, launches);

@@ -405,8 +405,10 @@ cudaError_t se::launch_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, const B
     return run_sep(ctx, pl, pattern_sep_args(pl, 0, dd, n, r0, scaled), st);
 }
 
-cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched)
+cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched,
+                                      bool *model_done)
 {
+    if (model_done) *model_done = false;
     if (pl->sym && !a.cert_flag) {
         a.perm = pl->d_perm.as<int>();
         a.Cc = pl->d_Cc.as<float>();
@@ -416,6 +418,40 @@ cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a,
         int nb = 1;
         while (nb < a.n) nb <<= 1;
         const std::string skey = "sym:f32:" + std::to_string(pl->Kp) + ":n" + std::to_string(nb);
+        const int Mb = pl->box[1] - pl->box[0], Nb = pl->box[3] - pl->box[2];
+        if (model_done && pl->Kp == 2048 && pl->sep_full && pl->nB > 0 && pl->d_model_tab.ptr &&
+            sep_model_tc_box(Mb, Nb) && sym_model_box(Mb, Nb)) {
+            // the iterations and the model of eq. (9) as one stage: every form followed
+            // by the tensor-core model kernel, or the last-updated-class form that
+            // evaluates the model itself (the same operations, so the same bits)
+            FusedModel fm{};
+            fm.s = pattern_sep_args(pl, 0, nullptr, 0, nullptr);
+            fm.tab = pl->d_model_tab.as<float>();
+            fm.m0 = pl->box[0];
+            fm.Mb = Mb;
+            fm.n0 = pl->box[2];
+            fm.Nb = Nb;
+            {
+                // the tile shapes the launch takes for this box (16 MT x 8 NT)
+                const int MT = Mb <= 16 ? 1 : 2, NT = Nb <= 8 ? 1 : Nb <= 16 ? 2 : 4;
+                const int slots = 3 * (pl->Kp / 4), need = pl->sep_ntr * pl->M * 16 * MT + 128 + 16 * MT * (8 * NT + 1);
+                fm.compact = pl->M == pl->N && fm.m0 == fm.n0 && fm.m0 + 16 * MT <= pl->M && fm.n0 + 8 * NT <= pl->N &&
+                             8 * NT <= 16 * MT && need <= slots;
+            }
+            const int nv = iterate_sym_variants(pl->Kp);
+            *model_done = true;
+            return tune_run(ctx, skey + ":model" + std::to_string(Mb) + "x" + std::to_string(Nb), nv + 1, st,
+                            [&](int v) {
+                                *launched = 0;
+                                if (v == nv) return launch_iterate_sym_model(a, fm, st, launched);
+                                cudaError_t e = launch_iterate_sym(a, st, launched, v);
+                                if (e == cudaSuccess) {
+                                    e = launch_model(pl, a, st);
+                                    ++*launched;
+                                }
+                                return e;
+                            });
+        }
         return tune_run(ctx, skey, iterate_sym_variants(pl->Kp), st, [&](int v) {
             *launched = 0;
             return launch_iterate_sym(a, st, launched, v);
@@ -716,10 +752,12 @@ se_status se::run_batch(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, cons
         a.cert_delta = kCertGap;
     }
     int launched = 0;
+    bool model_done = false;   // the model of eq. (9) ran with the iterations
     tok = stage_begin(ctx, 3, st);
-    cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched) : launch_iterations_f32(ctx, pl, a, st, &launched);
+    cudaError_t e = fp64 ? launch_iterate_full<double>(a, st, &launched)
+                         : launch_iterations_f32(ctx, pl, a, st, &launched, &model_done);
     stage_end(ctx, tok, st);
-    if (e == cudaSuccess && !fp64) {
+    if (e == cudaSuccess && !fp64 && !model_done) {
         tok = stage_begin(ctx, 4, st);
         e = launch_model(pl, a, st);
         stage_end(ctx, tok, st);

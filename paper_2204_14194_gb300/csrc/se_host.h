@@ -279,6 +279,7 @@ struct se_plan_s {
     int sep_ntr = 0, sep_koff[2] = {0, 0};
     se::DevBuf d_sepM[2], d_sepN[2], d_rho;
     se::DevBuf d_sep_img;        // fp32 constants in the transform kernels' shared-memory layout
+    se::DevBuf d_model_tab;      // fp32 1-D rows in the model kernel's layout (T_t, then T'_t, per t)
     cudaEvent_t tables_ready = nullptr;
     std::mutex tmu;
     // measured costs (ms) for the full-versus-lazy choice: one table build, one
@@ -341,7 +342,10 @@ se_status run_complex(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, int I_
 // the permutation and the compact table buffers; sets pl->sym.
 se_status setup_sym(se_ctx_s *ctx, se_plan_s *pl);
 // The fp32 iterations: the parity-class kernel when pl->sym, else the tuned shapes.
-cudaError_t launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched);
+// With model_done given, a parity-class plan of the transform form may also run
+// the model (eq. 9) in the same tuned stage; *model_done then says so.
+cudaError_t launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a, cudaStream_t st, int *launched,
+                                  bool *model_done = nullptr);
 // A transform-domain launch with the schedule chosen by the autotuner.
 cudaError_t run_sep(se_ctx_s *ctx, se_plan_s *pl, const SepArgs &sa, cudaStream_t st);
 // R^(0) of n pattern blocks in the transform form (needs pl->sep_full): the

@@ -180,6 +180,12 @@ int iterate_cert_max_kp();
 // memory (more blocks per SM), 2 (Kp = 2048) in tensor memory, 3 (Kp = 2048) the
 // last-updated class in registers and the rest in shared memory; identical results.
 cudaError_t launch_iterate_sym(const IterArgs &a, cudaStream_t st, int *launches, int variant = 0);
+struct FusedModel;
+// The last-updated-class form (K = 2048) with the model of eq. (9) evaluated in
+// the same kernel, for loss boxes that sym_model_box accepts (up to 16 x 16 or
+// 32 x 8: one or two 16 x 8 output tiles).
+bool sym_model_box(int Mb, int Nb);
+cudaError_t launch_iterate_sym_model(const IterArgs &a, const FusedModel &fm, cudaStream_t st, int *launches);
 int iterate_sym_variants(int Kp);
 // Folded separable transforms of the parity-class form (M, N in {16, 32};
 // K = ntr M N, atoms k = t M N + p N + q; class c = 2 (p mod 2) + (q mod 2);
@@ -312,6 +318,23 @@ cudaError_t launch_model_f32(const IterArgs &a, cudaStream_t st);
 // s.N, s.ntr, s.TM, s.TN, s.koff.
 cudaError_t launch_sep_model(const IterArgs &a, const SepArgs &s, int m0, int m1, int n0, int n1,
                              cudaStream_t st);
+// True when launch_sep_model takes the tensor-core form for an Mb x Nb box.
+bool sep_model_tc_box(int Mb, int Nb);
+
+// The same model evaluated by the parity-class iteration kernel itself once a
+// block's iterations are done (same operations as the tensor-core model kernel,
+// so the same bits): the pattern's transforms, their 1-D rows in the model
+// kernel's layout and the loss box [m0, m0 + Mb) x [n0, n0 + Nb).
+struct FusedModel {
+    SepArgs s;
+    const float *tab;   // ntr (M M + N N) floats: T_t[p][m] at t (M M + N N) + p M + m,
+                        // then T'_t[q][n] at t (M M + N N) + M M + q N + n
+    int m0, Mb, n0, Nb;
+    int compact;        // 1: M = N, m0 = n0, no clamped box row or column, and the rows
+                        //   t_p[m0 .. m0 + 16 MT) of every transform fit the block's slots
+                        //   beside the log table and output tile (staged there, serving
+                        //   both factors); 0: the rows are read from tab
+};
 
 // Seeded synthetic samples in [0, 255) for the probe batches of the tuner.
 cudaError_t launch_probe_samples(double *s, long long total, uint32_t seed, cudaStream_t st);

@@ -151,12 +151,14 @@ se_status se::ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl)
         if (!pl->pc.fp64) {
             // the constants as the fp32 kernels hold them in shared memory
             const int M = pl->M, N = pl->N;
-            std::vector<float> img;
+            std::vector<float> img, mtab;
             img.reserve(static_cast<size_t>(t) * (M * M + N * N) + MN);
             for (int k = 0; k < t; ++k) {
                 std::vector<float> tm(static_cast<size_t>(M) * M), tn(static_cast<size_t>(N) * N);
                 LZ_CUDA(cudaMemcpy(tm.data(), pl->d_sepM[k].ptr, tm.size() * 4, cudaMemcpyDeviceToHost));
                 LZ_CUDA(cudaMemcpy(tn.data(), pl->d_sepN[k].ptr, tn.size() * 4, cudaMemcpyDeviceToHost));
+                mtab.insert(mtab.end(), tm.begin(), tm.end());
+                mtab.insert(mtab.end(), tn.begin(), tn.end());
                 for (int m = 0; m < M; ++m)
                     for (int p = 0; p < M; ++p) img.push_back(tm[static_cast<size_t>(p) * M + m]);
                 for (int n = 0; n < N; ++n)
@@ -165,6 +167,7 @@ se_status se::ensure_sep_ops(se_ctx_s *ctx, se_plan_s *pl)
             for (int p = 0; p < MN; ++p) img.push_back(static_cast<float>(rho[p]));
             while (img.size() % 4) img.push_back(0.0f);
             LZ_TRY(upload_vec(ctx, pl->d_sep_img, img));
+            LZ_TRY(upload_vec(ctx, pl->d_model_tab, mtab));
         }
     }
     pl->sep_checked = true;

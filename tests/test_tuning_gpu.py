@@ -92,11 +92,13 @@ def test_forced_variants_are_bitwise_identical(case):
 @pytest.mark.parametrize("n,I", [(300, 80), (4096, 80), (5, 33), (7, 1)])
 def test_parity_class_iteration_variants_are_bitwise_identical(n, I):
     """Projections in registers, in shared memory, in tensor memory, and the
-    last-updated class in registers with the rest in shared memory: the same
-    selections, coefficients and outputs, bit for bit."""
+    last-updated class in registers with the rest in shared memory, each
+    followed by the model kernel, and the last form evaluating the model of
+    eq. 9 itself (variant 4): the same selections, coefficients and outputs,
+    bit for bit."""
     samples = np.stack([W.patch(32, 7600 + i % 997) for i in range(n)])
     res = []
-    for v in (0, 1, 2, 3):
+    for v in (0, 1, 2, 3, 4):
         ctx = _ctx(force=f"sym:={v}")
         try:
             plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, I, prec="bf16x6")
@@ -271,3 +273,68 @@ def test_graph_replay_matches_direct_launches(basis, K):
         plan.close()
     finally:
         ctx.close()
+
+
+def _mirrored_pattern(kind):
+    """Symmetric 32 x 32 supports whose loss bounding boxes select each tile
+    shape of the model kernel (16 x 8 tiles) and each form of the model in the
+    iteration kernel: rows staged in the slots (square area, box from m0 = n0),
+    rows read from global memory, or no fused form (more than two tiles)."""
+    sup = np.ones((32, 32), dtype=np.uint8)
+    if kind == "box8x8":        # one tile, staged rows
+        sup[12:20, 12:20] = 0
+    elif kind == "box16x16":    # two tiles, staged rows (the headline box)
+        sup[8:24, 8:24] = 0
+    elif kind == "box16x8":     # one tile, m0 != n0: rows from global memory
+        sup[8:24, 12:20] = 0
+    elif kind == "strip32x8":   # two tiles of 16 rows, rows from global memory
+        sup[:, 12:20] = 0
+    else:   # a centred box and four mirrored 2 x 2 holes: a 30 x 30 box, separate model kernel only
+        sup[8:24, 8:24] = 0
+        for r, c in ((1, 2), (2, 28)):
+            for rr, cc in ((r, c), (30 - r, c), (r, 30 - c), (30 - r, 30 - c)):
+                sup[rr:rr + 2, cc:cc + 2] = 0
+    assert (sup == sup[::-1]).all() and (sup == sup[:, ::-1]).all()
+    return sup
+
+
+@pytest.mark.parametrize("kind", ["box8x8", "box16x16", "box16x8", "strip32x8", "holes"])
+def test_iterations_with_the_model_in_one_kernel(kind):
+    """The last-updated-class iterations that evaluate the model of eq. 9 in
+    the same kernel (variant 4) give the bits of the same iterations followed
+    by the tensor-core model kernel (variant 3) on every loss-box shape, and
+    meet the oracle's bars (indices up to the first near tie at 1e-4,
+    coefficients 1e-3, PSNR 0.05 dB).  Boxes of more than two output tiles
+    keep the separate model kernel."""
+    from helpers import OracleSetup, psnr
+    sup = _mirrored_pattern(kind)
+    n, I = 60, 70
+    samples = np.stack([W.patch(32, 8100 + i) for i in range(n)])
+    res, launches = [], []
+    for v in (3, 4):
+        ctx = _ctx(force=f"sym:={v}")
+        try:
+            plan = ctx.plan(32, 32, "dct_wht", 2048, 0.8, 0.5, I, prec="bf16x6", support=sup)
+            assert plan.info().get("iterations") == "parity-classes"
+            _run(ctx, plan, samples)   # the table is built by the first call
+            l0 = ctx.stats()["kernel_launches"]
+            res.append(_run(ctx, plan, samples))
+            launches.append(ctx.stats()["kernel_launches"] - l0)
+            plan.close()
+        finally:
+            ctx.close()
+    fused = kind != "holes"
+    assert launches[1] == launches[0] - int(fused), launches   # no separate model kernel when fused
+    for x, y in zip(res[0], res[1]):
+        np.testing.assert_array_equal(x, y)
+    out, u, c = res[1]
+    o = OracleSetup("dct_wht", 32, 32, 0.8, sup, tables=False)
+    ro, ru, rc, rm, st = O.se_original_batch(o.phi, o.w, samples, 0.5, I, o.dup, margins=True)
+    assert st == 0
+    for b in range(n):
+        t = first_near_tie(rm[b], 1e-4)
+        np.testing.assert_array_equal(u[b, :t], ru[b, :t])
+        assert coef_rel_err(c[b, :t], rc[b, :t]).max() <= 1e-3
+        np.testing.assert_array_equal(out[b][sup > 0], samples[b][sup > 0])
+    loss = np.broadcast_to(sup == 0, out.shape)
+    assert abs(psnr(out, samples, loss) - psnr(ro, samples, loss)) <= 0.05
