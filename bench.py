@@ -850,15 +850,19 @@ def secondary_gauss1080(prec: str, steps: int = 5, warmup: int = 3, oracle_block
     na = int(np.sum(wl.support))
     _hbm, tc_peak, peak_kind = measured_peaks()
     npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(prec, 0)
+    # the table of eq. 16 from two-part fp16 splits takes three products (fp16 runs at
+    # the bf16 rate on the tensor cores)
+    tpairs = 3 if plan.info().get("table_products") == "f16x3" else npairs
     tensor = None
     if npairs and stages.get("projections", 0) > 0 and stages.get("tables", 0) > 0:
         proj = 2.0 * K * n * na * npairs / (stages["projections"] / 1e3) / 1e12
-        tab = 1.0 * K * (K + 1) * na * npairs / (stages["tables"] / 1e3) / 1e12
+        tab = 1.0 * K * (K + 1) * na * tpairs / (stages["tables"] / 1e3) / 1e12
         tensor = {"projections_tflops": proj, "tables_tflops": tab, "peak": tc_peak,
                   "projections_frac": proj / tc_peak, "tables_frac": tab / tc_peak,
+                  "tables_ms": stages["tables"], "projections_ms": stages["projections"],
                   "peak_kind": peak_kind + " bf16 dense",
                   "flops": "split products counted: 2 K |A| n x %d (eq. 12), K (K + 1) |A| x %d "
-                           "(eq. 16, the symmetric half)" % (npairs, npairs)}
+                           "(eq. 16, the symmetric half)" % (npairs, tpairs)}
     # error against the FP64 oracle on the first blocks
     import oracle as O
     phi = np.ascontiguousarray(wl.dictionary, dtype=np.float64)

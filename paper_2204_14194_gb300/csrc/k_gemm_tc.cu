@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "se_internal.h"
@@ -105,6 +106,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+
+// Bulk tensor store of a shared-memory box to global memory (bulk async-group
+// completion); the box is the tensor map's, the coordinates its origin.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_commit_and_wait_read()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -186,7 +203,8 @@ struct TcCfg {
 template <int BN, int NP, bool GROUPED, int CPS = 1>
 __global__ void __launch_bounds__(THREADS, CPS)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-               const __grid_constant__ TcGemmArgs p, int mt, int nt)
+               const __grid_constant__ CUtensorMap tmO, const __grid_constant__ TcGemmArgs p, int mt, int nt,
+               int tma_out)
 {
     using Cfg = TcCfg<BN, NP, GROUPED, CPS>;
     constexpr int STAGES = Cfg::STAGES;
@@ -344,12 +362,106 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // -------------------------------------------------------------- epilogue
     bool ok = mbar_wait(accum, 0, nullptr, WAIT_NS);
     if (!ok) atomicOr(p.err, 1 << DEV_ERR_WAIT_TIMEOUT);
-    ok = ok && !*abort_flag;
+    ok = __syncthreads_and(ok && !*abort_flag) != 0;   // one outcome for the whole CTA
     tc_fence_after();
     __syncwarp();
 
     const int m = tm * BM + warp * 32 + lane;
     const bool diag_tile = p.symmetric && tm == tn;
+    if (BN == BM && p.symmetric && tma_out) {
+        // Gram mode through shared memory and bulk tensor stores: the pipeline ring
+        // (idle once the accumulator is complete) holds the tile as four boxes of
+        // 128 rows x 32 floats in the 128-byte swizzled layout of the output map
+        // (16-byte chunk c of row r at r * 128 + ((c ^ (r mod 8)) * 16)).  Pass 0
+        // writes the direct half out[m][n] = D[m][n] scale[n]; pass 1 the mirrored
+        // half out[n][m] = D[m][n] scale[m] (a diagonal tile takes both triangles
+        // in one pass: n >= m direct, n > m mirrored).  Two buffers when the ring
+        // holds them, else one reused after the first stores have read it.
+        constexpr int BOX = BM * 32 * 4;                                   // 16 KiB
+        constexpr bool TWO = STAGES * Cfg::STAGE >= 8 * BOX;
+        static_assert(BN != BM || STAGES * Cfg::STAGE >= 4 * BOX, "one tile buffer fits the ring");
+        const int r = warp * 32 + lane;                                    // tile row of this thread
+        const float sm = p.scale && m < p.M ? p.scale[m] : 1.0f;
+#pragma unroll 1
+        for (int pass = 0; pass < (diag_tile ? 1 : 2); ++pass) {
+            const uint32_t buf = base + (TWO ? pass * 4 * BOX : 0);
+            if (pass == 1 && !TWO) {
+                // the first pass's stores have read the buffer (thread 0 waited)
+                __syncthreads();
+            }
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32;
+                TMEM_LD_32x32b_X32(taddr, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (has_small) {
+                    uint32_t q[32];
+                    TMEM_LD_32x32b_X32(taddr + BN, q);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(q[j]) + __uint_as_float(v[j]));
+                }
+                if (p.post != 0.0f) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) * p.post);
+                }
+                const int n0 = tn * BN + c * 32;
+                if (pass == 0) {
+                    // row r of box c: 8 chunks of 4 floats, scaled by the column's factor
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float f[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int n = n0 + 4 * q + e;
+                            const float sn = p.scale && n < p.N ? __ldg(p.scale + n) : 1.0f;
+                            f[e] = __uint_as_float(v[4 * q + e]) * sn;
+                        }
+                        const bool keep = !diag_tile || c * 32 + 4 * q + 3 >= r;   // some n >= m in the chunk
+                        if (keep) {
+                            const uint32_t a = buf + c * BOX + r * 128 + ((q ^ (r & 7)) << 4);
+                            if (!diag_tile || c * 32 + 4 * q >= r) {
+                                asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(f[0]),
+                                             "f"(f[1]), "f"(f[2]), "f"(f[3])
+                                             : "memory");
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (c * 32 + 4 * q + e >= r)
+                                        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a + 4 * e), "f"(f[e]) : "memory");
+                            }
+                        }
+                    }
+                }
+                if (pass == 1 || diag_tile) {
+                    // mirrored: element (row n - tn BN, column r) of box r / 32, scaled by
+                    // this row's factor; a diagonal tile keeps the rows below its diagonal
+                    const uint32_t bx = buf + (r >> 5) * BOX;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int rn = c * 32 + j;   // tile row of the mirrored element
+                        if (diag_tile && rn <= r) continue;
+                        const uint32_t a = bx + rn * 128 + ((((r & 31) >> 2) ^ (rn & 7)) << 4) + ((r & 3) << 2);
+                        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(__uint_as_float(v[j]) * sm) : "memory");
+                    }
+                }
+            }
+            if (!ok) continue;   // the same for every thread of the CTA
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+#pragma unroll 1
+                for (int b = 0; b < BN / 32; ++b) {
+                    if (pass == 0) tma_store_2d(&tmO, tn * BN + 32 * b, tm * BM, buf + b * BOX);   // direct
+                    else tma_store_2d(&tmO, tm * BM + 32 * b, tn * BN, buf + b * BOX);            // mirrored
+                }
+                tma_store_commit_and_wait_read();
+            }
+        }
+        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+        __syncthreads();
+    } else {
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
@@ -407,6 +519,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             }
             __syncwarp();
         }
+    }
     }
 
     tc_fence_before();
@@ -501,13 +614,32 @@ bool encode_map(CUtensorMap *map, const void *base, int rows, int cols, int pitc
     return true;
 }
 
+// The fp32 output of a Gram product for bulk tensor stores: boxes of 128 rows x
+// 32 floats (128 bytes, the 128-byte swizzle); false if the layout does not
+// allow it (the epilogue then stores element by element).
+bool encode_out_map(CUtensorMap *map, const float *out, int rows, int cols, long long ldo)
+{
+    auto fn = encode_fn(nullptr);
+    if (!fn || (reinterpret_cast<uintptr_t>(out) & 15u) || (ldo * 4) % 16 || ldo < cols || rows <= 0 || cols <= 0)
+        return false;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldo) * 4};
+    cuuint32_t box[2] = {32, static_cast<cuuint32_t>(BM)};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(out), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN, int NP, bool GROUPED, int CPS = 1>
 cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 {
     using Cfg = TcCfg<BN, NP, GROUPED, CPS>;
-    CUtensorMap mA, mB;
+    CUtensorMap mA, mB, mO;
     if (!make_map(&mA, a.A, a.M, a.lda, a.lda, BM, why, a.f16 != 0)) return cudaErrorInvalidValue;
     if (!make_map(&mB, a.B, a.N, a.ldb, a.ldb, BN, why, a.f16 != 0)) return cudaErrorInvalidValue;
+    std::memset(&mO, 0, sizeof(mO));
+    const int tma_out = BN == BM && a.symmetric && encode_out_map(&mO, a.out, a.M, a.N, a.ldo) ? 1 : 0;
     const int mt = (a.M + BM - 1) / BM;
     const int nt = (a.N + BN - 1) / BN;
     const int grid = a.symmetric ? mt * (mt + 1) / 2 : mt * nt;
@@ -519,7 +651,7 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_gemm_kernel<BN, NP, GROUPED, CPS><<<grid, THREADS, Cfg::SMEM, st>>>(mA, mB, a, mt, nt);
+    tc_gemm_kernel<BN, NP, GROUPED, CPS><<<grid, THREADS, Cfg::SMEM, st>>>(mA, mB, mO, a, mt, nt, tma_out);
     return cudaGetLastError();
 }
 

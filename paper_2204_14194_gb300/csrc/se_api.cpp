@@ -557,21 +557,31 @@ se_status build_tables(se_ctx_s *ctx, se_plan_s *pl, cudaStream_t st)
                                               pl->K, Kp, pl->d_invC.as<float>(), pl->d_Dk.as<float>(),
                                               pl->d_nadm.as<int>(), st));
         TcGemmArgs g{};
-        g.A = pl->d_Gbf.ptr;
-        g.B = pl->d_Gbf.ptr;
         g.M = Kp;
         g.N = Kp;
-        g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
         g.ka_pad = pl->ka_pad;
-        g.npairs = pl->pc.npairs;
-        for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+        if (pl->f16_table) {
+            // hh, hl, lh of the fp16 parts (the small products first); both scales undone
+            const int pa[3] = {1, 0, 0}, pb[3] = {0, 1, 0};
+            g.A = g.B = pl->d_GH.ptr;
+            g.lda = g.ldb = 2 * pl->ka_pad;
+            g.npairs = 3;
+            for (int i = 0; i < 3; ++i) { g.pa[i] = pa[i]; g.pb[i] = pb[i]; }
+            g.f16 = 1;
+            g.post = 1.0f / (pl->g_f16_scale * pl->g_f16_scale);
+        } else {
+            g.A = g.B = pl->d_Gbf.ptr;
+            g.lda = g.ldb = pl->pc.nparts * pl->ka_pad;
+            g.npairs = pl->pc.npairs;
+            for (int i = 0; i < 8; ++i) { g.pa[i] = pl->pc.pa[i]; g.pb[i] = pl->pc.pb[i]; }
+        }
         g.out = pl->d_C.as<float>();
         g.ldo = Kp;
         g.symmetric = 1;
         g.err = ctx->ws_err.as<int>();
         g.scale = pl->d_Dk.as<float>();
         const std::string key = "gemm_table:" + std::to_string(Kp) + ":" + std::to_string(pl->ka_pad) + ":p" +
-                                std::to_string(pl->pc.npairs);
+                                std::to_string(g.npairs) + (pl->f16_table ? "h" : "");
         cudaError_t e = tune_run(ctx, key, tc_gemm_variants(g), st,
                                  [&](int v) { return launch_tc_gemm(g, st, &why, v); });
         if (e != cudaSuccess) return fail(SE_ERR_CUDA, "table GEMM: " + why + " " + cudaGetErrorString(e));
@@ -1055,9 +1065,27 @@ se_status se_plan(se_ctx_t *ctx, const se_plan_desc *desc, se_plan_t **out)
                 pb[static_cast<size_t>(k) * nBa + j] =
                     static_cast<float>(pl->phi[static_cast<size_t>(k) * MN + pl->b_idx[j]]);
         SE_TRY(upload(ctx, pl->d_PhiB, pb));
-        SE_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka * 2));
-        SE_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka, ka, ka, pl->pc.nparts,
-                                  pl->d_Gbf.as<uint16_t>(), ctx->stream));
+        if (d.prec == SE_PREC_BF16X6) {
+            // the table of eq. (16) from two fp16 parts per entry of G (11 + 11 significant
+            // bits) and three products, about 2^-21 relative like the six split-bf16
+            // products, for half the tensor work and two thirds of the operand bytes; G is
+            // scaled by a power of two that puts its largest entry at or below 2^14 (no
+            // overflow of either part, low parts normal) and the epilogue undoes it
+            double gmax = 0.0;
+            for (int k = 0; k < K; ++k)
+                for (int j = 0; j < pl->nA; ++j)
+                    gmax = std::max(gmax, std::fabs(pl->phi[static_cast<size_t>(k) * MN + pl->a_idx[j]] * sqw[j]));
+            pl->g_f16_scale = gmax > 0.0 ? static_cast<float>(std::ldexp(1.0, 14 - static_cast<int>(std::ceil(std::log2(gmax)))))
+                                         : 1.0f;
+            SE_TRY(dev_alloc(ctx, pl->d_GH, static_cast<size_t>(Kp) * 2 * ka * 2));
+            SE_CUDA(launch_split_f16(pl->d_G64.as<double>(), Kp, ka, ka, ka, pl->g_f16_scale, pl->d_GH.as<uint16_t>(),
+                                     ctx->stream));
+            pl->f16_table = true;
+        } else {
+            SE_TRY(dev_alloc(ctx, pl->d_Gbf, static_cast<size_t>(Kp) * pl->pc.nparts * ka * 2));
+            SE_CUDA(launch_split_bf16(pl->d_G64.as<double>(), Kp, ka, ka, ka, pl->pc.nparts,
+                                      pl->d_Gbf.as<uint16_t>(), ctx->stream));
+        }
         // Phi_A w for the projections of eq. (12): the samples enter unweighted
         std::vector<double> Gw(static_cast<size_t>(Kp) * ka, 0.0);
         for (int k = 0; k < K; ++k) {
@@ -1561,7 +1589,7 @@ se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len)
                     " table=" + (plan->dft_w ? "dft-of-weights" : "table") + " iterations=" +
                     (plan->cplx ? "complex" : plan->pc.fp64 ? "fp64" : plan->sym ? "parity-classes" : "general") +
                     (plan->sym_tc ? " projections=split-tf32" : "") + (plan->certified ? " certified" : "") +
-                    (plan->f16_cols ? " columns=f16x3" : "");
+                    (plan->f16_cols ? " columns=f16x3" : "") + (plan->f16_table ? " table_products=f16x3" : "");
     std::snprintf(buf, len, "%s", t.c_str());
     return SE_OK;
 }

@@ -243,6 +243,9 @@ struct se_plan_s {
     se::DevBuf d_a_idx, d_b_idx, d_sqrtw, d_pattern, d_dup;
     se::DevBuf d_G64;                     // Kp x ka_pad fp64, G = phi_A sqrt(w)
     se::DevBuf d_Gbf;                     // Kp x nparts*ka_pad bf16 split of G (tables)
+    se::DevBuf d_GH;                      // Kp x 2*ka_pad fp16 split of g_f16_scale * G (tables, f16_table)
+    bool f16_table = false;               // the table of eq. (16) from two-part fp16 splits (3 products)
+    float g_f16_scale = 1.0f;             // power of two putting the largest |G| at or below 2^14
     se::DevBuf d_Gwbf;                    // Kp x nparts*ka_pad bf16 split of Phi_A w (projections)
     se::DevBuf d_PhiB;                    // Kp x nB (T) atoms on the loss pixels ([Kp][2][nB] complex)
     // complex atoms: [Gi|-Gr] rows for Im C (fp64 / bf16 split), [phi_r w; -phi_i w] rows of eq. 12 (fp64)
