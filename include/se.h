@@ -266,6 +266,39 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n,
                               const double *samples, double *out,
                               int32_t *sel_idx, double *sel_coef, int iterations);
 
+/* Asynchronous form of se_extrapolate_host (the same operation: Alg. 2 table
+ * if not cached, eq. 12, Alg. 3 with eqs. 18-20, eq. 9 and the replacement of
+ * the loss area), for a stream of batches: it enqueues the batch and returns a
+ * ticket; the results are in out (and the optional logs) once
+ * se_host_wait(ctx, ticket) has returned SE_OK.  Each call copies its n
+ * blocks of samples (host, MN doubles each, block-major) into a device buffer
+ * of one of the context's three host slots with a copy engine, runs the batch
+ * there in place, and copies back: with out == samples, of every block, the
+ * samples from the first to the last one of the pattern's loss bounding box
+ * (every sample of a 3-D block), else every sample; then the logs (host int32
+ * [n][I] and fp64 [n][I], each optional).
+ * So the copies of one call overlap the computation of the calls in flight
+ * beside it.  The caller keeps samples, out and the logs unchanged and valid
+ * until the wait; they should be pinned (page-locked: cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory), since copies from pageable memory are
+ * not asynchronous.  A call that finds all three slots busy first waits for
+ * the oldest one.  A table rebuild (first use, se_plan_reset_tables) waits on
+ * the device for the calls still in flight.  Device errors of any call of the
+ * context are reported by the next se_host_wait or se_sync.  Returns
+ * SE_ERR_INVALID for NULL arguments, n < 0, iterations < 0, complex plans or
+ * a plan of another context; n = 0 returns SE_OK and ticket 0.  Serialised
+ * with the other batch calls of the context on the host. */
+se_status se_extrapolate_host_async(se_ctx_t *ctx, const se_plan_t *plan, int n,
+                                    const double *samples, double *out,
+                                    int32_t *sel_idx, double *sel_coef, int iterations,
+                                    uint64_t *ticket);
+
+/* Wait for the asynchronous host-buffer call `ticket` (0 and tickets already
+ * waited for return SE_OK at once).  SE_ERR_CUDA with a message if the
+ * context's device status word reports an error (it is then cleared);
+ * SE_ERR_UNKNOWN_TICKET for a ticket that was never issued. */
+se_status se_host_wait(se_ctx_t *ctx, uint64_t ticket);
+
 /* Exercises the device failure path: queues on `cuda_stream` one CTA that
  * waits on an mbarrier nothing arrives at.  Like every wait in the library's
  * kernels the wait is bounded (%globaltimer); after limit_us microseconds

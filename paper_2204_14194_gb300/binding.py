@@ -31,7 +31,8 @@ EXPORTS = ["se_ctx_create", "se_ctx_destroy", "se_plan", "se_plan_destroy", "se_
            "se_submit", "se_poll", "se_cancel", "se_last_error", "se_stats", "se_set_profiling",
            "se_stage_times", "se_extrapolate_noalloc", "se_plan_autotune", "se_plan_costs",
            "se_set_graphs", "se_tuning_stats", "se_tuned_variant", "se_cert_stats", "se_plan_info",
-           "se_check_wait_timeout", "se_check_sample_conversion"]
+           "se_check_wait_timeout", "se_check_sample_conversion", "se_extrapolate_host_async",
+           "se_host_wait"]
 STAGES = ["pack", "tables", "projections", "iterate", "model"]
 
 
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True):
             "se_extrapolate_batch": ([vp, vp, i32, C.POINTER(Block), vp], i32),
             "se_extrapolate_strided": ([vp, vp, i32, vp, vp, vp, vp, i32, vp], i32),
             "se_extrapolate_host": ([vp, vp, i32, vp, vp, vp, vp, i32], i32),
+            "se_extrapolate_host_async": ([vp, vp, i32, vp, vp, vp, vp, i32, C.POINTER(u64)], i32),
+            "se_host_wait": ([vp, u64], i32),
             "se_extrapolate_noalloc": ([vp, vp, i32, vp, vp, vp, vp, i32, vp], i32),
             "se_sync": ([vp, vp], i32),
             "se_submit": ([vp, vp, C.POINTER(Request), C.POINTER(u64)], i32),
@@ -164,6 +167,10 @@ class Context:
 
     def sync(self, stream=None):
         _check(self._lib.se_sync(self.handle, _stream_handle(stream)), "se_sync")
+
+    def host_wait(self, ticket: int):
+        """Wait for an asynchronous host-buffer call (Plan.extrapolate_host_async)."""
+        _check(self._lib.se_host_wait(self.handle, int(ticket)), "se_host_wait")
 
     def stats(self):
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
@@ -322,6 +329,16 @@ class Plan:
                            int(b.get("iterations", 0)))
         _check(self._lib.se_extrapolate_batch(self.ctx.handle, self.handle, len(blocks), arr,
                                               _stream_handle(stream)), "se_extrapolate_batch")
+
+    def extrapolate_host_async(self, samples, out, sel_idx=None, sel_coef=None, iterations: int = 0) -> int:
+        """Host buffers (pinned torch CPU tensors, or numpy); returns a ticket for
+        Context.host_wait.  The buffers must stay unchanged until the wait."""
+        n = int(samples.shape[0])
+        t = C.c_uint64(0)
+        _check(self._lib.se_extrapolate_host_async(self.ctx.handle, self.handle, n, _ptr(samples), _ptr(out),
+                                                   _ptr(sel_idx), _ptr(sel_coef), int(iterations), C.byref(t)),
+               "se_extrapolate_host_async")
+        return int(t.value)
 
     def extrapolate_host(self, samples: np.ndarray, out: np.ndarray, sel_idx=None, sel_coef=None,
                          iterations: int = 0):

@@ -1451,6 +1451,117 @@ se_status se_extrapolate_host(se_ctx_t *ctx, const se_plan_t *plan, int n, const
     return SE_OK;
 }
 
+namespace {
+
+se_status host_slots_init(se_ctx_s *ctx)
+{
+    if (ctx->hslot_ready) return SE_OK;
+    for (auto &h : ctx->hslot) {
+        SE_CUDA(cudaStreamCreateWithFlags(&h.st, cudaStreamNonBlocking));
+        SE_CUDA(cudaEventCreateWithFlags(&h.done, cudaEventDisableTiming));
+        SE_CUDA(cudaEventCreateWithFlags(&h.computed, cudaEventDisableTiming));
+        SE_CUDA(h.ws.init());
+    }
+    ctx->hslot_ready = true;
+    return SE_OK;
+}
+
+// Read and clear the context's device status word (ctx->mu held).
+se_status take_device_status(se_ctx_s *ctx)
+{
+    int bits = 0;
+    SE_CUDA(cudaMemcpy(&bits, ctx->ws_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) {
+        SE_CUDA(cudaMemset(ctx->ws_err.ptr, 0, sizeof(int)));
+        const se_status code = bits == (1 << DEV_ERR_EMPTY_SUPPORT) ? SE_ERR_EMPTY_SUPPORT : SE_ERR_CUDA;
+        return fail(code, std::string("device status: ") + dev_err_text(bits));
+    }
+    return SE_OK;
+}
+
+}  // namespace
+
+se_status se_extrapolate_host_async(se_ctx_t *ctx, const se_plan_t *plan, int n, const double *samples,
+                                    double *out, int32_t *sel_idx, double *sel_coef, int iterations,
+                                    uint64_t *ticket)
+{
+    if (!ctx || !plan || !ticket || n < 0) return fail(SE_ERR_INVALID, "NULL argument or n < 0");
+    *ticket = 0;
+    if (plan->cplx) return fail(SE_ERR_INVALID, "complex plans: device entry points only");
+    if (iterations < 0) return fail(SE_ERR_INVALID, "iterations < 0");
+    if (plan->ctx != ctx) return fail(SE_ERR_INVALID, "plan belongs to another context");
+    if (n == 0) return SE_OK;
+    if (!samples || !out) return fail(SE_ERR_INVALID, "NULL samples or out");
+    SE_CUDA(cudaSetDevice(ctx->device));
+    se_plan_s *pl = const_cast<se_plan_s *>(plan);
+    const int I = iterations ? iterations : plan->desc.iterations;
+    const size_t MN = static_cast<size_t>(plan->MN), nn = static_cast<size_t>(n);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    SE_TRY(host_slots_init(ctx));
+    const uint64_t t = ctx->host_next;
+    HostSlot &h = ctx->hslot[t % se_ctx_s::kHostSlots];
+    if (h.busy) {   // the oldest call in flight: its buffers are reused below
+        SE_CUDA(cudaEventSynchronize(h.done));
+        h.busy = false;
+    }
+    // device copy of the samples (computed in place), then the logs
+    const size_t s_bytes = MN * nn * sizeof(double);
+    const size_t i_off = round_up(s_bytes, 256), i_bytes = sel_idx ? sizeof(int32_t) * I * nn : 0;
+    const size_t c_off = round_up(i_off + i_bytes, 256), c_bytes = sel_coef ? sizeof(double) * I * nn : 0;
+    SE_TRY(dev_alloc(ctx, h.io, c_off + c_bytes));
+    double *d_s = h.io.as<double>();
+    int32_t *d_i = sel_idx ? reinterpret_cast<int32_t *>(h.io.as<char>() + i_off) : nullptr;
+    double *d_c = sel_coef ? reinterpret_cast<double *>(h.io.as<char>() + c_off) : nullptr;
+    // one contiguous copy in (a copy of the support alone would take one strided copy
+    // per block, whose host cost outweighs the quarter of the bytes it saves)
+    const int N = plan->N, m0 = pl->box[0], m1 = pl->box[1], n0 = pl->box[2], n1 = pl->box[3];
+    SE_CUDA(cudaMemcpyAsync(d_s, samples, s_bytes, cudaMemcpyHostToDevice, h.st));
+    {
+        // a table (re)build must not overwrite the table under the kernels of the
+        // calls in flight (their copies out may still run)
+        std::lock_guard<std::mutex> tl(pl->tmu);
+        if (!pl->tables_valid)
+            for (auto &o : ctx->hslot)
+                if (o.busy && &o != &h) SE_CUDA(cudaStreamWaitEvent(h.st, o.computed, 0));
+    }
+    const StridedSpec ss{d_s, d_s, d_i, d_c, I, 1};
+    SE_TRY(run_strided(ctx, pl, h.ws, n, ss, h.st));
+    SE_CUDA(cudaEventRecord(h.computed, h.st));
+    if (out == samples && plan->T == 1 && m1 > m0) {
+        // in place: of every block the span from the first to the last sample of its
+        // loss bounding box, one strided copy (the support samples in the span are
+        // the caller's own values)
+        const size_t first = static_cast<size_t>(m0) * N + n0, last = static_cast<size_t>(m1 - 1) * N + n1;
+        SE_CUDA(cudaMemcpy2DAsync(out + first, MN * sizeof(double), d_s + first, MN * sizeof(double),
+                                  (last - first) * sizeof(double), nn, cudaMemcpyDeviceToHost, h.st));
+    } else if (out != samples || plan->T > 1) {
+        SE_CUDA(cudaMemcpyAsync(out, d_s, s_bytes, cudaMemcpyDeviceToHost, h.st));
+    }
+    if (sel_idx) SE_CUDA(cudaMemcpyAsync(sel_idx, d_i, i_bytes, cudaMemcpyDeviceToHost, h.st));
+    if (sel_coef) SE_CUDA(cudaMemcpyAsync(sel_coef, d_c, c_bytes, cudaMemcpyDeviceToHost, h.st));
+    SE_CUDA(cudaEventRecord(h.done, h.st));
+    h.busy = true;
+    h.ticket = t;
+    ctx->host_next = t + 1;
+    *ticket = t;
+    return SE_OK;
+}
+
+se_status se_host_wait(se_ctx_t *ctx, uint64_t ticket)
+{
+    if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
+    if (ticket == 0) return SE_OK;
+    SE_CUDA(cudaSetDevice(ctx->device));
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ticket >= ctx->host_next) return fail(SE_ERR_UNKNOWN_TICKET, "no such host-call ticket");
+    for (auto &h : ctx->hslot)
+        if (h.busy && h.ticket == ticket) {
+            SE_CUDA(cudaEventSynchronize(h.done));
+            h.busy = false;
+        }
+    return take_device_status(ctx);
+}
+
 se_status se_set_profiling(se_ctx_t *ctx, int enable)
 {
     if (!ctx) return fail(SE_ERR_INVALID, "NULL context");

@@ -157,6 +157,24 @@ struct ServeLane {
     }
 };
 
+// One slot of the asynchronous host-buffer calls: a stream, a batch workspace,
+// the device copy of the call's samples (computed in place) and its logs.
+struct HostSlot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;           // the call's copies out have landed
+    cudaEvent_t computed = nullptr;       // its kernels are done (the table is no longer read)
+    se::Workspace ws;
+    se::DevBuf io;
+    uint64_t ticket = 0;
+    bool busy = false;
+    ~HostSlot()
+    {
+        if (done) cudaEventDestroy(done);
+        if (computed) cudaEventDestroy(computed);
+        if (st) cudaStreamDestroy(st);
+    }
+};
+
 struct se_ctx_s {
     int device = 0;
     size_t budget = 0;
@@ -177,6 +195,11 @@ struct se_ctx_s {
     cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
     cudaEvent_t pipe_ev_in[kPipe] = {}, pipe_ev_done[kPipe] = {};
     bool pipe_ready = false;
+    // asynchronous host-buffer calls (se_extrapolate_host_async): round-robin slots
+    static constexpr int kHostSlots = 3;
+    HostSlot hslot[kHostSlots];
+    bool hslot_ready = false;
+    uint64_t host_next = 1;               // the next ticket
     se::DevBuf ws_err;                    // device status word shared by all kernels
     void *noalloc_scratch = nullptr;      // device address of se_extrapolate_noalloc's static array
 

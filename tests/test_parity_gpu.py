@@ -314,6 +314,47 @@ def test_host_entry_point_with_pinned_buffers(ctx, n, logs, chunks, monkeypatch)
     plan.close()
 
 
+@pytest.mark.parametrize("shift,prec", [(0, "bf16x6"), (1, "bf16x6"), (0, "fp64")])
+def test_asynchronous_host_calls_match_device_path(ctx, shift, prec):
+    """Five asynchronous host-buffer calls in flight on three slots (the fourth
+    and fifth reuse slots and wait for the oldest calls), in place and with
+    separate outputs, with and without logs, the table dropped before two of
+    them (its rebuild waits for the calls in flight): every result equals a
+    device call on the same blocks, bit for bit."""
+    L, I = 32, 60
+    sup = np.ones((L, L), dtype=np.uint8)
+    sup[8:24, 8 + shift:24 + shift] = 0
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, I, prec=prec, support=sup)
+    sizes = [700, 1300, 5, 1024, 333]
+    batches = [np.stack([W.patch(L, 9000 + 37 * k + i) for i in range(n)]) for k, n in enumerate(sizes)]
+    refs = [gpu_run(plan, b) for b in batches]
+    calls = []
+    for k, b in enumerate(batches):
+        in_place, logs = k % 2 == 0, k != 2
+        s_h = torch.from_numpy(b.copy()).pin_memory()
+        o_h = s_h if in_place else torch.full_like(s_h, float("nan")).pin_memory()
+        u_h = torch.full((b.shape[0], I), -1, dtype=torch.int32).pin_memory() if logs else None
+        c_h = torch.zeros((b.shape[0], I), dtype=torch.float64).pin_memory() if logs else None
+        if k in (1, 3):
+            plan.reset_tables()
+        t = plan.extrapolate_host_async(s_h, o_h, u_h, c_h)
+        assert t > 0
+        calls.append((t, o_h, u_h, c_h))
+    for k, (t, o_h, u_h, c_h) in enumerate(calls):
+        ctx.host_wait(t)
+        out, u, c = refs[k]
+        np.testing.assert_array_equal(o_h.numpy(), out)
+        if u_h is not None:
+            np.testing.assert_array_equal(u_h.numpy(), u)
+            np.testing.assert_array_equal(c_h.numpy(), c)
+    ctx.host_wait(calls[0][0])   # a ticket already waited for
+    assert plan.extrapolate_host_async(batches[0][:0], batches[0][:0]) == 0   # n = 0
+    with pytest.raises(B.SeError) as e:
+        ctx.host_wait(10 ** 12)
+    assert "UNKNOWN_TICKET" in str(e.value)
+    plan.close()
+
+
 @pytest.mark.parametrize("shift", [0, 1])
 def test_symmetric_and_shifted_patterns(ctx, shift):
     """A centred loss box makes w symmetric (the parity-class iterations run);
