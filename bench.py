@@ -39,14 +39,15 @@ WORKLOAD = "img512_4096blk_32x32_16x16loss_dctwht_K2048_I100_rho0.8_gamma0.5"
 # traffic was captured for (ncu on this workload, see profiles/); None for a
 # shape without a capture or once the kernel changes.
 ITERATE_SHAPES = {0: "iterate_f32_kernel<1,64,4>", 1: "iterate_f32_kernel<2,32,1>"}
-TRAFFIC_ITERATE = {}
+TRAFFIC_ITERATE = {0: 46.37e6}
 SYM_SHAPES = {0: "iterate_sym_kernel<64>", 1: "iterate_sym_smem_kernel<64,3,9>", 2: "iterate_sym_tmem_kernel",
               3: "iterate_sym_hot_kernel<64,3,9>", 4: "iterate_sym_hot_kernel<64,3,9,1,2> with the model of eq. 9"}
 TRAFFIC_ITERATE_SYM = {1: 36.91e6, 3: 36.92e6}
 # On-chip roofs of the parity-class iteration kernel as ncu measured them per
 # launch shape (fractions of peak; see profiles/).
 ONCHIP_ITERATE_SYM = {
-    1: {"l1tex_data_pipe_busy": 0.799, "source": "ncu --set full, profiles/iterate_sym_img512_4096blk.md"},
+    1: {"l1tex_data_pipe_busy": 0.795, "l2_throughput": 0.338, "issue_active": 0.465,
+        "source": "ncu --set full, profiles/iterate_sym_img512_4096blk.md"},
     3: {"l1tex_data_pipe_busy": 0.672, "l1tex_data_pipe_busy_of_active": 0.723, "l2_throughput": 0.365,
         "issue_active": 0.565, "source": "ncu --set full, profiles/iterate_sym_hot_img512_4096blk.md"},
 }
