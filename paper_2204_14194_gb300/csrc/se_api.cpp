@@ -439,8 +439,18 @@ cudaError_t se::launch_iterations_f32(se_ctx_s *ctx, se_plan_s *pl, IterArgs &a,
                              8 * NT <= 16 * MT && need <= slots;
             }
             const int nv = iterate_sym_variants(pl->Kp);
+            const std::string mkey = skey + ":model" + std::to_string(Mb) + "x" + std::to_string(Nb);
+            const int pick = tune_lookup(ctx, mkey, nv + 1);
+            if (pick >= 0 && pick < nv) {   // the kept form has its own model kernel: the caller runs it
+                *launched = 0;
+                return launch_iterate_sym(a, st, launched, pick);
+            }
             *model_done = true;
-            return tune_run(ctx, skey + ":model" + std::to_string(Mb) + "x" + std::to_string(Nb), nv + 1, st,
+            if (pick == nv) {
+                *launched = 0;
+                return launch_iterate_sym_model(a, fm, st, launched);
+            }
+            return tune_run(ctx, mkey, nv + 1, st,
                             [&](int v) {
                                 *launched = 0;
                                 if (v == nv) return launch_iterate_sym_model(a, fm, st, launched);
@@ -1700,7 +1710,7 @@ se_status se_plan_info(const se_plan_t *plan, char *buf, size_t len)
                     " table=" + (plan->dft_w ? "dft-of-weights" : "table") + " iterations=" +
                     (plan->cplx ? "complex" : plan->pc.fp64 ? "fp64" : plan->sym ? "parity-classes" : "general") +
                     (plan->sym_tc ? " projections=split-tf32" : "") + (plan->certified ? " certified" : "") +
-                    (plan->f16_cols ? " columns=f16x3" : "") + (plan->f16_table ? " table_products=f16x3" : "");
+                    (plan->f16_cols ? " columns=f16x3" : "") + (plan->f16_table && !plan->sep_full ? " table_products=f16x3" : "");
     std::snprintf(buf, len, "%s", t.c_str());
     return SE_OK;
 }

@@ -384,6 +384,8 @@ void route_pattern_blocks(se_plan_s *pl, std::vector<BlockDesc> &full, std::vect
                           int *I_full, int *I_lazy);
 // Autotuner: run the fastest of n_cand interchangeable launches (identical
 // results) for this shape key, timing all of them on first use.
+// The forced or kept variant of a shape key (-1: none yet; the next tune_run times them).
+int tune_lookup(se_ctx_s *ctx, const std::string &key, int n_cand);
 cudaError_t tune_run(se_ctx_s *ctx, const std::string &key, int n_cand, cudaStream_t st,
                      const std::function<cudaError_t(int)> &run);
 // SE_GRAM_AUTO, table not built: serve n pattern blocks lazily (true) or

@@ -64,20 +64,25 @@ void Tuner::save() const
     for (const auto &kv : best) out << kv.first << ' ' << kv.second << '\n';
 }
 
+int tune_lookup(se_ctx_s *ctx, const std::string &key, int n_cand)
+{
+    Tuner &t = ctx->tuner;
+    int pick = -1;
+    std::lock_guard<std::mutex> lk(t.mu);
+    for (const auto &f : t.force)
+        if (key.compare(0, f.first.size(), f.first) == 0) pick = std::min(std::max(f.second, 0), n_cand - 1);
+    if (pick < 0) {
+        auto it = t.best.find(key);
+        if (it != t.best.end() && it->second < n_cand) pick = it->second;
+    }
+    return pick;
+}
+
 cudaError_t tune_run(se_ctx_s *ctx, const std::string &key, int n_cand, cudaStream_t st,
                      const std::function<cudaError_t(int)> &run)
 {
     Tuner &t = ctx->tuner;
-    int pick = -1;
-    {
-        std::lock_guard<std::mutex> lk(t.mu);
-        for (const auto &f : t.force)
-            if (key.compare(0, f.first.size(), f.first) == 0) pick = std::min(std::max(f.second, 0), n_cand - 1);
-        if (pick < 0) {
-            auto it = t.best.find(key);
-            if (it != t.best.end() && it->second < n_cand) pick = it->second;
-        }
-    }
+    int pick = tune_lookup(ctx, key, n_cand);
     if (pick < 0 && (n_cand <= 1 || tl_no_tune || capturing(st))) pick = 0;
     if (pick >= 0) return run(pick);
 
