@@ -1562,13 +1562,19 @@ se_status se_host_wait(se_ctx_t *ctx, uint64_t ticket)
     if (!ctx) return fail(SE_ERR_INVALID, "NULL context");
     if (ticket == 0) return SE_OK;
     SE_CUDA(cudaSetDevice(ctx->device));
+    cudaEvent_t done = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ticket >= ctx->host_next) return fail(SE_ERR_UNKNOWN_TICKET, "no such host-call ticket");
+        for (auto &h : ctx->hslot)
+            if (h.busy && h.ticket == ticket) done = h.done;
+    }
+    // the wait itself does not hold the context: other threads keep enqueueing (a
+    // slot is reused only after its call has completed, so the event stays this call's)
+    if (done) SE_CUDA(cudaEventSynchronize(done));
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (ticket >= ctx->host_next) return fail(SE_ERR_UNKNOWN_TICKET, "no such host-call ticket");
     for (auto &h : ctx->hslot)
-        if (h.busy && h.ticket == ticket) {
-            SE_CUDA(cudaEventSynchronize(h.done));
-            h.busy = false;
-        }
+        if (h.busy && h.ticket == ticket) h.busy = false;
     return take_device_status(ctx);
 }
 
