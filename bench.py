@@ -536,7 +536,8 @@ def run_ours(args):
         npairs = {"bf16x6": 6, "bf16x3": 3, "bf16": 1}.get(args.prec, 0)
         tflops = 2.0 * K * n * na * npairs / pr_avg_s / 1e12 if npairs else None
         roofline_gemm = None if tflops is None else {
-            "kernel": "tc_gemm_kernel<256,1,0> (eq. 12 projections)", "bound": "tensor",
+            "kernel": "tc_gemm_kernel<128,%d,1> (eq. 12 projections, every split part of a k-slice per stage)"
+                      % {6: 3, 3: 2, 1: 1}.get(npairs, 3), "bound": "tensor",
             "achieved": tflops, "peak": tc_peak, "unit": "TFLOP/s", "frac": tflops / tc_peak,
             "peak_kind": peak_kind + " bf16 dense"}
 

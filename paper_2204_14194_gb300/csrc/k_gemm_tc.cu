@@ -659,7 +659,7 @@ cudaError_t launch_bn(const TcGemmArgs &a, cudaStream_t st, std::string *why)
 
 int tc_gemm_variants(const TcGemmArgs &a)
 {
-    return a.symmetric ? 2 : 4;
+    return a.symmetric || a.grouped ? 2 : 4;
 }
 
 int tc_gemm_fill_variant(int M, int N)
@@ -694,6 +694,14 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *wh
     if (a.symmetric) {
         if (npa != npb) return cudaErrorInvalidValue;
         // variant 1: two CTAs per SM (one stage each); same accumulation order
+        switch (np) {
+        case 1: return variant == 1 ? launch_bn<128, 1, true, 2>(a, st, why) : launch_bn<128, 1, true>(a, st, why);
+        case 2: return variant == 1 ? launch_bn<128, 2, true, 2>(a, st, why) : launch_bn<128, 2, true>(a, st, why);
+        case 3: return variant == 1 ? launch_bn<128, 3, true, 2>(a, st, why) : launch_bn<128, 3, true>(a, st, why);
+        default: break;
+        }
+    } else if (a.grouped) {
+        // every part of a k-slice per stage: each part is read once per k-slice
         switch (np) {
         case 1: return variant == 1 ? launch_bn<128, 1, true, 2>(a, st, why) : launch_bn<128, 1, true>(a, st, why);
         case 2: return variant == 1 ? launch_bn<128, 2, true, 2>(a, st, why) : launch_bn<128, 2, true>(a, st, why);

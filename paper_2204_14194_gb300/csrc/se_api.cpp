@@ -637,9 +637,10 @@ se_status dense_pattern_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws,
         g.out = ws.r0.as<float>();
         g.ldo = Kp;
         g.symmetric = 0;
+        g.grouped = 1;
         g.err = ctx->ws_err.as<int>();
         g.scale = pl->d_Dk.as<float>();
-        const std::string key = "gemm_proj:" + std::to_string(Kp) + ":" + std::to_string(pl->ka_pad) + ":p" +
+        const std::string key = "gemm_projg:" + std::to_string(Kp) + ":" + std::to_string(pl->ka_pad) + ":p" +
                                 std::to_string(pl->pc.npairs) + ":n" + nclass(n);
         cudaError_t e = tune_run(ctx, key, tc_gemm_variants(g), st,
                                  [&](int v) { return launch_tc_gemm(g, st, &why, v); });

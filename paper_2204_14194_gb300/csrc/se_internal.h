@@ -57,11 +57,14 @@ struct TcGemmArgs {
     int f16;             // 1: the parts are fp16 (kind::f16 with f16 operands), else bf16
     float post;          // factor applied to every sum before the scale above (0: none); a power
                          //   of two undoes the scaling of fp16 parts exactly
+    int grouped;         // non-symmetric products: 1 = 128 x 128 tiles holding every split part
+                         //   of a k-slice per stage (each part read once per k-slice), else one
+                         //   partial product per stage; the two orders give different roundings
 };
 // variant: non-symmetric products 0 = 128 x 256 tiles, 1 = 128 x 128, 2 =
 // 128 x 64, 3 = 128 x 128 with two CTAs per SM (all stream one partial
 // product per stage, so they accumulate in the same order and give identical
-// results); symmetric products 0 = one CTA
+// results); symmetric and grouped products 0 = one CTA
 // per SM with a two-stage ring, 1 = two CTAs per SM of one stage each (the
 // same kernel and order, identical results).
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, cudaStream_t st, std::string *why, int variant = 0);

@@ -131,6 +131,7 @@ extern "C" se_status se_extrapolate_noalloc(se_ctx_t *ctx, const se_plan_t *plan
             g.out = static_cast<float *>(d_r0);
             g.ldo = Kp;
             g.symmetric = 0;
+            g.grouped = 1;   // the order of the batched entry points (same bits)
             g.err = ctx->ws_err.as<int>();
             g.scale = pl->d_Dk.as<float>();
             e = launch_tc_gemm(g, st, &why);

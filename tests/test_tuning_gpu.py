@@ -77,7 +77,8 @@ def test_forced_variants_are_bitwise_identical(case):
     # variants 2 and 3 exist only for the projection GEMM (128 x 64 tiles, two
     # CTAs per SM); other keys take their last variant
     for v in (0, 1, 2, 3):
-        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},gemm_table:={v},iterate:={v},sym:={v},symr0:={v}")
+        ctx = _ctx(force=f"sep:={v},gemm_proj:={v},gemm_projg:={v},gemm_table:={v},iterate:={v},sym:={v},"
+                         f"symr0:={v}")
         try:
             plan = ctx.plan(L, L, basis, K, 0.8, 0.5, I, prec=prec, dictionary=dic)
             res.append(_run(ctx, plan, samples))
