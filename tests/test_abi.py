@@ -46,4 +46,7 @@ def test_null_arguments_rejected():
     assert lib.se_extrapolate_batch(None, None, 0, None, None) == -1
     assert lib.se_poll(None, 1, 0, None) == -1
     assert lib.se_plan_reset_tables(None) == -1
+    t = C.c_uint64(7)
+    assert lib.se_extrapolate_host_async(None, None, 4, None, None, None, None, 0, C.byref(t)) == -1
+    assert lib.se_host_wait(None, 1) == -1
     assert b"NULL" in lib.se_last_error()
