@@ -167,3 +167,40 @@ def test_empty_block_mask_reports_empty_support(ctx):
         ctx.sync()
     assert e.value.status == -5
     plan.close()
+
+
+@pytest.mark.parametrize("form", ["tensor", "ffma"])
+def test_per_block_masks_64x64_column_forms(ctx, form, monkeypatch):
+    """The lazy columns of 64 x 64 areas on the tensor cores (two-part fp16
+    splits with power-of-two scales, the default) and in the fp32 transform
+    kernel (SE_COL_FFMA=1):
+    16 blocks with rectangles and scattered holes, I up to 120, each form
+    against the oracle with the bars of the other parity tests, and the two
+    forms' coefficients within 1e-3 of each other where their sequences agree
+    (both run the iterations in fp32; their residuals drift apart by rounding
+    over a hundred updates, as each drifts from the FP64 oracle)."""
+    L, n = 64, 16
+    samples = np.stack([W.patch(L, 7300 + i) for i in range(n)])
+    masks = _masks(L, n, 73)
+    iters = np.random.default_rng(64).integers(60, 121, size=n)
+    ro, ru, rc, rm, st = _oracle_masked("dct_wht", samples, masks, iters)
+    assert st == 0
+    res = {}
+    for f in ("tensor", "ffma"):
+        if f == "ffma":
+            monkeypatch.setenv("SE_COL_FFMA", "1")
+        else:
+            monkeypatch.delenv("SE_COL_FFMA", raising=False)
+        plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, int(iters.max()), prec="bf16x6")
+        res[f] = _run_masked(plan, samples, masks, iters)
+        plan.close()
+    monkeypatch.delenv("SE_COL_FFMA", raising=False)
+    out, u, c = res[form]
+    _check("bf16x6", out, u, c, ro, ru, rc, rm, iters, samples, masks)
+    (_, ut, ct), (_, uf, cf) = res["tensor"], res["ffma"]
+    for b in range(n):
+        diff = np.nonzero(ut[b] != uf[b])[0]
+        t = int(diff[0]) if len(diff) else len(ut[b])
+        assert t >= first_near_tie(rm[b, :len(ut[b])], 1e-4)
+        if t:
+            assert coef_rel_err(ct[b][:t], cf[b][:t]).max() <= 1e-3
