@@ -314,6 +314,194 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
     }
 }
 
+// The same round in fp32 with vector accesses: a worker of NW threads takes
+// atoms 4 t + 4 NW j .. + 3 (float4 rows of D, the column and R', float2 pairs
+// of the double-float R'), two steps j per pass with every load of the pass
+// issued before its first use, and the loads that do not need the cached
+// column ahead of those that do.  Rows must be 16-byte aligned (the host
+// checks).  Same arithmetic per atom as lazy_round_kernel, so the same results.
+struct RoundRow {
+    const float4 *D4;
+    float4 *R4, *P4;
+    const float4 *C4;
+    float cprev;
+    float2 c2;
+};
+
+template <bool DF, int NW>
+__device__ __forceinline__ void round_scan(const RoundRow &w, int q4, int t, float &s, int &kb, float &rb)
+{
+    for (int j0 = t; j0 < q4; j0 += 2 * NW) {
+        float4 dv[2], cv[2], rv[2], pv[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + NW * h;
+            if (j < q4) {
+                if (DF) {
+                    pv[h][0] = w.P4[2 * j];
+                    pv[h][1] = w.P4[2 * j + 1];
+                } else {
+                    rv[h] = w.R4[j];
+                }
+                if (w.C4) dv[h] = __ldg(w.D4 + j);
+            }
+        }
+        if (w.C4) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (j0 + NW * h < q4) cv[h] = __ldg(w.C4 + j0 + NW * h);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j0 + NW * h;
+            if (j >= q4) continue;
+            float r[4];
+            if (DF) {
+                float2 p[4] = {make_float2(pv[h][0].x, pv[h][0].y), make_float2(pv[h][0].z, pv[h][0].w),
+                               make_float2(pv[h][1].x, pv[h][1].y), make_float2(pv[h][1].z, pv[h][1].w)};
+                if (w.C4) {
+                    const float cc[4] = {cv[h].x, cv[h].y, cv[h].z, cv[h].w};
+                    const float dd[4] = {dv[h].x, dv[h].y, dv[h].z, dv[h].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) p[e] = df_update(p[e], w.c2, cc[e], dd[e]);
+                    w.P4[2 * j] = make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
+                    w.P4[2 * j + 1] = make_float4(p[2].x, p[2].y, p[3].x, p[3].y);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r[e] = p[e].x;
+            } else {
+                r[0] = rv[h].x; r[1] = rv[h].y; r[2] = rv[h].z; r[3] = rv[h].w;
+                if (w.C4) {
+                    r[0] = fmaf(-w.cprev, cv[h].x * dv[h].x, r[0]);
+                    r[1] = fmaf(-w.cprev, cv[h].y * dv[h].y, r[1]);
+                    r[2] = fmaf(-w.cprev, cv[h].z * dv[h].z, r[2]);
+                    r[3] = fmaf(-w.cprev, cv[h].w * dv[h].w, r[3]);
+                    w.R4[j] = make_float4(r[0], r[1], r[2], r[3]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float sc = fabsf(r[e]);
+                if (sc > s) { s = sc; kb = 4 * j + e; rb = r[e]; }
+            }
+        }
+    }
+}
+
+// Row pointers of block b for round nu (false: the block takes no round).
+template <bool DF>
+__device__ __forceinline__ bool round_row(const LazyArgs &a, int b, int nu, int &Ib, int &ns, RoundRow &w)
+{
+    Ib = a.blocks[b].iterations;
+    ns = a.n_slots[b];
+    if (nu >= Ib || ns < 0) return false;
+    const size_t row = static_cast<size_t>(b) * a.Kp;
+    w.D4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.Dk) + row);
+    w.R4 = reinterpret_cast<float4 *>(static_cast<float *>(a.R) + row);
+    w.P4 = DF ? reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(a.R64) + row) : nullptr;
+    w.C4 = nullptr;
+    w.cprev = 0.0f;
+    w.c2 = make_float2(0.0f, 0.0f);
+    if (nu > 0) {
+        const int up = a.cur_u[b];
+        if (DF) w.c2 = reinterpret_cast<const float2 *>(a.cur_c64)[b];
+        else w.cprev = static_cast<const float *>(a.cur_c)[b];
+        w.C4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.cache) +
+                                                (static_cast<size_t>(b) * a.slots + a.slot_of[row + up]) * a.Kp);
+    }
+    return true;
+}
+
+// Selection bookkeeping of one block (one thread): the coefficient of eq. (19),
+// the logs and the column request of the next round.
+template <bool DF>
+__device__ __forceinline__ void round_tail(const LazyArgs &a, int b, int nu, int Ib, int ns, int kb, float rb)
+{
+    const size_t row = static_cast<size_t>(b) * a.Kp;
+    int u = kb;
+    if (u < 0 || u >= a.K) {
+        atomicOr(a.err, 1 << DEV_ERR_BAD_INDEX);
+        u = 0;
+        rb = 0.0f;
+    }
+    const float du = static_cast<const float *>(a.Dk)[row + u];
+    int *slot_of = a.slot_of + row;
+    const int su = slot_of[u];
+    float c;
+    if (DF) {
+        // c = gamma R'_u D_u from the pair (the winner's lo part is in global
+        // memory, written by this block's threads before the argmax's exchange)
+        const float2 ru = (u == kb) ? reinterpret_cast<const float2 *>(a.R64)[row + u] : make_float2(0.0f, 0.0f);
+        const double cd = a.gamma * (static_cast<double>(ru.x) + static_cast<double>(ru.y)) *
+                          static_cast<double>(du);
+        const float ch = static_cast<float>(cd);
+        reinterpret_cast<float2 *>(a.cur_c64)[b] = make_float2(ch, static_cast<float>(cd - ch));
+        a.c_log64[static_cast<size_t>(b) * a.I_max + nu] = cd;
+        c = ch;
+    } else {
+        c = static_cast<float>(a.gamma) * rb * du;
+        static_cast<float *>(a.cur_c)[b] = c;
+    }
+    a.cur_u[b] = u;
+    a.u_log[static_cast<size_t>(b) * a.I_max + nu] = u;
+    static_cast<float *>(a.c_log)[static_cast<size_t>(b) * a.I_max + nu] = c;
+    if (nu + 1 < Ib && su < 0) {
+        // n_slots[b] is written only by this block's worker, one round at a time
+        if (ns >= a.slots) {
+            atomicOr(a.err, 1 << DEV_ERR_LAZY_CACHE);
+            a.n_slots[b] = -1;
+        } else {
+            a.n_slots[b] = ns + 1;
+            slot_of[u] = ns;
+            const int jm = atomicAdd(a.miss_n + (nu & 1), 1);
+            a.miss_blk[jm] = b;
+            a.miss_rows[jm] = (static_cast<long long>(b) * a.slots + ns) * a.Kp;
+        }
+    }
+}
+
+// One CTA of 256 threads per block (long rows).
+template <bool DF>
+__global__ void __launch_bounds__(256) lazy_round_f32v_kernel(LazyArgs a, int nu)
+{
+    __shared__ Cand<float> red[8];
+    const int b = blockIdx.x;
+    if (b == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
+    int Ib, ns;
+    RoundRow w;
+    if (!round_row<DF>(a, b, nu, Ib, ns, w)) return;
+    float s = -1.0f, rb = 0.0f;
+    int kb = INT_MAX;
+    round_scan<DF, 256>(w, a.Kp / 4, threadIdx.x, s, kb, rb);
+    block_argmax<float>(s, kb, rb, red);
+    if (threadIdx.x == 0) round_tail<DF>(a, b, nu, Ib, ns, kb, rb);
+}
+
+// One warp per block (short rows: many blocks' rounds in flight per SM, the
+// argmax within the warp).
+template <bool DF>
+__global__ void __launch_bounds__(256) lazy_round_f32w_kernel(LazyArgs a, int nu)
+{
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
+    if (b >= a.n) return;
+    int Ib, ns;
+    RoundRow w;
+    if (!round_row<DF>(a, b, nu, Ib, ns, w)) return;
+    float s = -1.0f, rb = 0.0f;
+    int kb = INT_MAX;
+    round_scan<DF, 32>(w, a.Kp / 4, lane, s, kb, rb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const int ko = __shfl_xor_sync(0xffffffffu, kb, o);
+        const float ro = __shfl_xor_sync(0xffffffffu, rb, o);
+        if (so > s || (so == s && ko < kb)) { s = so; kb = ko; rb = ro; }
+    }
+    __syncwarp();   // the lanes' stores of R' are visible to lane 0
+    if (lane == 0) round_tail<DF>(a, b, nu, Ib, ns, kb, rb);
+}
+
 // Model on the block's loss pixels (eq. 9) and replacement; logs out.
 template <typename T>
 __global__ void lazy_model_kernel(LazyArgs a)
@@ -380,6 +568,18 @@ cudaError_t launch_lazy_init(const LazyArgs &a, cudaStream_t st)
 template <typename T>
 cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st)
 {
+    auto al16 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    if (sizeof(T) == 4 && a.Kp % 4 == 0 && al16(a.R) && al16(a.Dk) && al16(a.cache) && (!a.R64 || al16(a.R64))) {
+        if (a.Kp <= 2048) {
+            const int grid = (a.n + 7) / 8;
+            if (a.R64) lazy_round_f32w_kernel<true><<<grid, 256, 0, st>>>(a, nu);
+            else lazy_round_f32w_kernel<false><<<grid, 256, 0, st>>>(a, nu);
+        } else {
+            if (a.R64) lazy_round_f32v_kernel<true><<<a.n, 256, 0, st>>>(a, nu);
+            else lazy_round_f32v_kernel<false><<<a.n, 256, 0, st>>>(a, nu);
+        }
+        return cudaGetLastError();
+    }
     lazy_round_kernel<T><<<a.n, 256, 0, st>>>(a, nu);
     return cudaGetLastError();
 }

@@ -329,26 +329,41 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
 // fp32 operand, scaled by a power of two that puts its largest entry in
 // [2^14, 2^15), is v = v_h + v_l with fp16 parts, and v_l w_h + v_h w_l +
 // v_h w_h is accumulated in fp32 (about 2^-22 of the largest entry per
-// product); the scales are undone exactly on the result.  x and U take one
-// scale per item (the group's largest entry), the 1-D rows one per CTA.
-// One item per group of 64 threads (two warps, 32 rows of each product per
-// warp).  Shared memory per CTA: the 1-D rows of every transform, split and
-// packed in pairs along the sample index (square areas: the same rows serve
-// both directions), rho, and per item the split x and U; rows are padded so
-// that the fragment loads of a warp hit 32 different banks.  Global reads are
-// issued in batches: the constants as float4 together with the first item's
+// product); the scales are undone exactly on the result.  The 1-D rows take
+// one scale per CTA, x one per item, U one per warp.
+// One item per group of four warps; warp w computes rows 16 w .. 16 w + 15 of
+// U and then the same rows of Y, which need only its own rows of U, so the
+// two products of a warp are separated by warp synchronisation alone.  Shared
+// memory per CTA: the 1-D rows of every transform, split and packed in pairs
+// along the sample index (square areas: the same rows serve both directions),
+// rho, and per item the split x and U; rows are padded so that the fragment
+// loads of a warp hit 32 different banks.  Global reads are issued in
+// batches: the constants as float4 together with the first item's
 // descriptor, mask and atom rows, and each next item's before the current
 // item's products.
-constexpr int kColGroups = 4;             // items (64-thread groups) per CTA
-constexpr int kColW = 72;                 // words per row of a pair-packed operand with 64 columns
-constexpr int kColV = 36;                 // words per row of the pair-packed U (32 pairs)
-constexpr int kColOp = 32 * kColW;        // words of one pair-packed 64 x 64 part (32 row pairs)
-constexpr int kColUp = 64 * kColV;        // words of one part of U
+constexpr int kColGroups = 4;                      // items per CTA
+constexpr int kColThreads = 128;                   // threads per item
+constexpr int kColW = 72;                          // words per row of a pair-packed operand with 64 columns
+constexpr int kColV = 36;                          // words per row of the pair-packed U (32 pairs)
+constexpr int kColOp = 32 * kColW;                 // words of one pair-packed 64 x 64 part (32 row pairs)
+constexpr int kColUp = 64 * kColV;                 // words of one part of U
 constexpr int kColItemWords = 2 * kColOp + 2 * kColUp;
+constexpr int kColRed = 64;                        // words of reduction scratch
+
+// barrier of one item's four warps (ids 1-4; 0 is __syncthreads)
+__device__ __forceinline__ void col_sync(int id)
+{
+    switch (id) {
+    case 1: asm volatile("bar.sync 1, %0;" ::"n"(kColThreads) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"n"(kColThreads) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"n"(kColThreads) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"n"(kColThreads) : "memory"); break;
+    }
+}
 
 struct ColItem {
-    uint32_t w[16];   // mask bytes of rows 2 jp, 2 jp + 1 at columns n0 .. n0 + 3, jp = tg / 16 + 4 i
-    float2 rm[8];     // t_p[2 jp], t_p[2 jp + 1] of the atom's first factor
+    uint32_t w[8];    // mask bytes of rows 2 jp, 2 jp + 1 at columns n0 .. n0 + 3, jp = tg / 16 + 8 i
+    float2 rm[4];     // t_p[2 jp], t_p[2 jp + 1] of the atom's first factor
     float4 rn;        // t'_q[n0 .. n0 + 3] of its second factor
 };
 
@@ -366,22 +381,22 @@ __device__ __forceinline__ void col64_load_item(const SepArgs &a, int i, int tg,
     const int cq = tg % 16;
     it.rn = __ldg(reinterpret_cast<const float4 *>(rowN) + cq);
 #pragma unroll
-    for (int i8 = 0; i8 < 8; ++i8) it.rm[i8] = __ldg(reinterpret_cast<const float2 *>(rowM) + tg / 16 + 4 * i8);
+    for (int i4 = 0; i4 < 4; ++i4) it.rm[i4] = __ldg(reinterpret_cast<const float2 *>(rowM) + tg / 16 + 8 * i4);
     if ((reinterpret_cast<uintptr_t>(mask) & 3) == 0) {
         const uint32_t *m4 = reinterpret_cast<const uint32_t *>(mask);
 #pragma unroll
-        for (int i8 = 0; i8 < 8; ++i8) {
-            const int jp = tg / 16 + 4 * i8;
-            it.w[2 * i8] = __ldg(m4 + (2 * jp) * 16 + cq);
-            it.w[2 * i8 + 1] = __ldg(m4 + (2 * jp + 1) * 16 + cq);
+        for (int i4 = 0; i4 < 4; ++i4) {
+            const int jp = tg / 16 + 8 * i4;
+            it.w[2 * i4] = __ldg(m4 + (2 * jp) * 16 + cq);
+            it.w[2 * i4 + 1] = __ldg(m4 + (2 * jp + 1) * 16 + cq);
         }
     } else {
 #pragma unroll
-        for (int i8 = 0; i8 < 8; ++i8)
+        for (int i4 = 0; i4 < 4; ++i4)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint8_t *q = mask + (2 * (tg / 16 + 4 * i8) + h) * M + 4 * cq;
-                it.w[2 * i8 + h] = static_cast<uint32_t>(q[0]) | static_cast<uint32_t>(q[1]) << 8 |
+                const uint8_t *q = mask + (2 * (tg / 16 + 8 * i4) + h) * M + 4 * cq;
+                it.w[2 * i4 + h] = static_cast<uint32_t>(q[0]) | static_cast<uint32_t>(q[1]) << 8 |
                                    static_cast<uint32_t>(q[2]) << 16 | static_cast<uint32_t>(q[3]) << 24;
             }
     }
@@ -421,55 +436,45 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-// acc[mt][nt] += A B over k = 64 from pair-packed parts: A rows 32 wg + 16 mt
-// + (gq, gq + 8), B columns 8 nt + gq.  A_h/A_l: A(r, 2j .. 2j + 1) at
-// a_row(r) + j (pitch per row given by the caller through ra); B_h/B_l:
-// B(2j .. 2j + 1, c) at j kColW + c.
+// acc[nt] += A B over k = 64 from pair-packed parts, A rows r0 + (gq, gq + 8),
+// B columns 8 nt + gq.  A word (r, j) (the pair A(r, 2j), A(r, 2j + 1)) at
+// r APITCH + j when A_BY_ROW, else at j APITCH + r; B word (j, c) at j kColW + c.
 template <int APITCH, bool A_BY_ROW>
-__device__ __forceinline__ void col_mma_pass(float (&acc)[2][8][4], const uint32_t *Ah, const uint32_t *Al,
-                                             const uint32_t *Bh, const uint32_t *Bl, int wg, int gq, int q)
+__device__ __forceinline__ void col_mma_pass(float (&acc)[8][4], const uint32_t *Ah, const uint32_t *Al,
+                                             const uint32_t *Bh, const uint32_t *Bl, int r0, int gq, int q)
 {
-#pragma unroll 1
+#pragma unroll 2
     for (int ks = 0; ks < 4; ++ks) {
-        const int j0 = 8 * ks + q;
-        uint32_t ah[2][4], al[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r = 32 * wg + 16 * mt + gq;
-            // A_BY_ROW: word (r, j) at r APITCH + j; else at j APITCH + r
-            const int o0 = A_BY_ROW ? r * APITCH + j0 : j0 * APITCH + r;
-            const int o1 = A_BY_ROW ? (r + 8) * APITCH + j0 : j0 * APITCH + r + 8;
-            const int o2 = A_BY_ROW ? r * APITCH + j0 + 4 : (j0 + 4) * APITCH + r;
-            const int o3 = A_BY_ROW ? (r + 8) * APITCH + j0 + 4 : (j0 + 4) * APITCH + r + 8;
-            ah[mt][0] = Ah[o0]; ah[mt][1] = Ah[o1]; ah[mt][2] = Ah[o2]; ah[mt][3] = Ah[o3];
-            al[mt][0] = Al[o0]; al[mt][1] = Al[o1]; al[mt][2] = Al[o2]; al[mt][3] = Al[o3];
-        }
+        const int j0 = 8 * ks + q, r = r0 + gq;
+        const int o0 = A_BY_ROW ? r * APITCH + j0 : j0 * APITCH + r;
+        const int o1 = A_BY_ROW ? (r + 8) * APITCH + j0 : j0 * APITCH + r + 8;
+        const int o2 = A_BY_ROW ? r * APITCH + j0 + 4 : (j0 + 4) * APITCH + r;
+        const int o3 = A_BY_ROW ? (r + 8) * APITCH + j0 + 4 : (j0 + 4) * APITCH + r + 8;
+        const uint32_t ah[4] = {Ah[o0], Ah[o1], Ah[o2], Ah[o3]};
+        const uint32_t al[4] = {Al[o0], Al[o1], Al[o2], Al[o3]};
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             const int c = 8 * nt + gq;
             const uint32_t bh0 = Bh[j0 * kColW + c], bh1 = Bh[(j0 + 4) * kColW + c];
             const uint32_t bl0 = Bl[j0 * kColW + c], bl1 = Bl[(j0 + 4) * kColW + c];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                mma_f16(acc[mt][nt], al[mt], bh0, bh1);
-                mma_f16(acc[mt][nt], ah[mt], bl0, bl1);
-                mma_f16(acc[mt][nt], ah[mt], bh0, bh1);
-            }
+            mma_f16(acc[nt], al, bh0, bh1);
+            mma_f16(acc[nt], ah, bl0, bl1);
+            mma_f16(acc[nt], ah, bh0, bh1);
         }
     }
 }
 
-__global__ void __launch_bounds__(kSepGroup * kColGroups) sep_col64_tc_kernel(const SepArgs a)
+__global__ void __launch_bounds__(kColThreads * kColGroups, 1) sep_col64_tc_kernel(const SepArgs a)
 {
-    constexpr int M = 64, N = 64, MN = M * N, NT = kSepGroup * kColGroups;
+    constexpr int M = 64, N = 64, MN = M * N, NT = kColThreads * kColGroups;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *Tp = reinterpret_cast<uint32_t *>(smem);                  // per transform: hi part, lo part
     float *Wr = reinterpret_cast<float *>(Tp + a.ntr * 2 * kColOp);      // [MN] rho
-    float *red = Wr + MN;                                                 // [8] CTA, then [groups][4]
-    const int g = threadIdx.x / kSepGroup, tg = threadIdx.x % kSepGroup;
-    uint32_t *XH = reinterpret_cast<uint32_t *>(red + 32) + g * kColItemWords;
+    float *red = Wr + MN;                                                 // [16] CTA, then [groups][4]
+    const int g = threadIdx.x / kColThreads, tg = threadIdx.x % kColThreads;
+    uint32_t *XH = reinterpret_cast<uint32_t *>(red + kColRed) + g * kColItemWords;
     uint32_t *XL = XH + kColOp, *UH = XL + kColOp, *UL = UH + kColUp;
-    float *gred = red + 8 + 4 * g;
+    float *gred = red + 16 + 4 * g;
     const int n_items = a.n_dev ? min(a.n, *a.n_dev) : a.n;
     int i = blockIdx.x * kColGroups + g;
     ColItem it;
@@ -479,35 +484,35 @@ __global__ void __launch_bounds__(kSepGroup * kColGroups) sep_col64_tc_kernel(co
         // rows 2 j and 2 j + 1, packed in pairs along m
         const float4 *img4 = static_cast<const float4 *>(static_cast<const void *>(a.img));
         const int cstride4 = (M * M + N * N) / 4, units = a.ntr * 32 * 16;
-        float4 v0[4], v1[4], wv[4];
+        float4 v0[2], v1[2], wv[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
             const int e = threadIdx.x + k * NT;
             if (e < units) {
                 const int t = e / 512, j = (e / 16) % 32, c4 = e % 16;
                 v0[k] = __ldg(img4 + t * cstride4 + (2 * j) * (M / 4) + c4);
                 v1[k] = __ldg(img4 + t * cstride4 + (2 * j + 1) * (M / 4) + c4);
             }
-            wv[k] = __ldg(img4 + a.ntr * cstride4 + threadIdx.x + k * NT);   // MN / 4 = 4 NT float4
+            wv[k] = __ldg(img4 + a.ntr * cstride4 + threadIdx.x + k * NT);   // MN / 4 = 2 NT float4
         }
         if (i < n_items) col64_load_item(a, i, tg, it);
         float mx = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 2; ++k)
             if (threadIdx.x + k * NT < units)
                 mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(fabsf(v0[k].x), fabsf(v0[k].y)), fmaxf(fabsf(v0[k].z), fabsf(v0[k].w))),
                                      fmaxf(fmaxf(fabsf(v1[k].x), fabsf(v1[k].y)), fmaxf(fabsf(v1[k].z), fabsf(v1[k].w)))));
         mx = warp_max(mx);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) reinterpret_cast<float4 *>(Wr)[threadIdx.x + k * NT] = wv[k];
+        for (int k = 0; k < 2; ++k) reinterpret_cast<float4 *>(Wr)[threadIdx.x + k * NT] = wv[k];
         __syncthreads();
         mx = red[0];
         for (int w = 1; w < NT / 32; ++w) mx = fmaxf(mx, red[w]);
         eT = col_scale_exp(mx);
         const float sT = col_pow2(eT);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 2; ++k) {
             const int e = threadIdx.x + k * NT;
             if (e < units) {
                 const int t = e / 512, j = (e / 16) % 32, c4 = e % 16;
@@ -524,125 +529,109 @@ __global__ void __launch_bounds__(kSepGroup * kColGroups) sep_col64_tc_kernel(co
     }
     __syncthreads();
     const int wg = tg >> 5, lane = tg & 31, gq = lane >> 2, q = lane & 3;
-    const int cq = tg % 16;
+    const int cq = tg % 16, r0 = 16 * wg;
     for (; i < n_items; i += gridDim.x * kColGroups) {
         // x = rho m_b phi_u on the item's support, rows 2 jp, 2 jp + 1 and columns n0 .. n0 + 3
-        float xv[8][2][4];
+        float xv[4][2][4];
         float mx = 0.0f;
 #pragma unroll
-        for (int i8 = 0; i8 < 8; ++i8) {
-            const int jp = tg / 16 + 4 * i8;
+        for (int i4 = 0; i4 < 4; ++i4) {
+            const int jp = tg / 16 + 8 * i4;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float4 w = reinterpret_cast<const float4 *>(Wr)[(2 * jp + h) * 16 + cq];
-                const float rm = h ? it.rm[i8].y : it.rm[i8].x;
-                const uint32_t mw = it.w[2 * i8 + h];
-                xv[i8][h][0] = (mw & 0xffu) ? w.x * (rm * it.rn.x) : 0.0f;
-                xv[i8][h][1] = (mw & 0xff00u) ? w.y * (rm * it.rn.y) : 0.0f;
-                xv[i8][h][2] = (mw & 0xff0000u) ? w.z * (rm * it.rn.z) : 0.0f;
-                xv[i8][h][3] = (mw & 0xff000000u) ? w.w * (rm * it.rn.w) : 0.0f;
+                const float rm = h ? it.rm[i4].y : it.rm[i4].x;
+                const uint32_t mw = it.w[2 * i4 + h];
+                xv[i4][h][0] = (mw & 0xffu) ? w.x * (rm * it.rn.x) : 0.0f;
+                xv[i4][h][1] = (mw & 0xff00u) ? w.y * (rm * it.rn.y) : 0.0f;
+                xv[i4][h][2] = (mw & 0xff0000u) ? w.z * (rm * it.rn.z) : 0.0f;
+                xv[i4][h][3] = (mw & 0xff000000u) ? w.w * (rm * it.rn.w) : 0.0f;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) mx = fmaxf(mx, fabsf(xv[i8][h][c]));
+                for (int c = 0; c < 4; ++c) mx = fmaxf(mx, fabsf(xv[i4][h][c]));
             }
         }
         mx = warp_max(mx);
         if (lane == 0) gred[wg] = mx;
         const int b = a.item_blk ? a.item_blk[i] : i;
         float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
-        group_sync(1 + g);
-        const int ex = col_scale_exp(fmaxf(gred[0], gred[1]));
+        col_sync(1 + g);   // also: every warp is done with the previous item's x
+        const int ex = col_scale_exp(fmaxf(fmaxf(gred[0], gred[1]), fmaxf(gred[2], gred[3])));
         {
             const float sx = col_pow2(ex);
 #pragma unroll
-            for (int i8 = 0; i8 < 8; ++i8) {
-                const int jp = tg / 16 + 4 * i8;
+            for (int i4 = 0; i4 < 4; ++i4) {
+                const int jp = tg / 16 + 8 * i4;
                 uint4 h, l;
-                col_split2(xv[i8][0][0] * sx, xv[i8][1][0] * sx, h.x, l.x);
-                col_split2(xv[i8][0][1] * sx, xv[i8][1][1] * sx, h.y, l.y);
-                col_split2(xv[i8][0][2] * sx, xv[i8][1][2] * sx, h.z, l.z);
-                col_split2(xv[i8][0][3] * sx, xv[i8][1][3] * sx, h.w, l.w);
+                col_split2(xv[i4][0][0] * sx, xv[i4][1][0] * sx, h.x, l.x);
+                col_split2(xv[i4][0][1] * sx, xv[i4][1][1] * sx, h.y, l.y);
+                col_split2(xv[i4][0][2] * sx, xv[i4][1][2] * sx, h.z, l.z);
+                col_split2(xv[i4][0][3] * sx, xv[i4][1][3] * sx, h.w, l.w);
                 *reinterpret_cast<uint4 *>(XH + jp * kColW + 4 * cq) = h;
                 *reinterpret_cast<uint4 *>(XL + jp * kColW + 4 * cq) = l;
             }
         }
         if (i + static_cast<int>(gridDim.x) * kColGroups < n_items)
             col64_load_item(a, i + gridDim.x * kColGroups, tg, it);   // in flight during the products
-        group_sync(1 + g);
+        col_sync(1 + g);   // x complete; gred read by every warp
 
         for (int t = 0; t < a.ntr; ++t) {
             const uint32_t *TH = Tp + t * 2 * kColOp, *TL = TH + kColOp;
-            if (t) group_sync(1 + g);   // the previous transform is done reading U
-            float acc[2][8][4];
+            float acc[8][4];
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.0f;
-            // U[p][n] = sum_m t_p[m] x[m][n]: A(p, m) = t_p[m] (pairs along m at j kColW + p)
-            col_mma_pass<kColW, false>(acc, TH, TL, XH, XL, wg, gq, q);
+                for (int k = 0; k < 4; ++k) acc[nt][k] = 0.0f;
+            // U[p][n] = sum_m t_p[m] x[m][n] for p = r0 + (gq, gq + 8): A(p, m) = t_p[m]
+            col_mma_pass<kColW, false>(acc, TH, TL, XH, XL, r0, gq, q);
             float mu = 0.0f;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mu = fmaxf(mu, fabsf(acc[mt][nt][k]));
-            mu = warp_max(mu);
-            if (lane == 0) gred[2 + wg] = mu;
-            group_sync(1 + g);
-            const int eu = col_scale_exp(fmaxf(gred[2], gred[3]));
+                for (int k = 0; k < 4; ++k) mu = fmaxf(mu, fabsf(acc[nt][k]));
+            const int eu = col_scale_exp(warp_max(mu));
             {
                 const float su = col_pow2(eu);
+                const int r = r0 + gq;
+                __syncwarp();   // the previous transform's reads of these rows of U are done
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < 8; ++nt) {
-                        const int r = 32 * wg + 16 * mt + gq;
-                        uint32_t h, l;
-                        col_split2(acc[mt][nt][0] * su, acc[mt][nt][1] * su, h, l);
-                        UH[r * kColV + 4 * nt + q] = h;
-                        UL[r * kColV + 4 * nt + q] = l;
-                        col_split2(acc[mt][nt][2] * su, acc[mt][nt][3] * su, h, l);
-                        UH[(r + 8) * kColV + 4 * nt + q] = h;
-                        UL[(r + 8) * kColV + 4 * nt + q] = l;
-                    }
+                for (int nt = 0; nt < 8; ++nt) {
+                    uint32_t h, l;
+                    col_split2(acc[nt][0] * su, acc[nt][1] * su, h, l);
+                    UH[r * kColV + 4 * nt + q] = h;
+                    UL[r * kColV + 4 * nt + q] = l;
+                    col_split2(acc[nt][2] * su, acc[nt][3] * su, h, l);
+                    UH[(r + 8) * kColV + 4 * nt + q] = h;
+                    UL[(r + 8) * kColV + 4 * nt + q] = l;
+                }
+                __syncwarp();
             }
-            group_sync(1 + g);
             // Y[p][q'] = sum_n U[p][n] t'_q'[n] (square area: the rows of T_N are those of T_M)
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.0f;
-            col_mma_pass<kColV, true>(acc, UH, UL, TH, TL, wg, gq, q);
+                for (int k = 0; k < 4; ++k) acc[nt][k] = 0.0f;
+            col_mma_pass<kColV, true>(acc, UH, UL, TH, TL, r0, gq, q);
             // Y = acc 2^-(2 eT + ex + eu)
             const int etot = 2 * eT + ex + eu;
             const bool onef = etot >= -126 && etot <= 127;
             const float f = onef ? col_pow2(-etot) : 1.0f;
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
+            for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int k = a.koff[t] + (32 * wg + 16 * mt + gq + 8 * h) * N + 8 * nt + 2 * q;
-                        float2 y = onef ? make_float2(acc[mt][nt][2 * h] * f, acc[mt][nt][2 * h + 1] * f)
-                                        : make_float2(ldexpf(acc[mt][nt][2 * h], -etot),
-                                                      ldexpf(acc[mt][nt][2 * h + 1], -etot));
-                        if (a.scale) {
-                            const float2 sv = __ldg(reinterpret_cast<const float2 *>(a.scale + k));
-                            y.x *= sv.x;
-                            y.y *= sv.y;
-                        }
-                        *reinterpret_cast<float2 *>(out + k) = y;
+                for (int h = 0; h < 2; ++h) {
+                    const int k = a.koff[t] + (r0 + gq + 8 * h) * N + 8 * nt + 2 * q;
+                    float2 y = onef ? make_float2(acc[nt][2 * h] * f, acc[nt][2 * h + 1] * f)
+                                    : make_float2(ldexpf(acc[nt][2 * h], -etot), ldexpf(acc[nt][2 * h + 1], -etot));
+                    if (a.scale) {
+                        const float2 sv = __ldg(reinterpret_cast<const float2 *>(a.scale + k));
+                        y.x *= sv.x;
+                        y.y *= sv.y;
                     }
+                    *reinterpret_cast<float2 *>(out + k) = y;
+                }
         }
-        for (int k = a.koff[a.ntr - 1] + MN + tg; k < a.kfill; k += kSepGroup)
+        for (int k = a.koff[a.ntr - 1] + MN + tg; k < a.kfill; k += kColThreads)
             out[k] = a.scale ? NAN : 0.0f;
-        // the next item's x is written only after every thread of the group has
-        // passed the barrier that follows its last read (after the last stage 1)
     }
 }
 
@@ -1023,13 +1012,13 @@ static cudaError_t launch_col64_tc(const SepArgs &a, cudaStream_t st, bool *done
         return cudaSuccess;
     for (int t = 0; t < a.ntr; ++t)
         if (a.koff[t] % 2 || !al16(a.TM[t]) || !al16(a.TN[t])) return cudaSuccess;   // float2 / float4 accesses
-    const size_t smem = sizeof(uint32_t) * (static_cast<size_t>(a.ntr) * 2 * kColOp + 64 * 64 + 32 +
+    const size_t smem = sizeof(uint32_t) * (static_cast<size_t>(a.ntr) * 2 * kColOp + 64 * 64 + kColRed +
                                             static_cast<size_t>(kColGroups) * kColItemWords);
     int grid = 0;
-    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_col64_tc_kernel), kSepGroup * kColGroups, smem,
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_col64_tc_kernel), kColThreads * kColGroups, smem,
                                 (a.n + kColGroups - 1) / kColGroups, &grid);
     if (e != cudaSuccess) return e;
-    sep_col64_tc_kernel<<<grid, kSepGroup * kColGroups, smem, st>>>(a);
+    sep_col64_tc_kernel<<<grid, kColThreads * kColGroups, smem, st>>>(a);
     *done = true;
     return cudaGetLastError();
 }
