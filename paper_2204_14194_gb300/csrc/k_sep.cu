@@ -322,17 +322,17 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
     }
 }
 
-// The lazy columns of eq. (16) for 64 x 64 areas (mode 2: the column of atom u
-// for block b, C_b(k, u) = sum_mn rho m_b phi_u phi_k) on the tensor cores.
-// Per item and transform the two 64 x 64 x 64 products U = T_M x and
-// Y = U T_N^T run as mma.sync m16n8k16 products of two-part fp16 splits: each
-// fp32 operand, scaled by a power of two that puts its largest entry in
+// The lazy columns of eq. (16) for 32 x 32 and 64 x 64 areas (mode 2: the
+// column of atom u for block b, C_b(k, u) = sum_mn rho m_b phi_u phi_k) on the
+// tensor cores.  Per item and transform the two M x M x M products U = T_M x
+// and Y = U T_N^T run as mma.sync m16n8k16 products of two-part fp16 splits:
+// each fp32 operand, scaled by a power of two that puts its largest entry in
 // [2^14, 2^15), is v = v_h + v_l with fp16 parts, and v_l w_h + v_h w_l +
 // v_h w_h is accumulated in fp32 (about 2^-22 of the largest entry per
 // product); the scales are undone exactly on the result.  The 1-D rows take
 // one scale per CTA, x one per item, U one per warp.
-// One item per group of four warps; warp w computes rows 16 w .. 16 w + 15 of
-// U and then the same rows of Y, which need only its own rows of U, so the
+// One item per group of M / 16 warps; warp w computes rows 16 w .. 16 w + 15
+// of U and then the same rows of Y, which need only its own rows of U, so the
 // two products of a warp are separated by warp synchronisation alone.  Shared
 // memory per CTA: the 1-D rows of every transform, split and packed in pairs
 // along the sample index (square areas: the same rows serve both directions),
@@ -341,61 +341,80 @@ __global__ void __launch_bounds__(256) sep_group_kernel(const SepArgs a, int gro
 // batches: the constants as float4 together with the first item's
 // descriptor, mask and atom rows, and each next item's before the current
 // item's products.
-constexpr int kColGroups = 4;                      // items per CTA
-constexpr int kColThreads = 128;                   // threads per item
-constexpr int kColW = 72;                          // words per row of a pair-packed operand with 64 columns
-constexpr int kColV = 36;                          // words per row of the pair-packed U (32 pairs)
-constexpr int kColOp = 32 * kColW;                 // words of one pair-packed 64 x 64 part (32 row pairs)
-constexpr int kColUp = 64 * kColV;                 // words of one part of U
-constexpr int kColItemWords = 2 * kColOp + 2 * kColUp;
-constexpr int kColRed = 64;                        // words of reduction scratch
+template <int M> struct ColCfg {
+    static constexpr int MN = M * M;
+    static constexpr int Groups = M == 64 ? 4 : 8;     // items per CTA (512 threads)
+    static constexpr int Threads = 2 * M;              // threads per item (M / 16 warps)
+    static constexpr int NT = Threads * Groups;
+    static constexpr int W = M + 8;                    // words per row of a pair-packed operand with M columns
+    static constexpr int V = M / 2 + 4;                // words per row of the pair-packed U (M / 2 pairs)
+    static constexpr int Op = (M / 2) * W;             // words of one pair-packed M x M part
+    static constexpr int Up = M * V;                   // words of one part of U
+    static constexpr int ItemWords = 2 * Op + 2 * Up;
+    static constexpr int Red = 64;                     // words of reduction scratch
+    static constexpr int Q = M / 4;                    // column quads per row
+    static constexpr int Units = M / 16;               // x units (row pair, column quad) per thread
+    static constexpr int KS = M / 16;                  // k-steps of 16
+    static constexpr int NTile = M / 8;                // n tiles of 8
+    static constexpr int CK = (MN / 4 + NT - 1) / NT;  // float4 of the constants per thread and part
+    static constexpr int MinBlocks = M == 64 ? 1 : 2;
+};
 
-// barrier of one item's four warps (ids 1-4; 0 is __syncthreads)
+// barrier of one item's warps (ids 1-8; 0 is __syncthreads)
+template <int NTH>
 __device__ __forceinline__ void col_sync(int id)
 {
     switch (id) {
-    case 1: asm volatile("bar.sync 1, %0;" ::"n"(kColThreads) : "memory"); break;
-    case 2: asm volatile("bar.sync 2, %0;" ::"n"(kColThreads) : "memory"); break;
-    case 3: asm volatile("bar.sync 3, %0;" ::"n"(kColThreads) : "memory"); break;
-    default: asm volatile("bar.sync 4, %0;" ::"n"(kColThreads) : "memory"); break;
+    case 1: asm volatile("bar.sync 1, %0;" ::"n"(NTH) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"n"(NTH) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"n"(NTH) : "memory"); break;
+    case 4: asm volatile("bar.sync 4, %0;" ::"n"(NTH) : "memory"); break;
+    case 5: asm volatile("bar.sync 5, %0;" ::"n"(NTH) : "memory"); break;
+    case 6: asm volatile("bar.sync 6, %0;" ::"n"(NTH) : "memory"); break;
+    case 7: asm volatile("bar.sync 7, %0;" ::"n"(NTH) : "memory"); break;
+    default: asm volatile("bar.sync 8, %0;" ::"n"(NTH) : "memory"); break;
     }
 }
 
-struct ColItem {
-    uint32_t w[8];    // mask bytes of rows 2 jp, 2 jp + 1 at columns n0 .. n0 + 3, jp = tg / 16 + 8 i
-    float2 rm[4];     // t_p[2 jp], t_p[2 jp + 1] of the atom's first factor
-    float4 rn;        // t'_q[n0 .. n0 + 3] of its second factor
+template <int M> struct ColItem {
+    uint32_t w[2 * ColCfg<M>::Units];   // mask bytes of rows 2 jp, 2 jp + 1 at columns n0 .. n0 + 3
+    float2 rm[ColCfg<M>::Units];        // t_p[2 jp], t_p[2 jp + 1] of the atom's first factor
+    float4 rn;                          // t'_q[n0 .. n0 + 3] of its second factor
 };
 
-__device__ __forceinline__ void col64_load_item(const SepArgs &a, int i, int tg, ColItem &it)
+// thread tg of an item takes the units jp = tg / Q + 8 i (row pairs) at the
+// column quad tg % Q
+template <int M>
+__device__ __forceinline__ void col_load_item(const SepArgs &a, int i, int tg, ColItem<M> &it)
 {
-    constexpr int M = 64;
+    using C = ColCfg<M>;
     const int b = a.item_blk ? a.item_blk[i] : i;
     const uint8_t *sup = a.blocks[b].support;
     const uint8_t *mask = sup ? sup : a.pattern;
     const int u = a.cur_u[b];
     const int tu = (a.ntr > 1 && u >= a.koff[1]) ? 1 : 0;
-    const int ku = min(max(u - a.koff[tu], 0), M * M - 1);   // valid atoms only reach here
+    const int ku = min(max(u - a.koff[tu], 0), C::MN - 1);   // valid atoms only reach here
     const float *rowM = static_cast<const float *>(a.TM[tu]) + (ku / M) * M;
     const float *rowN = static_cast<const float *>(a.TN[tu]) + (ku % M) * M;
-    const int cq = tg % 16;
+    const int cq = tg % C::Q;
     it.rn = __ldg(reinterpret_cast<const float4 *>(rowN) + cq);
 #pragma unroll
-    for (int i4 = 0; i4 < 4; ++i4) it.rm[i4] = __ldg(reinterpret_cast<const float2 *>(rowM) + tg / 16 + 8 * i4);
+    for (int i4 = 0; i4 < C::Units; ++i4)
+        it.rm[i4] = __ldg(reinterpret_cast<const float2 *>(rowM) + tg / C::Q + 8 * i4);
     if ((reinterpret_cast<uintptr_t>(mask) & 3) == 0) {
         const uint32_t *m4 = reinterpret_cast<const uint32_t *>(mask);
 #pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-            const int jp = tg / 16 + 8 * i4;
-            it.w[2 * i4] = __ldg(m4 + (2 * jp) * 16 + cq);
-            it.w[2 * i4 + 1] = __ldg(m4 + (2 * jp + 1) * 16 + cq);
+        for (int i4 = 0; i4 < C::Units; ++i4) {
+            const int jp = tg / C::Q + 8 * i4;
+            it.w[2 * i4] = __ldg(m4 + (2 * jp) * C::Q + cq);
+            it.w[2 * i4 + 1] = __ldg(m4 + (2 * jp + 1) * C::Q + cq);
         }
     } else {
 #pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4)
+        for (int i4 = 0; i4 < C::Units; ++i4)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint8_t *q = mask + (2 * (tg / 16 + 8 * i4) + h) * M + 4 * cq;
+                const uint8_t *q = mask + (2 * (tg / C::Q + 8 * i4) + h) * M + 4 * cq;
                 it.w[2 * i4 + h] = static_cast<uint32_t>(q[0]) | static_cast<uint32_t>(q[1]) << 8 |
                                    static_cast<uint32_t>(q[2]) << 16 | static_cast<uint32_t>(q[3]) << 24;
             }
@@ -436,15 +455,17 @@ __device__ __forceinline__ float warp_max(float v)
     return v;
 }
 
-// acc[nt] += A B over k = 64 from pair-packed parts, A rows r0 + (gq, gq + 8),
+// acc[nt] += A B over k = M from pair-packed parts, A rows r0 + (gq, gq + 8),
 // B columns 8 nt + gq.  A word (r, j) (the pair A(r, 2j), A(r, 2j + 1)) at
-// r APITCH + j when A_BY_ROW, else at j APITCH + r; B word (j, c) at j kColW + c.
-template <int APITCH, bool A_BY_ROW>
-__device__ __forceinline__ void col_mma_pass(float (&acc)[8][4], const uint32_t *Ah, const uint32_t *Al,
-                                             const uint32_t *Bh, const uint32_t *Bl, int r0, int gq, int q)
+// r APITCH + j when A_BY_ROW, else at j APITCH + r; B word (j, c) at j W + c.
+template <int M, int APITCH, bool A_BY_ROW>
+__device__ __forceinline__ void col_mma_pass(float (&acc)[ColCfg<M>::NTile][4], const uint32_t *Ah,
+                                             const uint32_t *Al, const uint32_t *Bh, const uint32_t *Bl, int r0,
+                                             int gq, int q)
 {
+    constexpr int W = ColCfg<M>::W;
 #pragma unroll 2
-    for (int ks = 0; ks < 4; ++ks) {
+    for (int ks = 0; ks < ColCfg<M>::KS; ++ks) {
         const int j0 = 8 * ks + q, r = r0 + gq;
         const int o0 = A_BY_ROW ? r * APITCH + j0 : j0 * APITCH + r;
         const int o1 = A_BY_ROW ? (r + 8) * APITCH + j0 : j0 * APITCH + r + 8;
@@ -453,10 +474,10 @@ __device__ __forceinline__ void col_mma_pass(float (&acc)[8][4], const uint32_t 
         const uint32_t ah[4] = {Ah[o0], Ah[o1], Ah[o2], Ah[o3]};
         const uint32_t al[4] = {Al[o0], Al[o1], Al[o2], Al[o3]};
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
+        for (int nt = 0; nt < ColCfg<M>::NTile; ++nt) {
             const int c = 8 * nt + gq;
-            const uint32_t bh0 = Bh[j0 * kColW + c], bh1 = Bh[(j0 + 4) * kColW + c];
-            const uint32_t bl0 = Bl[j0 * kColW + c], bl1 = Bl[(j0 + 4) * kColW + c];
+            const uint32_t bh0 = Bh[j0 * W + c], bh1 = Bh[(j0 + 4) * W + c];
+            const uint32_t bl0 = Bl[j0 * W + c], bl1 = Bl[(j0 + 4) * W + c];
             mma_f16(acc[nt], al, bh0, bh1);
             mma_f16(acc[nt], ah, bl0, bl1);
             mma_f16(acc[nt], ah, bh0, bh1);
@@ -464,82 +485,85 @@ __device__ __forceinline__ void col_mma_pass(float (&acc)[8][4], const uint32_t 
     }
 }
 
-__global__ void __launch_bounds__(kColThreads * kColGroups, 1) sep_col64_tc_kernel(const SepArgs a)
+template <int M>
+__global__ void __launch_bounds__(ColCfg<M>::NT, ColCfg<M>::MinBlocks) sep_col_tc_kernel(const SepArgs a)
 {
-    constexpr int M = 64, N = 64, MN = M * N, NT = kColThreads * kColGroups;
+    using C = ColCfg<M>;
+    constexpr int N = M, MN = C::MN, NT = C::NT;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *Tp = reinterpret_cast<uint32_t *>(smem);                  // per transform: hi part, lo part
-    float *Wr = reinterpret_cast<float *>(Tp + a.ntr * 2 * kColOp);      // [MN] rho
+    float *Wr = reinterpret_cast<float *>(Tp + a.ntr * 2 * C::Op);       // [MN] rho
     float *red = Wr + MN;                                                 // [16] CTA, then [groups][4]
-    const int g = threadIdx.x / kColThreads, tg = threadIdx.x % kColThreads;
-    uint32_t *XH = reinterpret_cast<uint32_t *>(red + kColRed) + g * kColItemWords;
-    uint32_t *XL = XH + kColOp, *UH = XL + kColOp, *UL = UH + kColUp;
+    const int g = threadIdx.x / C::Threads, tg = threadIdx.x % C::Threads;
+    uint32_t *XH = reinterpret_cast<uint32_t *>(red + C::Red) + g * C::ItemWords;
+    uint32_t *XL = XH + C::Op, *UH = XL + C::Op, *UL = UH + C::Up;
     float *gred = red + 16 + 4 * g;
     const int n_items = a.n_dev ? min(a.n, *a.n_dev) : a.n;
-    int i = blockIdx.x * kColGroups + g;
-    ColItem it;
+    int i = blockIdx.x * C::Groups + g;
+    ColItem<M> it;
     int eT;
     {
         // TmT [M][M] of the image holds t_p[m] at m M + p; unit (t, j, quad of p):
         // rows 2 j and 2 j + 1, packed in pairs along m
         const float4 *img4 = static_cast<const float4 *>(static_cast<const void *>(a.img));
-        const int cstride4 = (M * M + N * N) / 4, units = a.ntr * 32 * 16;
-        float4 v0[2], v1[2], wv[2];
+        const int cstride4 = 2 * MN / 4, units = a.ntr * (M / 2) * C::Q;
+        float4 v0[C::CK], v1[C::CK], wv[C::CK];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < C::CK; ++k) {
             const int e = threadIdx.x + k * NT;
             if (e < units) {
-                const int t = e / 512, j = (e / 16) % 32, c4 = e % 16;
-                v0[k] = __ldg(img4 + t * cstride4 + (2 * j) * (M / 4) + c4);
-                v1[k] = __ldg(img4 + t * cstride4 + (2 * j + 1) * (M / 4) + c4);
+                const int t = e / (MN / 8), j = (e / C::Q) % (M / 2), c4 = e % C::Q;
+                v0[k] = __ldg(img4 + t * cstride4 + (2 * j) * C::Q + c4);
+                v1[k] = __ldg(img4 + t * cstride4 + (2 * j + 1) * C::Q + c4);
             }
-            wv[k] = __ldg(img4 + a.ntr * cstride4 + threadIdx.x + k * NT);   // MN / 4 = 2 NT float4
+            if (e < MN / 4) wv[k] = __ldg(img4 + a.ntr * cstride4 + e);
         }
-        if (i < n_items) col64_load_item(a, i, tg, it);
+        if (i < n_items) col_load_item<M>(a, i, tg, it);
         float mx = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < C::CK; ++k)
             if (threadIdx.x + k * NT < units)
                 mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(fabsf(v0[k].x), fabsf(v0[k].y)), fmaxf(fabsf(v0[k].z), fabsf(v0[k].w))),
                                      fmaxf(fmaxf(fabsf(v1[k].x), fabsf(v1[k].y)), fmaxf(fabsf(v1[k].z), fabsf(v1[k].w)))));
         mx = warp_max(mx);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) reinterpret_cast<float4 *>(Wr)[threadIdx.x + k * NT] = wv[k];
+        for (int k = 0; k < C::CK; ++k)
+            if (threadIdx.x + k * NT < MN / 4) reinterpret_cast<float4 *>(Wr)[threadIdx.x + k * NT] = wv[k];
         __syncthreads();
         mx = red[0];
         for (int w = 1; w < NT / 32; ++w) mx = fmaxf(mx, red[w]);
         eT = col_scale_exp(mx);
         const float sT = col_pow2(eT);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < C::CK; ++k) {
             const int e = threadIdx.x + k * NT;
             if (e < units) {
-                const int t = e / 512, j = (e / 16) % 32, c4 = e % 16;
+                const int t = e / (MN / 8), j = (e / C::Q) % (M / 2), c4 = e % C::Q;
                 uint4 h, l;
                 col_split2(v0[k].x * sT, v1[k].x * sT, h.x, l.x);
                 col_split2(v0[k].y * sT, v1[k].y * sT, h.y, l.y);
                 col_split2(v0[k].z * sT, v1[k].z * sT, h.z, l.z);
                 col_split2(v0[k].w * sT, v1[k].w * sT, h.w, l.w);
-                uint32_t *dst = Tp + t * 2 * kColOp + j * kColW + 4 * c4;
+                uint32_t *dst = Tp + t * 2 * C::Op + j * C::W + 4 * c4;
                 *reinterpret_cast<uint4 *>(dst) = h;
-                *reinterpret_cast<uint4 *>(dst + kColOp) = l;
+                *reinterpret_cast<uint4 *>(dst + C::Op) = l;
             }
         }
     }
     __syncthreads();
     const int wg = tg >> 5, lane = tg & 31, gq = lane >> 2, q = lane & 3;
-    const int cq = tg % 16, r0 = 16 * wg;
-    for (; i < n_items; i += gridDim.x * kColGroups) {
+    const int cq = tg % C::Q, r0 = 16 * wg;
+    for (; i < n_items; i += gridDim.x * C::Groups) {
         // x = rho m_b phi_u on the item's support, rows 2 jp, 2 jp + 1 and columns n0 .. n0 + 3
-        float xv[4][2][4];
+        float xv[C::Units][2][4];
         float mx = 0.0f;
 #pragma unroll
-        for (int i4 = 0; i4 < 4; ++i4) {
-            const int jp = tg / 16 + 8 * i4;
+        for (int i4 = 0; i4 < C::Units; ++i4) {
+            const int jp = tg / C::Q + 8 * i4;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float4 w = reinterpret_cast<const float4 *>(Wr)[(2 * jp + h) * 16 + cq];
+                const float4 w = reinterpret_cast<const float4 *>(Wr)[(2 * jp + h) * C::Q + cq];
                 const float rm = h ? it.rm[i4].y : it.rm[i4].x;
                 const uint32_t mw = it.w[2 * i4 + h];
                 xv[i4][h][0] = (mw & 0xffu) ? w.x * (rm * it.rn.x) : 0.0f;
@@ -554,38 +578,41 @@ __global__ void __launch_bounds__(kColThreads * kColGroups, 1) sep_col64_tc_kern
         if (lane == 0) gred[wg] = mx;
         const int b = a.item_blk ? a.item_blk[i] : i;
         float *out = static_cast<float *>(a.out) + (a.out_rows ? a.out_rows[i] : static_cast<long long>(b) * a.ldo);
-        col_sync(1 + g);   // also: every warp is done with the previous item's x
-        const int ex = col_scale_exp(fmaxf(fmaxf(gred[0], gred[1]), fmaxf(gred[2], gred[3])));
+        col_sync<C::Threads>(1 + g);   // also: every warp is done with the previous item's x
+        float gm = gred[0];
+#pragma unroll
+        for (int w = 1; w < M / 16; ++w) gm = fmaxf(gm, gred[w]);
+        const int ex = col_scale_exp(gm);
         {
             const float sx = col_pow2(ex);
 #pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4) {
-                const int jp = tg / 16 + 8 * i4;
+            for (int i4 = 0; i4 < C::Units; ++i4) {
+                const int jp = tg / C::Q + 8 * i4;
                 uint4 h, l;
                 col_split2(xv[i4][0][0] * sx, xv[i4][1][0] * sx, h.x, l.x);
                 col_split2(xv[i4][0][1] * sx, xv[i4][1][1] * sx, h.y, l.y);
                 col_split2(xv[i4][0][2] * sx, xv[i4][1][2] * sx, h.z, l.z);
                 col_split2(xv[i4][0][3] * sx, xv[i4][1][3] * sx, h.w, l.w);
-                *reinterpret_cast<uint4 *>(XH + jp * kColW + 4 * cq) = h;
-                *reinterpret_cast<uint4 *>(XL + jp * kColW + 4 * cq) = l;
+                *reinterpret_cast<uint4 *>(XH + jp * C::W + 4 * cq) = h;
+                *reinterpret_cast<uint4 *>(XL + jp * C::W + 4 * cq) = l;
             }
         }
-        if (i + static_cast<int>(gridDim.x) * kColGroups < n_items)
-            col64_load_item(a, i + gridDim.x * kColGroups, tg, it);   // in flight during the products
-        col_sync(1 + g);   // x complete; gred read by every warp
+        if (i + static_cast<int>(gridDim.x) * C::Groups < n_items)
+            col_load_item<M>(a, i + gridDim.x * C::Groups, tg, it);   // in flight during the products
+        col_sync<C::Threads>(1 + g);   // x complete; gred read by every warp
 
         for (int t = 0; t < a.ntr; ++t) {
-            const uint32_t *TH = Tp + t * 2 * kColOp, *TL = TH + kColOp;
-            float acc[8][4];
+            const uint32_t *TH = Tp + t * 2 * C::Op, *TL = TH + C::Op;
+            float acc[C::NTile][4];
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
+            for (int nt = 0; nt < C::NTile; ++nt)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[nt][k] = 0.0f;
             // U[p][n] = sum_m t_p[m] x[m][n] for p = r0 + (gq, gq + 8): A(p, m) = t_p[m]
-            col_mma_pass<kColW, false>(acc, TH, TL, XH, XL, r0, gq, q);
+            col_mma_pass<M, C::W, false>(acc, TH, TL, XH, XL, r0, gq, q);
             float mu = 0.0f;
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
+            for (int nt = 0; nt < C::NTile; ++nt)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) mu = fmaxf(mu, fabsf(acc[nt][k]));
             const int eu = col_scale_exp(warp_max(mu));
@@ -594,29 +621,29 @@ __global__ void __launch_bounds__(kColThreads * kColGroups, 1) sep_col64_tc_kern
                 const int r = r0 + gq;
                 __syncwarp();   // the previous transform's reads of these rows of U are done
 #pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
+                for (int nt = 0; nt < C::NTile; ++nt) {
                     uint32_t h, l;
                     col_split2(acc[nt][0] * su, acc[nt][1] * su, h, l);
-                    UH[r * kColV + 4 * nt + q] = h;
-                    UL[r * kColV + 4 * nt + q] = l;
+                    UH[r * C::V + 4 * nt + q] = h;
+                    UL[r * C::V + 4 * nt + q] = l;
                     col_split2(acc[nt][2] * su, acc[nt][3] * su, h, l);
-                    UH[(r + 8) * kColV + 4 * nt + q] = h;
-                    UL[(r + 8) * kColV + 4 * nt + q] = l;
+                    UH[(r + 8) * C::V + 4 * nt + q] = h;
+                    UL[(r + 8) * C::V + 4 * nt + q] = l;
                 }
                 __syncwarp();
             }
             // Y[p][q'] = sum_n U[p][n] t'_q'[n] (square area: the rows of T_N are those of T_M)
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
+            for (int nt = 0; nt < C::NTile; ++nt)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) acc[nt][k] = 0.0f;
-            col_mma_pass<kColV, true>(acc, UH, UL, TH, TL, r0, gq, q);
+            col_mma_pass<M, C::V, true>(acc, UH, UL, TH, TL, r0, gq, q);
             // Y = acc 2^-(2 eT + ex + eu)
             const int etot = 2 * eT + ex + eu;
             const bool onef = etot >= -126 && etot <= 127;
             const float f = onef ? col_pow2(-etot) : 1.0f;
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
+            for (int nt = 0; nt < C::NTile; ++nt)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int k = a.koff[t] + (r0 + gq + 8 * h) * N + 8 * nt + 2 * q;
@@ -630,7 +657,7 @@ __global__ void __launch_bounds__(kColThreads * kColGroups, 1) sep_col64_tc_kern
                     *reinterpret_cast<float2 *>(out + k) = y;
                 }
         }
-        for (int k = a.koff[a.ntr - 1] + MN + tg; k < a.kfill; k += kColThreads)
+        for (int k = a.koff[a.ntr - 1] + MN + tg; k < a.kfill; k += C::Threads)
             out[k] = a.scale ? NAN : 0.0f;
     }
 }
@@ -999,28 +1026,35 @@ int sep_variants(const SepArgs &a, bool fp64)
     return !fp64 && ((a.M == 32 && a.N == 32) || (a.M == 16 && a.N == 16)) ? 2 : 1;
 }
 
-// The tensor-core lazy columns of 64 x 64 areas (SE_COL_FFMA=1: the fp32
-// transform kernel); *done stays false if the launch does not apply.
-static cudaError_t launch_col64_tc(const SepArgs &a, cudaStream_t st, bool *done)
+// The tensor-core lazy columns of 32 x 32 and 64 x 64 areas (SE_COL_FFMA=1:
+// the fp32 transform kernels); *done stays false if the launch does not apply.
+template <int M>
+static cudaError_t launch_col_tc_m(const SepArgs &a, cudaStream_t st)
+{
+    using C = ColCfg<M>;
+    const size_t smem = sizeof(uint32_t) * (static_cast<size_t>(a.ntr) * 2 * C::Op + C::MN + C::Red +
+                                            static_cast<size_t>(C::Groups) * C::ItemWords);
+    int grid = 0;
+    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_col_tc_kernel<M>), C::NT, smem,
+                                (a.n + C::Groups - 1) / C::Groups, &grid);
+    if (e != cudaSuccess) return e;
+    sep_col_tc_kernel<M><<<grid, C::NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_col_tc(const SepArgs &a, cudaStream_t st, bool *done)
 {
     *done = false;
     const char *env = std::getenv("SE_COL_FFMA");   // read at every launch: tests switch it per plan
     const bool ffma = env && env[0] == '1';
     auto al16 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
-    if (ffma || a.mode != 2 || a.M != 64 || a.N != 64 || !a.img || a.ntr < 1 || a.ntr > 2 || !a.cur_u ||
-        (a.out_rows == nullptr && a.ldo < a.kfill) || !al16(a.img))
+    if (ffma || a.mode != 2 || a.M != a.N || (a.M != 64 && a.M != 32) || !a.img || a.ntr < 1 || a.ntr > 2 ||
+        !a.cur_u || (a.out_rows == nullptr && a.ldo < a.kfill) || !al16(a.img))
         return cudaSuccess;
     for (int t = 0; t < a.ntr; ++t)
         if (a.koff[t] % 2 || !al16(a.TM[t]) || !al16(a.TN[t])) return cudaSuccess;   // float2 / float4 accesses
-    const size_t smem = sizeof(uint32_t) * (static_cast<size_t>(a.ntr) * 2 * kColOp + 64 * 64 + kColRed +
-                                            static_cast<size_t>(kColGroups) * kColItemWords);
-    int grid = 0;
-    cudaError_t e = launch_grid(reinterpret_cast<const void *>(sep_col64_tc_kernel), kColThreads * kColGroups, smem,
-                                (a.n + kColGroups - 1) / kColGroups, &grid);
-    if (e != cudaSuccess) return e;
-    sep_col64_tc_kernel<<<grid, kColThreads * kColGroups, smem, st>>>(a);
     *done = true;
-    return cudaGetLastError();
+    return a.M == 64 ? launch_col_tc_m<64>(a, st) : launch_col_tc_m<32>(a, st);
 }
 
 template <typename T>
@@ -1029,7 +1063,7 @@ cudaError_t launch_sep(const SepArgs &a, cudaStream_t st, int variant)
     if (a.n <= 0) return cudaSuccess;
     if (sizeof(T) == 4) {
         bool done = false;
-        cudaError_t e = launch_col64_tc(a, st, &done);
+        cudaError_t e = launch_col_tc(a, st, &done);
         if (e != cudaSuccess || done) return e;
         if (a.M == 32 && a.N == 32 && variant == 0)
             return launch_sep_warp<32, 32, 8, 4>(a, st);

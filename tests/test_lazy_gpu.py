@@ -169,17 +169,17 @@ def test_empty_block_mask_reports_empty_support(ctx):
     plan.close()
 
 
-@pytest.mark.parametrize("form", ["tensor", "ffma"])
-def test_per_block_masks_64x64_column_forms(ctx, form, monkeypatch):
-    """The lazy columns of 64 x 64 areas on the tensor cores (two-part fp16
-    splits with power-of-two scales, the default) and in the fp32 transform
-    kernel (SE_COL_FFMA=1):
+@pytest.mark.parametrize("L,form", [(32, "tensor"), (32, "ffma"), (64, "tensor"), (64, "ffma")])
+def test_per_block_masks_column_forms(ctx, L, form, monkeypatch):
+    """The lazy columns of 32 x 32 and 64 x 64 areas on the tensor cores
+    (two-part fp16 splits with power-of-two scales, the default) and in the
+    fp32 transform kernels (SE_COL_FFMA=1):
     16 blocks with rectangles and scattered holes, I up to 120, each form
     against the oracle with the bars of the other parity tests, and the two
     forms' coefficients within 1e-3 of each other where their sequences agree
     (both run the iterations in fp32; their residuals drift apart by rounding
     over a hundred updates, as each drifts from the FP64 oracle)."""
-    L, n = 64, 16
+    n = 16
     samples = np.stack([W.patch(L, 7300 + i) for i in range(n)])
     masks = _masks(L, n, 73)
     iters = np.random.default_rng(64).integers(60, 121, size=n)
