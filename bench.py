@@ -625,8 +625,12 @@ def run_ours(args):
         line["sustained"] = sustained
     if rank == 0 and args.secondary and args.prec != "fp64":
         # secondary measurements recorded in the same line: the Gaussian-dictionary
-        # workload and a short serving run at the mixed-size request stream
+        # workload, the mixed-size batch and a short serving run at the mixed-size
+        # request stream
         line["gauss1080"] = secondary_gauss1080(args.prec)
+        # the mixed-size batch with per-block masks (20000 blocks of 16, 32 and 64
+        # samples square, I from 50 to 500): lazy columns, one stream per size
+        line["mixed"] = measure_workload("mixed", 0, 3, 3, args.prec)
         line["serving"] = [serve_measure(float(r), args.serve_s, 0.5, args.gauss_share, args.budget_gb, args.prec)
                            for r in args.serve_rates.split(",")]
     if args.prec == "certified":
@@ -647,49 +651,56 @@ def run_workload(args):
     """Secondary measurements (not the headline): the 1920x1080 Gaussian-dictionary
     workload (shared pattern, K = 4096, I = 200) and the mixed-size workload with
     per-block masks (16/32/64 areas, I in [50, 500])."""
+    print(json.dumps(measure_workload(args.workload, args.blocks, args.steps, args.warmup, args.prec,
+                                      args.no_graphs)), flush=True)
+    return 0
+
+
+def measure_workload(workload: str, blocks: int, steps: int, warmup: int, prec: str, no_graphs: bool = False):
+    """One secondary workload's line (see run_workload)."""
     import torch
     from paper_2204_14194_gb300 import binding as B
     from paper_2204_14194_gb300 import workloads as W
 
     # one context (and stream) per plan, so the three area sizes overlap on the device
     ctxs, streams, groups = [], [], []
-    if args.workload in ("dft64", "video"):
+    if workload in ("dft64", "video"):
         # complex DFT atoms on 64 x 64 areas (the processing-time scenario of the
         # paper's Fig. 7: K = 4096, 32 x 32 loss) or 3-D video blocks 16 x 16 x 4
         # with 3-D DCT atoms (K = 1024); I = 100, gamma = 0.5, rho_hat = 0.8
         ctxs.append(B.Context(0))
         streams.append(torch.cuda.Stream())
-        if args.workload == "dft64":
-            n = args.blocks or 1024
-            plan = ctxs[0].plan(64, 64, "dft", 4096, 0.8, 0.5, 100, prec=args.prec)
+        if workload == "dft64":
+            n = blocks or 1024
+            plan = ctxs[0].plan(64, 64, "dft", 4096, 0.8, 0.5, 100, prec=prec)
             samples = W.tiled_image(2048, 2048, 64)
             rng = np.random.default_rng(64)
             corners = rng.integers(0, 2048 - 64, size=(n, 2))
             samples = np.stack([samples[r:r + 64, c:c + 64] for r, c in corners])
             name = "dft_64x64_K4096_I100_%dblk" % n
         else:
-            n = args.blocks or 4096
-            plan = ctxs[0].plan(16, 16, "dct", 1024, 0.8, 0.5, 100, prec=args.prec, T=4)
+            n = blocks or 4096
+            plan = ctxs[0].plan(16, 16, "dct", 1024, 0.8, 0.5, 100, prec=prec, T=4)
             samples = np.stack([W.video_block(16, 16, 4, 20000 + i) for i in range(n)])
             name = "video_16x16x4_dct_K1024_I100_%dblk" % n
         s = torch.from_numpy(np.ascontiguousarray(samples)).cuda()
         groups.append((plan, s, torch.empty_like(s), None, 100))
-    elif args.workload == "gauss1080":
-        wl = W.config3(args.blocks or None)
+    elif workload == "gauss1080":
+        wl = W.config3(blocks or None)
         ctxs.append(B.Context(0))
         streams.append(torch.cuda.Stream())
-        plan = ctxs[0].plan(32, 32, "numeric", 4096, wl.rho_hat, wl.gamma, wl.iterations, prec=args.prec,
+        plan = ctxs[0].plan(32, 32, "numeric", 4096, wl.rho_hat, wl.gamma, wl.iterations, prec=prec,
                             dictionary=wl.dictionary)
         s = torch.from_numpy(wl.samples).cuda()
         groups.append((plan, s, torch.empty_like(s), None, wl.iterations))
         name = wl.name
     else:
-        for wl in W.config4(args.blocks or 20000):
+        for wl in W.config4(blocks or 20000):
             c = B.Context(0)
             ctxs.append(c)
             streams.append(torch.cuda.Stream())
             plan = c.plan(wl.M, wl.N, "dct_wht", wl.K, wl.rho_hat, wl.gamma, int(wl.iters_per_block.max()),
-                          prec=args.prec)
+                          prec=prec)
             s = torch.from_numpy(wl.samples).cuda()
             m = torch.from_numpy(wl.support).cuda()
             groups.append((plan, s, torch.empty_like(s), m, wl.iters_per_block))
@@ -699,7 +710,7 @@ def run_workload(args):
               for b in range(g[1].shape[0])] for g in groups]
 
     for c in ctxs:
-        c.set_graphs(not args.no_graphs)
+        c.set_graphs(not no_graphs)
 
     def step():
         for (plan, s, o, m, it), d, stream in zip(groups, descs, streams):
@@ -713,7 +724,7 @@ def run_workload(args):
         for c, st in zip(ctxs, streams):
             c.sync(st)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     sync()
     for c in ctxs:
@@ -721,26 +732,25 @@ def run_workload(args):
         c.stage_times(reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     sync()
     torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    ms = (time.perf_counter() - t0) * 1000.0 / steps
     nb = sum(g[1].shape[0] for g in groups)
     stages = {}
     for c in ctxs:
         for k, v in c.stage_times(reset=True).items():
-            stages[k] = stages.get(k, 0.0) + v[0] / args.steps
+            stages[k] = stages.get(k, 0.0) + v[0] / steps
     line = {"metric": "extrapolated blocks/s", "workload": name, "value": nb / (ms / 1000.0),
-            "unit": "blocks/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-            "precision": args.prec, "timing": "host wall clock around the steps (several streams)",
-            "graphs": not args.no_graphs,
+            "unit": "blocks/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "precision": prec, "timing": "host wall clock around the steps (several streams)",
+            "graphs": not no_graphs,
             "tuning": [c.tuning_stats() for c in ctxs],
             "stages_ms_per_step_summed_over_streams": stages}
-    print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
-    return 0
+    return line
 
 
 def run_single(args):
@@ -998,7 +1008,7 @@ def main():
     ap.add_argument("--serve-s", type=float, default=3.0,
                     help="serving seconds measured inside the headline run (its 'serving' key)")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false",
-                    help="skip the Gaussian-dictionary and serving measurements of the headline run")
+                    help="skip the Gaussian-dictionary, mixed-batch and serving measurements of the headline run")
     ap.add_argument("--warm-s", type=float, default=1.0, help="serving: warm-up seconds")
     ap.add_argument("--gauss-share", type=float, default=0.5, help="serving: share of Gaussian dictionaries")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serving: HBM budget")
