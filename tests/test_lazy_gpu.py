@@ -36,10 +36,11 @@ def _masks(L, n, seed):
                      for i in range(n)])
 
 
-def _run_masked(plan, samples, masks, iters):
+def _run_masked(plan, samples, masks, iters, m=None):
     n, M, N = samples.shape
     s = torch.from_numpy(samples).cuda()
-    m = torch.from_numpy(masks).cuda()
+    if m is None:
+        m = torch.from_numpy(masks).cuda()
     out = torch.empty_like(s)
     us = [torch.full((i,), -1, dtype=torch.int32, device="cuda") for i in iters]
     cs = [torch.full((i,), float("nan"), dtype=torch.float64, device="cuda") for i in iters]
@@ -204,3 +205,40 @@ def test_per_block_masks_column_forms(ctx, L, form, monkeypatch):
         assert t >= first_near_tie(rm[b, :len(ut[b])], 1e-4)
         if t:
             assert coef_rel_err(ct[b][:t], cf[b][:t]).max() <= 1e-3
+
+
+def test_per_block_masks_single_transform_64x64(ctx):
+    """64 x 64 areas with DCT atoms only (K = 4096, one transform): the
+    tensor-core column kernel with a single transform and the round kernel
+    with one CTA per block at K = 4096, against the oracle."""
+    L, n = 64, 8
+    samples = np.stack([W.patch(L, 8100 + i) for i in range(n)])
+    masks = _masks(L, n, 81)
+    iters = np.random.default_rng(81).integers(40, 101, size=n)
+    ro, ru, rc, rm, st = _oracle_masked("dct", samples, masks, iters)
+    assert st == 0
+    plan = ctx.plan(L, L, "dct", L * L, 0.8, 0.5, int(iters.max()), prec="bf16x6")
+    out, u, c = _run_masked(plan, samples, masks, iters)
+    plan.close()
+    _check("bf16x6", out, u, c, ro, ru, rc, rm, iters, samples, masks)
+
+
+@pytest.mark.parametrize("L", [32, 64])
+def test_per_block_masks_unaligned_support(ctx, L):
+    """Masks that start one byte past a 4-byte boundary (views into one
+    buffer at offset 1): the column kernel reads them byte by byte instead of
+    as words; against the oracle."""
+    n = 6
+    samples = np.stack([W.patch(L, 8200 + L + i) for i in range(n)])
+    masks = _masks(L, n, 90 + L)
+    iters = np.random.default_rng(90 + L).integers(30, 81, size=n)
+    ro, ru, rc, rm, st = _oracle_masked("dct_wht", samples, masks, iters)
+    assert st == 0
+    buf = torch.zeros(n * L * L + 1, dtype=torch.uint8, device="cuda")
+    buf[1:] = torch.from_numpy(masks.reshape(-1)).cuda()
+    m = buf[1:].view(n, L, L)
+    assert all(m[b].data_ptr() % 4 != 0 for b in range(n))
+    plan = ctx.plan(L, L, "dct_wht", 2 * L * L, 0.8, 0.5, int(iters.max()), prec="bf16x6")
+    out, u, c = _run_masked(plan, samples, masks, iters, m=m)
+    plan.close()
+    _check("bf16x6", out, u, c, ro, ru, rc, rm, iters, samples, masks)
