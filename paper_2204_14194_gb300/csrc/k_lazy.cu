@@ -167,6 +167,23 @@ __device__ __forceinline__ void block_argmax(T &s, int &k, T &r, Cand<T> *red)
     __syncthreads();
 }
 
+// The lo part of a compensated pair hi + lo kept as fp16 in units of
+// 2^(e - 24), e the exponent of hi: round to nearest gives |lo| <= 2^(e - 24),
+// so the unit value lies in [-1, 1] and keeps 11 significant bits (hi + lo
+// then carries about 35).  Zero where |hi| < 2^-100.
+__device__ __forceinline__ uint16_t lo_encode(float hi, float lo)
+{
+    const int e = static_cast<int>((__float_as_uint(hi) >> 23) & 0xffu) - 127;
+    if (e < -100) return 0;
+    return __half_as_ushort(__float2half_rn(lo * __uint_as_float(static_cast<uint32_t>(127 + 24 - e) << 23)));
+}
+__device__ __forceinline__ float lo_decode(float hi, uint16_t q)
+{
+    const int e = static_cast<int>((__float_as_uint(hi) >> 23) & 0xffu) - 127;
+    if (e < -100) return 0.0f;
+    return __half2float(__ushort_as_half(q)) * __uint_as_float(static_cast<uint32_t>(127 - 24 + e) << 23);
+}
+
 // Per block: admissibility (not a duplicate, C_kk > 1e-14 max C_jj), D = 1 /
 // sqrt(C_kk) (NaN if inadmissible) and R' = R0 D, in place.
 template <typename T>
@@ -191,11 +208,12 @@ __global__ void lazy_init_kernel(LazyArgs a)
         const bool adm = k < a.K && !a.dup[k] && mx > T(0) && d > T(1e-14) * mx;
         const T Dv = adm ? T(1) / sqrt(d) : nan_of<T>();
         D[k] = Dv;
-        if (a.R64 && sizeof(T) == 4) {
-            // R' = R0 D as a pair of floats (hi + lo, the product's exact rounding error)
+        if (a.Rlo && sizeof(T) == 4) {
+            // R' = R0 D as hi + lo (lo the product's exact rounding error)
             const float r0 = static_cast<float>(R[k]), dv = static_cast<float>(Dv);
             const float hi = r0 * dv;
-            reinterpret_cast<float2 *>(a.R64)[static_cast<size_t>(b) * a.Kp + k] = make_float2(hi, fmaf(r0, dv, -hi));
+            R[k] = static_cast<T>(hi);
+            a.Rlo[static_cast<size_t>(b) * a.Kp + k] = lo_encode(hi, fmaf(r0, dv, -hi));
         } else {
             R[k] = R[k] * Dv;
         }
@@ -212,11 +230,11 @@ __global__ void lazy_init_kernel(LazyArgs a)
 // One round nu for every block: R' -= c_prev D col(u_prev); select u; record
 // c; request the column of u if it is not cached and another round follows.
 // The recurrence R'_k -= c_prev D_k col_k of eq. (20).  In T, or, for long
-// fp32 runs (a.R64 set), in double-float: R'_k = hi + lo and c = ch + cl as
-// pairs of floats, updated with exact products (fma) and exact sums (two-sum),
-// about 48 significant bits on the fp32 pipe; the product D_k col_k of two
-// floats enters with its exact rounding error.  The selection compares the hi
-// parts.
+// fp32 runs (a.Rlo set), compensated: R'_k = hi + lo and c = ch + cl as pairs
+// of floats, updated with exact products (fma) and exact sums (two-sum) on the
+// fp32 pipe, lo stored in 16 bits between rounds (about 35 significant bits in
+// all); the product D_k col_k of two floats enters with its exact rounding
+// error.  The selection compares the hi parts.
 __device__ __forceinline__ float2 df_update(float2 r, float2 c, float col, float d)
 {
     const float v = col * d, ev = fmaf(col, d, -v);          // v + ev = col d exactly
@@ -233,13 +251,13 @@ template <typename T>
 __global__ void lazy_round_kernel(LazyArgs a, int nu)
 {
     __shared__ Cand<T> red[32];
-    const bool df = a.R64 != nullptr && sizeof(T) == 4;
+    const bool df = a.Rlo != nullptr && sizeof(T) == 4;
     const int b = blockIdx.x;
     if (b == 0 && threadIdx.x == 0) a.miss_n[(nu + 1) & 1] = 0;   // unused since round nu - 1
     const int Ib = a.blocks[b].iterations;
     if (nu >= Ib || a.n_slots[b] < 0) return;
     T *R = static_cast<T *>(a.R) + static_cast<size_t>(b) * a.Kp;
-    float2 *R2 = df ? reinterpret_cast<float2 *>(a.R64) + static_cast<size_t>(b) * a.Kp : nullptr;
+    uint16_t *Rl = df ? a.Rlo + static_cast<size_t>(b) * a.Kp : nullptr;
     const T *D = static_cast<const T *>(a.Dk) + static_cast<size_t>(b) * a.Kp;
     int *slot_of = a.slot_of + static_cast<size_t>(b) * a.Kp;
     const T *col = nullptr;
@@ -257,10 +275,12 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
     for (int k = threadIdx.x; k < a.Kp; k += blockDim.x) {
         T r;
         if (df) {
-            float2 r2 = R2[k];
+            const float h = static_cast<float>(R[k]);
+            float2 r2 = make_float2(h, lo_decode(h, Rl[k]));
             if (col) {
                 r2 = df_update(r2, c2, static_cast<float>(col[k]), static_cast<float>(D[k]));
-                R2[k] = r2;
+                R[k] = static_cast<T>(r2.x);
+                Rl[k] = lo_encode(r2.x, r2.y);
             }
             r = static_cast<T>(r2.x);
         } else {
@@ -285,7 +305,8 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
         if (df) {
             // c = gamma R'_u D_u from the pair (the winner's lo part is in global
             // memory, written by this CTA before the barriers of the argmax)
-            const float2 ru = (u == kb) ? R2[u] : make_float2(0.0f, 0.0f);
+            const float hu = static_cast<float>(R[u]);
+            const float2 ru = (u == kb) ? make_float2(hu, lo_decode(hu, Rl[u])) : make_float2(0.0f, 0.0f);
             const double cd = a.gamma * (static_cast<double>(ru.x) + static_cast<double>(ru.y)) *
                               static_cast<double>(D[u]);
             const float ch = static_cast<float>(cd);
@@ -315,14 +336,15 @@ __global__ void lazy_round_kernel(LazyArgs a, int nu)
 }
 
 // The same round in fp32 with vector accesses: a worker of NW threads takes
-// atoms 4 t + 4 NW j .. + 3 (float4 rows of D, the column and R', float2 pairs
-// of the double-float R'), two steps j per pass with every load of the pass
+// atoms 4 t + 4 NW j .. + 3 (float4 rows of D, the column and R' (its hi parts
+// in the compensated form), four 16-bit lo parts as one uint2), two steps j per pass with every load of the pass
 // issued before its first use, and the loads that do not need the cached
 // column ahead of those that do.  Rows must be 16-byte aligned (the host
 // checks).  Same arithmetic per atom as lazy_round_kernel, so the same results.
 struct RoundRow {
     const float4 *D4;
-    float4 *R4, *P4;
+    float4 *R4;
+    uint2 *L4;   // lo parts of R', four per uint2 (compensated form)
     const float4 *C4;
     float cprev;
     float2 c2;
@@ -332,17 +354,14 @@ template <bool DF, int NW>
 __device__ __forceinline__ void round_scan(const RoundRow &w, int q4, int t, float &s, int &kb, float &rb)
 {
     for (int j0 = t; j0 < q4; j0 += 2 * NW) {
-        float4 dv[2], cv[2], rv[2], pv[2][2];
+        float4 dv[2], cv[2], rv[2];
+        uint2 lv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = j0 + NW * h;
             if (j < q4) {
-                if (DF) {
-                    pv[h][0] = w.P4[2 * j];
-                    pv[h][1] = w.P4[2 * j + 1];
-                } else {
-                    rv[h] = w.R4[j];
-                }
+                rv[h] = w.R4[j];
+                if (DF) lv[h] = w.L4[j];
                 if (w.C4) dv[h] = __ldg(w.D4 + j);
             }
         }
@@ -357,15 +376,22 @@ __device__ __forceinline__ void round_scan(const RoundRow &w, int q4, int t, flo
             if (j >= q4) continue;
             float r[4];
             if (DF) {
-                float2 p[4] = {make_float2(pv[h][0].x, pv[h][0].y), make_float2(pv[h][0].z, pv[h][0].w),
-                               make_float2(pv[h][1].x, pv[h][1].y), make_float2(pv[h][1].z, pv[h][1].w)};
+                const uint16_t lq[4] = {static_cast<uint16_t>(lv[h].x & 0xffffu), static_cast<uint16_t>(lv[h].x >> 16),
+                                        static_cast<uint16_t>(lv[h].y & 0xffffu), static_cast<uint16_t>(lv[h].y >> 16)};
+                const float hq[4] = {rv[h].x, rv[h].y, rv[h].z, rv[h].w};
+                float2 p[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) p[e] = make_float2(hq[e], lo_decode(hq[e], lq[e]));
                 if (w.C4) {
                     const float cc[4] = {cv[h].x, cv[h].y, cv[h].z, cv[h].w};
                     const float dd[4] = {dv[h].x, dv[h].y, dv[h].z, dv[h].w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) p[e] = df_update(p[e], w.c2, cc[e], dd[e]);
-                    w.P4[2 * j] = make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
-                    w.P4[2 * j + 1] = make_float4(p[2].x, p[2].y, p[3].x, p[3].y);
+                    w.R4[j] = make_float4(p[0].x, p[1].x, p[2].x, p[3].x);
+                    w.L4[j] = make_uint2(static_cast<uint32_t>(lo_encode(p[0].x, p[0].y)) |
+                                             static_cast<uint32_t>(lo_encode(p[1].x, p[1].y)) << 16,
+                                         static_cast<uint32_t>(lo_encode(p[2].x, p[2].y)) |
+                                             static_cast<uint32_t>(lo_encode(p[3].x, p[3].y)) << 16);
                 }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) r[e] = p[e].x;
@@ -398,7 +424,7 @@ __device__ __forceinline__ bool round_row(const LazyArgs &a, int b, int nu, int 
     const size_t row = static_cast<size_t>(b) * a.Kp;
     w.D4 = reinterpret_cast<const float4 *>(static_cast<const float *>(a.Dk) + row);
     w.R4 = reinterpret_cast<float4 *>(static_cast<float *>(a.R) + row);
-    w.P4 = DF ? reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(a.R64) + row) : nullptr;
+    w.L4 = DF ? reinterpret_cast<uint2 *>(a.Rlo + row) : nullptr;
     w.C4 = nullptr;
     w.cprev = 0.0f;
     w.c2 = make_float2(0.0f, 0.0f);
@@ -429,9 +455,10 @@ __device__ __forceinline__ void round_tail(const LazyArgs &a, int b, int nu, int
     const int su = slot_of[u];
     float c;
     if (DF) {
-        // c = gamma R'_u D_u from the pair (the winner's lo part is in global
+        // c = gamma R'_u D_u from the pair (the winner's parts are in global
         // memory, written by this block's threads before the argmax's exchange)
-        const float2 ru = (u == kb) ? reinterpret_cast<const float2 *>(a.R64)[row + u] : make_float2(0.0f, 0.0f);
+        const float hu = static_cast<const float *>(a.R)[row + u];
+        const float2 ru = (u == kb) ? make_float2(hu, lo_decode(hu, a.Rlo[row + u])) : make_float2(0.0f, 0.0f);
         const double cd = a.gamma * (static_cast<double>(ru.x) + static_cast<double>(ru.y)) *
                           static_cast<double>(du);
         const float ch = static_cast<float>(cd);
@@ -569,13 +596,13 @@ template <typename T>
 cudaError_t launch_lazy_round(const LazyArgs &a, int nu, cudaStream_t st)
 {
     auto al16 = [](const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
-    if (sizeof(T) == 4 && a.Kp % 4 == 0 && al16(a.R) && al16(a.Dk) && al16(a.cache) && (!a.R64 || al16(a.R64))) {
+    if (sizeof(T) == 4 && a.Kp % 4 == 0 && al16(a.R) && al16(a.Dk) && al16(a.cache) && (!a.Rlo || al16(a.Rlo))) {
         if (a.Kp <= 2048) {
             const int grid = (a.n + 7) / 8;
-            if (a.R64) lazy_round_f32w_kernel<true><<<grid, 256, 0, st>>>(a, nu);
+            if (a.Rlo) lazy_round_f32w_kernel<true><<<grid, 256, 0, st>>>(a, nu);
             else lazy_round_f32w_kernel<false><<<grid, 256, 0, st>>>(a, nu);
         } else {
-            if (a.R64) lazy_round_f32v_kernel<true><<<a.n, 256, 0, st>>>(a, nu);
+            if (a.Rlo) lazy_round_f32v_kernel<true><<<a.n, 256, 0, st>>>(a, nu);
             else lazy_round_f32v_kernel<false><<<a.n, 256, 0, st>>>(a, nu);
         }
         return cudaGetLastError();

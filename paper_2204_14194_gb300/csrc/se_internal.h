@@ -254,12 +254,14 @@ struct LazyArgs {
     long long *miss_rows;      // [n] element offset of the requested cache row
     double gamma;
     int *err;
-    // fp32 form with a double-float running recurrence (long iteration counts):
-    // R' as (hi, lo) float pairs [n][Kp] in R64 (from the fp32 R0 in R), the
-    // current coefficient as a float pair [n] in cur_c64 and the logged
-    // coefficients in fp64 [n][I_max] in c_log64; the columns, D, the diagonal and
-    // the float log of the model stay fp32.  NULL: off.
-    double *R64;
+    // fp32 form with a compensated running recurrence (long iteration counts):
+    // R' = hi + lo with hi the fp32 R' in R and lo [n][Kp] in Rlo as fp16 in
+    // units of 2^(e(hi) - 24) (e(hi) the exponent of hi; |lo| <= ulp(hi) / 2, so
+    // the unit value lies in [-1, 1]), the current coefficient as a float pair
+    // [n] in cur_c64 and the logged coefficients in fp64 [n][I_max] in c_log64;
+    // the columns, D, the diagonal and the float log of the model stay fp32.
+    // NULL: off.
+    uint16_t *Rlo;
     double *cur_c64;
     double *c_log64;
 };

@@ -254,7 +254,7 @@ se_status dense_projections(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, const B
 }  // namespace
 
 // Iteration counts above which the fp32 form keeps the running recurrence of
-// eq. (20) at fp64-class precision (double-float pairs, see k_lazy.cu): the fp32
+// eq. (20) compensated (hi + lo with a 16-bit lo, see k_lazy.cu): the fp32
 // recurrence's error is about constant in the scale of the initial projections,
 // so it grows relative to the projections as they decay; on 16 x 16 blocks with
 // scattered holes it passed a near tie of 1.5e-4 relative at iteration 286 while
@@ -271,7 +271,7 @@ size_t se::lazy_bytes_per_block(const se_plan_s *pl, int I_max)
     const size_t slots = static_cast<size_t>(std::max(1, I_max - 1));
     const size_t opnd = fp64 ? 8 * MNp * 3 : 2 * MNp * 7;
     return tsz * Kp * 3 + 4 * Kp + slots * Kp * tsz + static_cast<size_t>(I_max) * (4 + tsz) + opnd +
-           sizeof(BlockDesc) + 64 + (r64 ? 8 * Kp + 8 * static_cast<size_t>(I_max) + 8 : 0);
+           sizeof(BlockDesc) + 64 + (r64 ? 2 * Kp + 8 * static_cast<size_t>(I_max) + 8 : 0);
 }
 
 se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const BlockDesc *hdesc,
@@ -318,7 +318,7 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
     LZ_TRY(dev_alloc(ctx, ws.lz_cur, (4 + 8) * static_cast<size_t>(wave) + 16));
     LZ_TRY(dev_alloc(ctx, ws.lz_miss, 16 + (4 + 8) * static_cast<size_t>(wave) + 16));
     if (r64) {
-        LZ_TRY(dev_alloc(ctx, ws.lz_R64, 8 * static_cast<size_t>(Kp) * wave));
+        LZ_TRY(dev_alloc(ctx, ws.lz_R64, 2 * static_cast<size_t>(Kp) * wave));   // lo parts of R'
         LZ_TRY(dev_alloc(ctx, ws.lz_c64, 8 * (static_cast<size_t>(I_max) + 1) * wave));
     }
     if (fp64) {
@@ -396,7 +396,7 @@ se_status se::run_lazy(se_ctx_s *ctx, se_plan_s *pl, Workspace &ws, int n, const
         a.gamma = pl->desc.gamma;
         a.err = ctx->ws_err.as<int>();
         if (r64) {
-            a.R64 = ws.lz_R64.as<double>();
+            a.Rlo = ws.lz_R64.as<uint16_t>();
             a.cur_c64 = ws.lz_c64.as<double>();
             a.c_log64 = ws.lz_c64.as<double>() + wave;
         }
